@@ -1,0 +1,121 @@
+"""GMRES variants with modified Gram-Schmidt Arnoldi and Givens rotations,
+FP64 (Sec. 3.3, Algorithm 1).  Test infrastructure only.
+
+``gmres_right``  right-preconditioned GMRES; with ``flexible=True`` the
+                 preconditioned directions are kept (flexible GMRES, the
+                 outer solver named in Sec. 6.3 for loose coarse
+                 tolerances), otherwise the iterate is x0 + M^{-1} V y.
+``gmres_left``   Algorithm 1: GMRES on the preconditioned operator,
+                 stopping on the preconditioned relative residual.
+
+Stopping rule of ``gmres_right``: after iteration j the Givens-updated
+least-squares residual |g_{j+1}| is compared with ``tol * ||b||``.
+"""
+
+import numpy as np
+
+
+class Result:
+    def __init__(self, x, iters, res_est, converged):
+        self.x = x
+        self.iters = iters
+        self.res_est = res_est
+        self.converged = converged
+
+
+def _givens(a, b):
+    """Rotation (c real, s complex) with [c s; -conj(s) c] (a, b)^T = (r, 0)."""
+    if b == 0:
+        return 1.0, 0.0 + 0.0j
+    if a == 0:
+        return 0.0, 1.0 + 0.0j
+    t = np.sqrt(abs(a) ** 2 + abs(b) ** 2)
+    c = abs(a) / t
+    s = (a / abs(a)) * np.conj(b) / t
+    return c, s
+
+
+def _arnoldi_lsq(apply_op, v0, beta, tol_abs, maxit, keep_dirs=None):
+    """Shared Arnoldi/Givens loop.  ``apply_op(v) -> (w, z)`` returns the
+    new Krylov vector w and (for flexible GMRES) the direction z."""
+    n = v0.size
+    V = [v0]
+    Zs = []
+    H = np.zeros((maxit + 1, maxit), dtype=np.complex128)
+    g = np.zeros(maxit + 1, dtype=np.complex128)
+    g[0] = beta
+    cs = np.zeros(maxit)
+    sn = np.zeros(maxit, dtype=np.complex128)
+    k = 0
+    res = beta
+    for j in range(maxit):
+        w, z = apply_op(V[j])
+        if keep_dirs:
+            Zs.append(z)
+        for i in range(j + 1):                       # modified Gram-Schmidt
+            H[i, j] = np.vdot(V[i], w)
+            w = w - H[i, j] * V[i]
+        hn = np.linalg.norm(w)
+        H[j + 1, j] = hn
+        for i in range(j):                           # previous rotations
+            t = cs[i] * H[i, j] + sn[i] * H[i + 1, j]
+            H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]
+            H[i, j] = t
+        cs[j], sn[j] = _givens(H[j, j], H[j + 1, j])
+        H[j, j] = cs[j] * H[j, j] + sn[j] * H[j + 1, j]
+        H[j + 1, j] = 0.0
+        g[j + 1] = -np.conj(sn[j]) * g[j]
+        g[j] = cs[j] * g[j]
+        k = j + 1
+        res = abs(g[j + 1])
+        if res <= tol_abs or hn == 0.0:
+            break
+        V.append(w / hn)
+    y = np.zeros(k, dtype=np.complex128)
+    for i in range(k - 1, -1, -1):                   # back substitution
+        y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+    return V, Zs, y, k, res
+
+
+def gmres_right(matvec, b, tol, maxit, x0=None, prec=None, flexible=False):
+    """Right-preconditioned (flexible) GMRES for matvec(x) = b."""
+    b = np.asarray(b, dtype=np.complex128)
+    x0 = np.zeros_like(b) if x0 is None else np.asarray(x0, np.complex128)
+    bnorm = np.linalg.norm(b)
+    r0 = b - matvec(x0) if np.any(x0) else b.copy()
+    beta = np.linalg.norm(r0)
+    if bnorm == 0.0 or beta <= tol * bnorm:
+        return Result(x0.copy(), 0, beta, True)
+    prec = prec if prec is not None else (lambda v: v)
+
+    def op(v):
+        z = prec(v)
+        return matvec(z), z
+
+    V, Zs, y, k, res = _arnoldi_lsq(op, r0 / beta, beta, tol * bnorm, maxit,
+                                    keep_dirs=flexible)
+    if flexible:
+        upd = sum(y[i] * Zs[i] for i in range(k))
+    else:
+        upd = prec(sum(y[i] * V[i] for i in range(k)))
+    return Result(x0 + upd, k, res, res <= tol * bnorm)
+
+
+def gmres_left(matvec, prec, b, tol, maxit, x0=None):
+    """Algorithm 1 without the final deflation correction (which belongs to
+    the singular P A formulation and is not used by A-DEF1): GMRES on
+    prec(matvec(.)), stopping when the preconditioned residual falls below
+    ``tol`` times the initial preconditioned residual."""
+    b = np.asarray(b, dtype=np.complex128)
+    x0 = np.zeros_like(b) if x0 is None else np.asarray(x0, np.complex128)
+    r0 = prec(b - matvec(x0))
+    beta = np.linalg.norm(r0)
+    if beta == 0.0:
+        return Result(x0.copy(), 0, 0.0, True)
+
+    def op(v):
+        return prec(matvec(v)), None
+
+    V, _, y, k, res = _arnoldi_lsq(op, r0 / beta, beta, tol * beta, maxit)
+    return Result(x0 + sum(y[i] * V[i] for i in range(k)), k, res,
+                  res <= tol * beta)

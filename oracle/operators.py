@@ -1,0 +1,365 @@
+"""Assembled (CSR) operators of the method, FP64.  Test infrastructure only.
+
+Grid conventions
+----------------
+A level is a vertex-centred grid of ``nx * ny`` nodes with spacing ``h``
+(Sec. 2.1).  Arrays are ``(ny, nx)``, x fastest; the flat node index is
+``j * nx + i``.  The coarse node ``(I, J)`` sits on the fine node
+``(2I, 2J)`` (0-based form of the 1-based map ``(2i_c-1, 2j_c-1)``, Sec. 4).
+
+Unknowns: every node under first-order Sommerfeld boundaries; the interior
+nodes under homogeneous Dirichlet boundaries, where boundary nodes are fixed
+at zero and interior rows drop their couplings to them (the Dirichlet rows
+``ap = 1`` of Sec. 5.1 with zero boundary data give the same solution).
+
+Coarsening (Sec. 4): a level is coarsened while both interval counts are
+even and both coarse interval counts stay >= ``min_coarse_intervals``
+(2 by default, the "at least 2 x 2 points" rule).  The wavenumber of a
+coarse node is injected from the coincident fine node.
+"""
+
+import numpy as np
+import scipy.sparse as sp
+
+DIRICHLET = "dirichlet"
+SOMMERFELD = "sommerfeld"
+
+
+# --------------------------------------------------------------------------
+# grid hierarchy
+# --------------------------------------------------------------------------
+def level_shapes(nx, ny, min_coarse_intervals=2):
+    """Node counts of every level, finest first (Sec. 4 coarsening rule)."""
+    shapes = [(nx, ny)]
+    while True:
+        cx, cy = shapes[-1]
+        if (cx - 1) % 2 or (cy - 1) % 2:
+            break
+        ncx, ncy = (cx - 1) // 2 + 1, (cy - 1) // 2 + 1
+        if ncx - 1 < min_coarse_intervals or ncy - 1 < min_coarse_intervals:
+            break
+        shapes.append((ncx, ncy))
+    return shapes
+
+
+class Level:
+    """One grid level: shape, spacing, squared wavenumber and unknown set."""
+
+    def __init__(self, nx, ny, h, k2, bc):
+        if nx < 3 or ny < 3:
+            raise ValueError("a level needs at least 3 x 3 nodes")
+        if bc not in (DIRICHLET, SOMMERFELD):
+            raise ValueError("bc must be 'dirichlet' or 'sommerfeld'")
+        self.nx, self.ny, self.h, self.bc = int(nx), int(ny), float(h), bc
+        self.k2 = np.asarray(k2, dtype=np.float64).reshape(ny, nx)
+        mask = np.ones((ny, nx), dtype=bool)
+        if bc == DIRICHLET:
+            mask[0, :] = mask[-1, :] = False
+            mask[:, 0] = mask[:, -1] = False
+        self.mask = mask
+        self.unk = np.flatnonzero(mask.ravel())
+        self.n = self.unk.size
+
+    def to_unknowns(self, u_full):
+        return np.asarray(u_full, dtype=np.complex128).reshape(-1)[self.unk]
+
+    def to_full(self, vec):
+        out = np.zeros(self.nx * self.ny, dtype=np.complex128)
+        out[self.unk] = vec
+        return out.reshape(self.ny, self.nx)
+
+
+def build_levels(nx, ny, h, k2, bc, min_coarse_intervals=2):
+    """Levels 0..L with doubled spacing and injected wavenumber (Sec. 4)."""
+    shapes = level_shapes(nx, ny, min_coarse_intervals)
+    levels = [Level(nx, ny, h, k2, bc)]
+    for (cx, cy) in shapes[1:]:
+        prev = levels[-1]
+        levels.append(Level(cx, cy, 2.0 * prev.h, prev.k2[::2, ::2], bc))
+    return levels
+
+
+def _restrict_to_unknowns(mat, rows_level, cols_level):
+    return mat.tocsr()[rows_level.unk][:, cols_level.unk].tocsr()
+
+
+# --------------------------------------------------------------------------
+# Helmholtz and CSLP operators (Sec. 2.1, eqs. Helmstencil,
+# Sommerfeldstencil1/2; Sec. 3.1 CSLP def; Sec. 5.1)
+# --------------------------------------------------------------------------
+def five_point_full(nx, ny, h, k2, bc, shift=1.0):
+    """Full-grid (nx*ny square) 5-point operator -Lap_h - shift * k^2.
+
+    Interior rows follow eq. (Helmstencil) with k^2 multiplied by ``shift``
+    (``shift = 1`` gives A_h, ``shift = beta1 + i beta2`` gives the CSLP
+    M_h of eq. (CSLP def)).  Under Sommerfeld boundaries the ghost node of
+    eq. (GhostPoint) is eliminated: each boundary side of a node adds
+    ``-2 i k h / h^2`` to the centre, removes the outward neighbour and
+    doubles the opposite neighbour (eqs. Sommerfeldstencil1/2).  The
+    boundary term uses the unshifted k for both A and M.
+    """
+    k2 = np.asarray(k2, dtype=np.float64).reshape(ny, nx)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    idx = jj * nx + ii
+    inv_h2 = 1.0 / (h * h)
+    diag = (4.0 * inv_h2 - shift * k2).astype(np.complex128)
+    if bc == SOMMERFELD:
+        nsides = ((ii == 0).astype(int) + (ii == nx - 1) + (jj == 0)
+                  + (jj == ny - 1))
+        diag = diag - 2j * nsides * np.sqrt(k2) / h
+    rows = [idx.ravel()]
+    cols = [idx.ravel()]
+    vals = [diag.ravel()]
+    for di, dj in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        ni, nj = ii + di, jj + dj
+        inside = (ni >= 0) & (ni < nx) & (nj >= 0) & (nj < ny)
+        coef = np.full((ny, nx), -inv_h2, dtype=np.complex128)
+        if bc == SOMMERFELD:
+            mi, mj = ii - di, jj - dj
+            mirror_out = ~((mi >= 0) & (mi < nx) & (mj >= 0) & (mj < ny))
+            coef = np.where(mirror_out, 2.0 * coef, coef)
+        rows.append(idx[inside])
+        cols.append((nj * nx + ni)[inside])
+        vals.append(coef[inside])
+    n = nx * ny
+    return sp.csr_matrix((np.concatenate(vals),
+                          (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(n, n))
+
+
+def five_point(level, shift=1.0):
+    """A_h (shift=1) or M_h (shift=beta1+i*beta2) over the unknowns."""
+    full = five_point_full(level.nx, level.ny, level.h, level.k2, level.bc,
+                           shift)
+    return _restrict_to_unknowns(full, level, level)
+
+
+def symmetrizer(level):
+    """Diagonal D with D*A symmetric: 1 interior, 1/2 edge, 1/4 corner
+    under Sommerfeld boundaries (the ghost-eliminated rows carry the
+    doubled -2/h^2 couplings); the identity under Dirichlet boundaries."""
+    ny, nx = level.ny, level.nx
+    d = np.ones((ny, nx))
+    if level.bc == SOMMERFELD:
+        d[0, :] *= 0.5
+        d[-1, :] *= 0.5
+        d[:, 0] *= 0.5
+        d[:, -1] *= 0.5
+    return d.reshape(-1)[level.unk]
+
+
+# --------------------------------------------------------------------------
+# transfer operators and deflation vectors (Sec. 3.2.1)
+# --------------------------------------------------------------------------
+def _p1_bilinear(nc):
+    """1-D linear interpolation, eq. (linear iterpolation): a fine node on a
+    coarse node copies it, a fine node between two averages them."""
+    rows, cols, vals = [], [], []
+    for I in range(nc):
+        rows.append(2 * I); cols.append(I); vals.append(1.0)
+        if I + 1 < nc:
+            rows += [2 * I + 1, 2 * I + 1]
+            cols += [I, I + 1]
+            vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(2 * nc - 1, nc))
+
+
+def _p1_quadratic(nc):
+    """1-D higher-order (quadratic Bezier) interpolation, eq. (quadratic
+    approximation-a): a fine node on coarse node I takes
+    (u_{I-1} + 6 u_I + u_{I+1}) / 8, a fine node between I and I+1 takes
+    (u_I + u_{I+1}) / 2.  Coarse values outside the grid are zero."""
+    rows, cols, vals = [], [], []
+    for I in range(nc):
+        for J, w in ((I - 1, 0.125), (I, 0.75), (I + 1, 0.125)):
+            if 0 <= J < nc:
+                rows.append(2 * I); cols.append(J); vals.append(w)
+        if I + 1 < nc:
+            rows += [2 * I + 1, 2 * I + 1]
+            cols += [I, I + 1]
+            vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(2 * nc - 1, nc))
+
+
+def prolongation(fine, coarse, kind="bilinear"):
+    """Interpolation from ``coarse`` to ``fine`` over the unknowns.
+
+    ``kind='bilinear'``: the tensor product of the 1-D linear rule, whose
+    2-D stencil is (1/4)[1 2 1; 2 4 2; 1 2 1] (eq. bilinear operator).
+    ``kind='ho'``: the tensor product of the 1-D quadratic rule, whose 2-D
+    stencil is the (1/64) 5x5 stencil of eq. (higher-order intp-operator).
+    """
+    if kind == "bilinear":
+        p1 = _p1_bilinear
+    elif kind == "ho":
+        p1 = _p1_quadratic
+    else:
+        raise ValueError(kind)
+    assert fine.nx == 2 * coarse.nx - 1 and fine.ny == 2 * coarse.ny - 1
+    full = sp.kron(p1(coarse.ny), p1(coarse.nx), format="csr")
+    return _restrict_to_unknowns(full, fine, coarse)
+
+
+def restriction(P):
+    """R = Z^T / 4, the transpose scaled so that it is full weighting
+    (eq. weight operator, stencil sum 1) for bilinear Z."""
+    return (P.T / 4.0).tocsr()
+
+
+# --------------------------------------------------------------------------
+# coarse operators E (Sec. 5.2.1 - 5.2.4)
+# --------------------------------------------------------------------------
+# The 5x5 integer stencils printed for ReD-Glk: the Galerkin Laplacian
+# (eq. Glk Laplace, scale 1/(256 (2h)^2)) and the constant-wavenumber
+# mass term (eq. ReD-Glk Kh, scale k^2/64^2).  Rows are y offsets -2..2,
+# columns x offsets -2..2 (both are symmetric).
+GLK_LAPLACE = np.array([
+    [-3, -44, -98, -44, -3],
+    [-44, -112, 56, -112, -44],
+    [-98, 56, 980, 56, -98],
+    [-44, -112, 56, -112, -44],
+    [-3, -44, -98, -44, -3]], dtype=np.float64)
+GLK_MASS = np.array([
+    [1, 28, 70, 28, 1],
+    [28, 784, 1960, 784, 28],
+    [70, 1960, 4900, 1960, 70],
+    [28, 784, 1960, 784, 28],
+    [1, 28, 70, 28, 1]], dtype=np.float64)
+
+
+def galerkin(A0, Z):
+    """str-Glk: E = R A_h Z with R = Z^T / 4, as an explicit sparse product
+    of interpolation, fine operator and restriction (Sec. 5.2.1)."""
+    return (restriction(Z) @ A0 @ Z).tocsr()
+
+
+def red_o2(coarse):
+    """ReD-O2: the 2nd-order Helmholtz stencil re-discretised on the coarse
+    grid with the injected wavenumber (Sec. 5.2.3)."""
+    return five_point(coarse, 1.0)
+
+
+def _ghost_rule(bc, H, kb, u_bnd, u_in):
+    """Ghost value outside a boundary node as a linear combination (dict
+    node -> coefficient).  Sommerfeld: u_ghost = u_in + 2 i H k_b u_bnd
+    (eq. GhostPoint); Dirichlet: u_ghost = 2 u_bnd - u_in
+    (eq. DirchletGhostPoint)."""
+    out = {}
+    if bc == SOMMERFELD:
+        for key, c in u_in.items():
+            out[key] = out.get(key, 0) + c
+        for key, c in u_bnd.items():
+            out[key] = out.get(key, 0) + 2j * H * kb * c
+    else:
+        for key, c in u_bnd.items():
+            out[key] = out.get(key, 0) + 2.0 * c
+        for key, c in u_in.items():
+            out[key] = out.get(key, 0) - c
+    return out
+
+
+def ghost_values(level):
+    """Linear map from the real nodes to the values on the ring of ghost
+    nodes one layer outside the grid, as dict (i, j) -> {node: coef}.
+
+    Edge ghosts follow eq. (GhostPoint) (Sommerfeld) or eq.
+    (DirchletGhostPoint) (Dirichlet) with k of the boundary node.  A corner
+    ghost can be reached through either direction; the wavenumber of a
+    ghost node is zero (Sec. 5.2.4), and the two orders are averaged.
+    """
+    nx, ny, H, bc = level.nx, level.ny, level.h, level.bc
+    k = np.sqrt(level.k2)
+
+    def real(i, j):
+        return {j * nx + i: 1.0}
+
+    def kb(i, j):
+        if 0 <= i < nx and 0 <= j < ny:
+            return k[j, i]
+        return 0.0
+
+    g = {}
+    for j in range(ny):           # x ghosts on real rows
+        g[(-1, j)] = _ghost_rule(bc, H, kb(0, j), real(0, j), real(1, j))
+        g[(nx, j)] = _ghost_rule(bc, H, kb(nx - 1, j), real(nx - 1, j),
+                                 real(nx - 2, j))
+    for i in range(nx):           # y ghosts on real columns
+        g[(i, -1)] = _ghost_rule(bc, H, kb(i, 0), real(i, 0), real(i, 1))
+        g[(i, ny)] = _ghost_rule(bc, H, kb(i, ny - 1), real(i, ny - 1),
+                                 real(i, ny - 2))
+    for gi, bi, ii in ((-1, 0, 1), (nx, nx - 1, nx - 2)):
+        for gj, bj, jj in ((-1, 0, 1), (ny, ny - 1, ny - 2)):
+            # x rule on the ghost row gj (ghost k = 0 at (bi, gj))
+            ox = _ghost_rule(bc, H, kb(bi, gj), g[(bi, gj)], g[(ii, gj)])
+            # y rule on the ghost column gi (ghost k = 0 at (gi, bj))
+            oy = _ghost_rule(bc, H, kb(gi, bj), g[(gi, bj)], g[(gi, jj)])
+            avg = {}
+            for d in (ox, oy):
+                for key, c in d.items():
+                    avg[key] = avg.get(key, 0) + 0.5 * c
+            g[(gi, gj)] = avg
+    return g
+
+
+def stencil_with_ghosts(level, rows_mask, coef_fn, radius):
+    """Assemble rows (full-grid) for nodes in ``rows_mask`` from a stencil of
+    the given radius; neighbours one layer outside the grid are replaced by
+    their ghost combination.  ``coef_fn(i, j, di, dj, k2_nb)`` gives the
+    coefficient of offset (di, dj), with k2_nb the squared wavenumber of
+    that neighbour (zero at a ghost node)."""
+    nx, ny = level.nx, level.ny
+    g = ghost_values(level)
+    rows, cols, vals = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            if not rows_mask[j, i]:
+                continue
+            r = j * nx + i
+            for dj in range(-radius, radius + 1):
+                for di in range(-radius, radius + 1):
+                    ni, nj = i + di, j + dj
+                    inside = 0 <= ni < nx and 0 <= nj < ny
+                    k2nb = level.k2[nj, ni] if inside else 0.0
+                    c = coef_fn(i, j, di, dj, k2nb)
+                    if c == 0:
+                        continue
+                    if inside:
+                        rows.append(r); cols.append(nj * nx + ni)
+                        vals.append(c)
+                    else:
+                        if (ni, nj) not in g:
+                            raise ValueError("stencil reaches beyond the "
+                                             "single ghost layer")
+                        for col, w in g[(ni, nj)].items():
+                            rows.append(r); cols.append(col)
+                            vals.append(c * w)
+    n = nx * ny
+    return sp.csr_matrix((np.asarray(vals, dtype=np.complex128),
+                          (rows, cols)), shape=(n, n))
+
+
+def red_glk(coarse, variant=2):
+    """ReD-Glk1 / ReD-Glk2 (Sec. 5.2.4).
+
+    Interior coarse nodes use the Galerkin-derived 5x5 stencil
+    [-Lap_2h] - [k^2_2h] of eqs. (Glk Laplace) and (ReD-Glk Kh), each entry
+    of the mass part taking k^2 of its own coarse node, divided by 4 to
+    match R = Z^T / 4.  Glk1: the two outermost rings of nodes use ReD-O2.
+    Glk2: the outermost ring uses ReD-O2, the second ring the 5x5 stencil
+    with ghost values (wavenumber zero at ghost nodes).
+    """
+    nx, ny, H = coarse.nx, coarse.ny, coarse.h
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    dist = np.minimum(np.minimum(ii, nx - 1 - ii), np.minimum(jj, ny - 1 - jj))
+    o2_rows = dist <= (0 if variant == 2 else 1)
+    lap = GLK_LAPLACE / (1024.0 * H * H)     # (1/4) (1/256) (1/H^2)
+    mass = GLK_MASS / 16384.0                 # (1/4) (1/64^2)
+
+    def coef(i, j, di, dj, k2nb):
+        return lap[dj + 2, di + 2] - mass[dj + 2, di + 2] * k2nb
+
+    full_glk = stencil_with_ghosts(coarse, ~o2_rows, coef, 2)
+    full_o2 = five_point_full(nx, ny, H, coarse.k2, coarse.bc, 1.0)
+    keep = sp.diags(o2_rows.ravel().astype(np.float64))
+    full = (keep @ full_o2 + full_glk).tocsr()
+    return _restrict_to_unknowns(full, coarse, coarse)

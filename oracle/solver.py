@@ -1,0 +1,165 @@
+"""The method end to end, FP64 CPU: CSLP multigrid V-cycle, inner coarse
+solve, A-DEF1 / APD preconditioner and outer flexible GMRES.  Test
+infrastructure only.
+
+Passages followed: CSLP and its V-cycle (Sec. 3.1, Sec. 5.1 last
+paragraph, Sec. 6 coarsest-grid rule); deflation with Z = I_{2h}^h
+(Sec. 3.2.1); A-DEF1 (Sec. 3.2.2, eq. ADEF1); the coarse problem
+A_2h v_2 = v_1 solved by CSLP-preconditioned GMRES (Sec. 5.2, eqs.
+matvec-restriction .. matvec-interpolation); flexible GMRES outer
+iteration (Sec. 6.3).
+"""
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import operators as ops
+from .krylov import gmres_right, gmres_left
+
+
+class SolveInfo:
+    def __init__(self):
+        self.outer_iters = 0
+        self.inner_iters = []
+        self.relres = np.nan
+        self.converged = False
+
+    @property
+    def inner_total(self):
+        return int(sum(self.inner_iters))
+
+
+class Oracle:
+    """Assembled hierarchy plus the method's steps.
+
+    Parameters mirror the paper's defaults: beta = (1, -0.5) (Sec. 3.1),
+    Jacobi weight 0.8 with one pre- and one post-sweep (Sec. 3.1),
+    coarsest-level GMRES to 1e-8 (Sec. 6), coarse tolerance 1e-6 (Sec. 6.3).
+
+    ``z``: None (plain CSLP), 'bilinear' (A-DEF1) or 'ho' (APD).
+    ``e``: 'galerkin' (str-Glk), 'red_o2', 'red_glk1' or 'red_glk2'.
+    ``coarsest``: 'gmres' (paper) or 'direct' (sparse LU; used where an
+    exact coarsest solve is wanted for tight comparisons).
+    """
+
+    def __init__(self, nx, ny, h, k2, bc, z="ho", e="galerkin",
+                 beta=(1.0, -0.5), omega=0.8, min_coarse_intervals=2,
+                 coarsest="gmres", coarsest_tol=1e-8, coarse_tol=1e-6,
+                 coarse_maxit=3000):
+        self.levels = ops.build_levels(nx, ny, h, k2, bc,
+                                       min_coarse_intervals)
+        self.L = len(self.levels) - 1
+        self.shift = complex(beta[0], beta[1])
+        self.omega = omega
+        self.A = ops.five_point(self.levels[0], 1.0)
+        self.M = [ops.five_point(lv, self.shift) for lv in self.levels]
+        self.Dinv = [omega / m.diagonal() for m in self.M]
+        self.P = [ops.prolongation(self.levels[l], self.levels[l + 1],
+                                   "bilinear") for l in range(self.L)]
+        self.R = [ops.restriction(p) for p in self.P]
+        self.coarsest = coarsest
+        self.coarsest_tol = coarsest_tol
+        if coarsest == "direct":
+            self._lu = spla.splu(self.M[self.L].tocsc())
+        self.zkind, self.ekind = z, e
+        self.coarse_tol, self.coarse_maxit = coarse_tol, coarse_maxit
+        self.inner_log = []
+        if z is not None:
+            if self.L < 1:
+                raise ValueError("deflation needs at least one coarsening")
+            self.Z = ops.prolongation(self.levels[0], self.levels[1], z)
+            self.RZ = ops.restriction(self.Z)
+            if e == "galerkin":
+                self.E = ops.galerkin(self.A, self.Z)
+            elif e == "red_o2":
+                self.E = ops.red_o2(self.levels[1])
+            elif e == "red_glk1":
+                self.E = ops.red_glk(self.levels[1], 1)
+            elif e == "red_glk2":
+                self.E = ops.red_glk(self.levels[1], 2)
+            else:
+                raise ValueError(e)
+
+    # ---- CSLP multigrid V-cycle (Sec. 3.1) -------------------------------
+    def coarsest_solve(self, f):
+        if self.coarsest == "direct":
+            return self._lu.solve(f)
+        ML = self.M[self.L]
+        return gmres_right(lambda v: ML @ v, f, self.coarsest_tol,
+                           maxit=max(ML.shape[0], 1)).x
+
+    def vcycle(self, f, level=0):
+        """One V-cycle for M_level x = f from x = 0: damped-Jacobi pre-sweep,
+        full-weighting restriction of the residual, recursion, bilinear
+        interpolation of the correction, damped-Jacobi post-sweep."""
+        if level == self.L:
+            return self.coarsest_solve(f)
+        M, Dinv = self.M[level], self.Dinv[level]
+        x = Dinv * f
+        r = f - M @ x
+        xc = self.vcycle(self.R[level] @ r, level + 1)
+        x = x + self.P[level] @ xc
+        x = x + Dinv * (f - M @ x)
+        return x
+
+    # ---- deflation (Sec. 3.2, 5.2) ----------------------------------------
+    def coarse_solve(self, v1, tol=None, maxit=None):
+        """E v2 = v1 by GMRES right-preconditioned with the V-cycle on the
+        coarse CSLP (levels 1..L), x0 = 0."""
+        tol = self.coarse_tol if tol is None else tol
+        maxit = self.coarse_maxit if maxit is None else maxit
+        res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
+                          prec=lambda v: self.vcycle(v, 1))
+        self.inner_log.append(res.iters)
+        return res.x
+
+    def deflation_Q(self, v):
+        """Q v = Z E^{-1} R v with the inexact coarse solve (Sec. 5.2)."""
+        return self.Z @ self.coarse_solve(self.RZ @ v)
+
+    def adef1(self, v):
+        """P_A-DEF1 v = M^{-1}(v - A Q v) + Q v (eq. ADEF1); without
+        deflation vectors this is the plain CSLP V-cycle."""
+        if self.zkind is None:
+            return self.vcycle(v, 0)
+        q = self.deflation_Q(v)
+        return self.vcycle(v - self.A @ q, 0) + q
+
+    # ---- outer solve (Sec. 6.3) -------------------------------------------
+    def solve(self, b_full, tol=1e-6, maxit=500, x0_full=None):
+        """Flexible GMRES on A x = b right-preconditioned by A-DEF1.  Returns
+        the full-grid solution and a SolveInfo with the true relative
+        residual."""
+        lv = self.levels[0]
+        b = lv.to_unknowns(b_full)
+        x0 = None if x0_full is None else lv.to_unknowns(x0_full)
+        self.inner_log = []
+        res = gmres_right(lambda v: self.A @ v, b, tol, maxit, x0=x0,
+                          prec=self.adef1, flexible=True)
+        info = SolveInfo()
+        info.outer_iters = res.iters
+        info.inner_iters = list(self.inner_log)
+        bn = np.linalg.norm(b)
+        info.relres = (np.linalg.norm(b - self.A @ res.x) / bn) if bn else 0.0
+        info.converged = res.converged
+        return lv.to_full(res.x), info
+
+    def solve_left(self, b_full, tol=1e-6, maxit=500):
+        """Algorithm 1 (left preconditioning, preconditioned residual), for
+        comparison with the paper's iteration tables."""
+        lv = self.levels[0]
+        b = lv.to_unknowns(b_full)
+        self.inner_log = []
+        res = gmres_left(lambda v: self.A @ v, self.adef1, b, tol, maxit)
+        info = SolveInfo()
+        info.outer_iters = res.iters
+        info.inner_iters = list(self.inner_log)
+        bn = np.linalg.norm(b)
+        info.relres = np.linalg.norm(b - self.A @ res.x) / bn
+        info.converged = res.converged
+        return lv.to_full(res.x), info
+
+    # ---- full-grid wrappers used by the parity tests ----------------------
+    def apply_full(self, mat, level, u_full):
+        lv = self.levels[level]
+        return lv.to_full(mat @ lv.to_unknowns(u_full))

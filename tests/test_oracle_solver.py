@@ -1,0 +1,217 @@
+"""Pins of the oracle's V-cycle, deflation, Krylov solvers and gradient."""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from conftest import load_golden
+from oracle import gradient as grd
+from oracle import operators as ops
+from oracle.krylov import gmres_right
+from oracle.solver import Oracle
+
+
+def _k2(ny, nx, seed, lo=3.0, hi=25.0):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(ny, nx)) ** 2
+
+
+def _vcycle_matrix(orc, level):
+    n = orc.levels[level].n
+    B = np.zeros((n, n), dtype=complex)
+    for c in range(n):
+        e = np.zeros(n, dtype=complex)
+        e[c] = 1.0
+        B[:, c] = orc.vcycle(e, level)
+    return B
+
+
+@pytest.mark.parametrize("bc", [ops.SOMMERFELD, ops.DIRICHLET])
+def test_vcycle_error_propagation_identity(bc):
+    """Textbook multigrid identity, level by level:
+    I - B_l M_l = S_l (I - P_l B_{l+1} R_l M_l) S_l with S_l = I - w D^-1 M_l,
+    and B_L = M_L^{-1} at the coarsest level."""
+    nx, ny = 17, 9
+    orc = Oracle(nx, ny, 0.05, _k2(ny, nx, 0), bc, z=None,
+                 coarsest="direct")
+    assert orc.L >= 2
+    Bs = [_vcycle_matrix(orc, l) for l in range(orc.L + 1)]
+    ML = orc.M[orc.L].toarray()
+    np.testing.assert_allclose(Bs[orc.L] @ ML, np.eye(ML.shape[0]),
+                               atol=1e-10)
+    for l in range(orc.L):
+        M = orc.M[l].toarray()
+        n = M.shape[0]
+        S = np.eye(n) - np.diag(orc.omega / np.diag(M)) @ M
+        P, R = orc.P[l].toarray(), orc.R[l].toarray()
+        lhs = np.eye(n) - Bs[l] @ M
+        rhs = S @ (np.eye(n) - P @ Bs[l + 1] @ R @ M) @ S
+        np.testing.assert_allclose(lhs, rhs, atol=1e-10)
+
+
+def test_coarsest_gmres_meets_its_tolerance():
+    orc = Oracle(17, 17, 1 / 16, _k2(17, 17, 1), ops.SOMMERFELD, z=None)
+    f = np.random.default_rng(2).standard_normal(orc.levels[-1].n) + 0j
+    x = orc.coarsest_solve(f)
+    r = np.linalg.norm(f - orc.M[-1] @ x) / np.linalg.norm(f)
+    assert r <= 1e-8
+
+
+@pytest.mark.parametrize("z,bc", [("bilinear", ops.DIRICHLET),
+                                  ("ho", ops.SOMMERFELD),
+                                  ("ho", ops.DIRICHLET)])
+def test_deflation_invariants(z, bc):
+    """With the Galerkin E solved exactly: P A Z = 0, R P = 0, Q A Z = Z and
+    P_A-DEF1 A Z = Z for any M^{-1} (Sec. 3.2 definitions)."""
+    nx, ny = 17, 13
+    orc = Oracle(nx, ny, 0.04, _k2(ny, nx, 3), bc, z=z, e="galerkin",
+                 coarse_tol=1e-14, coarse_maxit=400, coarsest="direct")
+    A, Z, RZ = orc.A.toarray(), orc.Z.toarray(), orc.RZ.toarray()
+    E = orc.E.toarray()
+    Q = Z @ np.linalg.solve(E, RZ)
+    Pd = np.eye(A.shape[0]) - A @ Q
+    scale = np.abs(A @ Z).max()
+    assert np.abs(Pd @ A @ Z).max() < 1e-10 * scale
+    assert np.abs(RZ @ Pd).max() < 1e-10 * np.abs(RZ).max() * scale
+    np.testing.assert_allclose(Q @ A @ Z, Z, atol=1e-10)
+    # through the oracle's own inexact machinery at a tight tolerance
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal(Z.shape[1]) + 1j * rng.standard_normal(Z.shape[1])
+    v = A @ (Z @ c)
+    np.testing.assert_allclose(orc.adef1(v), Z @ c, atol=1e-8 *
+                               np.abs(Z @ c).max())
+
+
+CASES = [
+    (17, 17, ops.SOMMERFELD, "ho", "galerkin"),
+    (17, 33, ops.DIRICHLET, "bilinear", "galerkin"),
+    (17, 17, ops.SOMMERFELD, "ho", "red_glk2"),
+    (17, 17, ops.DIRICHLET, "ho", "red_glk1"),
+    (33, 17, ops.SOMMERFELD, "bilinear", "red_o2"),
+    (17, 17, ops.SOMMERFELD, None, "galerkin"),
+]
+
+
+@pytest.mark.parametrize("nx,ny,bc,z,e", CASES)
+def test_fgmres_matches_direct_solve(nx, ny, bc, z, e):
+    h = 1.0 / (max(nx, ny) - 1)
+    k2 = _k2(ny, nx, 5, lo=8, hi=20)
+    orc = Oracle(nx, ny, h, k2, bc, z=z, e=e, coarse_tol=1e-10)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    x, info = orc.solve(b, tol=1e-12, maxit=200)
+    lv = orc.levels[0]
+    xd = lv.to_full(spla.spsolve(orc.A.tocsc(), lv.to_unknowns(b)))
+    assert info.converged and info.relres < 1e-11
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_fgmres_warm_start_and_zero_rhs():
+    orc = Oracle(17, 17, 1 / 16, _k2(17, 17, 7), ops.SOMMERFELD, z="ho")
+    b = np.zeros((17, 17), complex)
+    x, info = orc.solve(b)
+    assert info.outer_iters == 0 and not np.any(x)
+    b[8, 8] = 1.0
+    x1, i1 = orc.solve(b, tol=1e-10)
+    x2, i2 = orc.solve(b, tol=1e-10, x0_full=x1)
+    assert i2.outer_iters <= 1 and i2.relres < 1e-9
+
+
+def test_gmres_lucky_breakdown_identity():
+    b = np.arange(1, 6) + 0j
+    res = gmres_right(lambda v: 3.0 * v, b, 1e-14, 10)
+    assert res.iters == 1
+    np.testing.assert_allclose(res.x, b / 3.0)
+
+
+def _band(paper, ours):
+    return abs(ours - paper) <= max(2, 0.3 * paper)
+
+
+def test_table2_band_mp2a_k20():
+    """MP-2a, 33 x 33, k = 20, A-DEF1 str-Glk + CSLP-GMRES coarse solve:
+    Table 2 prints 8 outer iterations (left preconditioning).  Plausibility
+    band, both for Algorithm 1 and for the flexible GMRES used here."""
+    g = load_golden("iteration_tables.txt")["table2_kh0625"]
+    n, k, paper = (int(v) for v in g[0])
+    orc = Oracle(n, n, 1.0 / (n - 1), np.full((n, n), float(k) ** 2),
+                 ops.DIRICHLET, z="bilinear", e="galerkin", coarse_tol=1e-6)
+    b = np.zeros((n, n), complex)
+    b[n // 2, n // 2] = 1.0
+    _, il = orc.solve_left(b, tol=1e-6)
+    _, ir = orc.solve(b, tol=1e-6)
+    assert _band(paper, il.outer_iters), il.outer_iters
+    assert _band(paper, ir.outer_iters), ir.outer_iters
+    assert ir.relres <= 1e-6
+
+
+@pytest.mark.slow
+def test_config1_iterations_between_table2_rows():
+    """81 x 81, k = 50, Dirichlet, bilinear str-Glk: the outer count lies
+    between Table 2's k = 40 and k = 80 rows."""
+    g = load_golden("iteration_tables.txt")["table2_kh0625"]
+    lo, hi = int(g[1, 2]), int(g[2, 2])
+    n = 81
+    orc = Oracle(n, n, 1 / 80, np.full((n, n), 2500.0), ops.DIRICHLET,
+                 z="bilinear", e="galerkin", coarse_tol=1e-6)
+    b = np.zeros((n, n), complex)
+    b[40, 40] = 1.0
+    _, info = orc.solve(b, tol=1e-6)
+    assert lo - 2 <= info.outer_iters <= hi + 2, info.outer_iters
+    assert info.relres <= 1e-6
+
+
+# ---------------------------------------------------------------- gradient
+def _fd_setup(bc, nx=9, ny=13, seed=8):
+    rng = np.random.default_rng(seed)
+    h, omega = 1.0 / 12, 30.0
+    m = rng.uniform(0.6, 1.4, size=(ny, nx))
+    src = np.zeros((2, ny, nx), complex)
+    src[0, ny // 2, nx // 2] = 1.0
+    src[1, 2, 3] = 1.0
+    row = 0 if bc == ops.SOMMERFELD else 1
+    rec = (row * nx + np.arange(1, nx - 1)).astype(np.int64)
+    d = (rng.standard_normal((2, rec.size))
+         + 1j * rng.standard_normal((2, rec.size))) * 1e-3
+    return nx, ny, h, m, omega, src, rec, d
+
+
+@pytest.mark.parametrize("bc", [ops.SOMMERFELD, ops.DIRICHLET])
+def test_gradient_matches_central_differences(bc):
+    nx, ny, h, m, omega, src, rec, d = _fd_setup(bc)
+    J, g = grd.misfit_and_gradient(nx, ny, h, m, omega, bc, src, rec, d)
+    rng = np.random.default_rng(9)
+    dirs = [rng.standard_normal((ny, nx)) for _ in range(3)]
+    for (i, j) in ((4, 6), (0, 5), (0, 0), (8, 12)):   # interior/edge/corner
+        e = np.zeros((ny, nx))
+        e[j, i] = 1.0
+        dirs.append(e)
+    for dm in dirs:
+        if bc == ops.DIRICHLET:
+            dm = dm.copy()
+            dm[0, :] = dm[-1, :] = dm[:, 0] = dm[:, -1] = 0.0
+            if not np.any(dm):
+                continue
+        eps = 1e-4 * np.abs(m).max() / np.abs(dm).max()
+        jp = grd.misfit(nx, ny, h, m + eps * dm, omega, bc, src, rec, d)
+        jm = grd.misfit(nx, ny, h, m - eps * dm, omega, bc, src, rec, d)
+        fd = (jp - jm) / (2 * eps)
+        an = float(np.sum(g * dm))
+        assert abs(fd - an) <= 1e-5 * max(abs(fd), 1e-30) + 1e-14, (fd, an)
+
+
+def test_gradient_with_iterative_solves_matches_direct():
+    nx, ny, h, m, omega, src, rec, d = _fd_setup(ops.SOMMERFELD, 9, 13)
+    J0, g0 = grd.misfit_and_gradient(nx, ny, h, m, omega, ops.SOMMERFELD,
+                                     src, rec, d)
+    orc = Oracle(nx, ny, h, omega ** 2 * m, ops.SOMMERFELD, z="ho",
+                 coarse_tol=1e-10, coarsest="direct")
+
+    def it_solve(A, rhs):
+        x, info = orc.solve(orc.levels[0].to_full(rhs), tol=1e-13)
+        return orc.levels[0].to_unknowns(x)
+
+    J1, g1 = grd.misfit_and_gradient(nx, ny, h, m, omega, ops.SOMMERFELD,
+                                     src, rec, d, solve=it_solve)
+    assert J1 == pytest.approx(J0, rel=1e-9)
+    np.testing.assert_allclose(g1, g0, atol=1e-8 * np.abs(g0).max())
