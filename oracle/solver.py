@@ -33,6 +33,7 @@ class Oracle:
     """Assembled hierarchy plus the method's steps.
 
     Parameters mirror the paper's defaults: beta = (1, -0.5) (Sec. 3.1),
+    entering the CSLP through the coefficient printed in Sec. 5.1,
     Jacobi weight 0.8 with one pre- and one post-sweep (Sec. 3.1),
     coarsest-level GMRES to 1e-8 (Sec. 6), coarse tolerance 1e-6 (Sec. 6.3).
 
@@ -49,7 +50,9 @@ class Oracle:
         self.levels = ops.build_levels(nx, ny, h, k2, bc,
                                        min_coarse_intervals)
         self.L = len(self.levels) - 1
-        self.shift = complex(beta[0], beta[1])
+        # CSLP coefficient as implemented in Sec. 5.1: ap = (4 - (beta1 -
+        # beta2 i) k^2 h^2) / h^2, i.e. M = -Lap - (beta1 - i beta2) k^2.
+        self.shift = complex(beta[0], -beta[1])
         self.omega = omega
         self.A = ops.five_point(self.levels[0], 1.0)
         self.M = [ops.five_point(lv, self.shift) for lv in self.levels]

@@ -105,14 +105,20 @@ def test_DA_symmetric(bc):
 
 @pytest.mark.parametrize("bc", [ops.SOMMERFELD, ops.DIRICHLET])
 def test_cslp_minus_helmholtz_is_imaginary_mass(bc):
-    """M = -Lap - (1 - 0.5 i) k^2 (eq. CSLP def, beta = (1, -0.5)) differs
-    from A by 0.5 i k^2 on the diagonal only."""
+    """The CSLP of Sec. 5.1, ap = (4 - (beta1 - beta2 i) k^2 h^2)/h^2 with
+    beta = (1, -0.5), differs from A by -0.5 i k^2 on the diagonal only:
+    the same (negative) imaginary sign as the Sommerfeld rows' -2 i k / h."""
+    from oracle.solver import Oracle
     nx, ny = 9, 7
     k2 = _rng_k2(ny, nx, 3)
-    lv = ops.Level(nx, ny, 0.03, k2, bc)
-    d = (ops.five_point(lv, 1 - 0.5j) - ops.five_point(lv, 1.0)).toarray()
-    np.testing.assert_allclose(d, np.diag(0.5j * k2.ravel()[lv.unk]),
+    orc = Oracle(nx, ny, 0.03, k2, bc, z=None, coarsest="direct")
+    d = (orc.M[0] - orc.A).toarray()
+    np.testing.assert_allclose(d, np.diag(-0.5j * k2.ravel()[orc.levels[0].unk]),
                                atol=1e-9)
+    if bc == ops.SOMMERFELD:
+        lv = orc.levels[0]
+        edge = lv.unk.tolist().index(3 * nx + 0)
+        assert orc.A.diagonal()[edge].imag < 0
 
 
 # ---------------------------------------------------------------- transfers

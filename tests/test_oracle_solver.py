@@ -145,6 +145,20 @@ def test_table2_band_mp2a_k20():
     assert ir.relres <= 1e-6
 
 
+@pytest.mark.parametrize("row", [0, 1])
+def test_table3_band_mp2b(row):
+    """MP-2b (Sommerfeld), bilinear str-Glk + CSLP-GMRES coarse solve:
+    Table 3 prints 9 and 13 outer iterations for 33^2 / 65^2, kh = 0.625."""
+    g = load_golden("iteration_tables.txt")["table3_kh0625"]
+    n, k, paper = (int(v) for v in g[row])
+    orc = Oracle(n, n, 1.0 / (n - 1), np.full((n, n), float(k) ** 2),
+                 ops.SOMMERFELD, z="bilinear", e="galerkin", coarse_tol=1e-6)
+    b = np.zeros((n, n), complex)
+    b[n // 2, n // 2] = 1.0
+    _, il = orc.solve_left(b, tol=1e-6)
+    assert _band(paper, il.outer_iters), il.outer_iters
+
+
 @pytest.mark.slow
 def test_config1_iterations_between_table2_rows():
     """81 x 81, k = 50, Dirichlet, bilinear str-Glk: the outer count lies
