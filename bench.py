@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 two-level-deflation Helmholtz solver.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME] [--prec mixed|fp64]
+
+A step is one complete solve of a batch of right-hand sides to relative
+residual 1e-6 through the C ABI (hz_solve): outer FP64 flexible GMRES, the
+A-DEF1 preconditioner with its inner coarse solve and V-cycles.  The metric
+is unknowns * solves per second (whole job), device-timed with CUDA events;
+``e2e`` repeats it through hz_solve_host with host buffers and the copies
+inside the timed region.  Under torchrun every rank solves its own shots
+(replicas, weak scaling; there is no exchange between ranks).
+
+``--impl reference`` times the CPU FP64 oracle (the plain restatement of the
+method used by the tests) on a bounded sample of the same workload.
+"""
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import tempfile  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "unknowns*solves/s to rel.res 1e-6"
+UNIT = "unknowns*solves/s"
+
+# Workloads (seeded, synthetic).  mp2b: unit square, constant k, Sommerfeld
+# boundaries, kh = 0.625; 16 point sources on a lattice around the centre.
+WORKLOADS = {
+    "mp2b_1281_k800_b16": dict(model=("constant_k", 1281, 800.0),
+                               bc="sommerfeld", z="ho", e="galerkin",
+                               nrhs=16, sources="centre_cluster",
+                               coarse_tol=1e-1, coarse_maxit=200,
+                               outer_maxit=60, tol=1e-6),
+    "mp2b_641_k400_b16": dict(model=("constant_k", 641, 400.0),
+                              bc="sommerfeld", z="ho", e="galerkin",
+                              nrhs=16, sources="centre_cluster",
+                              coarse_tol=1e-1, coarse_maxit=200,
+                              outer_maxit=60, tol=1e-6),
+    "mp2a_81_k50": dict(model=("constant_k", 81, 50.0), bc="dirichlet",
+                        z="bilinear", e="galerkin", nrhs=1,
+                        sources="centre", coarse_tol=1e-6,
+                        coarse_maxit=1000, outer_maxit=100, tol=1e-6),
+}
+DEFAULT_WORKLOAD = "mp2b_1281_k800_b16"
+ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_bench_counts.json")
+ORACLE_COUNT_KEY = {"mp2b_1281_k800_b16": "mp2b_1281_k800",
+                    "mp2b_641_k400_b16": None, "mp2a_81_k50": "mp2a_81_k50"}
+
+
+def build_inputs(wl_name, rank=0):
+    from paper_2308_06152_gb300 import workloads as wl
+    cfg = WORKLOADS[wl_name]
+    kind, n, k = cfg["model"]
+    model = wl.constant_k(n, k)
+    if cfg["sources"] == "centre":
+        nodes = [wl.centre_node(model.nx, model.ny)] * cfg["nrhs"]
+    else:
+        nodes = wl.centre_cluster(model.nx, model.ny, cfg["nrhs"])
+        if rank:
+            nodes = [(i + rank, j) for (i, j) in nodes]
+    b = wl.point_sources(model.nx, model.ny, nodes)
+    return cfg, model, b
+
+
+def unknowns(cfg, model):
+    if cfg["bc"] == "dirichlet":
+        return (model.nx - 2) * (model.ny - 2)
+    return model.nx * model.ny
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_uuid=None):
+        self.proc = None
+        self.path = None
+        self.uuid = dev_uuid
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}",
+               "--format=csv,noheader,nounits", "-lms", "200",
+               "-f", self.path]
+        if self.uuid:
+            cmd[1:1] = ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.DEVNULL,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4)
+                          if r[5 + i].lower().startswith("active")})
+        load = [v for v in sm if mx and v > 0.5 * max(mx)] or sm
+        return {"sm_mhz": float(np.median(load)) if load else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(wl_name, steps, warmup):
+    """Bounded CPU sample: one outer flexible-GMRES iteration of the oracle
+    (one A-DEF1 application with its inner coarse solve, one A product and
+    the Gram-Schmidt step) on one right-hand side, scaled to a whole solve by
+    the oracle's own outer-iteration count for this workload."""
+    from oracle.solver import Oracle
+    cfg, model, b = build_inputs(wl_name)
+    key = ORACLE_COUNT_KEY.get(wl_name)
+    counts = {}
+    if os.path.exists(ORACLE_COUNTS):
+        with open(ORACLE_COUNTS) as fh:
+            counts = json.load(fh)
+    outer = counts.get(key, {}).get("outer_iters") if key else None
+    orc = Oracle(model.nx, model.ny, model.h, model.k2, cfg["bc"], z=cfg["z"],
+                 e=cfg["e"], coarse_tol=cfg["coarse_tol"],
+                 coarse_maxit=cfg["coarse_maxit"])
+    lv = orc.levels[0]
+    bu = lv.to_unknowns(b[0])
+    v = bu / np.linalg.norm(bu)
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        z = orc.adef1(v)
+        w = orc.A @ z
+        w = w - np.vdot(v, w) * v
+        np.linalg.norm(w)
+        dt = time.perf_counter() - t0
+        if it >= warmup:
+            times.append(dt)
+    t_iter = float(np.mean(times))
+    n_unk = unknowns(cfg, model)
+    if outer:
+        value = n_unk / (t_iter * outer)
+    else:
+        value = None
+    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"one outer FGMRES iteration (A-DEF1 incl. inner "
+                       f"coarse solve) of 1 RHS of {wl_name}, "
+                       f"{t_iter:.2f} s mean over {len(times)}, scaled by the "
+                       f"oracle's {outer} outer iterations for a full solve")}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2308_06152_gb300._lib import load_library
+    from paper_2308_06152_gb300.api import Desc, Solver
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    lib = load_library()
+    cfg, model, b_np = build_inputs(args.workload, rank)
+    desc = Desc(model.nx, model.ny, model.h, bc=cfg["bc"], z=cfg["z"],
+                e=cfg["e"], prec=args.prec, nrhs_max=cfg["nrhs"],
+                coarse_tol=cfg["coarse_tol"], coarse_maxit=cfg["coarse_maxit"],
+                outer_maxit=cfg["outer_maxit"])
+    solver = Solver(desc, model.k2)
+    stream = solver.stream
+    b = torch.from_numpy(b_np).cuda()
+    tol = cfg["tol"]
+    for _ in range(args.warmup):
+        x, info = solver.solve(b, tol=tol)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    l0 = lib.hz_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    infos = []
+    for _ in range(args.steps):
+        x, info = solver.solve(b, tol=tol)
+        infos.append(info)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = lib.hz_kernel_launches() - l0
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    n_unk = unknowns(cfg, model)
+    units = n_unk * cfg["nrhs"] * world
+    value = units / (ms / 1000.0)
+    worst = max(i.relres for step in infos for i in step)
+    statuses = sorted({i.status for step in infos for i in step})
+    outer = [i.outer_iters for i in infos[-1]]
+    inner = [i.inner_iters_total for i in infos[-1]]
+
+    # end to end through the host-buffer entry point
+    bh = torch.from_numpy(b_np).pin_memory()
+    xh = torch.empty_like(bh).pin_memory()
+    solver.solve_host(bh, xh, tol=tol)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        solver.solve_host(bh, xh, tol=tol)
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    io_bytes = int(b_np.nbytes)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(args.workload, steps=1, warmup=0)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64" if args.prec == "mixed" else "c128",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "grid": [model.nx, model.ny],
+                       "k": cfg["model"][2], "bc": cfg["bc"],
+                       "deflation": f"{cfg['z']}/{cfg['e']}",
+                       "precision": ("complex-FP32 preconditioner in FP64 "
+                                     "FGMRES" if args.prec == "mixed"
+                                     else "complex-FP64 throughout"),
+                       "nrhs_per_gpu": cfg["nrhs"], "tol": tol,
+                       "coarse_tol": cfg["coarse_tol"],
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (each batch vector "
+                             f"{b_np.nbytes / 1e6:.0f} MB)"},
+            "e2e": {"value": units / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": io_bytes,
+                    "d2h_bytes_per_step": io_bytes},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "roofline": None,
+            "cpu_baseline": cpu,
+            "solve": {"outer_iters": outer, "inner_iters_total": inner,
+                      "max_true_relres": worst, "status": statuses},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cpu = oracle_sample(args.workload, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": cpu["value"],
+        "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+        "config": {"workload": args.workload},
+        "cpu_baseline": cpu,
+        "e2e": {"value": cpu["value"], "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=sorted(WORKLOADS))
+    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--no-cpu", action="store_true",
+                    help="skip the CPU oracle baseline sample")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,186 @@
+/*
+ * hz.h -- C ABI of the GB300 (sm_103a) matrix-free two-level deflation +
+ * CSLP-preconditioned Krylov solver for the 2-D finite-difference Helmholtz
+ * equation  -Lap u - k(x,y)^2 u = b  (Chen, Dwarka, Vuik, arXiv 2308.06152).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - A grid has nx * ny nodes, spacing h, node (i, j) at flat index
+ *    j * nx + i (x fastest).  Vectors are complex128 (interleaved re, im
+ *    doubles, i.e. double2) laid out [nrhs][ny][nx]; nrhs vectors are
+ *    stored back to back.
+ *  - Under HZ_BC_DIRICHLET the boundary nodes are not unknowns: inputs there
+ *    are ignored (read as 0) and outputs there are written as 0.
+ *  - Every pointer named *_dev is device memory of the current CUDA device;
+ *    *_host is host memory (pinned memory makes the copies asynchronous).
+ *    The library never allocates device memory: all device storage is the
+ *    caller's workspace (hz_workspace_bytes / hz_setup).  The caller keeps
+ *    ownership of every buffer it passes and must keep the workspace and
+ *    the k2 array alive until hz_destroy.
+ *  - Work is issued on the stream given to hz_setup, in stream order.
+ *    Entry points that return numbers on the host (hz_solve's info, J)
+ *    synchronise that stream before returning.
+ *  - Errors are return codes; nothing throws across the ABI.
+ *    hz_last_error gives a one-line description of the last failure.
+ */
+#ifndef HZ_H_
+#define HZ_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HZ_OK = 0,
+  HZ_INVALID_ARG = 1,         /* null pointer, nrhs out of range, bad enum  */
+  HZ_INVALID_GRID = 2,        /* too small, cannot be coarsened for
+                                 deflation, or coarsest level too large     */
+  HZ_WORKSPACE_TOO_SMALL = 3,
+  HZ_NOT_CONVERGED = 4,       /* iteration cap reached; x holds the last
+                                 iterate, info.relres its true residual     */
+  HZ_BREAKDOWN = 5,           /* Arnoldi breakdown without convergence      */
+  HZ_NAN = 6,                 /* NaN / Inf met in a residual norm           */
+  HZ_TIMEOUT = 7,             /* reserved: no kernel of this library waits */
+  HZ_CUDA_ERROR = 8
+} hz_status;
+
+typedef enum { HZ_BC_DIRICHLET = 0, HZ_BC_SOMMERFELD = 1 } hz_bc;
+
+/* Deflation vectors Z (Sec. 3.2.1): none (plain CSLP preconditioner),
+ * bilinear interpolation (A-DEF1) or the quadratic higher-order
+ * interpolation (APD). */
+typedef enum { HZ_Z_NONE = 0, HZ_Z_BILINEAR = 1, HZ_Z_HO = 2 } hz_zkind;
+
+/* Coarse operator E = A_2h (Sec. 5.2): the Galerkin product R A_h Z formed
+ * on the fly each application (str-Glk), 2nd-order re-discretisation
+ * (ReD-O2), or the Galerkin-derived 5x5 re-discretisation with 2nd-order
+ * rows on the two outer rings (ReD-Glk1) or on the outer ring with ghost
+ * values on the second (ReD-Glk2). */
+typedef enum {
+  HZ_E_GALERKIN = 0, HZ_E_RED_O2 = 1, HZ_E_RED_GLK1 = 2, HZ_E_RED_GLK2 = 3
+} hz_ekind;
+
+/* Arithmetic of the preconditioner (V-cycle, deflation, inner coarse
+ * solve).  The outer flexible GMRES, its Arnoldi process, Givens updates,
+ * residuals and solution update are always complex FP64. */
+typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_MIXED_FP32 = 1 } hz_precision;
+
+typedef struct {
+  int nx, ny;                 /* nodes; each >= 3                            */
+  double h;                   /* grid spacing                                */
+  hz_bc bc;
+  hz_zkind zkind;
+  hz_ekind ekind;
+  hz_precision prec;
+  double beta1, beta2;        /* CSLP shift, default (1, -0.5) (Sec. 3.1),
+                                 entering M = -Lap - (beta1 - i beta2) k^2 as
+                                 the coefficient printed in Sec. 5.1        */
+  double jacobi_omega;        /* damped Jacobi weight, default 0.8 (Sec. 3.1)*/
+  int min_coarse_intervals;   /* coarsening stop rule, default 2 (Sec. 4)    */
+  double coarse_tol;          /* inner coarse-solve tolerance (Sec. 6.3)     */
+  int coarse_maxit;           /* inner iteration cap (= its basis size)      */
+  int outer_maxit;            /* outer FGMRES cap (= its basis size)         */
+  int nrhs_max;               /* right-hand sides per hz_solve call          */
+} hz_desc;
+
+typedef struct {
+  int outer_iters;            /* outer FGMRES iterations of this RHS         */
+  int inner_iters_total;      /* inner coarse-solve iterations, summed       */
+  int inner_iters_max;        /* largest single coarse solve                 */
+  double relres;              /* true ||b - A x|| / ||b|| after the solve    */
+  hz_status status;
+} hz_solve_info;
+
+typedef struct hz_solver hz_solver;
+
+/* Operators exposed one by one (parity tests, benchmarks). */
+typedef enum {
+  HZ_OP_HELMHOLTZ = 0,     /* y = A_h x, level 0, FP64 (Sec. 2.1, Alg. 2)   */
+  HZ_OP_CSLP = 1,          /* y = M_l x on level l (Sec. 3.1, 5.1)          */
+  HZ_OP_VCYCLE = 2,        /* y = one V-cycle for M_l y = x from level l    */
+  HZ_OP_RESTRICT_FW = 3,   /* y(level l+1) = full weighting of x(level l)   */
+  HZ_OP_PROLONG_BILINEAR = 4, /* y(level l) = bilinear interp. of x(l+1)    */
+  HZ_OP_RESTRICT_Z = 5,    /* y(level 1) = Z^T x / 4                        */
+  HZ_OP_PROLONG_Z = 6,     /* y(level 0) = Z x(level 1)                     */
+  HZ_OP_COARSE_E = 7,      /* y = E x on level 1 (Sec. 5.2)                 */
+  HZ_OP_COARSE_SOLVE = 8,  /* y ~= E^-1 x by the inner CSLP-GMRES           */
+  HZ_OP_PRECOND = 9        /* y = P_A-DEF1 x = M^-1 (x - A Q x) + Q x       */
+} hz_op;
+
+/* Fills *d with the paper's defaults for an nx x ny grid of spacing h. */
+void hz_desc_default(hz_desc* d, int nx, int ny, double h);
+
+/* Device workspace bytes hz_setup needs for *d (grows with nrhs_max,
+ * outer_maxit and coarse_maxit).  Returns HZ_INVALID_GRID / HZ_INVALID_ARG
+ * for descriptors hz_setup would reject. */
+hz_status hz_workspace_bytes(const hz_desc* d, size_t* bytes);
+
+/* Builds the level hierarchy (Sec. 4 coarsening, injected wavenumber), the
+ * Jacobi diagonals and the inverted coarsest-level CSLP, all inside the
+ * workspace, on stream `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  k2_dev: device FP64 [ny][nx], k(x,y)^2; it is copied.
+ * workspace_dev must be 256-byte aligned.  *out receives a host handle. */
+hz_status hz_setup(const hz_desc* d, const double* k2_dev,
+                   void* workspace_dev, size_t workspace_bytes,
+                   void* cuda_stream, hz_solver** out);
+
+/* Solves A x = b for nrhs right-hand sides (nrhs <= nrhs_max) by flexible
+ * GMRES right-preconditioned with A-DEF1 (eq. ADEF1), stopping each RHS when
+ * its least-squares residual falls below tol * ||b|| (Sec. 6.3).  b_dev,
+ * x_dev: device complex128 [nrhs][ny][nx].  If use_x0 is nonzero x_dev holds
+ * the initial guess, otherwise it is ignored.  info_host: array of nrhs
+ * records, or NULL.  Returns HZ_OK when every RHS converged, else the first
+ * failing status. */
+hz_status hz_solve(hz_solver* s, const void* b_dev, void* x_dev, int nrhs,
+                   double tol, int use_x0, hz_solve_info* info_host);
+
+/* hz_solve with host buffers: copies b_host to the device, solves, copies
+ * the solution back to x_host, all on the solver's stream. */
+hz_status hz_solve_host(hz_solver* s, const void* b_host, void* x_host,
+                        int nrhs, double tol, hz_solve_info* info_host);
+
+/* Applies one operator of the method (see hz_op) to nrhs vectors.  x_dev and
+ * y_dev are device complex128 full grids of the levels the operator maps
+ * between.  Operators of the preconditioner run in the solver's precision
+ * (inputs rounded, outputs widened under HZ_PREC_MIXED_FP32). */
+hz_status hz_apply(hz_solver* s, hz_op op, int level, const void* x_dev,
+                   void* y_dev, int nrhs);
+
+/* Iteration counts of the most recent inner coarse solve, one per RHS. */
+hz_status hz_last_inner_iters(hz_solver* s, int* iters_host, int nrhs);
+
+/* Number of levels (finest = 0) and the node counts of level l. */
+int hz_num_levels(const hz_solver* s);
+hz_status hz_level_shape(const hz_solver* s, int level, int* nx, int* ny);
+
+/* Adjoint gradient of J(m) = 1/2 sum_s ||S u_s - d_s||^2 with respect to the
+ * squared slowness m, k^2 = omega^2 m (k^2 is the array given to hz_setup).
+ * S samples u at the nrec flat node indices rec_idx_dev (device int32).
+ * src_dev: device complex128 [nshots][ny][nx]; d_obs_dev: device complex128
+ * [nshots][nrec].  Shots are processed in batches of nrhs_max: forward
+ * solve, adjoint solve A x = conj(D^-1 S^T (S u - d)) with the same solver
+ * (D A is symmetric, so A^H = D conj(A) D^-1), lam = D conj(x), then
+ * grad_dev[n] = -sum_s Re(conj(lam_s,n) dA_nn/dm_n u_s,n).  grad_dev:
+ * device FP64 [ny][nx], overwritten.  *J_host receives J.  info_host: 2 *
+ * nshots records (forward then adjoint per shot) or NULL. */
+hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev,
+                      int nshots, const int* rec_idx_dev, int nrec,
+                      const void* d_obs_dev, double tol, double* J_host,
+                      double* grad_dev, hz_solve_info* info_host);
+
+/* Releases the host handle (the workspace stays the caller's). */
+hz_status hz_destroy(hz_solver* s);
+
+/* Kernels launched by this library since it was loaded (all solvers). */
+long long hz_kernel_launches(void);
+
+const char* hz_status_str(hz_status st);
+const char* hz_last_error(const hz_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HZ_H_ */

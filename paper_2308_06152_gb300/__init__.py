@@ -7,17 +7,13 @@ thin ctypes binding over it plus the seeded input generators in
 call into ``Solver`` does, and raises if it is missing.
 """
 
-__all__ = ["Solver", "Desc", "HzError", "load_library", "workloads"]
+__all__ = ["Solver", "Desc", "HzError", "load_library"]
 
 
 def __getattr__(name):
+    import importlib
     if name in ("Solver", "Desc", "HzError"):
-        from . import api
-        return getattr(api, name)
+        return getattr(importlib.import_module(__name__ + ".api"), name)
     if name == "load_library":
-        from ._lib import load_library
-        return load_library
-    if name == "workloads":
-        from . import workloads
-        return workloads
+        return importlib.import_module(__name__ + "._lib").load_library
     raise AttributeError(name)

@@ -1,0 +1,284 @@
+// Internal types and device helpers shared by the CUDA translation units of
+// libhz.so.  Complex numbers are double2 / float2 (x = real, y = imag).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+namespace hz {
+
+// Number of kernels this library has launched (all launchers count).
+inline std::atomic<long long>& launch_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+#define HZ_COUNT() (::hz::launch_counter().fetch_add(1, std::memory_order_relaxed))
+
+enum { BC_DIRICHLET = 0, BC_SOMMERFELD = 1 };
+enum { ZK_NONE = 0, ZK_BILINEAR = 1, ZK_HO = 2 };
+enum { EK_GALERKIN = 0, EK_RED_O2 = 1, EK_RED_GLK1 = 2, EK_RED_GLK2 = 3 };
+
+template <class T> struct CT;
+template <> struct CT<double> { typedef double2 t; };
+template <> struct CT<float> { typedef float2 t; };
+template <class T> using C = typename CT<T>::t;
+
+__host__ __device__ __forceinline__ double2 mkc(double r, double i) {
+  return make_double2(r, i);
+}
+__host__ __device__ __forceinline__ float2 mkc(float r, float i) {
+  return make_float2(r, i);
+}
+template <class T> __host__ __device__ __forceinline__ C<T> czero() {
+  return mkc(T(0), T(0));
+}
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) {
+  return make_double2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+  return make_float2(a.x + b.x, a.y + b.y);
+}
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) {
+  return make_double2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+  return make_float2(a.x - b.x, a.y - b.y);
+}
+__device__ __forceinline__ double2 operator*(double s, double2 a) {
+  return make_double2(s * a.x, s * a.y);
+}
+__device__ __forceinline__ float2 operator*(float s, float2 a) {
+  return make_float2(s * a.x, s * a.y);
+}
+// complex product
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// acc + a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, acc.x)),
+                      fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 acc) {
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, acc.x)),
+                     fmaf(a.x, b.y, fmaf(a.y, b.x, acc.y)));
+}
+// acc + s * a (s real)
+__device__ __forceinline__ double2 rfma(double s, double2 a, double2 acc) {
+  return make_double2(fma(s, a.x, acc.x), fma(s, a.y, acc.y));
+}
+__device__ __forceinline__ float2 rfma(float s, float2 a, float2 acc) {
+  return make_float2(fmaf(s, a.x, acc.x), fmaf(s, a.y, acc.y));
+}
+
+// Level descriptor passed by value to kernels.
+struct LevelDev {
+  int nx, ny;
+  double h;
+  double ih2d, tihd;      // 1/h^2 and 2/h
+  float ih2f, tihf;
+  const double* k2d;      // k^2, FP64
+  const float* k2f;       // k^2, FP32 (mixed precision only)
+  const double2* dinv_d;  // omega / diag(M), FP64 precision path
+  const float2* dinv_f;   // omega / diag(M), FP32 precision path
+};
+
+template <class T> __device__ __forceinline__ const T* k2_of(const LevelDev& L);
+template <> __device__ __forceinline__ const double* k2_of<double>(const LevelDev& L) {
+  return L.k2d;
+}
+template <> __device__ __forceinline__ const float* k2_of<float>(const LevelDev& L) {
+  return L.k2f;
+}
+template <class T> __device__ __forceinline__ T ih2_of(const LevelDev& L);
+template <> __device__ __forceinline__ double ih2_of<double>(const LevelDev& L) {
+  return L.ih2d;
+}
+template <> __device__ __forceinline__ float ih2_of<float>(const LevelDev& L) {
+  return L.ih2f;
+}
+template <class T> __device__ __forceinline__ T tih_of(const LevelDev& L);
+template <> __device__ __forceinline__ double tih_of<double>(const LevelDev& L) {
+  return L.tihd;
+}
+template <> __device__ __forceinline__ float tih_of<float>(const LevelDev& L) {
+  return L.tihf;
+}
+template <class T> __device__ __forceinline__ const C<T>* dinv_of(const LevelDev& L);
+template <> __device__ __forceinline__ const double2* dinv_of<double>(const LevelDev& L) {
+  return L.dinv_d;
+}
+template <> __device__ __forceinline__ const float2* dinv_of<float>(const LevelDev& L) {
+  return L.dinv_f;
+}
+
+// A vector argument whose base may be indexed by a device-side counter:
+// the vector used is base + (*jidx + jofs) * jstride (jidx may be null).
+// Lets one launch configuration serve every iteration of a Krylov loop.
+template <class T> struct VRef {
+  C<T>* base;
+  const int* jidx;
+  int jofs;
+  long long jstride;
+  __device__ __forceinline__ C<T>* get() const {
+    return jidx ? base + (long long)(*jidx + jofs) * jstride : base;
+  }
+};
+template <class T> inline VRef<T> vref(const void* p) {
+  VRef<T> r;
+  r.base = (C<T>*)p;
+  r.jidx = nullptr;
+  r.jofs = 0;
+  r.jstride = 0;
+  return r;
+}
+template <class T>
+inline VRef<T> vref_j(const void* p, const int* jidx, int jofs, long long stride) {
+  VRef<T> r;
+  r.base = (C<T>*)p;
+  r.jidx = jidx;
+  r.jofs = jofs;
+  r.jstride = stride;
+  return r;
+}
+
+// ---------------------------------------------------------------------
+// launchers (defined in hz_stencil.cu / hz_krylov.cu, instantiated for
+// float and double)
+// ---------------------------------------------------------------------
+struct Shift {
+  double re, im;
+};
+
+// y = op(x) or y = b - op(x), op = -Lap_h - shift k^2 (+ Sommerfeld rows)
+template <class T>
+void launch_helm(const LevelDev& L, int bc, Shift s, VRef<T> x, VRef<T> b,
+                 C<T>* y, int nrhs, const int* done, cudaStream_t st);
+// x = dinv .* f
+template <class T>
+void launch_jacobi0(const LevelDev& L, int bc, VRef<T> f, C<T>* x, int nrhs,
+                    const int* done, cudaStream_t st);
+// fc = R_fw (f - M x)
+template <class T>
+void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc,
+                           Shift s, VRef<T> f, const C<T>* x, C<T>* fc,
+                           int nrhs, const int* done, cudaStream_t st);
+// x += P_bilinear xc
+template <class T>
+void launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, int bc,
+                        const C<T>* xc, C<T>* x, int nrhs, const int* done,
+                        cudaStream_t st);
+// xo = x + dinv .* (f - M x)  (+ addv if non-null)
+template <class T>
+void launch_smooth(const LevelDev& L, int bc, Shift s, VRef<T> f,
+                   const C<T>* x, C<T>* xo, int nrhs, const int* done,
+                   cudaStream_t st);
+// coarse = R_Z fine  (zk = bilinear: full weighting; ho: 5x5 / 256)
+template <class T>
+void launch_restrict_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
+                       VRef<T> fine, C<T>* coarse, int nrhs, const int* done,
+                       cudaStream_t st);
+// fine = Z coarse (or fine += Z coarse when add != 0)
+template <class T>
+void launch_prolong_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
+                      const C<T>* coarse, C<T>* fine, int add, int nrhs,
+                      const int* done, cudaStream_t st);
+// y = E_glk x on level 1 (variant 1 or 2)
+template <class T>
+void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
+                int nrhs, const int* done, cudaStream_t st);
+// zero the Dirichlet boundary nodes of nrhs vectors in place (no-op for
+// Sommerfeld grids)
+template <class T>
+void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
+                           cudaStream_t st);
+// x = Minv f on the coarsest level (dense)
+template <class T>
+void launch_dense_mv(int n, const C<T>* minv, VRef<T> f, C<T>* x, int nrhs,
+                     const int* done, cudaStream_t st);
+// out = a + b (b may be null), with conversion of the precision
+template <class Ti, class To>
+void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
+                     int nrhs, const int* done, cudaStream_t st);
+// setup helpers
+void launch_inject(const LevelDev& Lf, const LevelDev& Lc, double* k2c,
+                   cudaStream_t st);
+void launch_cast_k2(const double* k2d, float* k2f, long long n, cudaStream_t st);
+void launch_dinv(const LevelDev& L, int bc, Shift s, double omega, double2* dd,
+                 float2* df, cudaStream_t st);
+void launch_dense_assemble(const LevelDev& L, int bc, Shift s, double2* aug,
+                           cudaStream_t st);
+void launch_gauss_jordan(int n, double2* aug, int* err, cudaStream_t st);
+// inverse = right half of [I | M^-1]; rows and columns of Dirichlet
+// boundary nodes are zeroed (those nodes are not unknowns)
+void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
+                            double2* md, float2* mf, cudaStream_t st);
+
+// Krylov kernels (basis precision T, scalars FP64)
+struct KState {
+  // per-RHS arrays of length nrhs_max unless noted
+  int* jctr;        // [1] current Arnoldi column
+  int* done;        // 1 once the RHS stopped iterating
+  int* iters;       // iterations taken
+  int* stat;        // hz_status per RHS
+  int* alldone;     // [1]
+  double* bnorm;    // ||b|| (stopping reference)
+  double* beta;     // ||r0||
+  double* hnorm;    // ||w|| of the current column
+  double2* H;       // [nrhs_max][m+1][m] column j at H[(b*(m+1)+i)*m + j]
+  double2* g;       // [nrhs_max][m+1]
+  double* cs;       // [nrhs_max][m]
+  double2* sn;      // [nrhs_max][m]
+  double2* y;       // [nrhs_max][m]
+  double2* hcol;    // [nrhs_max][m+1] scratch column (one CGS pass)
+  double2* part;    // partial sums [nrhs_max][m+1][nblk_max]
+  double* npart;    // partial squared norms [nrhs_max][nblk_max]
+  int m;            // basis size (max iterations)
+  int nblk_max;
+};
+
+int krylov_nblk(long long n);
+template <class T>
+void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
+                 int nrhs, const KState& ks, cudaStream_t st);
+void launch_reduce_cols(const KState& ks, long long n, int nrhs, int accumulate,
+                        cudaStream_t st);
+template <class T>
+void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
+                  int nrhs, const KState& ks, cudaStream_t st);
+template <class T>
+void launch_norm2_part(VRef<T> w, long long n, int nrhs, const KState& ks,
+                       const int* done, cudaStream_t st);
+void launch_reduce_norm(const KState& ks, long long n, int nrhs, double* out,
+                        int sqrt_it, cudaStream_t st);
+void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
+                        const double* bnorm_src, double tol, cudaStream_t st);
+template <class T>
+void launch_scale_into(VRef<T> w, VRef<T> out, const double* scale_inv, long long n,
+                       int nrhs, const int* done, int use_inverse, cudaStream_t st);
+void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
+                   cudaStream_t st);
+void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st);
+template <class Tv, class Tx>
+void launch_update(const C<Tv>* V, long long vstride, const KState& ks,
+                   C<Tx>* x, int accumulate, long long n, int nrhs,
+                   cudaStream_t st);
+void launch_fill_int(int* p, int v, int count, cudaStream_t st);
+// total[r] += iters[r], maxv[r] = max(maxv[r], iters[r]) for RHS not masked
+void launch_accum_iters(const int* iters, int* total, int* maxv, int nrhs,
+                        const int* mask, cudaStream_t st);
+// gradient: adjoint source conj(D^-1 S^T (S u - d)) and misfit J
+void launch_adjoint_source(int nx, int ny, int bc, const double2* u,
+                           const int* rec, int nrec, const double2* d,
+                           double2* adj, double* J, int nrhs, cudaStream_t st);
+// grad[n] += -sum_r Re(D_n x_r[n] dA_nn/dm_n u_r[n])
+void launch_image(const LevelDev& L, int bc, double omega, const double2* u,
+                  const double2* x, double* grad, int nrhs, cudaStream_t st);
+void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st);
+
+}  // namespace hz

@@ -1,0 +1,506 @@
+// Batched Krylov kernels for GMRES / flexible GMRES (Sec. 3.3, Algorithm 1):
+// multi-vector dot products against the Arnoldi basis (one read of w, one
+// read of each basis vector), deterministic two-pass reductions, multi-axpy,
+// norms, Givens updates of the Hessenberg columns and the triangular solve.
+// Each right-hand side owns its basis, Hessenberg matrix and stopping state;
+// all of them live in device memory so that no launch depends on host data.
+#include "hz_common.cuh"
+
+namespace hz {
+
+namespace {
+
+constexpr int NT = 256;   // threads per block
+constexpr int EPT = 4;    // elements per thread
+constexpr int CHUNK = NT * EPT;
+
+template <class T> __device__ __forceinline__ C<T> cvt_to(double2 v);
+template <> __device__ __forceinline__ double2 cvt_to<double>(double2 v) { return v; }
+template <> __device__ __forceinline__ float2 cvt_to<float>(double2 v) {
+  return make_float2((float)v.x, (float)v.y);
+}
+__device__ __forceinline__ double2 wide(double2 v) { return v; }
+__device__ __forceinline__ double2 wide(float2 v) { return make_double2(v.x, v.y); }
+
+__device__ __forceinline__ double2 shfl_down2(double2 v, int o) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, o);
+  return v;
+}
+__device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
+  v.x = __shfl_down_sync(0xffffffffu, v.x, o);
+  v.y = __shfl_down_sync(0xffffffffu, v.y, o);
+  return v;
+}
+
+// part[r][i][blk] = sum_{e in blk} conj(V_i[e]) * w[e],  i = 0..j
+template <class T>
+__global__ void __launch_bounds__(NT)
+k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w,
+       long long n, KState ks) {
+  constexpr int G = 4;
+  __shared__ double2 red[NT / 32][G];
+  const int r = blockIdx.y, blk = blockIdx.x;
+  if (ks.done[r]) return;
+  const int j = *ks.jctr;
+  const long long base = (long long)blk * CHUNK + threadIdx.x;
+  const C<T>* wr = w + r * n;
+  C<T> wv[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const long long e = base + k * NT;
+    wv[k] = (e < n) ? wr[e] : czero<T>();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int i0 = 0; i0 <= j; i0 += G) {
+    C<T> d[G];
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      d[q] = czero<T>();
+      const int i = i0 + q;
+      if (i <= j) {
+        const C<T>* vr = V + (long long)i * vstride + r * n;
+#pragma unroll
+        for (int k = 0; k < EPT; ++k) {
+          const long long e = base + k * NT;
+          if (e < n) {
+            const C<T> v = vr[e];
+            d[q].x += v.x * wv[k].x + v.y * wv[k].y;
+            d[q].y += v.x * wv[k].y - v.y * wv[k].x;
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const C<T> t = shfl_down2(d[q], o);
+        d[q].x += t.x;
+        d[q].y += t.y;
+      }
+    }
+    if (lane == 0) {
+#pragma unroll
+      for (int q = 0; q < G; ++q) red[warp][q] = wide(d[q]);
+    }
+    __syncthreads();
+    if (threadIdx.x < G && i0 + threadIdx.x <= j) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int q = 0; q < NT / 32; ++q) {
+        s.x += red[q][threadIdx.x].x;
+        s.y += red[q][threadIdx.x].y;
+      }
+      ks.part[((long long)r * (ks.m + 1) + i0 + threadIdx.x) * ks.nblk_max + blk] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] (+)= hcol[r][i]
+__global__ void k_reduce_cols(KState ks, int nblk, int accumulate) {
+  const int r = blockIdx.y;
+  if (ks.done[r]) return;
+  const int j = *ks.jctr;
+  const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i > j) return;
+  const double2* p = ks.part + ((long long)r * (ks.m + 1) + i) * ks.nblk_max;
+  double2 s = make_double2(0.0, 0.0);
+  for (int b = lane; b < nblk; b += 32) {
+    s.x += p[b].x;
+    s.y += p[b].y;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double2 t = shfl_down2(s, o);
+    s.x += t.x;
+    s.y += t.y;
+  }
+  if (lane == 0) {
+    ks.hcol[(long long)r * (ks.m + 1) + i] = s;
+    double2* hp = ks.H + ((long long)r * (ks.m + 1) + i) * ks.m + j;
+    if (accumulate) {
+      double2 t = *hp;
+      t.x += s.x;
+      t.y += s.y;
+      *hp = t;
+    } else {
+      *hp = s;
+    }
+  }
+}
+
+// w -= sum_{i<=j} V_i hcol_i
+template <class T>
+__global__ void __launch_bounds__(NT)
+k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
+        long long n, KState ks) {
+  constexpr int TILE = 512;
+  __shared__ C<T> hs[TILE];
+  const int r = blockIdx.y;
+  if (ks.done[r]) return;
+  const int j = *ks.jctr;
+  const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
+  C<T>* wr = w + r * n;
+  C<T> acc[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const long long e = base + k * NT;
+    acc[k] = (e < n) ? wr[e] : czero<T>();
+  }
+  for (int t0 = 0; t0 <= j; t0 += TILE) {
+    const int cnt = min(TILE, j + 1 - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += NT)
+      hs[q] = cvt_to<T>(ks.hcol[(long long)r * (ks.m + 1) + t0 + q]);
+    __syncthreads();
+    for (int q = 0; q < cnt; ++q) {
+      const C<T>* vr = V + (long long)(t0 + q) * vstride + r * n;
+      const C<T> h = hs[q];
+#pragma unroll
+      for (int k = 0; k < EPT; ++k) {
+        const long long e = base + k * NT;
+        if (e < n) {
+          const C<T> v = vr[e];
+          acc[k].x -= v.x * h.x - v.y * h.y;
+          acc[k].y -= v.x * h.y + v.y * h.x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const long long e = base + k * NT;
+    if (e < n) wr[e] = acc[k];
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(NT)
+k_norm2_part(VRef<T> w, long long n, KState ks, const int* __restrict__ done) {
+  __shared__ double red[NT / 32];
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
+  const C<T>* wr = w.get() + r * n;
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const long long e = base + k * NT;
+    if (e < n) {
+      const C<T> v = wr[e];
+      s += v.x * v.x + v.y * v.y;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < NT / 32; ++q) t += red[q];
+    ks.npart[(long long)r * ks.nblk_max + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_reduce_norm(KState ks, int nblk, double* out, int sqrt_it) {
+  __shared__ double red[32];
+  const int r = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x)
+    s += ks.npart[(long long)r * ks.nblk_max + b];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+    out[r] = sqrt_it ? sqrt(t) : t;
+  }
+}
+
+// status codes mirrored from hz.h
+enum { ST_OK = 0, ST_NOT_CONVERGED = 4, ST_BREAKDOWN = 5, ST_NAN = 6 };
+
+__global__ void k_krylov_init(KState ks, int nrhs, const int* done_in,
+                              const double* bnorm_src, double tol) {
+  const int r = threadIdx.x;
+  int d = 1;
+  if (r < nrhs) {
+    d = done_in ? done_in[r] : 0;
+    const double b = ks.beta[r];
+    const double bn = bnorm_src ? bnorm_src[r] : b;
+    ks.bnorm[r] = bn;
+    ks.iters[r] = 0;
+    ks.stat[r] = ST_OK;
+    ks.g[(long long)r * (ks.m + 1)] = make_double2(b, 0.0);
+    ks.hnorm[r] = b;
+    if (!d) {
+      if (!isfinite(b)) {
+        d = 1;
+        ks.stat[r] = ST_NAN;
+      } else if (b == 0.0 || b <= tol * bn) {
+        d = 1;
+      }
+    }
+    ks.done[r] = d;
+  }
+  const int all = __syncthreads_and(d);
+  if (r == 0) {
+    *ks.jctr = 0;
+    *ks.alldone = all;
+  }
+}
+
+template <class T>
+__global__ void k_scale_into(VRef<T> w, VRef<T> out, const double* __restrict__ s,
+                             long long n, const int* __restrict__ done) {
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  const double sv = s[r];
+  const T f = (sv != 0.0) ? T(1.0 / sv) : T(0);
+  const C<T>* wr = w.get() + r * n;
+  C<T>* orow = out.get() + r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    orow[e] = f * wr[e];
+}
+
+// Apply the previous rotations to column j, build the rotation that
+// annihilates h_{j+1,j}, update the least-squares right-hand side g and
+// decide convergence (|g_{j+1}| <= tol ||b||), breakdown, NaN or the cap.
+__global__ void k_givens(KState ks, int nrhs, double tol, int maxit) {
+  const int r = threadIdx.x;
+  const int j = *ks.jctr;
+  int d = 1;
+  if (r < nrhs) {
+    d = ks.done[r];
+    if (!d) {
+      const int m = ks.m;
+      double2* Hc = ks.H + (long long)r * (m + 1) * m + j;   // H[r][i][j] = Hc[i*m]
+      double* cs = ks.cs + (long long)r * m;
+      double2* sn = ks.sn + (long long)r * m;
+      double2* g = ks.g + (long long)r * (m + 1);
+      for (int i = 0; i < j; ++i) {
+        const double2 a = Hc[(long long)i * m], b = Hc[(long long)(i + 1) * m];
+        const double c = cs[i];
+        const double2 s = sn[i];
+        // t = c a + s b ; b' = -conj(s) a + c b
+        const double2 t = make_double2(c * a.x + (s.x * b.x - s.y * b.y),
+                                       c * a.y + (s.x * b.y + s.y * b.x));
+        const double2 bb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x,
+                                        -(s.x * a.y - s.y * a.x) + c * b.y);
+        Hc[(long long)i * m] = t;
+        Hc[(long long)(i + 1) * m] = bb;
+      }
+      const double2 a = Hc[(long long)j * m];
+      const double hb = ks.hnorm[r];
+      const double am = sqrt(a.x * a.x + a.y * a.y);
+      double c;
+      double2 s;
+      if (hb == 0.0) {
+        c = 1.0;
+        s = make_double2(0.0, 0.0);
+      } else if (am == 0.0) {
+        c = 0.0;
+        s = make_double2(1.0, 0.0);
+      } else {
+        const double t = sqrt(am * am + hb * hb);
+        c = am / t;
+        s = make_double2(a.x / am * hb / t, a.y / am * hb / t);
+      }
+      cs[j] = c;
+      sn[j] = s;
+      Hc[(long long)j * m] = make_double2(c * a.x + s.x * hb, c * a.y + s.y * hb);
+      Hc[(long long)(j + 1) * m] = make_double2(0.0, 0.0);
+      const double2 gj = g[j];
+      g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
+      g[j] = make_double2(c * gj.x, c * gj.y);
+      const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+      ks.iters[r] = j + 1;
+      if (!isfinite(res) || !isfinite(hb)) {
+        d = 1;
+        ks.stat[r] = ST_NAN;
+      } else if (res <= tol * ks.bnorm[r]) {
+        d = 1;
+      } else if (hb == 0.0) {
+        d = 1;
+        ks.stat[r] = ST_BREAKDOWN;
+      } else if (j + 1 >= maxit) {
+        d = 1;
+        ks.stat[r] = ST_NOT_CONVERGED;
+      }
+      ks.done[r] = d;
+    }
+  }
+  const int all = __syncthreads_and(d);
+  if (r == 0) {
+    *ks.alldone = all;
+    if (!all) *ks.jctr = j + 1;
+  }
+}
+
+__global__ void k_trisolve(KState ks, int nrhs) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrhs) return;
+  const int m = ks.m, k = ks.iters[r];
+  const double2* H = ks.H + (long long)r * (m + 1) * m;
+  const double2* g = ks.g + (long long)r * (m + 1);
+  double2* y = ks.y + (long long)r * m;
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = g[i];
+    for (int c = i + 1; c < k; ++c) {
+      const double2 h = H[(long long)i * m + c], yc = y[c];
+      s.x -= h.x * yc.x - h.y * yc.y;
+      s.y -= h.x * yc.y + h.y * yc.x;
+    }
+    const double2 d = H[(long long)i * m + i];
+    const double dm = d.x * d.x + d.y * d.y;
+    y[i] = (dm > 0.0) ? make_double2((s.x * d.x + s.y * d.y) / dm,
+                                     (s.y * d.x - s.x * d.y) / dm)
+                      : make_double2(0.0, 0.0);
+  }
+}
+
+// x (+)= sum_{i < iters} y_i V_i
+template <class Tv, class Tx>
+__global__ void __launch_bounds__(NT)
+k_update(const C<Tv>* __restrict__ V, long long vstride, KState ks,
+         C<Tx>* __restrict__ x, int accumulate, long long n) {
+  constexpr int TILE = 512;
+  __shared__ C<Tx> ys[TILE];
+  const int r = blockIdx.y;
+  const int k = ks.iters[r];
+  if (accumulate && k == 0) return;
+  const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
+  C<Tx>* xr = x + r * n;
+  C<Tx> acc[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const long long e = base + q * NT;
+    acc[q] = (accumulate && e < n) ? xr[e] : czero<Tx>();
+  }
+  for (int t0 = 0; t0 < k; t0 += TILE) {
+    const int cnt = min(TILE, k - t0);
+    __syncthreads();
+    for (int q = threadIdx.x; q < cnt; q += NT)
+      ys[q] = cvt_to<Tx>(ks.y[(long long)r * ks.m + t0 + q]);
+    __syncthreads();
+    for (int i = 0; i < cnt; ++i) {
+      const C<Tv>* vr = V + (long long)(t0 + i) * vstride + r * n;
+      const C<Tx> yi = ys[i];
+#pragma unroll
+      for (int q = 0; q < EPT; ++q) {
+        const long long e = base + q * NT;
+        if (e < n) {
+          const C<Tv> v = vr[e];
+          acc[q].x += (Tx)v.x * yi.x - (Tx)v.y * yi.y;
+          acc[q].y += (Tx)v.x * yi.y + (Tx)v.y * yi.x;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    const long long e = base + q * NT;
+    if (e < n) xr[e] = acc[q];
+  }
+}
+
+__global__ void k_fill_int(int* p, int v, int count) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) p[e] = v;
+}
+__global__ void k_copy_int(const int* s, int* d, int count) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) d[e] = s[e];
+}
+
+}  // namespace
+
+int krylov_nblk(long long n) { return (int)((n + CHUNK - 1) / CHUNK); }
+
+template <class T>
+void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
+                 int nrhs, const KState& ks, cudaStream_t st) {
+  HZ_COUNT();
+  k_mdot<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks);
+}
+void launch_reduce_cols(const KState& ks, long long n, int nrhs, int accumulate,
+                        cudaStream_t st) {
+  HZ_COUNT();
+  const int wpb = NT / 32;
+  k_reduce_cols<<<dim3((ks.m + 1 + wpb - 1) / wpb, nrhs), NT, 0, st>>>(
+      ks, krylov_nblk(n), accumulate);
+}
+template <class T>
+void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
+                  int nrhs, const KState& ks, cudaStream_t st) {
+  HZ_COUNT();
+  k_maxpy<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks);
+}
+template <class T>
+void launch_norm2_part(VRef<T> w, long long n, int nrhs, const KState& ks,
+                       const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_norm2_part<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(w, n, ks, done);
+}
+void launch_reduce_norm(const KState& ks, long long n, int nrhs, double* out,
+                        int sqrt_it, cudaStream_t st) {
+  HZ_COUNT();
+  k_reduce_norm<<<nrhs, NT, 0, st>>>(ks, krylov_nblk(n), out, sqrt_it);
+}
+void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
+                        const double* bnorm_src, double tol, cudaStream_t st) {
+  HZ_COUNT();
+  k_krylov_init<<<1, 1024, 0, st>>>(ks, nrhs, done_in, bnorm_src, tol);
+}
+template <class T>
+void launch_scale_into(VRef<T> w, VRef<T> out, const double* s, long long n,
+                       int nrhs, const int* done, int use_inverse,
+                       cudaStream_t st) {
+  HZ_COUNT();
+  (void)use_inverse;
+  long long nb = (n + 255) / 256;
+  if (nb > 2048) nb = 2048;
+  k_scale_into<T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, s, n, done);
+}
+void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
+                   cudaStream_t st) {
+  HZ_COUNT();
+  k_givens<<<1, 1024, 0, st>>>(ks, nrhs, tol, maxit);
+}
+void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st) {
+  HZ_COUNT();
+  k_trisolve<<<(nrhs + 63) / 64, 64, 0, st>>>(ks, nrhs);
+}
+template <class Tv, class Tx>
+void launch_update(const C<Tv>* V, long long vstride, const KState& ks,
+                   C<Tx>* x, int accumulate, long long n, int nrhs,
+                   cudaStream_t st) {
+  HZ_COUNT();
+  k_update<Tv, Tx><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, ks, x,
+                                                              accumulate, n);
+}
+void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
+  HZ_COUNT();
+  k_fill_int<<<(count + 255) / 256, 256, 0, st>>>(p, v, count);
+}
+void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
+  HZ_COUNT();
+  k_copy_int<<<(count + 255) / 256, 256, 0, st>>>(src, dst, count);
+}
+
+#define HZ_KINST(T)                                                            \
+  template void launch_mdot<T>(const C<T>*, long long, const C<T>*, long long, \
+                               int, const KState&, cudaStream_t);              \
+  template void launch_maxpy<T>(const C<T>*, long long, C<T>*, long long, int, \
+                                const KState&, cudaStream_t);                  \
+  template void launch_norm2_part<T>(VRef<T>, long long, int, const KState&,   \
+                                     const int*, cudaStream_t);                \
+  template void launch_scale_into<T>(VRef<T>, VRef<T>, const double*,          \
+                                     long long, int, const int*, int,          \
+                                     cudaStream_t);                            \
+  template void launch_update<T, T>(const C<T>*, long long, const KState&,     \
+                                    C<T>*, int, long long, int, cudaStream_t);
+
+HZ_KINST(double)
+HZ_KINST(float)
+
+}  // namespace hz

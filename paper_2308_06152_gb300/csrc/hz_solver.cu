@@ -1,0 +1,861 @@
+// Host orchestration of the method and the C ABI of include/hz.h.
+//
+// The host only sequences kernel launches on the caller's stream and reads
+// a few convergence flags; every arithmetic step runs in the kernels of
+// hz_stencil.cu, hz_krylov.cu and hz_gradient.cu.  All device storage is
+// carved out of the caller's workspace; the library never allocates device
+// memory.
+//
+// Method (arXiv 2308.06152):
+//   outer   flexible GMRES on A x = b, right-preconditioned (Sec. 6.3)
+//   precond P_A-DEF1 v = M^-1 (v - A Q v) + Q v (Sec. 3.2.2, eq. ADEF1),
+//           Q v = Z E^-1 R v with R = Z^T / 4 (Sec. 5.2, eqs. matvec-*)
+//   E^-1    GMRES on E v2 = v1, right-preconditioned by a V-cycle on the
+//           coarse CSLP (Sec. 5.2, Sec. 6)
+//   M^-1    one V-cycle: damped Jacobi (w = 0.8) pre/post sweep, full
+//           weighting, bilinear interpolation, re-discretised coarse CSLP,
+//           direct coarsest solve (Sec. 3.1, 4, 5.1)
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "hz.h"
+#include "hz_common.cuh"
+
+using namespace hz;
+
+namespace {
+
+constexpr int kMaxLevels = 24;
+constexpr int kMaxCoarsest = 1024;
+constexpr int kMaxRhs = 1024;
+
+struct LevelHost {
+  int nx = 0, ny = 0;
+  long long n = 0;
+  double h = 0;
+  double* k2d = nullptr;
+  float* k2f = nullptr;
+  double2* dinv_d = nullptr;
+  float2* dinv_f = nullptr;
+  void* f = nullptr;   // level right-hand side (levels >= 1)
+  void* x = nullptr;   // level solution (levels >= 1)
+  void* xa = nullptr;  // pre-smoothed iterate (all levels)
+  LevelDev dev() const {
+    LevelDev d;
+    d.nx = nx;
+    d.ny = ny;
+    d.h = h;
+    d.ih2d = 1.0 / (h * h);
+    d.tihd = 2.0 / h;
+    d.ih2f = (float)d.ih2d;
+    d.tihf = (float)d.tihd;
+    d.k2d = k2d;
+    d.k2f = k2f;
+    d.dinv_d = dinv_d;
+    d.dinv_f = dinv_f;
+    return d;
+  }
+};
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0;
+  bool dry = true;
+  void* take(size_t bytes) {
+    off = (off + 255) & ~size_t(255);
+    void* p = dry ? nullptr : base + off;
+    off += bytes;
+    return p;
+  }
+};
+
+bool valid_desc(const hz_desc* d, std::string* why) {
+  if (!d) { *why = "null descriptor"; return false; }
+  if (d->nx < 3 || d->ny < 3) { *why = "grid needs at least 3 x 3 nodes"; return false; }
+  if (!(d->h > 0)) { *why = "h must be positive"; return false; }
+  if (d->bc != HZ_BC_DIRICHLET && d->bc != HZ_BC_SOMMERFELD) { *why = "bad bc"; return false; }
+  if (d->zkind < HZ_Z_NONE || d->zkind > HZ_Z_HO) { *why = "bad zkind"; return false; }
+  if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_GLK2) { *why = "bad ekind"; return false; }
+  if (d->prec != HZ_PREC_FP64 && d->prec != HZ_PREC_MIXED_FP32) { *why = "bad prec"; return false; }
+  if (d->nrhs_max < 1 || d->nrhs_max > kMaxRhs) { *why = "nrhs_max must be in 1..1024"; return false; }
+  if (d->outer_maxit < 1 || d->coarse_maxit < 1) { *why = "iteration caps must be >= 1"; return false; }
+  if (d->min_coarse_intervals < 1) { *why = "min_coarse_intervals must be >= 1"; return false; }
+  if (!(d->jacobi_omega > 0)) { *why = "jacobi_omega must be positive"; return false; }
+  return true;
+}
+
+std::vector<std::pair<int, int>> level_shapes(int nx, int ny, int min_ci) {
+  std::vector<std::pair<int, int>> s{{nx, ny}};
+  while ((int)s.size() < kMaxLevels) {
+    const int cx = s.back().first, cy = s.back().second;
+    if ((cx - 1) % 2 || (cy - 1) % 2) break;
+    const int ncx = (cx - 1) / 2 + 1, ncy = (cy - 1) / 2 + 1;
+    if (ncx - 1 < min_ci || ncy - 1 < min_ci) break;
+    s.push_back({ncx, ncy});
+  }
+  return s;
+}
+
+}  // namespace
+
+struct hz_solver {
+  hz_desc d{};
+  cudaStream_t st = nullptr;
+  int L = 0;
+  LevelHost lv[kMaxLevels];
+  bool mixed = false;
+  size_t esz = 16;       // bytes of one complex value of the preconditioner
+  int nL = 0;            // unknowns of the dense coarsest level
+  void* minv = nullptr;  // coarsest inverse, preconditioner precision
+  double2* aug = nullptr;
+  int* gj_err = nullptr;
+  // preconditioner scratch (preconditioner precision), fine level
+  void *fz1 = nullptr, *fz2 = nullptr, *t = nullptr, *yv = nullptr, *q = nullptr,
+       *vin = nullptr;
+  // coarse level (level 1)
+  void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
+  KState kin{}, kout{};
+  int* in_total = nullptr;
+  int* in_max = nullptr;
+  // outer FGMRES (FP64)
+  double2 *Vo = nullptr, *Zo = nullptr, *wo = nullptr;
+  double* bnorm_o = nullptr;
+  double* relres = nullptr;
+  // host-buffer solve and gradient storage
+  double2 *io0 = nullptr, *io1 = nullptr, *io2 = nullptr;
+  double* Jd = nullptr;
+  int check_every = 4;
+  std::string err;
+  size_t ws_bytes = 0;
+};
+
+namespace {
+
+void set_err(hz_solver* s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (s) s->err = buf;
+}
+
+hz_status cuda_check(hz_solver* s, const char* where) {
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_err(s, "%s: %s", where, cudaGetErrorString(e));
+    return HZ_CUDA_ERROR;
+  }
+  return HZ_OK;
+}
+
+KState plan_kstate(Arena& a, int B, int m, long long n) {
+  KState k{};
+  k.m = m;
+  k.nblk_max = krylov_nblk(n);
+  k.jctr = (int*)a.take(sizeof(int));
+  k.alldone = (int*)a.take(sizeof(int));
+  k.done = (int*)a.take(sizeof(int) * B);
+  k.iters = (int*)a.take(sizeof(int) * B);
+  k.stat = (int*)a.take(sizeof(int) * B);
+  k.bnorm = (double*)a.take(sizeof(double) * B);
+  k.beta = (double*)a.take(sizeof(double) * B);
+  k.hnorm = (double*)a.take(sizeof(double) * B);
+  k.H = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1) * m);
+  k.g = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1));
+  k.cs = (double*)a.take(sizeof(double) * (size_t)B * m);
+  k.sn = (double2*)a.take(sizeof(double2) * (size_t)B * m);
+  k.y = (double2*)a.take(sizeof(double2) * (size_t)B * m);
+  k.hcol = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1));
+  k.part = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1) * k.nblk_max);
+  k.npart = (double*)a.take(sizeof(double) * (size_t)B * k.nblk_max);
+  return k;
+}
+
+// Assigns every device buffer of the solver inside the arena.
+void plan(hz_solver* s, Arena& a) {
+  const hz_desc& d = s->d;
+  const int B = d.nrhs_max;
+  const size_t es = s->esz;
+  for (int l = 0; l <= s->L; ++l) {
+    LevelHost& v = s->lv[l];
+    v.k2d = (double*)a.take(sizeof(double) * v.n);
+    v.k2f = s->mixed ? (float*)a.take(sizeof(float) * v.n) : nullptr;
+    v.dinv_d = s->mixed ? nullptr : (double2*)a.take(sizeof(double2) * v.n);
+    v.dinv_f = s->mixed ? (float2*)a.take(sizeof(float2) * v.n) : nullptr;
+    v.xa = a.take(es * B * v.n);
+    if (l >= 1) {
+      v.f = a.take(es * B * v.n);
+      v.x = a.take(es * B * v.n);
+    }
+  }
+  s->minv = a.take(es * (size_t)s->nL * s->nL);
+  s->aug = (double2*)a.take(sizeof(double2) * (size_t)s->nL * 2 * s->nL);
+  s->gj_err = (int*)a.take(sizeof(int));
+  const long long n0 = s->lv[0].n;
+  s->t = a.take(es * B * n0);
+  s->yv = a.take(es * B * n0);
+  s->vin = s->mixed ? a.take(es * B * n0) : nullptr;
+  if (d.zkind != HZ_Z_NONE) {
+    const long long n1 = s->lv[1].n;
+    s->q = a.take(es * B * n0);
+    if (d.ekind == HZ_E_GALERKIN) {
+      s->fz1 = a.take(es * B * n0);
+      s->fz2 = a.take(es * B * n0);
+    }
+    s->v1 = a.take(es * B * n1);
+    s->v2 = a.take(es * B * n1);
+    s->sb = a.take(es * B * n1);
+    s->eb = a.take(es * B * n1);
+    s->Qb = a.take(es * (size_t)B * n1 * (d.coarse_maxit + 1));
+    s->kin = plan_kstate(a, B, d.coarse_maxit, n1);
+  }
+  s->in_total = (int*)a.take(sizeof(int) * B);
+  s->in_max = (int*)a.take(sizeof(int) * B);
+  s->Vo = (double2*)a.take(sizeof(double2) * (size_t)B * n0 * (d.outer_maxit + 1));
+  s->Zo = (double2*)a.take(sizeof(double2) * (size_t)B * n0 * d.outer_maxit);
+  s->wo = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
+  s->kout = plan_kstate(a, B, d.outer_maxit, n0);
+  s->bnorm_o = (double*)a.take(sizeof(double) * B);
+  s->relres = (double*)a.take(sizeof(double) * B);
+  s->io0 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
+  s->io1 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
+  s->io2 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
+  s->Jd = (double*)a.take(sizeof(double));
+}
+
+hz_status init_shapes(hz_solver* s) {
+  const hz_desc& d = s->d;
+  const auto sh = level_shapes(d.nx, d.ny, d.min_coarse_intervals);
+  s->L = (int)sh.size() - 1;
+  double h = d.h;
+  for (int l = 0; l <= s->L; ++l) {
+    s->lv[l].nx = sh[l].first;
+    s->lv[l].ny = sh[l].second;
+    s->lv[l].n = (long long)sh[l].first * sh[l].second;
+    s->lv[l].h = h;
+    h *= 2.0;
+  }
+  s->nL = (int)s->lv[s->L].n;
+  if (d.zkind != HZ_Z_NONE && s->L < 1) {
+    set_err(s, "deflation needs a grid that coarsens at least once "
+               "(nx-1, ny-1 even, coarse intervals >= %d)", d.min_coarse_intervals);
+    return HZ_INVALID_GRID;
+  }
+  if (s->nL > kMaxCoarsest) {
+    set_err(s, "coarsest level has %d nodes; the dense coarsest solve allows "
+               "at most %d (choose nx-1, ny-1 with more factors of 2)",
+            s->nL, kMaxCoarsest);
+    return HZ_INVALID_GRID;
+  }
+  s->mixed = d.prec == HZ_PREC_MIXED_FP32;
+  s->esz = s->mixed ? sizeof(float2) : sizeof(double2);
+  return HZ_OK;
+}
+
+// CSLP coefficient as printed in Sec. 5.1: ap = (4 - (beta1 - beta2 i) k^2 h^2)
+// / h^2, i.e. M = -Lap - (beta1 - i beta2) k^2 (with beta2 = -0.5 the shift
+// damps with the same sign as the Sommerfeld rows).
+inline Shift cslp(const hz_solver* s) { return Shift{s->d.beta1, -s->d.beta2}; }
+inline Shift helm1() { return Shift{1.0, 0.0}; }
+
+// FP64 view of level l (k2d present at every level)
+inline LevelDev dev64(const hz_solver* s, int l) { return s->lv[l].dev(); }
+
+// ------------------------------------------------------------ V-cycle
+template <class T>
+void vcycle(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs, const int* done) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const Shift sh = cslp(s);
+  if (l0 == s->L) {
+    launch_dense_mv<T>(s->nL, (const C<T>*)s->minv, f, xout, nrhs, done, st);
+    return;
+  }
+  VRef<T> fl = f;
+  for (int l = l0; l < s->L; ++l) {
+    const LevelHost& A = s->lv[l];
+    const LevelHost& Bc = s->lv[l + 1];
+    launch_jacobi0<T>(A.dev(), bc, fl, (C<T>*)A.xa, nrhs, done, st);
+    launch_resid_restrict<T>(A.dev(), Bc.dev(), bc, sh, fl, (const C<T>*)A.xa,
+                             (C<T>*)Bc.f, nrhs, done, st);
+    fl = vref<T>(Bc.f);
+  }
+  launch_dense_mv<T>(s->nL, (const C<T>*)s->minv, vref<T>(s->lv[s->L].f),
+                     (C<T>*)s->lv[s->L].x, nrhs, done, st);
+  for (int l = s->L - 1; l >= l0; --l) {
+    const LevelHost& A = s->lv[l];
+    const LevelHost& Bc = s->lv[l + 1];
+    launch_prolong_add<T>(A.dev(), Bc.dev(), bc, (const C<T>*)Bc.x, (C<T>*)A.xa,
+                          nrhs, done, st);
+    const VRef<T> fa = (l == l0) ? f : vref<T>(A.f);
+    C<T>* xo = (l == l0) ? xout : (C<T>*)A.x;
+    launch_smooth<T>(A.dev(), bc, sh, fa, (const C<T>*)A.xa, xo, nrhs, done, st);
+  }
+}
+
+// ------------------------------------------------------------ coarse E
+template <class T>
+void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const LevelHost& F = s->lv[0];
+  const LevelHost& Cc = s->lv[1];
+  switch (s->d.ekind) {
+    case HZ_E_GALERKIN:
+      launch_prolong_z<T>(F.dev(), Cc.dev(), bc, s->d.zkind, x, (C<T>*)s->fz1, 0,
+                          nrhs, done, st);
+      launch_helm<T>(F.dev(), bc, helm1(), vref<T>(s->fz1), vref<T>(nullptr),
+                     (C<T>*)s->fz2, nrhs, done, st);
+      launch_restrict_z<T>(F.dev(), Cc.dev(), bc, s->d.zkind, vref<T>(s->fz2), y,
+                           nrhs, done, st);
+      break;
+    case HZ_E_RED_O2:
+      launch_helm<T>(Cc.dev(), bc, helm1(), vref<T>(x), vref<T>(nullptr), y, nrhs,
+                     done, st);
+      break;
+    case HZ_E_RED_GLK1:
+      launch_glk<T>(Cc.dev(), bc, 1, x, y, nrhs, done, st);
+      break;
+    default:
+      launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st);
+      break;
+  }
+}
+
+hz_status read_flag(hz_solver* s, const int* dptr, int* out) {
+  if (cudaMemcpyAsync(out, dptr, sizeof(int), cudaMemcpyDeviceToHost, s->st) !=
+      cudaSuccess)
+    return cuda_check(s, "flag copy");
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "flag sync");
+  return HZ_OK;
+}
+
+// Opt-in trace (environment HZ_DEBUG=1): Arnoldi state of RHS 0 after a
+// Givens step, printed to stderr.  Synchronises the stream.
+void debug_trace(hz_solver* s, const KState& ks, const char* label) {
+  static const bool on = std::getenv("HZ_DEBUG") != nullptr;
+  if (!on) return;
+  cudaStreamSynchronize(s->st);
+  int j = 0, done = 0, it = 0;
+  double hn = 0, bn = 0;
+  cudaMemcpy(&j, ks.jctr, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&done, ks.done, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&it, ks.iters, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&hn, ks.hnorm, sizeof(double), cudaMemcpyDeviceToHost);
+  cudaMemcpy(&bn, ks.bnorm, sizeof(double), cudaMemcpyDeviceToHost);
+  const int jj = it > 0 ? it - 1 : 0;
+  std::vector<double2> col(jj + 2), g(jj + 2);
+  for (int i = 0; i <= jj + 1 && i <= ks.m; ++i)
+    cudaMemcpy(&col[i], ks.H + (long long)i * ks.m + jj, sizeof(double2),
+               cudaMemcpyDeviceToHost);
+  cudaMemcpy(g.data(), ks.g, sizeof(double2) * (jj + 2), cudaMemcpyDeviceToHost);
+  fprintf(stderr, "[hz %s] jctr=%d done=%d iters=%d hnorm=%.3e bnorm=%.3e "
+          "H[jj][jj]=(%.3e,%.3e) g[jj]=(%.3e,%.3e) g[jj+1]=(%.3e,%.3e) err=%s\n",
+          label, j, done, it, hn, bn, col[jj].x, col[jj].y, g[jj].x, g[jj].y,
+          g[jj + 1].x, g[jj + 1].y, cudaGetErrorString(cudaGetLastError()));
+}
+
+// Classical Gram-Schmidt with one re-orthogonalisation (CGS2) of w against
+// basis columns 0..j, then ||w|| into ks.hnorm.
+template <class T>
+void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
+          long long n, int nrhs) {
+  cudaStream_t st = s->st;
+  launch_mdot<T>(V, vs, w, n, nrhs, ks, st);
+  launch_reduce_cols(ks, n, nrhs, 0, st);
+  launch_maxpy<T>(V, vs, w, n, nrhs, ks, st);
+  launch_mdot<T>(V, vs, w, n, nrhs, ks, st);
+  launch_reduce_cols(ks, n, nrhs, 1, st);
+  launch_maxpy<T>(V, vs, w, n, nrhs, ks, st);
+  launch_norm2_part<T>(vref<T>(w), n, nrhs, ks, ks.done, st);
+  launch_reduce_norm(ks, n, nrhs, ks.hnorm, 1, st);
+}
+
+// ------------------------------------------------------------ inner solve
+// E v2 = v1 by right-preconditioned GMRES (V-cycle on the coarse CSLP from
+// level 1), x0 = 0, stopping at |g_{j+1}| <= coarse_tol ||v1||.
+template <class T>
+hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
+                       const int* done_in) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin;
+  const long long n1 = s->lv[1].n;
+  const long long vs = (long long)s->d.nrhs_max * n1;
+  C<T>* Q = (C<T>*)s->Qb;
+  C<T>* sb = (C<T>*)s->sb;
+  C<T>* eb = (C<T>*)s->eb;
+  const int m = s->d.coarse_maxit;
+  const double tol = s->d.coarse_tol;
+  launch_norm2_part<T>(vref<T>(v1), n1, nrhs, ks, nullptr, st);
+  launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
+  launch_krylov_init(ks, nrhs, done_in, nullptr, tol, st);
+  launch_scale_into<T>(vref<T>(v1), vref<T>(Q), ks.hnorm, n1, nrhs, ks.done, 1, st);
+  int all = 0;
+  for (int it = 0; it < m; ++it) {
+    vcycle<T>(s, 1, vref_j<T>(Q, ks.jctr, 0, vs), sb, nrhs, ks.done);
+    apply_E<T>(s, sb, eb, nrhs, ks.done);
+    cgs2<T>(s, ks, Q, vs, eb, n1, nrhs);
+    launch_givens(ks, nrhs, tol, m, st);
+    debug_trace(s, ks, "inner");
+    launch_scale_into<T>(vref<T>(eb), vref_j<T>(Q, ks.jctr, 0, vs), ks.hnorm, n1,
+                         nrhs, ks.done, 1, st);
+    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
+      const hz_status e = read_flag(s, ks.alldone, &all);
+      if (e != HZ_OK) return e;
+      if (all) break;
+    }
+  }
+  launch_trisolve(ks, nrhs, st);
+  launch_update<T, T>(Q, vs, ks, eb, 0, n1, nrhs, st);
+  vcycle<T>(s, 1, vref<T>(eb), v2, nrhs, done_in);
+  launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
+  return cuda_check(s, "coarse solve");
+}
+
+// ------------------------------------------------------------ A-DEF1
+// z = M^-1 (v - A q) + q, q = Z E^-1 R v; v, z FP64 (possibly indexed by the
+// outer Arnoldi counter), the preconditioner in precision T.
+template <class T>
+hz_status precond(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
+                  const int* done) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const long long n0 = s->lv[0].n;
+  VRef<T> v;
+  if (std::is_same<T, double>::value) {
+    v.base = (C<T>*)vin.base;
+    v.jidx = vin.jidx;
+    v.jofs = vin.jofs;
+    v.jstride = vin.jstride;
+  } else {
+    launch_add_conv<double, T>(vin, nullptr, vref<T>(s->vin), n0, nrhs, done, st);
+    v = vref<T>(s->vin);
+  }
+  C<T>* yv = (C<T>*)s->yv;
+  if (s->d.zkind == HZ_Z_NONE) {
+    vcycle<T>(s, 0, v, yv, nrhs, done);
+    launch_add_conv<T, double>(vref<T>(yv), nullptr, zout, n0, nrhs, done, st);
+    return cuda_check(s, "precond");
+  }
+  const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
+  launch_restrict_z<T>(F, Cc, bc, s->d.zkind, v, (C<T>*)s->v1, nrhs, done, st);
+  hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
+  if (e != HZ_OK) return e;
+  launch_prolong_z<T>(F, Cc, bc, s->d.zkind, (const C<T>*)s->v2, (C<T>*)s->q, 0, nrhs,
+                      done, st);
+  launch_helm<T>(F, bc, helm1(), vref<T>(s->q), v, (C<T>*)s->t, nrhs, done, st);
+  vcycle<T>(s, 0, vref<T>(s->t), yv, nrhs, done);
+  launch_add_conv<T, double>(vref<T>(yv), (const C<T>*)s->q, zout, n0, nrhs, done, st);
+  return cuda_check(s, "precond");
+}
+
+hz_status precond_any(hz_solver* s, VRef<double> v, VRef<double> z, int nrhs,
+                      const int* done) {
+  return s->mixed ? precond<float>(s, v, z, nrhs, done)
+                  : precond<double>(s, v, z, nrhs, done);
+}
+
+// ------------------------------------------------------------ outer FGMRES
+hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
+                    double tol, int use_x0, hz_solve_info* info) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const long long n0 = s->lv[0].n;
+  const long long vs = (long long)s->d.nrhs_max * n0;
+  const int m = s->d.outer_maxit;
+  const int bc = s->d.bc;
+  const LevelDev F = dev64(s, 0);
+  cudaMemsetAsync(s->in_total, 0, sizeof(int) * nrhs, st);
+  cudaMemsetAsync(s->in_max, 0, sizeof(int) * nrhs, st);
+  // ||b|| over the unknowns (Dirichlet boundary entries of b are ignored)
+  launch_add_conv<double, double>(vref<double>(b), nullptr, vref<double>(s->wo), n0,
+                                  nrhs, nullptr, st);
+  launch_mask_dirichlet<double>(F, bc, s->wo, nrhs, st);
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, s->bnorm_o, 1, st);
+  if (use_x0) {
+    launch_mask_dirichlet<double>(F, bc, x, nrhs, st);
+    launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo,
+                        nrhs, nullptr, st);
+  } else {
+    cudaMemsetAsync(x, 0, sizeof(double2) * n0 * nrhs, st);
+  }
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
+  launch_krylov_init(ko, nrhs, nullptr, s->bnorm_o, tol, st);
+  launch_scale_into<double>(vref<double>(s->wo), vref<double>(s->Vo), ko.hnorm, n0,
+                            nrhs, ko.done, 1, st);
+  hz_status e = cuda_check(s, "outer init");
+  if (e != HZ_OK) return e;
+  int all = 0;
+  e = read_flag(s, ko.alldone, &all);
+  if (e != HZ_OK) return e;
+  for (int it = 0; it < m && !all; ++it) {
+    e = precond_any(s, vref_j<double>(s->Vo, ko.jctr, 0, vs),
+                    vref_j<double>(s->Zo, ko.jctr, 0, vs), nrhs, ko.done);
+    if (e != HZ_OK) return e;
+    launch_helm<double>(F, bc, helm1(), vref_j<double>(s->Zo, ko.jctr, 0, vs),
+                        vref<double>(nullptr), s->wo, nrhs, ko.done, st);
+    cgs2<double>(s, ko, s->Vo, vs, s->wo, n0, nrhs);
+    launch_givens(ko, nrhs, tol, m, st);
+    debug_trace(s, ko, "outer");
+    launch_scale_into<double>(vref<double>(s->wo), vref_j<double>(s->Vo, ko.jctr, 0, vs),
+                              ko.hnorm, n0, nrhs, ko.done, 1, st);
+    e = read_flag(s, ko.alldone, &all);
+    if (e != HZ_OK) return e;
+  }
+  launch_trisolve(ko, nrhs, st);
+  launch_update<double, double>(s->Zo, vs, ko, x, 1, n0, nrhs, st);
+  // true residual
+  launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo, nrhs,
+                      nullptr, st);
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, s->relres, 1, st);
+  e = cuda_check(s, "outer finish");
+  if (e != HZ_OK) return e;
+  std::vector<int> it(nrhs), stt(nrhs), itot(nrhs), imax(nrhs);
+  std::vector<double> rr(nrhs), bn(nrhs);
+  cudaMemcpyAsync(it.data(), ko.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(stt.data(), ko.stat, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(itot.data(), s->in_total, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(imax.data(), s->in_max, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(rr.data(), s->relres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(bn.data(), s->bnorm_o, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(s, "outer sync");
+  hz_status worst = HZ_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    hz_status sr = (hz_status)stt[r];
+    const double rel = bn[r] > 0 ? rr[r] / bn[r] : 0.0;
+    if (sr == HZ_OK && !std::isfinite(rel)) sr = HZ_NAN;
+    if (info) {
+      info[r].outer_iters = it[r];
+      info[r].inner_iters_total = itot[r];
+      info[r].inner_iters_max = imax[r];
+      info[r].relres = rel;
+      info[r].status = sr;
+    }
+    if (worst == HZ_OK && sr != HZ_OK) worst = sr;
+  }
+  return worst;
+}
+
+template <class T>
+hz_status apply_op(hz_solver* s, hz_op op, int level, const double2* x, double2* y,
+                   int nrhs) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const int L = s->L;
+  auto conv_in = [&](long long n) {
+    launch_add_conv<double, T>(vref<double>(x), nullptr, vref<T>(s->t), n, nrhs,
+                               nullptr, st);
+  };
+  auto conv_out = [&](long long n) {
+    launch_add_conv<T, double>(vref<T>(s->yv), nullptr, vref<double>(y), n, nrhs,
+                               nullptr, st);
+  };
+  C<T>* tin = (C<T>*)s->t;
+  C<T>* yout = (C<T>*)s->yv;
+  switch (op) {
+    case HZ_OP_HELMHOLTZ:
+      if (level != 0) break;
+      launch_helm<double>(dev64(s, 0), bc, helm1(), vref<double>(x),
+                          vref<double>(nullptr), y, nrhs, nullptr, st);
+      return cuda_check(s, "apply helmholtz");
+    case HZ_OP_CSLP:
+      if (level < 0 || level > L) break;
+      conv_in(s->lv[level].n);
+      launch_helm<T>(s->lv[level].dev(), bc, cslp(s), vref<T>(tin), vref<T>(nullptr),
+                     yout, nrhs, nullptr, st);
+      conv_out(s->lv[level].n);
+      return cuda_check(s, "apply cslp");
+    case HZ_OP_VCYCLE:
+      if (level < 0 || level > L) break;
+      conv_in(s->lv[level].n);
+      vcycle<T>(s, level, vref<T>(tin), yout, nrhs, nullptr);
+      conv_out(s->lv[level].n);
+      return cuda_check(s, "apply vcycle");
+    case HZ_OP_RESTRICT_FW:
+      if (level < 0 || level >= L) break;
+      conv_in(s->lv[level].n);
+      launch_restrict_z<T>(s->lv[level].dev(), s->lv[level + 1].dev(), bc, ZK_BILINEAR,
+                           vref<T>(tin), yout, nrhs, nullptr, st);
+      conv_out(s->lv[level + 1].n);
+      return cuda_check(s, "apply restrict");
+    case HZ_OP_PROLONG_BILINEAR:
+      if (level < 0 || level >= L) break;
+      conv_in(s->lv[level + 1].n);
+      launch_prolong_z<T>(s->lv[level].dev(), s->lv[level + 1].dev(), bc, ZK_BILINEAR,
+                          tin, yout, 0, nrhs, nullptr, st);
+      conv_out(s->lv[level].n);
+      return cuda_check(s, "apply prolong");
+    default:
+      break;
+  }
+  if (s->d.zkind == HZ_Z_NONE) {
+    if (op == HZ_OP_PRECOND) {
+      hz_status e = precond<T>(s, vref<double>(x), vref<double>(y), nrhs, nullptr);
+      return e;
+    }
+    set_err(s, "operator %d needs deflation vectors (zkind != HZ_Z_NONE) or a "
+               "valid level", (int)op);
+    return HZ_INVALID_ARG;
+  }
+  switch (op) {
+    case HZ_OP_RESTRICT_Z:
+      conv_in(s->lv[0].n);
+      launch_restrict_z<T>(s->lv[0].dev(), s->lv[1].dev(), bc, s->d.zkind, vref<T>(tin),
+                           yout, nrhs, nullptr, st);
+      conv_out(s->lv[1].n);
+      return cuda_check(s, "apply restrict_z");
+    case HZ_OP_PROLONG_Z:
+      conv_in(s->lv[1].n);
+      launch_prolong_z<T>(s->lv[0].dev(), s->lv[1].dev(), bc, s->d.zkind, tin, yout, 0,
+                          nrhs, nullptr, st);
+      conv_out(s->lv[0].n);
+      return cuda_check(s, "apply prolong_z");
+    case HZ_OP_COARSE_E:
+      conv_in(s->lv[1].n);
+      apply_E<T>(s, tin, yout, nrhs, nullptr);
+      conv_out(s->lv[1].n);
+      return cuda_check(s, "apply E");
+    case HZ_OP_COARSE_SOLVE: {
+      conv_in(s->lv[1].n);
+      launch_mask_dirichlet<T>(s->lv[1].dev(), bc, tin, nrhs, st);
+      hz_status e = coarse_solve<T>(s, tin, yout, nrhs, nullptr);
+      if (e != HZ_OK) return e;
+      conv_out(s->lv[1].n);
+      return cuda_check(s, "apply coarse solve");
+    }
+    case HZ_OP_PRECOND:
+      return precond<T>(s, vref<double>(x), vref<double>(y), nrhs, nullptr);
+    default:
+      break;
+  }
+  set_err(s, "invalid operator %d / level %d", (int)op, level);
+  return HZ_INVALID_ARG;
+}
+
+}  // namespace
+
+// ================================================================= C ABI
+extern "C" {
+
+void hz_desc_default(hz_desc* d, int nx, int ny, double h) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->nx = nx;
+  d->ny = ny;
+  d->h = h;
+  d->bc = HZ_BC_SOMMERFELD;
+  d->zkind = HZ_Z_HO;
+  d->ekind = HZ_E_GALERKIN;
+  d->prec = HZ_PREC_FP64;
+  d->beta1 = 1.0;
+  d->beta2 = -0.5;
+  d->jacobi_omega = 0.8;
+  d->min_coarse_intervals = 2;
+  d->coarse_tol = 1e-6;
+  d->coarse_maxit = 500;
+  d->outer_maxit = 100;
+  d->nrhs_max = 1;
+}
+
+hz_status hz_workspace_bytes(const hz_desc* d, size_t* bytes) {
+  std::string why;
+  if (!bytes || !valid_desc(d, &why)) return HZ_INVALID_ARG;
+  hz_solver tmp;
+  tmp.d = *d;
+  const hz_status e = init_shapes(&tmp);
+  if (e != HZ_OK) return e;
+  Arena a;
+  plan(&tmp, a);
+  *bytes = a.off + 256;
+  return HZ_OK;
+}
+
+hz_status hz_setup(const hz_desc* d, const double* k2_dev, void* ws, size_t ws_bytes,
+                   void* stream, hz_solver** out) {
+  std::string why;
+  if (!out) return HZ_INVALID_ARG;
+  *out = nullptr;
+  if (!valid_desc(d, &why) || !k2_dev || !ws) return HZ_INVALID_ARG;
+  if (((uintptr_t)ws) & 255) return HZ_INVALID_ARG;
+  hz_solver* s = new hz_solver();
+  s->d = *d;
+  s->st = (cudaStream_t)stream;
+  if (const char* ce = std::getenv("HZ_CHECK_EVERY")) {
+    const int v = std::atoi(ce);
+    if (v > 0) s->check_every = v;
+  }
+  hz_status e = init_shapes(s);
+  if (e != HZ_OK) {
+    delete s;
+    return e;
+  }
+  Arena dry;
+  plan(s, dry);
+  if (dry.off + 256 > ws_bytes) {
+    delete s;
+    return HZ_WORKSPACE_TOO_SMALL;
+  }
+  Arena a;
+  a.dry = false;
+  a.base = (char*)ws;
+  plan(s, a);
+  s->ws_bytes = ws_bytes;
+  cudaStream_t st = s->st;
+  cudaMemcpyAsync(s->lv[0].k2d, k2_dev, sizeof(double) * s->lv[0].n,
+                  cudaMemcpyDeviceToDevice, st);
+  for (int l = 1; l <= s->L; ++l)
+    launch_inject(dev64(s, l - 1), dev64(s, l), s->lv[l].k2d, st);
+  const Shift sh = cslp(s);
+  for (int l = 0; l <= s->L; ++l) {
+    if (s->mixed) launch_cast_k2(s->lv[l].k2d, s->lv[l].k2f, s->lv[l].n, st);
+    launch_dinv(dev64(s, l), s->d.bc, sh, s->d.jacobi_omega, s->lv[l].dinv_d,
+                s->lv[l].dinv_f, st);
+  }
+  cudaMemsetAsync(s->gj_err, 0, sizeof(int), st);
+  launch_dense_assemble(dev64(s, s->L), s->d.bc, sh, s->aug, st);
+  launch_gauss_jordan(s->nL, s->aug, s->gj_err, st);
+  launch_extract_inverse(dev64(s, s->L), s->d.bc, s->aug,
+                         s->mixed ? nullptr : (double2*)s->minv,
+                         s->mixed ? (float2*)s->minv : nullptr, st);
+  int gerr = 0;
+  e = cuda_check(s, "setup");
+  if (e == HZ_OK) e = read_flag(s, s->gj_err, &gerr);
+  if (e == HZ_OK && gerr) {
+    set_err(s, "coarsest-level CSLP matrix is singular");
+    e = HZ_INVALID_GRID;
+  }
+  if (e != HZ_OK) {
+    delete s;
+    return e;
+  }
+  *out = s;
+  return HZ_OK;
+}
+
+hz_status hz_solve(hz_solver* s, const void* b_dev, void* x_dev, int nrhs, double tol,
+                   int use_x0, hz_solve_info* info) {
+  if (!s || !b_dev || !x_dev || nrhs < 1 || nrhs > s->d.nrhs_max || !(tol > 0))
+    return HZ_INVALID_ARG;
+  return solve_dev(s, (const double2*)b_dev, (double2*)x_dev, nrhs, tol, use_x0, info);
+}
+
+hz_status hz_solve_host(hz_solver* s, const void* b_host, void* x_host, int nrhs,
+                        double tol, hz_solve_info* info) {
+  if (!s || !b_host || !x_host || nrhs < 1 || nrhs > s->d.nrhs_max || !(tol > 0))
+    return HZ_INVALID_ARG;
+  const size_t bytes = sizeof(double2) * (size_t)s->lv[0].n * nrhs;
+  if (cudaMemcpyAsync(s->io0, b_host, bytes, cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+    return cuda_check(s, "h2d");
+  const hz_status e = solve_dev(s, s->io0, s->io1, nrhs, tol, 0, info);
+  if (e != HZ_OK && e != HZ_NOT_CONVERGED && e != HZ_BREAKDOWN) return e;
+  if (cudaMemcpyAsync(x_host, s->io1, bytes, cudaMemcpyDeviceToHost, s->st) != cudaSuccess)
+    return cuda_check(s, "d2h");
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "d2h sync");
+  return e;
+}
+
+hz_status hz_apply(hz_solver* s, hz_op op, int level, const void* x_dev, void* y_dev,
+                   int nrhs) {
+  if (!s || !x_dev || !y_dev || nrhs < 1 || nrhs > s->d.nrhs_max) return HZ_INVALID_ARG;
+  return s->mixed ? apply_op<float>(s, op, level, (const double2*)x_dev,
+                                    (double2*)y_dev, nrhs)
+                  : apply_op<double>(s, op, level, (const double2*)x_dev,
+                                     (double2*)y_dev, nrhs);
+}
+
+hz_status hz_last_inner_iters(hz_solver* s, int* iters_host, int nrhs) {
+  if (!s || !iters_host || nrhs < 1 || nrhs > s->d.nrhs_max) return HZ_INVALID_ARG;
+  if (s->d.zkind == HZ_Z_NONE) {
+    for (int r = 0; r < nrhs; ++r) iters_host[r] = 0;
+    return HZ_OK;
+  }
+  cudaMemcpyAsync(iters_host, s->kin.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost,
+                  s->st);
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "iters");
+  return HZ_OK;
+}
+
+int hz_num_levels(const hz_solver* s) { return s ? s->L + 1 : 0; }
+
+hz_status hz_level_shape(const hz_solver* s, int level, int* nx, int* ny) {
+  if (!s || level < 0 || level > s->L || !nx || !ny) return HZ_INVALID_ARG;
+  *nx = s->lv[level].nx;
+  *ny = s->lv[level].ny;
+  return HZ_OK;
+}
+
+hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev, int nshots,
+                      const int* rec_idx_dev, int nrec, const void* d_obs_dev,
+                      double tol, double* J_host, double* grad_dev,
+                      hz_solve_info* info) {
+  if (!s || !src_dev || nshots < 1 || !rec_idx_dev || nrec < 1 || !d_obs_dev ||
+      !J_host || !grad_dev || !(tol > 0) || !(omega > 0))
+    return HZ_INVALID_ARG;
+  cudaStream_t st = s->st;
+  const long long n0 = s->lv[0].n;
+  const int B = s->d.nrhs_max;
+  const int bc = s->d.bc;
+  cudaMemsetAsync(grad_dev, 0, sizeof(double) * n0, st);
+  cudaMemsetAsync(s->Jd, 0, sizeof(double), st);
+  hz_status worst = HZ_OK;
+  std::vector<hz_solve_info> inf(B);
+  for (int s0 = 0; s0 < nshots; s0 += B) {
+    const int nb = (nshots - s0 < B) ? nshots - s0 : B;
+    const double2* src = (const double2*)src_dev + (long long)s0 * n0;
+    hz_status e = solve_dev(s, src, s->io2, nb, tol, 0, inf.data());
+    if (e != HZ_OK && e != HZ_NOT_CONVERGED && e != HZ_BREAKDOWN) return e;
+    if (worst == HZ_OK) worst = e;
+    if (info)
+      for (int r = 0; r < nb; ++r) info[2 * (s0 + r)] = inf[r];
+    cudaMemsetAsync(s->io0, 0, sizeof(double2) * n0 * nb, st);
+    launch_adjoint_source(s->lv[0].nx, s->lv[0].ny, bc, s->io2, rec_idx_dev, nrec,
+                          (const double2*)d_obs_dev + (long long)s0 * nrec, s->io0,
+                          s->Jd, nb, st);
+    e = solve_dev(s, s->io0, s->io1, nb, tol, 0, inf.data());
+    if (e != HZ_OK && e != HZ_NOT_CONVERGED && e != HZ_BREAKDOWN) return e;
+    if (worst == HZ_OK) worst = e;
+    if (info)
+      for (int r = 0; r < nb; ++r) info[2 * (s0 + r) + 1] = inf[r];
+    launch_image(dev64(s, 0), bc, omega, s->io2, s->io1, grad_dev, nb, st);
+  }
+  cudaMemcpyAsync(J_host, s->Jd, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(s, "gradient");
+  const hz_status e = cuda_check(s, "gradient");
+  return e != HZ_OK ? e : worst;
+}
+
+hz_status hz_destroy(hz_solver* s) {
+  delete s;
+  return HZ_OK;
+}
+
+const char* hz_status_str(hz_status st) {
+  switch (st) {
+    case HZ_OK: return "ok";
+    case HZ_INVALID_ARG: return "invalid argument";
+    case HZ_INVALID_GRID: return "invalid grid";
+    case HZ_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case HZ_NOT_CONVERGED: return "not converged";
+    case HZ_BREAKDOWN: return "breakdown";
+    case HZ_NAN: return "NaN or Inf in a residual";
+    case HZ_TIMEOUT: return "timeout";
+    case HZ_CUDA_ERROR: return "CUDA error";
+  }
+  return "unknown status";
+}
+
+const char* hz_last_error(const hz_solver* s) { return s ? s->err.c_str() : ""; }
+
+long long hz_kernel_launches(void) { return hz::launch_counter().load(); }
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+"""The C-ABI library builds, loads and exports every symbol include/hz.h
+declares; struct layouts agree between the header and the binding; the
+host-side descriptor logic (no GPU compute) behaves as documented."""
+
+import ctypes
+import os
+import re
+import shutil
+import subprocess
+
+import pytest
+
+from paper_2308_06152_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "hz.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(hz_[a-z_0-9]+)\s*\(", text)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if shutil.which("nvcc") is None and not os.path.exists(_lib.LIB_PATH):
+        pytest.skip("no nvcc to build libhz.so")
+    path = build.build()
+    return _lib.load_library(path)
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for must in ("hz_workspace_bytes", "hz_setup", "hz_solve", "hz_solve_host",
+                 "hz_apply", "hz_gradient", "hz_destroy", "hz_status_str"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(declared_functions()) <= set(_lib.SIGNATURES)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    src = tmp_path / "layout.c"
+    fields = [f[0] for f in _lib.HzDesc._fields_]
+    ifields = [f[0] for f in _lib.HzSolveInfo._fields_]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hz.h"',
+             "int main(void){",
+             'printf("%zu\\n", sizeof(hz_desc));',
+             'printf("%zu\\n", sizeof(hz_solve_info));']
+    lines += [f'printf("%zu\\n", offsetof(hz_desc, {f}));' for f in fields]
+    lines += [f'printf("%zu\\n", offsetof(hz_solve_info, {f}));'
+              for f in ifields]
+    lines += ["return 0;}"]
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o",
+                    str(exe)], check=True)
+    out = [int(v) for v in subprocess.run([str(exe)], capture_output=True,
+                                          text=True).stdout.split()]
+    assert out[0] == ctypes.sizeof(_lib.HzDesc)
+    assert out[1] == ctypes.sizeof(_lib.HzSolveInfo)
+    k = 2
+    for f in fields:
+        assert out[k] == getattr(_lib.HzDesc, f).offset, f
+        k += 1
+    for f in ifields:
+        assert out[k] == getattr(_lib.HzSolveInfo, f).offset, f
+        k += 1
+
+
+def _ws(lib, **kw):
+    d = _lib.HzDesc()
+    lib.hz_desc_default(ctypes.byref(d), kw.pop("nx", 33), kw.pop("ny", 33),
+                        kw.pop("h", 1 / 32))
+    for k, v in kw.items():
+        setattr(d, k, v)
+    n = ctypes.c_size_t(0)
+    st = lib.hz_workspace_bytes(ctypes.byref(d), ctypes.byref(n))
+    return st, n.value
+
+
+def test_desc_defaults_are_the_papers(lib):
+    d = _lib.HzDesc()
+    lib.hz_desc_default(ctypes.byref(d), 81, 81, 1 / 80)
+    assert (d.beta1, d.beta2, d.jacobi_omega) == (1.0, -0.5, 0.8)
+    assert d.min_coarse_intervals == 2 and d.coarse_tol == 1e-6
+
+
+def test_workspace_bytes_host_logic(lib):
+    st, b1 = _ws(lib)
+    assert st == 0 and b1 > 0
+    st, b4 = _ws(lib, nrhs_max=4)
+    assert st == 0 and b4 > 3 * b1 // 2
+    assert _ws(lib, nx=2)[0] == 1                       # too small
+    assert _ws(lib, nrhs_max=0)[0] == 1
+    assert _ws(lib, bc=7)[0] == 1
+    assert _ws(lib, nx=34, ny=34)[0] == 2                # cannot coarsen
+    assert _ws(lib, nx=20, ny=20, zkind=0)[0] == 0       # plain CSLP is fine
+    assert _ws(lib, nx=34, ny=34, zkind=0)[0] == 2       # 1156-node coarsest
+    assert _ws(lib, nx=2301, ny=751, h=4.0)[0] == 2      # coarsest too large
+    assert _ws(lib, nx=2305, ny=769, h=4.0)[0] == 0
+
+
+def test_status_strings(lib):
+    for code in range(9):
+        assert lib.hz_status_str(code)
+    assert lib.hz_status_str(0) == b"ok"

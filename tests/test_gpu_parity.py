@@ -1,0 +1,295 @@
+"""GPU path (through the C ABI) against the CPU FP64 oracle, element by
+element on seeded inputs.
+
+Tolerances: FP64 operators 1e-12 relative (rounding-order differences
+only); FP64 solves: outer iterations within +-1 of the oracle and, at tight
+tolerances, solutions within 1e-8 relative; complex-FP32 preconditioner
+operators 2e-5 relative (single-precision rounding of O(10) terms), and
+mixed solves must still reach the FP64 residual target.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import gradient as grd
+from oracle import operators as ops
+from oracle.solver import Oracle
+from paper_2308_06152_gb300 import workloads as wl
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2308_06152_gb300 import build
+    build.build()
+
+
+def solver(nx, ny, h, k2, bc, z="ho", e="galerkin", prec="fp64", nrhs=1,
+           **kw):
+    from paper_2308_06152_gb300.api import Desc, Solver
+    return Solver(Desc(nx, ny, h, bc=bc, z=z, e=e, prec=prec, nrhs_max=nrhs,
+                       **kw), k2)
+
+
+def rk2(ny, nx, seed, lo=4.0, hi=30.0):
+    return np.random.default_rng(seed).uniform(lo, hi, size=(ny, nx)) ** 2
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def to_np(t):
+    return t.cpu().numpy()
+
+
+def oapply(orc, mat, lin, lout, x):
+    return orc.levels[lout].to_full(mat @ orc.levels[lin].to_unknowns(x))
+
+
+# ragged grid: 97 = 3*32 + 1 columns, 73 = 9*8 + 1 rows of 32x8 tiles
+NX, NY = 97, 73
+H = 1.0 / 96
+BCS = ["sommerfeld", "dirichlet"]
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-5)])
+def test_level_operators(bc, prec, tol):
+    k2 = rk2(NY, NX, 1)
+    s = solver(NX, NY, H, k2, bc, z="ho", prec=prec, nrhs=2)
+    orc = Oracle(NX, NY, H, k2, bc, z="ho", coarsest="direct")
+    assert s.num_levels == orc.L + 1
+    for l in range(orc.L + 1):
+        lv = orc.levels[l]
+        assert s.level_shape(l) == (lv.nx, lv.ny)
+        x = wl.random_complex((2, lv.ny, lv.nx), 10 + l)
+        y = to_np(s.apply("cslp", x, l))
+        for r in range(2):
+            assert rel(y[r], oapply(orc, orc.M[l], l, l, x[r])) < tol
+        if l < orc.L:
+            y = to_np(s.apply("restrict_fw", x, l))
+            assert rel(y[0], oapply(orc, orc.R[l], l, l + 1, x[0])) < tol
+            lc = orc.levels[l + 1]
+            xc = wl.random_complex((2, lc.ny, lc.nx), 20 + l)
+            y = to_np(s.apply("prolong_bilinear", xc, l))
+            assert rel(y[1], oapply(orc, orc.P[l], l + 1, l, xc[1])) < tol
+    x = wl.random_complex((2, NY, NX), 3)
+    y = to_np(s.apply("helmholtz", x))
+    assert rel(y[1], oapply(orc, orc.A, 0, 0, x[1])) < 1e-12
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("z", ["bilinear", "ho"])
+@pytest.mark.parametrize("e", ["galerkin", "red_o2", "red_glk1", "red_glk2"])
+def test_deflation_operators(bc, z, e):
+    k2 = rk2(NY, NX, 2)
+    s = solver(NX, NY, H, k2, bc, z=z, e=e)
+    orc = Oracle(NX, NY, H, k2, bc, z=z, e=e, coarsest="direct")
+    lc = orc.levels[1]
+    x = wl.random_complex((1, NY, NX), 4)
+    xc = wl.random_complex((1, lc.ny, lc.nx), 5)
+    assert rel(to_np(s.apply("restrict_z", x))[0],
+               oapply(orc, orc.RZ, 0, 1, x[0])) < 1e-12
+    assert rel(to_np(s.apply("prolong_z", xc))[0],
+               oapply(orc, orc.Z, 1, 0, xc[0])) < 1e-12
+    assert rel(to_np(s.apply("coarse_e", xc))[0],
+               oapply(orc, orc.E, 1, 1, xc[0])) < 1e-12
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 5e-5)])
+def test_vcycle(bc, prec, tol):
+    k2 = rk2(NY, NX, 6)
+    s = solver(NX, NY, H, k2, bc, z="ho", prec=prec)
+    orc = Oracle(NX, NY, H, k2, bc, z="ho", coarsest="direct")
+    for l in (0, 1, orc.L):
+        lv = orc.levels[l]
+        f = wl.random_complex((1, lv.ny, lv.nx), 30 + l)
+        y = to_np(s.apply("vcycle", f, l))[0]
+        ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[0]), l))
+        assert rel(y, ref) < tol, (l, rel(y, ref))
+
+
+@pytest.mark.parametrize("bc,z,e", [("sommerfeld", "ho", "galerkin"),
+                                    ("dirichlet", "bilinear", "galerkin"),
+                                    ("sommerfeld", "ho", "red_glk2")])
+def test_coarse_solve_and_precond(bc, z, e):
+    n = 65
+    h = 1.0 / 64
+    k2 = np.full((n, n), 30.0 ** 2)
+    s = solver(n, n, h, k2, bc, z=z, e=e, coarse_tol=1e-12, coarse_maxit=600)
+    orc = Oracle(n, n, h, k2, bc, z=z, e=e, coarsest="direct",
+                 coarse_tol=1e-12, coarse_maxit=600)
+    lc = orc.levels[1]
+    v1 = wl.random_complex((1, lc.ny, lc.nx), 7)
+    v2 = to_np(s.apply("coarse_solve", v1))[0]
+    exact = lc.to_full(spla.spsolve(orc.E.tocsc(), lc.to_unknowns(v1[0])))
+    assert rel(v2, exact) < 1e-9
+    its = s.last_inner_iters(1)[0]
+    orc.inner_log = []
+    orc.coarse_solve(lc.to_unknowns(v1[0]))
+    assert abs(its - orc.inner_log[0]) <= 1, (its, orc.inner_log)
+    v = wl.random_complex((1, n, n), 8)
+    z_gpu = to_np(s.apply("precond", v))[0]
+    z_orc = orc.levels[0].to_full(orc.adef1(orc.levels[0].to_unknowns(v[0])))
+    assert rel(z_gpu, z_orc) < 1e-8
+
+
+def _solve_pair(n, k, bc, z, e, tol, ctol, prec="fp64", nodes=None):
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), float(k) ** 2)
+    nodes = nodes or [wl.centre_node(n, n)]
+    b = wl.point_sources(n, n, nodes)
+    s = solver(n, n, h, k2, bc, z=z, e=e, prec=prec, nrhs=len(nodes),
+               coarse_tol=ctol, coarse_maxit=1500, outer_maxit=200)
+    x, info = s.solve(b, tol=tol)
+    orc = Oracle(n, n, h, k2, bc, z=z, e=e, coarse_tol=ctol,
+                 coarse_maxit=1500)
+    return orc, b, to_np(x), info
+
+
+def test_config1_fp64_iterations_and_residual():
+    """81 x 81, k = 50, Dirichlet, bilinear str-Glk, tol 1e-6, coarse 1e-6."""
+    orc, b, x, info = _solve_pair(81, 50, "dirichlet", "bilinear", "galerkin",
+                                  1e-6, 1e-6)
+    xo, io = orc.solve(b[0], tol=1e-6)
+    assert info[0].status == "HZ_OK"
+    assert abs(info[0].outer_iters - io.outer_iters) <= 1
+    lv = orc.levels[0]
+    r = np.linalg.norm(lv.to_unknowns(b[0]) - orc.A @ lv.to_unknowns(x[0]))
+    assert r / np.linalg.norm(lv.to_unknowns(b[0])) <= 1e-6
+    assert info[0].relres <= 1e-6
+    tot = info[0].inner_iters_total
+    assert abs(tot - io.inner_total) <= max(3, 0.05 * io.inner_total), \
+        (tot, io.inner_total)
+
+
+@pytest.mark.parametrize("bc,z,e", [("sommerfeld", "ho", "galerkin"),
+                                    ("sommerfeld", "ho", "red_glk2"),
+                                    ("dirichlet", "ho", "red_o2"),
+                                    ("sommerfeld", "bilinear", "red_glk1"),
+                                    ("sommerfeld", None, "galerkin")])
+def test_solve_parity_tight(bc, z, e):
+    """At tight tolerances GPU and oracle solutions agree to 1e-8."""
+    orc, b, x, info = _solve_pair(65, 30, bc, z, e, 1e-11, 1e-11)
+    xo, io = orc.solve(b[0], tol=1e-11)
+    assert rel(x[0], xo) < 1e-8
+    assert abs(info[0].outer_iters - io.outer_iters) <= 1
+
+
+def test_mixed_precision_reaches_fp64_residual():
+    n, k = 129, 80
+    orc, b, x, info = _solve_pair(n, k, "sommerfeld", "ho", "galerkin", 1e-6,
+                                  1e-1, prec="mixed")
+    lv = orc.levels[0]
+    bu = lv.to_unknowns(b[0])
+    r = np.linalg.norm(bu - orc.A @ lv.to_unknowns(x[0])) / np.linalg.norm(bu)
+    assert r <= 1e-6 and info[0].status == "HZ_OK"
+    xd = lv.to_full(spla.spsolve(orc.A.tocsc(), bu))
+    # error against the exact discrete solution, stated per result
+    err = rel(x[0], xd)
+    assert err < 1e-3, err
+
+
+def test_batched_equals_single_and_host_io():
+    n = 65
+    nodes = [(32, 32), (10, 50), (40, 5), (60, 60)]
+    h = 1.0 / 64
+    k2 = rk2(n, n, 9, 20, 40)
+    b = wl.point_sources(n, n, nodes)
+    sb = solver(n, n, h, k2, "sommerfeld", nrhs=4, coarse_tol=1e-6)
+    xb, ib = sb.solve(b, tol=1e-8)
+    s1 = solver(n, n, h, k2, "sommerfeld", nrhs=1, coarse_tol=1e-6)
+    for r in range(4):
+        x1, i1 = s1.solve(b[r:r + 1], tol=1e-8)
+        assert i1[0].outer_iters == ib[r].outer_iters
+        assert rel(to_np(xb[r]), to_np(x1[0])) < 1e-12
+    bh = torch.from_numpy(b).pin_memory()
+    xh, ih = sb.solve_host(bh, tol=1e-8)
+    assert rel(xh.numpy(), to_np(xb)) < 1e-12
+
+
+def test_edge_cases():
+    from paper_2308_06152_gb300.api import Desc, HzError, Solver
+    n = 33
+    h = 1.0 / 32
+    k2 = np.full((n, n), 400.0)
+    s = solver(n, n, h, k2, "sommerfeld", nrhs=2, outer_maxit=3)
+    b = np.zeros((2, n, n), complex)
+    b[1, 16, 16] = 1.0
+    x, info = s.solve(b, tol=1e-6)
+    assert info[0].outer_iters == 0 and not np.any(to_np(x[0]))
+    assert info[1].status in ("HZ_OK", "HZ_NOT_CONVERGED")
+    # tolerance out of reach within outer_maxit
+    x, info = s.solve(b[1:], tol=1e-15)
+    assert info[0].status == "HZ_NOT_CONVERGED" and info[0].outer_iters == 3
+    assert np.isfinite(info[0].relres)
+    with pytest.raises(HzError):
+        s.solve(np.zeros((3, n, n), complex))
+    bn = b[1:].copy()
+    bn[0, 3, 3] = np.nan
+    x, info = s.solve(bn)
+    assert info[0].status == "HZ_NAN"
+    # smallest grids: one coarsening (5 x 5 -> 3 x 3) and none (3 x 3)
+    s5 = solver(5, 5, 0.25, np.full((5, 5), 4.0), "sommerfeld", z="ho")
+    o5 = Oracle(5, 5, 0.25, np.full((5, 5), 4.0), "sommerfeld", z="ho",
+                coarse_tol=1e-12)
+    b5 = wl.point_sources(5, 5, [(2, 2)])
+    x5, i5 = s5.solve(b5, tol=1e-12)
+    assert rel(to_np(x5[0]), o5.solve(b5[0], tol=1e-12)[0]) < 1e-9
+    s3 = solver(3, 3, 0.5, np.full((3, 3), 1.0), "dirichlet", z=None)
+    b3 = wl.point_sources(3, 3, [(1, 1)])
+    x3, i3 = s3.solve(b3, tol=1e-12)
+    assert abs(to_np(x3)[0, 1, 1] - 1.0 / (4 / 0.25 - 1.0)) < 1e-12
+    with pytest.raises(HzError):
+        Solver(Desc(34, 34, 1 / 33), np.ones((34, 34)))
+
+
+def test_gradient_matches_oracle():
+    nx, ny, h, omega = 17, 13, 1.0 / 16, 25.0
+    rng = np.random.default_rng(11)
+    m = rng.uniform(0.7, 1.3, size=(ny, nx))
+    src = wl.point_sources(nx, ny, [(8, 6), (3, 2), (12, 9)])
+    rec = wl.surface_receivers(nx, 0)
+    d = (rng.standard_normal((3, nx)) + 1j * rng.standard_normal((3, nx))) * 1e-3
+    s = solver(nx, ny, h, omega ** 2 * m, "sommerfeld", z="ho", nrhs=2,
+               coarse_tol=1e-12, coarse_maxit=400)
+    J, g, infos = s.gradient(omega, src, rec, d, tol=1e-12)
+    J0, g0 = grd.misfit_and_gradient(nx, ny, h, m, omega, "sommerfeld", src,
+                                     rec, d)
+    assert J == pytest.approx(J0, rel=1e-8)
+    assert rel(to_np(g), g0) < 1e-7
+    assert len(infos) == 6 and all(i.status == "HZ_OK" for i in infos)
+
+
+@pytest.mark.slow
+def test_full_size_1281_mixed_batch_properties():
+    """The bench workload (1281^2, k = 800, Sommerfeld, higher-order
+    str-Glk, mixed precision, 16 shots): every RHS reaches a true FP64
+    relative residual <= 1e-6 measured by the oracle's own A, and sampled
+    entries of A x agree with the oracle."""
+    model = wl.constant_k(1281, 800.0)
+    nodes = wl.centre_cluster(1281, 1281, 16)
+    b = wl.point_sources(1281, 1281, nodes)
+    s = solver(1281, 1281, model.h, model.k2, "sommerfeld", z="ho",
+               e="galerkin", prec="mixed", nrhs=16, coarse_tol=1e-1,
+               coarse_maxit=200, outer_maxit=60)
+    x, info = s.solve(b, tol=1e-6)
+    lv = ops.Level(1281, 1281, model.h, model.k2, "sommerfeld")
+    A = ops.five_point(lv)
+    xs = to_np(x)
+    for r in range(16):
+        bu = lv.to_unknowns(b[r])
+        res = np.linalg.norm(bu - A @ lv.to_unknowns(xs[r])) / np.linalg.norm(bu)
+        assert res <= 1e-6 and info[r].status == "HZ_OK", (r, res)
+    y = to_np(s.apply("helmholtz", xs[:1]))[0].reshape(-1)
+    idx = np.random.default_rng(0).integers(0, 1281 * 1281, 4096)
+    ref = (A @ lv.to_unknowns(xs[0]))[idx]
+    np.testing.assert_allclose(y[idx], ref, rtol=1e-12,
+                               atol=1e-12 * np.abs(ref).max())
