@@ -137,6 +137,20 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+KERNEL_NAMES = {"mdot": "k_mdot (CGS2 multi-vector dot product)",
+                "maxpy": "k_maxpy (CGS2 multi-vector update)"}
+
+
+def hbm_peak():
+    """Measured HBM copy bandwidth of the GB300s, else the fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 # ------------------------------------------------------------------ oracle
 def oracle_sample(wl_name, steps, warmup):
     """Bounded CPU sample: one outer flexible-GMRES iteration of the oracle
@@ -217,6 +231,8 @@ def run_ours(args):
     sampler = ClockSampler(uuid)
     sampler.start()
     time.sleep(0.3)
+    if args.profile_kernel != "none":
+        solver.profile_begin(args.profile_kernel, max_launches=200000)
     l0 = lib.hz_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -228,6 +244,7 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = lib.hz_kernel_launches() - l0
+    prof = solver.profile_end() if args.profile_kernel != "none" else None
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     if world > 1:
@@ -257,6 +274,19 @@ def run_ours(args):
         e2e_s = float(t.item())
     io_bytes = int(b_np.nbytes)
 
+    roof = None
+    if prof and prof[0] > 0:
+        n_l, ms_k, by = prof
+        peak, peak_src = hbm_peak()
+        achieved = by / (ms_k / 1e3) / 1e9
+        roof = {"kernel": KERNEL_NAMES[args.profile_kernel], "bound": "hbm",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": None, "launches": int(n_l),
+                "alg_bytes_per_launch": by / n_l,
+                "avg_launch_us": 1e3 * ms_k / n_l,
+                "share_of_step": ms_k / (ms * args.steps)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.workload, steps=1, warmup=0)
@@ -284,7 +314,7 @@ def run_ours(args):
                     "d2h_bytes_per_step": io_bytes},
             "gpu_launches": int(launches),
             "clocks": clocks,
-            "roofline": None,
+            "roofline": roof,
             "cpu_baseline": cpu,
             "solve": {"outer_iters": outer, "inner_iters_total": inner,
                       "max_true_relres": worst, "status": statuses},
@@ -324,6 +354,9 @@ def main():
     ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU oracle baseline sample")
+    ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],
+                    default="mdot",
+                    help="kernel class timed live for the roofline entry")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -173,6 +173,23 @@ hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev,
 /* Releases the host handle (the workspace stays the caller's). */
 hz_status hz_destroy(hz_solver* s);
 
+/* Kernel classes that hz_profile_* can time: the multi-vector dot product
+ * and the multi-vector update of the Gram-Schmidt step (Alg. 1 inner loop),
+ * which carry the basis traffic of both Krylov solvers. */
+typedef enum { HZ_KC_NONE = 0, HZ_KC_MDOT = 1, HZ_KC_MAXPY = 2 } hz_kernel_class;
+
+/* Starts timing every launch of kernel class kc on the solver's stream:
+ * CUDA events bracket each launch (at most max_launches are kept) and the
+ * kernels add their algorithmic bytes (basis vectors and w read, w written,
+ * per active RHS) to a counter in the workspace.  HZ_KC_NONE stops it. */
+hz_status hz_profile_begin(hz_solver* s, hz_kernel_class kc, int max_launches);
+
+/* Synchronises the stream and returns the launches timed, their summed
+ * duration in ms and their summed algorithmic bytes; ends profiling.
+ * HZ_INVALID_ARG if the event pool overflowed (totals then incomplete). */
+hz_status hz_profile_end(hz_solver* s, long long* launches, double* ms_total,
+                         double* alg_bytes);
+
 /* Kernels launched by this library since it was loaded (all solvers). */
 long long hz_kernel_launches(void);
 

@@ -54,6 +54,8 @@ SIGNATURES = {
                             c_void_p]),
     "hz_destroy": (c_int, [c_void_p]),
     "hz_kernel_launches": (ctypes.c_longlong, []),
+    "hz_profile_begin": (c_int, [c_void_p, c_int, c_int]),
+    "hz_profile_end": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hz_status_str": (ctypes.c_char_p, [c_int]),
     "hz_last_error": (ctypes.c_char_p, [c_void_p]),
 }

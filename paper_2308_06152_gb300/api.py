@@ -214,6 +214,26 @@ class Solver:
             self._check(st, "hz_gradient")
         return J.value, grad, _infos(infos, 2 * nshots)
 
+    KERNEL_CLASSES = {"mdot": 1, "maxpy": 2}
+
+    def profile_begin(self, kernel, max_launches=100000):
+        """Time every launch of one kernel class (see hz_profile_begin)."""
+        self._check(self.lib.hz_profile_begin(self.handle,
+                                              self.KERNEL_CLASSES[kernel],
+                                              int(max_launches)),
+                    "hz_profile_begin")
+
+    def profile_end(self):
+        """(launches, total ms, algorithmic bytes) since profile_begin."""
+        n = ctypes.c_longlong(0)
+        ms = ctypes.c_double(0.0)
+        by = ctypes.c_double(0.0)
+        self._check(self.lib.hz_profile_end(self.handle, ctypes.byref(n),
+                                            ctypes.byref(ms),
+                                            ctypes.byref(by)),
+                    "hz_profile_end")
+        return n.value, ms.value, by.value
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.hz_destroy(self.handle)

@@ -238,6 +238,7 @@ struct KState {
   double2* hcol;    // [nrhs_max][m+1] scratch column (one CGS pass)
   double2* part;    // partial sums [nrhs_max][m+1][nblk_max]
   double* npart;    // partial squared norms [nrhs_max][nblk_max]
+  unsigned long long* abytes;  // [1] algorithmic-byte counter or null
   int m;            // basis size (max iterations)
   int nblk_max;
 };

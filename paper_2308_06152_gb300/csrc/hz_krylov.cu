@@ -43,6 +43,9 @@ k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w
   const int r = blockIdx.y, blk = blockIdx.x;
   if (ks.done[r]) return;
   const int j = *ks.jctr;
+  // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
+  if (ks.abytes && blk == 0 && threadIdx.x == 0)
+    atomicAdd(ks.abytes, (unsigned long long)(j + 2) * n * sizeof(C<T>));
   const long long base = (long long)blk * CHUNK + threadIdx.x;
   const C<T>* wr = w + r * n;
   C<T> wv[EPT];
@@ -137,6 +140,9 @@ k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
   const int r = blockIdx.y;
   if (ks.done[r]) return;
   const int j = *ks.jctr;
+  // algorithmic bytes of this RHS: read w and basis 0..j, write w
+  if (ks.abytes && blockIdx.x == 0 && threadIdx.x == 0)
+    atomicAdd(ks.abytes, (unsigned long long)(j + 3) * n * sizeof(C<T>));
   const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
   C<T>* wr = w + r * n;
   C<T> acc[EPT];

@@ -133,6 +133,12 @@ struct hz_solver {
   int check_every = 4;
   std::string err;
   size_t ws_bytes = 0;
+  // opt-in per-kernel-class timing (hz_profile_begin / hz_profile_end)
+  unsigned long long* prof_bytes = nullptr;
+  int prof_kc = HZ_KC_NONE;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_used = 0;
+  long long prof_dropped = 0;
 };
 
 namespace {
@@ -228,6 +234,7 @@ void plan(hz_solver* s, Arena& a) {
   s->io1 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
   s->io2 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
   s->Jd = (double*)a.take(sizeof(double));
+  s->prof_bytes = (unsigned long long*)a.take(sizeof(unsigned long long));
 }
 
 hz_status init_shapes(hz_solver* s) {
@@ -362,18 +369,35 @@ void debug_trace(hz_solver* s, const KState& ks, const char* label) {
           g[jj + 1].x, g[jj + 1].y, cudaGetErrorString(cudaGetLastError()));
 }
 
+// Event pair around one launch of the profiled kernel class.
+inline void prof_mark(hz_solver* s, int kc) {
+  if (s->prof_kc != kc) return;
+  if (s->prof_used < s->prof_ev.size())
+    cudaEventRecord(s->prof_ev[s->prof_used++], s->st);
+  else
+    ++s->prof_dropped;
+}
+
 // Classical Gram-Schmidt with one re-orthogonalisation (CGS2) of w against
 // basis columns 0..j, then ||w|| into ks.hnorm.
 template <class T>
 void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
           long long n, int nrhs) {
   cudaStream_t st = s->st;
-  launch_mdot<T>(V, vs, w, n, nrhs, ks, st);
-  launch_reduce_cols(ks, n, nrhs, 0, st);
-  launch_maxpy<T>(V, vs, w, n, nrhs, ks, st);
-  launch_mdot<T>(V, vs, w, n, nrhs, ks, st);
-  launch_reduce_cols(ks, n, nrhs, 1, st);
-  launch_maxpy<T>(V, vs, w, n, nrhs, ks, st);
+  KState k = ks;
+  k.abytes = nullptr;
+  KState kd = k, ka = k;
+  if (s->prof_kc == HZ_KC_MDOT) kd.abytes = s->prof_bytes;
+  if (s->prof_kc == HZ_KC_MAXPY) ka.abytes = s->prof_bytes;
+  for (int pass = 0; pass < 2; ++pass) {
+    prof_mark(s, HZ_KC_MDOT);
+    launch_mdot<T>(V, vs, w, n, nrhs, kd, st);
+    prof_mark(s, HZ_KC_MDOT);
+    launch_reduce_cols(k, n, nrhs, pass, st);
+    prof_mark(s, HZ_KC_MAXPY);
+    launch_maxpy<T>(V, vs, w, n, nrhs, ka, st);
+    prof_mark(s, HZ_KC_MAXPY);
+  }
   launch_norm2_part<T>(vref<T>(w), n, nrhs, ks, ks.done, st);
   launch_reduce_norm(ks, n, nrhs, ks.hnorm, 1, st);
 }
@@ -834,7 +858,50 @@ hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev, int nshot
   return e != HZ_OK ? e : worst;
 }
 
+hz_status hz_profile_begin(hz_solver* s, hz_kernel_class kc, int max_launches) {
+  if (!s || kc < HZ_KC_NONE || kc > HZ_KC_MAXPY || max_launches < 0)
+    return HZ_INVALID_ARG;
+  for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
+  s->prof_ev.clear();
+  s->prof_used = 0;
+  s->prof_dropped = 0;
+  s->prof_kc = HZ_KC_NONE;
+  if (kc == HZ_KC_NONE) return HZ_OK;
+  s->prof_ev.resize(2 * (size_t)max_launches);
+  for (auto& e : s->prof_ev)
+    if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(s, "profile events");
+  cudaMemsetAsync(s->prof_bytes, 0, sizeof(unsigned long long), s->st);
+  s->prof_kc = kc;
+  return cuda_check(s, "profile begin");
+}
+
+hz_status hz_profile_end(hz_solver* s, long long* launches, double* ms_total,
+                         double* alg_bytes) {
+  if (!s || !launches || !ms_total || !alg_bytes) return HZ_INVALID_ARG;
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "profile sync");
+  double ms = 0.0;
+  const size_t pairs = s->prof_used / 2;
+  for (size_t p = 0; p < pairs; ++p) {
+    float t = 0.f;
+    cudaEventElapsedTime(&t, s->prof_ev[2 * p], s->prof_ev[2 * p + 1]);
+    ms += t;
+  }
+  unsigned long long b = 0;
+  cudaMemcpy(&b, s->prof_bytes, sizeof(b), cudaMemcpyDeviceToHost);
+  *launches = (long long)pairs;
+  *ms_total = ms;
+  *alg_bytes = (double)b;
+  const bool complete = s->prof_dropped == 0;
+  hz_profile_begin(s, HZ_KC_NONE, 0);
+  if (!complete) {
+    set_err(s, "profile event pool too small: launches dropped");
+    return HZ_INVALID_ARG;
+  }
+  return cuda_check(s, "profile end");
+}
+
 hz_status hz_destroy(hz_solver* s) {
+  if (s) hz_profile_begin(s, HZ_KC_NONE, 0);
   delete s;
   return HZ_OK;
 }
