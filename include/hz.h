@@ -173,6 +173,43 @@ hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev,
 /* Releases the host handle (the workspace stays the caller's). */
 hz_status hz_destroy(hz_solver* s);
 
+/* Size of the fixed device scratch array used by
+ * hz_coarse_galerkin_noalloc (32 MiB). */
+#define HZ_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+
+/* y = (Z^T / 4) A_h Z x, the straightforward Galerkin coarse operator (the
+ * same result as hz_apply with HZ_OP_COARSE_E on an FP64 solver set up with
+ * HZ_E_GALERKIN), for callers that cannot allocate device memory: services
+ * whose device-memory budget is fixed when they start, plug-ins running
+ * inside a host framework that owns all device memory, and latency-critical
+ * loops that must not block in an allocator.  The paper has no counterpart;
+ * this entry point exists only for such callers.
+ *
+ * Nothing is allocated: the two fine-grid intermediates live in one
+ * library-owned device array of HZ_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until the process exits.  The caller still
+ * passes the inputs and the output:
+ *   nx, ny      fine grid nodes (odd, >= 5); the coarse grid has
+ *               ((nx+1)/2) x ((ny+1)/2) nodes
+ *   h           fine spacing; bc, zkind (HZ_Z_BILINEAR or HZ_Z_HO)
+ *   k2_dev      device FP64 [ny][nx] squared wavenumber of the fine grid
+ *   x_dev/y_dev device complex128 [nrhs][ncy][ncx] coarse vectors
+ *   cuda_stream cudaStream_t the work is issued on (NULL = default stream)
+ * Returns HZ_WORKSPACE_TOO_SMALL when 2 * nrhs * nx * ny * 16 bytes exceed
+ * HZ_NOALLOC_SCRATCH_BYTES (no work is issued), HZ_INVALID_ARG for bad
+ * arguments, HZ_CUDA_ERROR if a launch fails.
+ *
+ * The first call on each device looks up the array's device address with
+ * cudaGetSymbolAddress (with that device current); make that first call
+ * before any stream capture begins.  All calls share the one array: calls
+ * whose work overlaps on the GPU (other streams, other threads) race and
+ * must be serialised by the caller.  No state carries over between calls:
+ * every scratch entry read is written by the same call first. */
+hz_status hz_coarse_galerkin_noalloc(int nx, int ny, double h, hz_bc bc,
+                                     hz_zkind zkind, const double* k2_dev,
+                                     const void* x_dev, void* y_dev, int nrhs,
+                                     void* cuda_stream);
+
 /* Kernel classes that hz_profile_* can time: the multi-vector dot product
  * and the multi-vector update of the Gram-Schmidt step (Alg. 1 inner loop),
  * which carry the basis traffic of both Krylov solvers. */

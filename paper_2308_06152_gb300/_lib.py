@@ -52,6 +52,9 @@ SIGNATURES = {
     "hz_gradient": (c_int, [c_void_p, c_double, c_void_p, c_int, c_void_p,
                             c_int, c_void_p, c_double, c_void_p, c_void_p,
                             c_void_p]),
+    "hz_coarse_galerkin_noalloc": (c_int, [c_int, c_int, c_double, c_int,
+                                           c_int, c_void_p, c_void_p,
+                                           c_void_p, c_int, c_void_p]),
     "hz_destroy": (c_int, [c_void_p]),
     "hz_kernel_launches": (ctypes.c_longlong, []),
     "hz_profile_begin": (c_int, [c_void_p, c_int, c_int]),

@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhz.so")
-SOURCES = ["hz_stencil.cu", "hz_krylov.cu", "hz_gradient.cu", "hz_solver.cu"]
+SOURCES = ["hz_stencil.cu", "hz_krylov.cu", "hz_gradient.cu", "hz_solver.cu",
+           "hz_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
