@@ -49,6 +49,12 @@ WORKLOADS = {
                               nrhs=16, sources="centre_cluster",
                               coarse_tol=1e-1, coarse_maxit=200,
                               outer_maxit=60, tol=1e-6),
+    # small case for ncu captures (about 2.5 GB of workspace)
+    "mp2b_641_k400_b8_prof": dict(model=("constant_k", 641, 400.0),
+                                  bc="sommerfeld", z="ho", e="galerkin",
+                                  nrhs=8, sources="centre_cluster",
+                                  coarse_tol=1e-1, coarse_maxit=120,
+                                  outer_maxit=16, tol=1e-6),
     "mp2a_81_k50": dict(model=("constant_k", 81, 50.0), bc="dirichlet",
                         z="bilinear", e="galerkin", nrhs=1,
                         sources="centre", coarse_tol=1e-6,
@@ -57,7 +63,7 @@ WORKLOADS = {
 DEFAULT_WORKLOAD = "mp2b_1281_k800_b16"
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_bench_counts.json")
 ORACLE_COUNT_KEY = {"mp2b_1281_k800_b16": "mp2b_1281_k800",
-                    "mp2b_641_k400_b16": None, "mp2a_81_k50": "mp2a_81_k50"}
+                    "mp2a_81_k50": "mp2a_81_k50"}
 
 
 def build_inputs(wl_name, rank=0):

@@ -80,8 +80,10 @@ typedef struct {
   double jacobi_omega;        /* damped Jacobi weight, default 0.8 (Sec. 3.1)*/
   int min_coarse_intervals;   /* coarsening stop rule, default 2 (Sec. 4)    */
   double coarse_tol;          /* inner coarse-solve tolerance (Sec. 6.3)     */
-  int coarse_maxit;           /* inner iteration cap (= its basis size)      */
-  int outer_maxit;            /* outer FGMRES cap (= its basis size)         */
+  int coarse_maxit;           /* inner iteration cap (= its basis size),
+                                 1..3000                                    */
+  int outer_maxit;            /* outer FGMRES cap (= its basis size),
+                                 1..3000                                    */
   int nrhs_max;               /* right-hand sides per hz_solve call          */
 } hz_desc;
 

@@ -238,20 +238,26 @@ struct KState {
   double2* hcol;    // [nrhs_max][m+1] scratch column (one CGS pass)
   double2* part;    // partial sums [nrhs_max][m+1][nblk_max]
   double* npart;    // partial squared norms [nrhs_max][nblk_max]
+  double* wpart;    // partial ||w||^2 before projection [nrhs_max][nblk_max]
+  int* reorth;      // second Gram-Schmidt pass needed [nrhs_max]
   unsigned long long* abytes;  // [1] algorithmic-byte counter or null
   int m;            // basis size (max iterations)
   int nblk_max;
 };
 
 int krylov_nblk(long long n);
+// classical Gram-Schmidt pass `pass` (0, or 1 = re-orthogonalisation for
+// the RHS flagged by launch_reorth_decide)
 template <class T>
 void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
-                 int nrhs, const KState& ks, cudaStream_t st);
-void launch_reduce_cols(const KState& ks, long long n, int nrhs, int accumulate,
+                 int nrhs, const KState& ks, int pass, cudaStream_t st);
+void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st);
 template <class T>
 void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
-                  int nrhs, const KState& ks, cudaStream_t st);
+                  int nrhs, const KState& ks, int pass, cudaStream_t st);
+void launch_reorth_decide(const KState& ks, long long n, int nrhs, double eta,
+                          cudaStream_t st);
 template <class T>
 void launch_norm2_part(VRef<T> w, long long n, int nrhs, const KState& ks,
                        const int* done, cudaStream_t st);

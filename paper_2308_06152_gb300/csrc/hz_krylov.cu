@@ -11,7 +11,7 @@ namespace hz {
 namespace {
 
 constexpr int NT = 256;   // threads per block
-constexpr int EPT = 4;    // elements per thread
+constexpr int EPT = 8;    // elements per thread
 constexpr int CHUNK = NT * EPT;
 
 template <class T> __device__ __forceinline__ C<T> cvt_to(double2 v);
@@ -33,15 +33,31 @@ __device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
   return v;
 }
 
-// part[r][i][blk] = sum_{e in blk} conj(V_i[e]) * w[e],  i = 0..j
+// Block-wide sum of a double held by every thread (result valid in thread 0).
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < (int)(blockDim.x / 32); ++q) t += red[q];
+  __syncthreads();
+  return t;
+}
+
+// Pass `pass` (0 or 1) of classical Gram-Schmidt: partial dot products
+// part[r][i][blk] = sum_{e in blk} conj(V_i[e]) w[e], i = 0..j.  Pass 0 also
+// stores the partial ||w||^2 in wpart; pass 1 runs only for the RHS whose
+// reorth flag the first pass raised.
 template <class T>
 __global__ void __launch_bounds__(NT)
 k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w,
-       long long n, KState ks) {
-  constexpr int G = 4;
-  __shared__ double2 red[NT / 32][G];
+       long long n, KState ks, int pass) {
+  constexpr int G = 4, TILE = 32, NW = NT / 32;
+  __shared__ double2 wred[NW][TILE];
+  __shared__ double red[NW];
   const int r = blockIdx.y, blk = blockIdx.x;
-  if (ks.done[r]) return;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   const int j = *ks.jctr;
   // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
@@ -49,58 +65,65 @@ k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w
   const long long base = (long long)blk * CHUNK + threadIdx.x;
   const C<T>* wr = w + r * n;
   C<T> wv[EPT];
+  T wn = T(0);
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const long long e = base + k * NT;
     wv[k] = (e < n) ? wr[e] : czero<T>();
+    wn += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
+  }
+  if (pass == 0) {
+    const double t = block_sum((double)wn, red);
+    if (threadIdx.x == 0) ks.wpart[(long long)r * ks.nblk_max + blk] = t;
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int i0 = 0; i0 <= j; i0 += G) {
-    C<T> d[G];
+  for (int t0 = 0; t0 <= j; t0 += TILE) {
+    const int tend = min(t0 + TILE, j + 1);
+    for (int i0 = t0; i0 < tend; i0 += G) {
+      C<T> d[G];
 #pragma unroll
-    for (int q = 0; q < G; ++q) {
-      d[q] = czero<T>();
-      const int i = i0 + q;
-      if (i <= j) {
-        const C<T>* vr = V + (long long)i * vstride + r * n;
+      for (int q = 0; q < G; ++q) {
+        d[q] = czero<T>();
+        const int i = i0 + q;
+        if (i < tend) {
+          const C<T>* vr = V + (long long)i * vstride + r * n;
 #pragma unroll
-        for (int k = 0; k < EPT; ++k) {
-          const long long e = base + k * NT;
-          if (e < n) {
-            const C<T> v = vr[e];
-            d[q].x += v.x * wv[k].x + v.y * wv[k].y;
-            d[q].y += v.x * wv[k].y - v.y * wv[k].x;
+          for (int k = 0; k < EPT; ++k) {
+            const long long e = base + k * NT;
+            if (e < n) {
+              const C<T> v = vr[e];
+              d[q].x += v.x * wv[k].x + v.y * wv[k].y;
+              d[q].y += v.x * wv[k].y - v.y * wv[k].x;
+            }
           }
         }
-      }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const C<T> t = shfl_down2(d[q], o);
-        d[q].x += t.x;
-        d[q].y += t.y;
+        for (int o = 16; o > 0; o >>= 1) {
+          const C<T> t = shfl_down2(d[q], o);
+          d[q].x += t.x;
+          d[q].y += t.y;
+        }
+        if (lane == 0 && i0 + q < tend) wred[warp][i0 + q - t0] = wide(d[q]);
       }
-    }
-    if (lane == 0) {
-#pragma unroll
-      for (int q = 0; q < G; ++q) red[warp][q] = wide(d[q]);
     }
     __syncthreads();
-    if (threadIdx.x < G && i0 + threadIdx.x <= j) {
-      double2 s = make_double2(0.0, 0.0);
-      for (int q = 0; q < NT / 32; ++q) {
-        s.x += red[q][threadIdx.x].x;
-        s.y += red[q][threadIdx.x].y;
+    if (threadIdx.x < tend - t0) {
+      double2 sum = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int q = 0; q < NW; ++q) {
+        sum.x += wred[q][threadIdx.x].x;
+        sum.y += wred[q][threadIdx.x].y;
       }
-      ks.part[((long long)r * (ks.m + 1) + i0 + threadIdx.x) * ks.nblk_max + blk] = s;
+      ks.part[((long long)r * (ks.m + 1) + t0 + threadIdx.x) * ks.nblk_max + blk] = sum;
     }
     __syncthreads();
   }
 }
 
-// hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] (+)= hcol[r][i]
-__global__ void k_reduce_cols(KState ks, int nblk, int accumulate) {
+// hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] = (pass 0) or += (pass 1)
+__global__ void k_reduce_cols(KState ks, int nblk, int pass) {
   const int r = blockIdx.y;
-  if (ks.done[r]) return;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   const int j = *ks.jctr;
   const int i = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -119,7 +142,7 @@ __global__ void k_reduce_cols(KState ks, int nblk, int accumulate) {
   if (lane == 0) {
     ks.hcol[(long long)r * (ks.m + 1) + i] = s;
     double2* hp = ks.H + ((long long)r * (ks.m + 1) + i) * ks.m + j;
-    if (accumulate) {
+    if (pass) {
       double2 t = *hp;
       t.x += s.x;
       t.y += s.y;
@@ -130,15 +153,16 @@ __global__ void k_reduce_cols(KState ks, int nblk, int accumulate) {
   }
 }
 
-// w -= sum_{i<=j} V_i hcol_i
+// w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
 template <class T>
 __global__ void __launch_bounds__(NT)
 k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
-        long long n, KState ks) {
+        long long n, KState ks, int pass) {
   constexpr int TILE = 512;
   __shared__ C<T> hs[TILE];
+  __shared__ double red[NT / 32];
   const int r = blockIdx.y;
-  if (ks.done[r]) return;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   const int j = *ks.jctr;
   // algorithmic bytes of this RHS: read w and basis 0..j, write w
   if (ks.abytes && blockIdx.x == 0 && threadIdx.x == 0)
@@ -171,10 +195,40 @@ k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
       }
     }
   }
+  T wn = T(0);
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const long long e = base + k * NT;
-    if (e < n) wr[e] = acc[k];
+    if (e < n) {
+      wr[e] = acc[k];
+      wn += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+    }
+  }
+  const double t = block_sum((double)wn, red);
+  if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blockIdx.x] = t;
+}
+
+// After the first pass: ||w|| (wpart) and ||w - V h|| (npart) per RHS; the
+// second pass runs only where the first cancelled more than a factor 1/eta
+// (Kahan-Parlett "twice is enough" test).  hnorm = ||w - V h||.
+__global__ void k_reorth_decide(KState ks, int nblk, double eta) {
+  __shared__ double red[32];
+  const int r = blockIdx.x;
+  if (ks.done[r]) {
+    if (threadIdx.x == 0) ks.reorth[r] = 0;
+    return;
+  }
+  double a = 0.0, b = 0.0;
+  for (int q = threadIdx.x; q < nblk; q += blockDim.x) {
+    a += ks.wpart[(long long)r * ks.nblk_max + q];
+    b += ks.npart[(long long)r * ks.nblk_max + q];
+  }
+  a = block_sum(a, red);
+  b = block_sum(b, red);
+  if (threadIdx.x == 0) {
+    const double nw = sqrt(a), nw1 = sqrt(b);
+    ks.hnorm[r] = nw1;
+    ks.reorth[r] = (nw1 < eta * nw) ? 1 : 0;
   }
 }
 
@@ -271,74 +325,83 @@ __global__ void k_scale_into(VRef<T> w, VRef<T> out, const double* __restrict__ 
 // Apply the previous rotations to column j, build the rotation that
 // annihilates h_{j+1,j}, update the least-squares right-hand side g and
 // decide convergence (|g_{j+1}| <= tol ||b||), breakdown, NaN or the cap.
-__global__ void k_givens(KState ks, int nrhs, double tol, int maxit) {
-  const int r = threadIdx.x;
+// One block per RHS: the column is staged in shared memory so the
+// sequential rotation chain runs out of shared memory, not DRAM.
+__global__ void k_givens(KState ks, double tol, int maxit) {
+  extern __shared__ unsigned char smraw[];
+  double2* col = reinterpret_cast<double2*>(smraw);   // j + 2 entries
+  const int r = blockIdx.x;
+  if (ks.done[r]) return;
   const int j = *ks.jctr;
-  int d = 1;
-  if (r < nrhs) {
-    d = ks.done[r];
-    if (!d) {
-      const int m = ks.m;
-      double2* Hc = ks.H + (long long)r * (m + 1) * m + j;   // H[r][i][j] = Hc[i*m]
-      double* cs = ks.cs + (long long)r * m;
-      double2* sn = ks.sn + (long long)r * m;
-      double2* g = ks.g + (long long)r * (m + 1);
-      for (int i = 0; i < j; ++i) {
-        const double2 a = Hc[(long long)i * m], b = Hc[(long long)(i + 1) * m];
-        const double c = cs[i];
-        const double2 s = sn[i];
-        // t = c a + s b ; b' = -conj(s) a + c b
-        const double2 t = make_double2(c * a.x + (s.x * b.x - s.y * b.y),
-                                       c * a.y + (s.x * b.y + s.y * b.x));
-        const double2 bb = make_double2(-(s.x * a.x + s.y * a.y) + c * b.x,
-                                        -(s.x * a.y - s.y * a.x) + c * b.y);
-        Hc[(long long)i * m] = t;
-        Hc[(long long)(i + 1) * m] = bb;
-      }
-      const double2 a = Hc[(long long)j * m];
-      const double hb = ks.hnorm[r];
-      const double am = sqrt(a.x * a.x + a.y * a.y);
-      double c;
-      double2 s;
-      if (hb == 0.0) {
-        c = 1.0;
-        s = make_double2(0.0, 0.0);
-      } else if (am == 0.0) {
-        c = 0.0;
-        s = make_double2(1.0, 0.0);
-      } else {
-        const double t = sqrt(am * am + hb * hb);
-        c = am / t;
-        s = make_double2(a.x / am * hb / t, a.y / am * hb / t);
-      }
-      cs[j] = c;
-      sn[j] = s;
-      Hc[(long long)j * m] = make_double2(c * a.x + s.x * hb, c * a.y + s.y * hb);
-      Hc[(long long)(j + 1) * m] = make_double2(0.0, 0.0);
-      const double2 gj = g[j];
-      g[j + 1] = make_double2(-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x));
-      g[j] = make_double2(c * gj.x, c * gj.y);
-      const double res = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
-      ks.iters[r] = j + 1;
-      if (!isfinite(res) || !isfinite(hb)) {
-        d = 1;
-        ks.stat[r] = ST_NAN;
-      } else if (res <= tol * ks.bnorm[r]) {
-        d = 1;
-      } else if (hb == 0.0) {
-        d = 1;
-        ks.stat[r] = ST_BREAKDOWN;
-      } else if (j + 1 >= maxit) {
-        d = 1;
-        ks.stat[r] = ST_NOT_CONVERGED;
-      }
-      ks.done[r] = d;
-    }
+  const int m = ks.m;
+  double2* Hc = ks.H + (long long)r * (m + 1) * m + j;  // H[r][i][j] = Hc[i*m]
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = Hc[(long long)i * m];
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double* cs = ks.cs + (long long)r * m;
+  const double2* sn = ks.sn + (long long)r * m;
+  double2 a = col[0];
+  for (int i = 0; i < j; ++i) {
+    const double2 b = col[i + 1];
+    const double c = cs[i];
+    const double2 sv = sn[i];
+    // t = c a + s b ; b' = -conj(s) a + c b
+    col[i] = make_double2(c * a.x + (sv.x * b.x - sv.y * b.y),
+                          c * a.y + (sv.x * b.y + sv.y * b.x));
+    a = make_double2(-(sv.x * a.x + sv.y * a.y) + c * b.x,
+                     -(sv.x * a.y - sv.y * a.x) + c * b.y);
   }
+  const double hb = ks.hnorm[r];
+  const double am = sqrt(a.x * a.x + a.y * a.y);
+  double c;
+  double2 sv;
+  if (hb == 0.0) {
+    c = 1.0;
+    sv = make_double2(0.0, 0.0);
+  } else if (am == 0.0) {
+    c = 0.0;
+    sv = make_double2(1.0, 0.0);
+  } else {
+    const double t = sqrt(am * am + hb * hb);
+    c = am / t;
+    sv = make_double2(a.x / am * hb / t, a.y / am * hb / t);
+  }
+  ks.cs[(long long)r * m + j] = c;
+  ks.sn[(long long)r * m + j] = sv;
+  col[j] = make_double2(c * a.x + sv.x * hb, c * a.y + sv.y * hb);
+  for (int i = 0; i <= j; ++i) Hc[(long long)i * m] = col[i];
+  Hc[(long long)(j + 1) * m] = make_double2(0.0, 0.0);
+  double2* g = ks.g + (long long)r * (m + 1);
+  const double2 gj = g[j];
+  const double2 g1 = make_double2(-(sv.x * gj.x + sv.y * gj.y), -(sv.x * gj.y - sv.y * gj.x));
+  g[j + 1] = g1;
+  g[j] = make_double2(c * gj.x, c * gj.y);
+  const double res = sqrt(g1.x * g1.x + g1.y * g1.y);
+  ks.iters[r] = j + 1;
+  int d = 0;
+  if (!isfinite(res) || !isfinite(hb)) {
+    d = 1;
+    ks.stat[r] = ST_NAN;
+  } else if (res <= tol * ks.bnorm[r]) {
+    d = 1;
+  } else if (hb == 0.0) {
+    d = 1;
+    ks.stat[r] = ST_BREAKDOWN;
+  } else if (j + 1 >= maxit) {
+    d = 1;
+    ks.stat[r] = ST_NOT_CONVERGED;
+  }
+  ks.done[r] = d;
+}
+
+// All RHS done?  Otherwise advance the Arnoldi column counter.
+__global__ void k_givens_finish(KState ks, int nrhs) {
+  const int r = threadIdx.x;
+  const int d = (r < nrhs) ? ks.done[r] : 1;
   const int all = __syncthreads_and(d);
   if (r == 0) {
     *ks.alldone = all;
-    if (!all) *ks.jctr = j + 1;
+    if (!all) *ks.jctr = *ks.jctr + 1;
   }
 }
 
@@ -424,22 +487,27 @@ int krylov_nblk(long long n) { return (int)((n + CHUNK - 1) / CHUNK); }
 
 template <class T>
 void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
-                 int nrhs, const KState& ks, cudaStream_t st) {
+                 int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_mdot<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks);
+  k_mdot<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks, pass);
 }
-void launch_reduce_cols(const KState& ks, long long n, int nrhs, int accumulate,
+void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st) {
   HZ_COUNT();
   const int wpb = NT / 32;
   k_reduce_cols<<<dim3((ks.m + 1 + wpb - 1) / wpb, nrhs), NT, 0, st>>>(
-      ks, krylov_nblk(n), accumulate);
+      ks, krylov_nblk(n), pass);
 }
 template <class T>
 void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
-                  int nrhs, const KState& ks, cudaStream_t st) {
+                  int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_maxpy<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks);
+  k_maxpy<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks, pass);
+}
+void launch_reorth_decide(const KState& ks, long long n, int nrhs, double eta,
+                          cudaStream_t st) {
+  HZ_COUNT();
+  k_reorth_decide<<<nrhs, NT, 0, st>>>(ks, krylov_nblk(n), eta);
 }
 template <class T>
 void launch_norm2_part(VRef<T> w, long long n, int nrhs, const KState& ks,
@@ -470,7 +538,9 @@ void launch_scale_into(VRef<T> w, VRef<T> out, const double* s, long long n,
 void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
                    cudaStream_t st) {
   HZ_COUNT();
-  k_givens<<<1, 1024, 0, st>>>(ks, nrhs, tol, maxit);
+  k_givens<<<nrhs, 128, (size_t)(ks.m + 2) * sizeof(double2), st>>>(ks, tol, maxit);
+  HZ_COUNT();
+  k_givens_finish<<<1, 1024, 0, st>>>(ks, nrhs);
 }
 void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st) {
   HZ_COUNT();
@@ -495,9 +565,9 @@ void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
 
 #define HZ_KINST(T)                                                            \
   template void launch_mdot<T>(const C<T>*, long long, const C<T>*, long long, \
-                               int, const KState&, cudaStream_t);              \
+                               int, const KState&, int, cudaStream_t);         \
   template void launch_maxpy<T>(const C<T>*, long long, C<T>*, long long, int, \
-                                const KState&, cudaStream_t);                  \
+                                const KState&, int, cudaStream_t);             \
   template void launch_norm2_part<T>(VRef<T>, long long, int, const KState&,   \
                                      const int*, cudaStream_t);                \
   template void launch_scale_into<T>(VRef<T>, VRef<T>, const double*,          \

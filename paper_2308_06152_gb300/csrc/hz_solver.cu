@@ -34,6 +34,7 @@ namespace {
 constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarsest = 1024;
 constexpr int kMaxRhs = 1024;
+constexpr int kMaxIters = 3000;   // Krylov basis size (Givens column in smem)
 
 struct LevelHost {
   int nx = 0, ny = 0;
@@ -84,7 +85,11 @@ bool valid_desc(const hz_desc* d, std::string* why) {
   if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_GLK2) { *why = "bad ekind"; return false; }
   if (d->prec != HZ_PREC_FP64 && d->prec != HZ_PREC_MIXED_FP32) { *why = "bad prec"; return false; }
   if (d->nrhs_max < 1 || d->nrhs_max > kMaxRhs) { *why = "nrhs_max must be in 1..1024"; return false; }
-  if (d->outer_maxit < 1 || d->coarse_maxit < 1) { *why = "iteration caps must be >= 1"; return false; }
+  if (d->outer_maxit < 1 || d->coarse_maxit < 1 || d->outer_maxit > kMaxIters ||
+      d->coarse_maxit > kMaxIters) {
+    *why = "iteration caps must be in 1..3000";
+    return false;
+  }
   if (d->min_coarse_intervals < 1) { *why = "min_coarse_intervals must be >= 1"; return false; }
   if (!(d->jacobi_omega > 0)) { *why = "jacobi_omega must be positive"; return false; }
   return true;
@@ -181,6 +186,8 @@ KState plan_kstate(Arena& a, int B, int m, long long n) {
   k.hcol = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1));
   k.part = (double2*)a.take(sizeof(double2) * (size_t)B * (m + 1) * k.nblk_max);
   k.npart = (double*)a.take(sizeof(double) * (size_t)B * k.nblk_max);
+  k.wpart = (double*)a.take(sizeof(double) * (size_t)B * k.nblk_max);
+  k.reorth = (int*)a.take(sizeof(int) * B);
   return k;
 }
 
@@ -378,8 +385,12 @@ inline void prof_mark(hz_solver* s, int kc) {
     ++s->prof_dropped;
 }
 
-// Classical Gram-Schmidt with one re-orthogonalisation (CGS2) of w against
-// basis columns 0..j, then ||w|| into ks.hnorm.
+// Classical Gram-Schmidt of w against basis columns 0..j with a second pass
+// only where the first one cancelled more than a factor 2 (Kahan-Parlett
+// "twice is enough": one pass then keeps the basis orthonormal to working
+// precision); ||w|| of the result lands in ks.hnorm.
+constexpr double kReorthEta = 0.5;
+
 template <class T>
 void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
           long long n, int nrhs) {
@@ -391,15 +402,15 @@ void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
   if (s->prof_kc == HZ_KC_MAXPY) ka.abytes = s->prof_bytes;
   for (int pass = 0; pass < 2; ++pass) {
     prof_mark(s, HZ_KC_MDOT);
-    launch_mdot<T>(V, vs, w, n, nrhs, kd, st);
+    launch_mdot<T>(V, vs, w, n, nrhs, kd, pass, st);
     prof_mark(s, HZ_KC_MDOT);
     launch_reduce_cols(k, n, nrhs, pass, st);
     prof_mark(s, HZ_KC_MAXPY);
-    launch_maxpy<T>(V, vs, w, n, nrhs, ka, st);
+    launch_maxpy<T>(V, vs, w, n, nrhs, ka, pass, st);
     prof_mark(s, HZ_KC_MAXPY);
+    if (pass == 0) launch_reorth_decide(k, n, nrhs, kReorthEta, st);
   }
-  launch_norm2_part<T>(vref<T>(w), n, nrhs, ks, ks.done, st);
-  launch_reduce_norm(ks, n, nrhs, ks.hnorm, 1, st);
+  launch_reduce_norm(k, n, nrhs, k.hnorm, 1, st);
 }
 
 // ------------------------------------------------------------ inner solve
