@@ -66,6 +66,23 @@ ORACLE_COUNT_KEY = {"mp2b_1281_k800_b16": "mp2b_1281_k800",
                     "mp2a_81_k50": "mp2a_81_k50"}
 
 
+def rank_sources(nodes, rank):
+    """Shots of one replica: the workload's source lattice shifted by the
+    rank along x, so that every rank solves different right-hand sides."""
+    return [(i + rank, j) for (i, j) in nodes] if rank else list(nodes)
+
+
+def max_over_ranks(value, world, device="cpu"):
+    """Max of a per-rank float over all ranks (the job's wall time)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def build_inputs(wl_name, rank=0):
     from paper_2308_06152_gb300 import workloads as wl
     cfg = WORKLOADS[wl_name]
@@ -74,9 +91,8 @@ def build_inputs(wl_name, rank=0):
     if cfg["sources"] == "centre":
         nodes = [wl.centre_node(model.nx, model.ny)] * cfg["nrhs"]
     else:
-        nodes = wl.centre_cluster(model.nx, model.ny, cfg["nrhs"])
-        if rank:
-            nodes = [(i + rank, j) for (i, j) in nodes]
+        nodes = rank_sources(wl.centre_cluster(model.nx, model.ny,
+                                               cfg["nrhs"]), rank)
     b = wl.point_sources(model.nx, model.ny, nodes)
     return cfg, model, b
 
@@ -143,6 +159,11 @@ class ClockSampler:
                 "samples": len(rows), "reasons": reasons}
 
 
+PREC_TEXT = {"mixed": "complex-FP32 preconditioner in FP64 FGMRES",
+             "mixed_bf16": ("complex-FP32 preconditioner with BF16-storage "
+                            "V-cycle vectors, in FP64 FGMRES"),
+             "fp64": "complex-FP64 throughout"}
+
 KERNEL_NAMES = {"mdot": "k_mdot (CGS2 multi-vector dot product)",
                 "maxpy": "k_maxpy (CGS2 multi-vector update)"}
 
@@ -174,11 +195,13 @@ def oracle_sample(wl_name, steps, warmup):
     orc = Oracle(model.nx, model.ny, model.h, model.k2, cfg["bc"], z=cfg["z"],
                  e=cfg["e"], coarse_tol=cfg["coarse_tol"],
                  coarse_maxit=cfg["coarse_maxit"])
+    inner_total = counts.get(key, {}).get("inner_iters_total") if key else None
     lv = orc.levels[0]
     bu = lv.to_unknowns(b[0])
     v = bu / np.linalg.norm(bu)
-    times = []
+    times, inner = [], []
     for it in range(warmup + steps):
+        orc.inner_log = []
         t0 = time.perf_counter()
         z = orc.adef1(v)
         w = orc.A @ z
@@ -187,17 +210,24 @@ def oracle_sample(wl_name, steps, warmup):
         dt = time.perf_counter() - t0
         if it >= warmup:
             times.append(dt)
+            inner.append(sum(orc.inner_log) or 1)
     t_iter = float(np.mean(times))
     n_unk = unknowns(cfg, model)
-    if outer:
-        value = n_unk / (t_iter * outer)
-    else:
-        value = None
+    value = None
+    how = "no recorded oracle iteration counts for this workload"
+    if outer and inner_total:
+        # full solve ~ outer iterations, each costing the sample's time per
+        # inner iteration times the inner iterations it needs on average
+        t_inner = t_iter / float(np.mean(inner))
+        t_full = t_inner * inner_total
+        value = n_unk / t_full
+        how = (f"scaled to the oracle's {outer} outer / {inner_total} inner "
+               f"iterations for a full solve ({t_full:.0f} s)")
     return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one outer FGMRES iteration (A-DEF1 incl. inner "
-                       f"coarse solve) of 1 RHS of {wl_name}, "
-                       f"{t_iter:.2f} s mean over {len(times)}, scaled by the "
-                       f"oracle's {outer} outer iterations for a full solve")}
+            "sample": (f"one outer FGMRES iteration (A-DEF1 with its "
+                       f"{int(np.mean(inner))}-iteration inner coarse solve) "
+                       f"of 1 RHS of {wl_name}, {t_iter:.2f} s mean over "
+                       f"{len(times)}; {how}")}
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -219,7 +249,8 @@ def run_ours(args):
     desc = Desc(model.nx, model.ny, model.h, bc=cfg["bc"], z=cfg["z"],
                 e=cfg["e"], prec=args.prec, nrhs_max=cfg["nrhs"],
                 coarse_tol=cfg["coarse_tol"], coarse_maxit=cfg["coarse_maxit"],
-                outer_maxit=cfg["outer_maxit"])
+                outer_maxit=cfg["outer_maxit"],
+                inner_basis_fp16=bool(args.basis16))
     solver = Solver(desc, model.k2)
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
@@ -252,11 +283,8 @@ def run_ours(args):
     launches = lib.hz_kernel_launches() - l0
     prof = solver.profile_end() if args.profile_kernel != "none" else None
     clocks = sampler.stop()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     n_unk = unknowns(cfg, model)
     units = n_unk * cfg["nrhs"] * world
@@ -273,11 +301,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         solver.solve_host(bh, xh, tol=tol)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world,
+                           "cuda")
     io_bytes = int(b_np.nbytes)
 
     roof = None
@@ -293,6 +318,30 @@ def run_ours(args):
                 "avg_launch_us": 1e3 * ms_k / n_l,
                 "share_of_step": ms_k / (ms * args.steps)}
 
+    fp64 = None
+    if args.compare_fp64 and args.prec != "fp64":
+        # the same workload with the preconditioner in FP64 (one timed solve)
+        solver.close()
+        del solver
+        torch.cuda.synchronize()
+        import dataclasses
+        s64 = Solver(dataclasses.replace(desc, prec="fp64",
+                                         inner_basis_fp16=False), model.k2)
+        s64.solve(b, tol=tol)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s64.stream)
+        _, info64 = s64.solve(b, tol=tol)
+        e1.record(s64.stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": units / (ms64 / 1e3), "unit": UNIT,
+                "ms_per_step": ms64, "steps": 1, "warmup": 1,
+                "outer_iters": [i.outer_iters for i in info64],
+                "max_true_relres": max(i.relres for i in info64),
+                "mixed_over_fp64": value / (units / (ms64 / 1e3))}
+        s64.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(args.workload, steps=1, warmup=0)
@@ -302,14 +351,16 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "c64" if args.prec == "mixed" else "c128",
+            "dtype": "c128" if args.prec == "fp64" else "c64",
             "data": "synthetic",
             "config": {"workload": args.workload, "grid": [model.nx, model.ny],
                        "k": cfg["model"][2], "bc": cfg["bc"],
                        "deflation": f"{cfg['z']}/{cfg['e']}",
-                       "precision": ("complex-FP32 preconditioner in FP64 "
-                                     "FGMRES" if args.prec == "mixed"
-                                     else "complex-FP64 throughout"),
+                       "precision": PREC_TEXT[args.prec],
+                       "inner_basis_storage": ("fp16" if args.basis16 and
+                                               args.prec != "fp64" else
+                                               ("c64" if args.prec != "fp64"
+                                                else "c128")),
                        "nrhs_per_gpu": cfg["nrhs"], "tol": tol,
                        "coarse_tol": cfg["coarse_tol"],
                        "parallelism": f"replicas{world}",
@@ -322,6 +373,7 @@ def run_ours(args):
             "clocks": clocks,
             "roofline": roof,
             "cpu_baseline": cpu,
+            "fp64": fp64,
             "solve": {"outer_iters": outer, "inner_iters_total": inner,
                       "max_true_relres": worst, "status": statuses},
         }
@@ -357,9 +409,14 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS))
-    ap.add_argument("--prec", choices=["mixed", "fp64"], default="mixed")
+    ap.add_argument("--prec", choices=["mixed", "mixed_bf16", "fp64"],
+                    default="mixed")
+    ap.add_argument("--basis16", type=int, default=0,
+                    help="store the inner coarse-solve Krylov basis as FP16")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU oracle baseline sample")
+    ap.add_argument("--compare-fp64", type=int, default=1,
+                    help="also time one solve with the FP64 preconditioner")
     ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],
                     default="mdot",
                     help="kernel class timed live for the roofline entry")

@@ -64,8 +64,13 @@ typedef enum {
 
 /* Arithmetic of the preconditioner (V-cycle, deflation, inner coarse
  * solve).  The outer flexible GMRES, its Arnoldi process, Givens updates,
- * residuals and solution update are always complex FP64. */
-typedef enum { HZ_PREC_FP64 = 0, HZ_PREC_MIXED_FP32 = 1 } hz_precision;
+ * residuals and solution update are always complex FP64.
+ * HZ_PREC_MIXED_BF16 is HZ_PREC_MIXED_FP32 with the vectors of the V-cycle
+ * hierarchy (level right-hand sides, iterates and smoothed iterates) stored
+ * as BF16 pairs; the V-cycle's input and output and all arithmetic stay FP32. */
+typedef enum {
+  HZ_PREC_FP64 = 0, HZ_PREC_MIXED_FP32 = 1, HZ_PREC_MIXED_BF16 = 2
+} hz_precision;
 
 typedef struct {
   int nx, ny;                 /* nodes; each >= 3                            */
@@ -85,6 +90,9 @@ typedef struct {
   int outer_maxit;            /* outer FGMRES cap (= its basis size),
                                  1..3000                                    */
   int nrhs_max;               /* right-hand sides per hz_solve call          */
+  int inner_basis_fp16;       /* mixed precisions only: store the inner
+                                 coarse-solve Krylov basis as FP16 pairs
+                                 (arithmetic stays FP32); 0 = FP32 basis   */
 } hz_desc;
 
 typedef struct {

@@ -21,7 +21,8 @@ class HzDesc(ctypes.Structure):
                 ("prec", c_int), ("beta1", c_double), ("beta2", c_double),
                 ("jacobi_omega", c_double), ("min_coarse_intervals", c_int),
                 ("coarse_tol", c_double), ("coarse_maxit", c_int),
-                ("outer_maxit", c_int), ("nrhs_max", c_int)]
+                ("outer_maxit", c_int), ("nrhs_max", c_int),
+                ("inner_basis_fp16", c_int)]
 
 
 class HzSolveInfo(ctypes.Structure):

@@ -15,7 +15,7 @@ from ._lib import HzDesc, HzSolveInfo, STATUS, load_library
 BC = {"dirichlet": 0, "sommerfeld": 1}
 ZKIND = {None: 0, "none": 0, "bilinear": 1, "ho": 2}
 EKIND = {"galerkin": 0, "red_o2": 1, "red_glk1": 2, "red_glk2": 3}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "mixed_bf16": 2}
 OPS = {"helmholtz": 0, "cslp": 1, "vcycle": 2, "restrict_fw": 3,
        "prolong_bilinear": 4, "restrict_z": 5, "prolong_z": 6, "coarse_e": 7,
        "coarse_solve": 8, "precond": 9}
@@ -48,6 +48,7 @@ class Desc:
     coarse_maxit: int = 500
     outer_maxit: int = 100
     nrhs_max: int = 1
+    inner_basis_fp16: bool = False
 
     def to_c(self):
         d = HzDesc()
@@ -63,6 +64,7 @@ class Desc:
         d.coarse_maxit = int(self.coarse_maxit)
         d.outer_maxit = int(self.outer_maxit)
         d.nrhs_max = int(self.nrhs_max)
+        d.inner_basis_fp16 = int(bool(self.inner_basis_fp16))
         return d
 
 

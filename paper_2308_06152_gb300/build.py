@@ -20,8 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libhz.so")
-SOURCES = ["hz_stencil.cu", "hz_krylov.cu", "hz_gradient.cu", "hz_solver.cu",
-           "hz_noalloc.cu"]
+SOURCES = ["hz_stencil.cu", "hz_vcycle.cu", "hz_krylov.cu", "hz_gradient.cu",
+           "hz_solver.cu", "hz_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
@@ -79,7 +79,8 @@ def build(verbose=False, force=False, extra_flags=()):
             if rc != 0:
                 raise RuntimeError(f"nvcc failed on {src}:\n{out}")
     if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs]
+        cmd = [nvcc, *ARCH, "-shared", "-Xlinker", "--no-undefined", "-o", LIB,
+               *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         p = subprocess.run(cmd, capture_output=True, text=True)

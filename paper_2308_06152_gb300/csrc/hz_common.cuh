@@ -2,6 +2,7 @@
 // libhz.so.  Complex numbers are double2 / float2 (x = real, y = imag).
 #pragma once
 
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -120,31 +121,51 @@ template <> __device__ __forceinline__ const float2* dinv_of<float>(const LevelD
 // A vector argument whose base may be indexed by a device-side counter:
 // the vector used is base + (*jidx + jofs) * jstride (jidx may be null).
 // Lets one launch configuration serve every iteration of a Krylov loop.
-template <class T> struct VRef {
-  C<T>* base;
+// E is the stored element type (double2, float2 or __half2).
+template <class E> struct VRefE {
+  E* base;
   const int* jidx;
   int jofs;
   long long jstride;
-  __device__ __forceinline__ C<T>* get() const {
+  __device__ __forceinline__ E* get() const {
     return jidx ? base + (long long)(*jidx + jofs) * jstride : base;
   }
 };
-template <class T> inline VRef<T> vref(const void* p) {
-  VRef<T> r;
-  r.base = (C<T>*)p;
+template <class T> using VRef = VRefE<C<T>>;
+template <class E> inline VRefE<E> vrefe(const void* p) {
+  VRefE<E> r;
+  r.base = (E*)p;
   r.jidx = nullptr;
   r.jofs = 0;
   r.jstride = 0;
   return r;
 }
-template <class T>
-inline VRef<T> vref_j(const void* p, const int* jidx, int jofs, long long stride) {
-  VRef<T> r;
-  r.base = (C<T>*)p;
+template <class E>
+inline VRefE<E> vrefe_j(const void* p, const int* jidx, int jofs, long long stride) {
+  VRefE<E> r;
+  r.base = (E*)p;
   r.jidx = jidx;
   r.jofs = jofs;
   r.jstride = stride;
   return r;
+}
+template <class T> inline VRef<T> vref(const void* p) { return vrefe<C<T>>(p); }
+template <class T>
+inline VRef<T> vref_j(const void* p, const int* jidx, int jofs, long long stride) {
+  return vrefe_j<C<T>>(p, jidx, jofs, stride);
+}
+
+// Loads and stores of a complex value kept in storage type E, computed in
+// the matching double2 / float2 (an FP16 pair is computed in FP32).
+__device__ __forceinline__ double2 ld2(const double2* p, long long i) { return p[i]; }
+__device__ __forceinline__ float2 ld2(const float2* p, long long i) { return p[i]; }
+__device__ __forceinline__ float2 ld2(const __half2* p, long long i) {
+  return __half22float2(p[i]);
+}
+__device__ __forceinline__ void st2(double2* p, long long i, double2 v) { p[i] = v; }
+__device__ __forceinline__ void st2(float2* p, long long i, float2 v) { p[i] = v; }
+__device__ __forceinline__ void st2(__half2* p, long long i, float2 v) {
+  p[i] = __float22half2_rn(v);
 }
 
 // ---------------------------------------------------------------------
@@ -159,25 +180,31 @@ struct Shift {
 template <class T>
 void launch_helm(const LevelDev& L, int bc, Shift s, VRef<T> x, VRef<T> b,
                  C<T>* y, int nrhs, const int* done, cudaStream_t st);
+// V-cycle kernels (hz_vcycle.cu).  SF: storage of the level right-hand side
+// f, SX: storage of the level iterate, SC: storage of the coarse vector,
+// SO: storage of the output; the arithmetic is C<T>.
 // x = dinv .* f
-template <class T>
-void launch_jacobi0(const LevelDev& L, int bc, VRef<T> f, C<T>* x, int nrhs,
+template <class T, class SF, class SX>
+void launch_jacobi0(const LevelDev& L, int bc, VRefE<SF> f, SX* x, int nrhs,
                     const int* done, cudaStream_t st);
 // fc = R_fw (f - M x)
-template <class T>
+template <class T, class SF, class SX, class SC>
 void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc,
-                           Shift s, VRef<T> f, const C<T>* x, C<T>* fc,
-                           int nrhs, const int* done, cudaStream_t st);
+                           Shift s, VRefE<SF> f, const SX* x, SC* fc, int nrhs,
+                           const int* done, cudaStream_t st);
 // x += P_bilinear xc
-template <class T>
+template <class T, class SC, class SX>
 void launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, int bc,
-                        const C<T>* xc, C<T>* x, int nrhs, const int* done,
+                        const SC* xc, SX* x, int nrhs, const int* done,
                         cudaStream_t st);
-// xo = x + dinv .* (f - M x)  (+ addv if non-null)
-template <class T>
-void launch_smooth(const LevelDev& L, int bc, Shift s, VRef<T> f,
-                   const C<T>* x, C<T>* xo, int nrhs, const int* done,
-                   cudaStream_t st);
+// xo = x + dinv .* (f - M x)
+template <class T, class SF, class SX, class SO>
+void launch_smooth(const LevelDev& L, int bc, Shift s, VRefE<SF> f, const SX* x,
+                   SO* xo, int nrhs, const int* done, cudaStream_t st);
+// x = Minv f on the coarsest level (dense)
+template <class T, class SF, class SO>
+void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
+                     const int* done, cudaStream_t st);
 // coarse = R_Z fine  (zk = bilinear: full weighting; ho: 5x5 / 256)
 template <class T>
 void launch_restrict_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
@@ -188,6 +215,11 @@ template <class T>
 void launch_prolong_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
                       const C<T>* coarse, C<T>* fine, int add, int nrhs,
                       const int* done, cudaStream_t st);
+// y = R_Z A_h Z x (str-Glk) in one fused tiled kernel
+template <class T>
+void launch_galerkin_fused(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
+                           const C<T>* x, C<T>* y, int nrhs, const int* done,
+                           cudaStream_t st);
 // y = E_glk x on level 1 (variant 1 or 2)
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
@@ -197,10 +229,7 @@ void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
 template <class T>
 void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
                            cudaStream_t st);
-// x = Minv f on the coarsest level (dense)
-template <class T>
-void launch_dense_mv(int n, const C<T>* minv, VRef<T> f, C<T>* x, int nrhs,
-                     const int* done, cudaStream_t st);
+
 // out = a + b (b may be null), with conversion of the precision
 template <class Ti, class To>
 void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
@@ -247,15 +276,16 @@ struct KState {
 
 int krylov_nblk(long long n);
 // classical Gram-Schmidt pass `pass` (0, or 1 = re-orthogonalisation for
-// the RHS flagged by launch_reorth_decide)
-template <class T>
-void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
-                 int nrhs, const KState& ks, int pass, cudaStream_t st);
+// the RHS flagged by launch_reorth_decide); the basis V is stored as SB,
+// w and the arithmetic are C<T>
+template <class T, class SB>
+void launch_mdot(const SB* V, long long vstride, long long rs, const C<T>* w,
+                 long long n, int nrhs, const KState& ks, int pass, cudaStream_t st);
 void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st);
-template <class T>
-void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
-                  int nrhs, const KState& ks, int pass, cudaStream_t st);
+template <class T, class SB>
+void launch_maxpy(const SB* V, long long vstride, long long rs, C<T>* w,
+                  long long n, int nrhs, const KState& ks, int pass, cudaStream_t st);
 void launch_reorth_decide(const KState& ks, long long n, int nrhs, double eta,
                           cudaStream_t st);
 template <class T>
@@ -265,14 +295,21 @@ void launch_reduce_norm(const KState& ks, long long n, int nrhs, double* out,
                         int sqrt_it, cudaStream_t st);
 void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
                         const double* bnorm_src, double tol, cudaStream_t st);
-template <class T>
-void launch_scale_into(VRef<T> w, VRef<T> out, const double* scale_inv, long long n,
-                       int nrhs, const int* done, int use_inverse, cudaStream_t st);
+// out = w / s[r], stored as SB
+template <class T, class SB>
+void launch_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* s,
+                       long long n, int nrhs, const int* done, cudaStream_t st);
+// out = basis vector v (stored as SB) in compute type T
+template <class SB, class T>
+void launch_basis_load(VRefE<SB> v, long long rs, C<T>* out, long long n, int nrhs,
+                       const int* done, cudaStream_t st);
 void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
                    cudaStream_t st);
 void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st);
-template <class Tv, class Tx>
-void launch_update(const C<Tv>* V, long long vstride, const KState& ks,
+// Basis rows: vector i of RHS r starts at V + i * vstride + r * rs; rs is a
+// multiple of 4 elements for 16-byte-aligned group loads (or n for FP64).
+template <class SB, class Tx>
+void launch_update(const SB* V, long long vstride, long long rs, const KState& ks,
                    C<Tx>* x, int accumulate, long long n, int nrhs,
                    cudaStream_t st);
 void launch_fill_int(int* p, int v, int count, cudaStream_t st);

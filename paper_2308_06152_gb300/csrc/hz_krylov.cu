@@ -4,6 +4,8 @@
 // norms, Givens updates of the Hessenberg columns and the triangular solve.
 // Each right-hand side owns its basis, Hessenberg matrix and stopping state;
 // all of them live in device memory so that no launch depends on host data.
+#include <type_traits>
+
 #include "hz_common.cuh"
 
 namespace hz {
@@ -33,6 +35,60 @@ __device__ __forceinline__ float2 shfl_down2(float2 v, int o) {
   return v;
 }
 
+// Basis rows are read in 16-byte groups of W values: 1 FP64 pair, 2 FP32
+// pairs or 4 FP16 pairs.  Rows start 16-byte aligned (padded row stride).
+template <class SB> struct VW;
+template <> struct VW<double2> { static constexpr int w = 1; };
+template <> struct VW<float2> { static constexpr int w = 2; };
+template <> struct VW<__half2> { static constexpr int w = 4; };
+
+__device__ __forceinline__ void ldgrp(const double2* p, long long g, double2* o) {
+  o[0] = p[g];
+}
+__device__ __forceinline__ void ldgrp(const float2* p, long long g, float2* o) {
+  const float4 v = reinterpret_cast<const float4*>(p)[g];
+  o[0] = make_float2(v.x, v.y);
+  o[1] = make_float2(v.z, v.w);
+}
+__device__ __forceinline__ void ldgrp(const __half2* p, long long g, float2* o) {
+  const uint4 v = reinterpret_cast<const uint4*>(p)[g];
+  o[0] = __half22float2(*reinterpret_cast<const __half2*>(&v.x));
+  o[1] = __half22float2(*reinterpret_cast<const __half2*>(&v.y));
+  o[2] = __half22float2(*reinterpret_cast<const __half2*>(&v.z));
+  o[3] = __half22float2(*reinterpret_cast<const __half2*>(&v.w));
+}
+
+// Raw 16-byte group g of a basis row and value U of it in compute precision.
+template <class SB>
+__device__ __forceinline__ uint4 ldraw(const SB* p, long long g) {
+  return reinterpret_cast<const uint4*>(p)[g];
+}
+template <int U>
+__device__ __forceinline__ double2 unpk(const uint4& v, const double2*) {
+  return make_double2(__hiloint2double((int)v.y, (int)v.x),
+                      __hiloint2double((int)v.w, (int)v.z));
+}
+template <int U>
+__device__ __forceinline__ float2 unpk(const uint4& v, const float2*) {
+  return U == 0 ? make_float2(__uint_as_float(v.x), __uint_as_float(v.y))
+                : make_float2(__uint_as_float(v.z), __uint_as_float(v.w));
+}
+template <int U>
+__device__ __forceinline__ float2 unpk(const uint4& v, const __half2*) {
+  const unsigned w = U == 0 ? v.x : (U == 1 ? v.y : (U == 2 ? v.z : v.w));
+  __half2 h;
+  memcpy(&h, &w, sizeof(h));
+  return __half22float2(h);
+}
+// compile-time loop: f(integral_constant<U>) for U = 0..N-1
+template <int N, int U = 0, class F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (U < N) {
+    f(std::integral_constant<int, U>{});
+    static_for<N, U + 1>(f);
+  }
+}
+
 // Block-wide sum of a double held by every thread (result valid in thread 0).
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -49,11 +105,12 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // part[r][i][blk] = sum_{e in blk} conj(V_i[e]) w[e], i = 0..j.  Pass 0 also
 // stores the partial ||w||^2 in wpart; pass 1 runs only for the RHS whose
 // reorth flag the first pass raised.
-template <class T>
+template <class T, class SB>
 __global__ void __launch_bounds__(NT)
-k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w,
-       long long n, KState ks, int pass) {
-  constexpr int G = 4, TILE = 32, NW = NT / 32;
+k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
+       const C<T>* __restrict__ w, long long n, KState ks, int pass) {
+  constexpr int TILE = 32, NW = NT / 32;
+  constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
   __shared__ double2 wred[NW][TILE];
   __shared__ double red[NW];
   const int r = blockIdx.y, blk = blockIdx.x;
@@ -61,17 +118,20 @@ k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w
   const int j = *ks.jctr;
   // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
-    atomicAdd(ks.abytes, (unsigned long long)(j + 2) * n * sizeof(C<T>));
-  const long long base = (long long)blk * CHUNK + threadIdx.x;
+    atomicAdd(ks.abytes, (unsigned long long)n * (sizeof(C<T>) + (j + 1) * sizeof(SB)));
+  // thread element e(k, u) = blk*CHUNK + (k*NT + tid)*W + u
+  const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
   const C<T>* wr = w + r * n;
   C<T> wv[EPT];
   T wn = T(0);
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const long long e = base + k * NT;
-    wv[k] = (e < n) ? wr[e] : czero<T>();
-    wn += wv[k].x * wv[k].x + wv[k].y * wv[k].y;
-  }
+  for (int k = 0; k < VPT; ++k)
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const long long e = (g0 + (long long)k * NT) * W + u;
+      wv[k * W + u] = (e < n) ? wr[e] : czero<T>();
+      wn += wv[k * W + u].x * wv[k * W + u].x + wv[k * W + u].y * wv[k * W + u].y;
+    }
   if (pass == 0) {
     const double t = block_sum((double)wn, red);
     if (threadIdx.x == 0) ks.wpart[(long long)r * ks.nblk_max + blk] = t;
@@ -80,30 +140,36 @@ k_mdot(const C<T>* __restrict__ V, long long vstride, const C<T>* __restrict__ w
   for (int t0 = 0; t0 <= j; t0 += TILE) {
     const int tend = min(t0 + TILE, j + 1);
     for (int i0 = t0; i0 < tend; i0 += G) {
-      C<T> d[G];
+      // issue every load of the G basis vectors first (16 per thread)
+      uint4 raw[G][VPT];
 #pragma unroll
       for (int q = 0; q < G; ++q) {
-        d[q] = czero<T>();
-        const int i = i0 + q;
-        if (i < tend) {
-          const C<T>* vr = V + (long long)i * vstride + r * n;
+        const SB* vr = V + (long long)(i0 + q) * vstride + r * rs;
 #pragma unroll
-          for (int k = 0; k < EPT; ++k) {
-            const long long e = base + k * NT;
-            if (e < n) {
-              const C<T> v = vr[e];
-              d[q].x += v.x * wv[k].x + v.y * wv[k].y;
-              d[q].y += v.x * wv[k].y - v.y * wv[k].x;
-            }
-          }
+        for (int k = 0; k < VPT; ++k) {
+          const long long g = g0 + (long long)k * NT;
+          raw[q][k] = (i0 + q < tend && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        C<T> d = czero<T>();
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          static_for<W>([&](auto U) {
+            const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
+            const C<T> wk = wv[k * W + U.value];
+            d.x += v.x * wk.x + v.y * wk.y;
+            d.y += v.x * wk.y - v.y * wk.x;
+          });
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-          const C<T> t = shfl_down2(d[q], o);
-          d[q].x += t.x;
-          d[q].y += t.y;
+          const C<T> t = shfl_down2(d, o);
+          d.x += t.x;
+          d.y += t.y;
         }
-        if (lane == 0 && i0 + q < tend) wred[warp][i0 + q - t0] = wide(d[q]);
+        if (lane == 0 && i0 + q < tend) wred[warp][i0 + q - t0] = wide(d);
       }
     }
     __syncthreads();
@@ -154,11 +220,12 @@ __global__ void k_reduce_cols(KState ks, int nblk, int pass) {
 }
 
 // w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
-template <class T>
+template <class T, class SB>
 __global__ void __launch_bounds__(NT)
-k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
-        long long n, KState ks, int pass) {
+k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
+        C<T>* __restrict__ w, long long n, KState ks, int pass) {
   constexpr int TILE = 512;
+  constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
   __shared__ C<T> hs[TILE];
   __shared__ double red[NT / 32];
   const int r = blockIdx.y;
@@ -166,44 +233,59 @@ k_maxpy(const C<T>* __restrict__ V, long long vstride, C<T>* __restrict__ w,
   const int j = *ks.jctr;
   // algorithmic bytes of this RHS: read w and basis 0..j, write w
   if (ks.abytes && blockIdx.x == 0 && threadIdx.x == 0)
-    atomicAdd(ks.abytes, (unsigned long long)(j + 3) * n * sizeof(C<T>));
-  const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
+    atomicAdd(ks.abytes, (unsigned long long)n * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB)));
+  const long long g0 = (long long)blockIdx.x * (CHUNK / W) + threadIdx.x;
   C<T>* wr = w + r * n;
   C<T> acc[EPT];
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const long long e = base + k * NT;
-    acc[k] = (e < n) ? wr[e] : czero<T>();
-  }
+  for (int k = 0; k < VPT; ++k)
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const long long e = (g0 + (long long)k * NT) * W + u;
+      acc[k * W + u] = (e < n) ? wr[e] : czero<T>();
+    }
   for (int t0 = 0; t0 <= j; t0 += TILE) {
     const int cnt = min(TILE, j + 1 - t0);
     __syncthreads();
     for (int q = threadIdx.x; q < cnt; q += NT)
       hs[q] = cvt_to<T>(ks.hcol[(long long)r * (ks.m + 1) + t0 + q]);
     __syncthreads();
-    for (int q = 0; q < cnt; ++q) {
-      const C<T>* vr = V + (long long)(t0 + q) * vstride + r * n;
-      const C<T> h = hs[q];
+    for (int q0 = 0; q0 < cnt; q0 += G) {
+      uint4 raw[G][VPT];
 #pragma unroll
-      for (int k = 0; k < EPT; ++k) {
-        const long long e = base + k * NT;
-        if (e < n) {
-          const C<T> v = vr[e];
-          acc[k].x -= v.x * h.x - v.y * h.y;
-          acc[k].y -= v.x * h.y + v.y * h.x;
+      for (int q = 0; q < G; ++q) {
+        const SB* vr = V + (long long)(t0 + q0 + q) * vstride + r * rs;
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          const long long g = g0 + (long long)k * NT;
+          raw[q][k] = (q0 + q < cnt && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const C<T> h = (q0 + q < cnt) ? hs[q0 + q] : czero<T>();
+#pragma unroll
+        for (int k = 0; k < VPT; ++k) {
+          static_for<W>([&](auto U) {
+            const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
+            acc[k * W + U.value].x -= v.x * h.x - v.y * h.y;
+            acc[k * W + U.value].y -= v.x * h.y + v.y * h.x;
+          });
         }
       }
     }
   }
   T wn = T(0);
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const long long e = base + k * NT;
-    if (e < n) {
-      wr[e] = acc[k];
-      wn += acc[k].x * acc[k].x + acc[k].y * acc[k].y;
+  for (int k = 0; k < VPT; ++k)
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const long long e = (g0 + (long long)k * NT) * W + u;
+      if (e < n) {
+        wr[e] = acc[k * W + u];
+        wn += acc[k * W + u].x * acc[k * W + u].x + acc[k * W + u].y * acc[k * W + u].y;
+      }
     }
-  }
   const double t = block_sum((double)wn, red);
   if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blockIdx.x] = t;
 }
@@ -308,18 +390,33 @@ __global__ void k_krylov_init(KState ks, int nrhs, const int* done_in,
   }
 }
 
-template <class T>
-__global__ void k_scale_into(VRef<T> w, VRef<T> out, const double* __restrict__ s,
-                             long long n, const int* __restrict__ done) {
+template <class T, class SB>
+__global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
+                             const double* __restrict__ s, long long n,
+                             const int* __restrict__ done) {
   const int r = blockIdx.y;
   if (done && done[r]) return;
   const double sv = s[r];
   const T f = (sv != 0.0) ? T(1.0 / sv) : T(0);
   const C<T>* wr = w.get() + r * n;
-  C<T>* orow = out.get() + r * n;
+  SB* orow = out.get() + r * rs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
-    orow[e] = f * wr[e];
+    st2(orow, e, f * wr[e]);
+  // the padding of the row reads as zero in the group loads
+  if (blockIdx.x == 0 && threadIdx.x < rs - n) st2(orow, n + threadIdx.x, czero<T>());
+}
+
+template <class SB, class T>
+__global__ void k_basis_load(VRefE<SB> v, long long rs, C<T>* __restrict__ out,
+                             long long n, const int* __restrict__ done) {
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  const SB* vr = v.get() + r * rs;
+  C<T>* orow = out + r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    orow[e] = ld2(vr, e);
 }
 
 // Apply the previous rotations to column j, build the rotation that
@@ -428,9 +525,9 @@ __global__ void k_trisolve(KState ks, int nrhs) {
 }
 
 // x (+)= sum_{i < iters} y_i V_i
-template <class Tv, class Tx>
+template <class SB, class Tx>
 __global__ void __launch_bounds__(NT)
-k_update(const C<Tv>* __restrict__ V, long long vstride, KState ks,
+k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
          C<Tx>* __restrict__ x, int accumulate, long long n) {
   constexpr int TILE = 512;
   __shared__ C<Tx> ys[TILE];
@@ -452,13 +549,13 @@ k_update(const C<Tv>* __restrict__ V, long long vstride, KState ks,
       ys[q] = cvt_to<Tx>(ks.y[(long long)r * ks.m + t0 + q]);
     __syncthreads();
     for (int i = 0; i < cnt; ++i) {
-      const C<Tv>* vr = V + (long long)(t0 + i) * vstride + r * n;
+      const SB* vr = V + (long long)(t0 + i) * vstride + r * rs;
       const C<Tx> yi = ys[i];
 #pragma unroll
       for (int q = 0; q < EPT; ++q) {
         const long long e = base + q * NT;
         if (e < n) {
-          const C<Tv> v = vr[e];
+          const C<Tx> v = ld2(vr, e);
           acc[q].x += (Tx)v.x * yi.x - (Tx)v.y * yi.y;
           acc[q].y += (Tx)v.x * yi.y + (Tx)v.y * yi.x;
         }
@@ -485,11 +582,12 @@ __global__ void k_copy_int(const int* s, int* d, int count) {
 
 int krylov_nblk(long long n) { return (int)((n + CHUNK - 1) / CHUNK); }
 
-template <class T>
-void launch_mdot(const C<T>* V, long long vstride, const C<T>* w, long long n,
-                 int nrhs, const KState& ks, int pass, cudaStream_t st) {
+template <class T, class SB>
+void launch_mdot(const SB* V, long long vstride, long long rs, const C<T>* w,
+                 long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_mdot<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks, pass);
+  k_mdot<T, SB><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, w, n, ks,
+                                                          pass);
 }
 void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st) {
@@ -498,11 +596,12 @@ void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
   k_reduce_cols<<<dim3((ks.m + 1 + wpb - 1) / wpb, nrhs), NT, 0, st>>>(
       ks, krylov_nblk(n), pass);
 }
-template <class T>
-void launch_maxpy(const C<T>* V, long long vstride, C<T>* w, long long n,
-                  int nrhs, const KState& ks, int pass, cudaStream_t st) {
+template <class T, class SB>
+void launch_maxpy(const SB* V, long long vstride, long long rs, C<T>* w,
+                  long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_maxpy<T><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, w, n, ks, pass);
+  k_maxpy<T, SB><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, w, n, ks,
+                                                           pass);
 }
 void launch_reorth_decide(const KState& ks, long long n, int nrhs, double eta,
                           cudaStream_t st) {
@@ -525,15 +624,21 @@ void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
   HZ_COUNT();
   k_krylov_init<<<1, 1024, 0, st>>>(ks, nrhs, done_in, bnorm_src, tol);
 }
-template <class T>
-void launch_scale_into(VRef<T> w, VRef<T> out, const double* s, long long n,
-                       int nrhs, const int* done, int use_inverse,
-                       cudaStream_t st) {
+template <class T, class SB>
+void launch_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* s,
+                       long long n, int nrhs, const int* done, cudaStream_t st) {
   HZ_COUNT();
-  (void)use_inverse;
   long long nb = (n + 255) / 256;
   if (nb > 2048) nb = 2048;
-  k_scale_into<T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, s, n, done);
+  k_scale_into<T, SB><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, rs, s, n, done);
+}
+template <class SB, class T>
+void launch_basis_load(VRefE<SB> v, long long rs, C<T>* out, long long n, int nrhs,
+                       const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  long long nb = (n + 255) / 256;
+  if (nb > 2048) nb = 2048;
+  k_basis_load<SB, T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(v, rs, out, n, done);
 }
 void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
                    cudaStream_t st) {
@@ -546,12 +651,12 @@ void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st) {
   HZ_COUNT();
   k_trisolve<<<(nrhs + 63) / 64, 64, 0, st>>>(ks, nrhs);
 }
-template <class Tv, class Tx>
-void launch_update(const C<Tv>* V, long long vstride, const KState& ks,
+template <class SB, class Tx>
+void launch_update(const SB* V, long long vstride, long long rs, const KState& ks,
                    C<Tx>* x, int accumulate, long long n, int nrhs,
                    cudaStream_t st) {
   HZ_COUNT();
-  k_update<Tv, Tx><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, ks, x,
+  k_update<SB, Tx><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, ks, x,
                                                               accumulate, n);
 }
 void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
@@ -563,20 +668,29 @@ void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
   k_copy_int<<<(count + 255) / 256, 256, 0, st>>>(src, dst, count);
 }
 
-#define HZ_KINST(T)                                                            \
-  template void launch_mdot<T>(const C<T>*, long long, const C<T>*, long long, \
-                               int, const KState&, int, cudaStream_t);         \
-  template void launch_maxpy<T>(const C<T>*, long long, C<T>*, long long, int, \
-                                const KState&, int, cudaStream_t);             \
-  template void launch_norm2_part<T>(VRef<T>, long long, int, const KState&,   \
-                                     const int*, cudaStream_t);                \
-  template void launch_scale_into<T>(VRef<T>, VRef<T>, const double*,          \
-                                     long long, int, const int*, int,          \
-                                     cudaStream_t);                            \
-  template void launch_update<T, T>(const C<T>*, long long, const KState&,     \
-                                    C<T>*, int, long long, int, cudaStream_t);
+#define HZ_KINST(T, SB)                                                         \
+  template void launch_mdot<T, SB>(const SB*, long long, long long, const C<T>*, \
+                                   long long, int, const KState&, int,          \
+                                   cudaStream_t);                               \
+  template void launch_maxpy<T, SB>(const SB*, long long, long long, C<T>*,      \
+                                    long long, int, const KState&, int,         \
+                                    cudaStream_t);                              \
+  template void launch_scale_into<T, SB>(VRef<T>, VRefE<SB>, long long,         \
+                                         const double*, long long, int,         \
+                                         const int*, cudaStream_t);             \
+  template void launch_basis_load<SB, T>(VRefE<SB>, long long, C<T>*, long long, \
+                                         int, const int*, cudaStream_t);        \
+  template void launch_update<SB, T>(const SB*, long long, long long,           \
+                                     const KState&, C<T>*, int, long long, int, \
+                                     cudaStream_t);
 
-HZ_KINST(double)
-HZ_KINST(float)
+template void launch_norm2_part<double>(VRef<double>, long long, int, const KState&,
+                                        const int*, cudaStream_t);
+template void launch_norm2_part<float>(VRef<float>, long long, int, const KState&,
+                                       const int*, cudaStream_t);
+
+HZ_KINST(double, double2)
+HZ_KINST(float, float2)
+HZ_KINST(float, __half2)
 
 }  // namespace hz

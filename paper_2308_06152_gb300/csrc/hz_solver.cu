@@ -24,6 +24,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "hz.h"
 #include "hz_common.cuh"
 
@@ -83,7 +85,7 @@ bool valid_desc(const hz_desc* d, std::string* why) {
   if (d->bc != HZ_BC_DIRICHLET && d->bc != HZ_BC_SOMMERFELD) { *why = "bad bc"; return false; }
   if (d->zkind < HZ_Z_NONE || d->zkind > HZ_Z_HO) { *why = "bad zkind"; return false; }
   if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_GLK2) { *why = "bad ekind"; return false; }
-  if (d->prec != HZ_PREC_FP64 && d->prec != HZ_PREC_MIXED_FP32) { *why = "bad prec"; return false; }
+  if (d->prec < HZ_PREC_FP64 || d->prec > HZ_PREC_MIXED_BF16) { *why = "bad prec"; return false; }
   if (d->nrhs_max < 1 || d->nrhs_max > kMaxRhs) { *why = "nrhs_max must be in 1..1024"; return false; }
   if (d->outer_maxit < 1 || d->coarse_maxit < 1 || d->outer_maxit > kMaxIters ||
       d->coarse_maxit > kMaxIters) {
@@ -115,7 +117,9 @@ struct hz_solver {
   int L = 0;
   LevelHost lv[kMaxLevels];
   bool mixed = false;
+  bool lvbf16 = false;   // V-cycle level vectors stored as BF16 pairs
   size_t esz = 16;       // bytes of one complex value of the preconditioner
+  size_t lsz = 16;       // bytes of one stored value of a V-cycle level vector
   int nL = 0;            // unknowns of the dense coarsest level
   void* minv = nullptr;  // coarsest inverse, preconditioner precision
   double2* aug = nullptr;
@@ -125,6 +129,8 @@ struct hz_solver {
        *vin = nullptr;
   // coarse level (level 1)
   void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
+  void* qf = nullptr;      // current basis vector in compute precision (FP16 basis)
+  bool basis16 = false;    // inner Krylov basis stored as FP16 pairs
   KState kin{}, kout{};
   int* in_total = nullptr;
   int* in_max = nullptr;
@@ -166,6 +172,10 @@ hz_status cuda_check(hz_solver* s, const char* where) {
   return HZ_OK;
 }
 
+// Row stride of the inner Krylov basis: padded to 4 elements so that every
+// row starts 16-byte aligned for the group loads of the Gram-Schmidt kernels.
+inline long long inner_row(long long n) { return (n + 3) & ~3LL; }
+
 KState plan_kstate(Arena& a, int B, int m, long long n) {
   KState k{};
   k.m = m;
@@ -202,10 +212,10 @@ void plan(hz_solver* s, Arena& a) {
     v.k2f = s->mixed ? (float*)a.take(sizeof(float) * v.n) : nullptr;
     v.dinv_d = s->mixed ? nullptr : (double2*)a.take(sizeof(double2) * v.n);
     v.dinv_f = s->mixed ? (float2*)a.take(sizeof(float2) * v.n) : nullptr;
-    v.xa = a.take(es * B * v.n);
+    v.xa = a.take(s->lsz * B * v.n);
     if (l >= 1) {
-      v.f = a.take(es * B * v.n);
-      v.x = a.take(es * B * v.n);
+      v.f = a.take(s->lsz * B * v.n);
+      v.x = a.take(s->lsz * B * v.n);
     }
   }
   s->minv = a.take(es * (size_t)s->nL * s->nL);
@@ -218,15 +228,14 @@ void plan(hz_solver* s, Arena& a) {
   if (d.zkind != HZ_Z_NONE) {
     const long long n1 = s->lv[1].n;
     s->q = a.take(es * B * n0);
-    if (d.ekind == HZ_E_GALERKIN) {
-      s->fz1 = a.take(es * B * n0);
-      s->fz2 = a.take(es * B * n0);
-    }
+
     s->v1 = a.take(es * B * n1);
     s->v2 = a.take(es * B * n1);
     s->sb = a.take(es * B * n1);
     s->eb = a.take(es * B * n1);
-    s->Qb = a.take(es * (size_t)B * n1 * (d.coarse_maxit + 1));
+    const size_t bes = s->basis16 ? sizeof(__half2) : es;
+    s->Qb = a.take(bes * (size_t)B * inner_row(n1) * (d.coarse_maxit + 1));
+    s->qf = a.take(es * B * n1);
     s->kin = plan_kstate(a, B, d.coarse_maxit, n1);
   }
   s->in_total = (int*)a.take(sizeof(int) * B);
@@ -268,8 +277,11 @@ hz_status init_shapes(hz_solver* s) {
             s->nL, kMaxCoarsest);
     return HZ_INVALID_GRID;
   }
-  s->mixed = d.prec == HZ_PREC_MIXED_FP32;
+  s->mixed = d.prec != HZ_PREC_FP64;
+  s->lvbf16 = d.prec == HZ_PREC_MIXED_BF16;
   s->esz = s->mixed ? sizeof(float2) : sizeof(double2);
+  s->lsz = s->lvbf16 ? sizeof(__nv_bfloat162) : s->esz;
+  s->basis16 = s->mixed && d.inner_basis_fp16;
   return HZ_OK;
 }
 
@@ -283,35 +295,61 @@ inline Shift helm1() { return Shift{1.0, 0.0}; }
 inline LevelDev dev64(const hz_solver* s, int l) { return s->lv[l].dev(); }
 
 // ------------------------------------------------------------ V-cycle
-template <class T>
-void vcycle(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs, const int* done) {
+// One V-cycle from level l0 for M_l0 x = f.  The hierarchy's own vectors are
+// stored as SL (C<T>, or BF16 pairs for the BF16-storage smoother); the
+// input f and the result xout are C<T>.
+template <class T, class SL>
+void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
+               const int* done) {
   cudaStream_t st = s->st;
   const int bc = s->d.bc;
   const Shift sh = cslp(s);
+  const C<T>* minv = (const C<T>*)s->minv;
   if (l0 == s->L) {
-    launch_dense_mv<T>(s->nL, (const C<T>*)s->minv, f, xout, nrhs, done, st);
+    launch_dense_mv<T, C<T>, C<T>>(s->nL, minv, f, xout, nrhs, done, st);
     return;
   }
-  VRef<T> fl = f;
   for (int l = l0; l < s->L; ++l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
-    launch_jacobi0<T>(A.dev(), bc, fl, (C<T>*)A.xa, nrhs, done, st);
-    launch_resid_restrict<T>(A.dev(), Bc.dev(), bc, sh, fl, (const C<T>*)A.xa,
-                             (C<T>*)Bc.f, nrhs, done, st);
-    fl = vref<T>(Bc.f);
+    if (l == l0) {
+      launch_jacobi0<T, C<T>, SL>(A.dev(), bc, f, (SL*)A.xa, nrhs, done, st);
+      launch_resid_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f,
+                                             (const SL*)A.xa, (SL*)Bc.f, nrhs,
+                                             done, st);
+    } else {
+      const VRefE<SL> fl = vrefe<SL>(A.f);
+      launch_jacobi0<T, SL, SL>(A.dev(), bc, fl, (SL*)A.xa, nrhs, done, st);
+      launch_resid_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, fl,
+                                           (const SL*)A.xa, (SL*)Bc.f, nrhs, done,
+                                           st);
+    }
   }
-  launch_dense_mv<T>(s->nL, (const C<T>*)s->minv, vref<T>(s->lv[s->L].f),
-                     (C<T>*)s->lv[s->L].x, nrhs, done, st);
+  launch_dense_mv<T, SL, SL>(s->nL, minv, vrefe<SL>(s->lv[s->L].f),
+                             (SL*)s->lv[s->L].x, nrhs, done, st);
   for (int l = s->L - 1; l >= l0; --l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
-    launch_prolong_add<T>(A.dev(), Bc.dev(), bc, (const C<T>*)Bc.x, (C<T>*)A.xa,
-                          nrhs, done, st);
-    const VRef<T> fa = (l == l0) ? f : vref<T>(A.f);
-    C<T>* xo = (l == l0) ? xout : (C<T>*)A.x;
-    launch_smooth<T>(A.dev(), bc, sh, fa, (const C<T>*)A.xa, xo, nrhs, done, st);
+    launch_prolong_add<T, SL, SL>(A.dev(), Bc.dev(), bc, (const SL*)Bc.x, (SL*)A.xa,
+                                  nrhs, done, st);
+    if (l == l0)
+      launch_smooth<T, C<T>, SL, C<T>>(A.dev(), bc, sh, f, (const SL*)A.xa, xout,
+                                       nrhs, done, st);
+    else
+      launch_smooth<T, SL, SL, SL>(A.dev(), bc, sh, vrefe<SL>(A.f), (const SL*)A.xa,
+                                   (SL*)A.x, nrhs, done, st);
   }
+}
+
+template <class T>
+void vcycle(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs, const int* done) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (s->lvbf16) {
+      vcycle_sl<T, __nv_bfloat162>(s, l0, f, xout, nrhs, done);
+      return;
+    }
+  }
+  vcycle_sl<T, C<T>>(s, l0, f, xout, nrhs, done);
 }
 
 // ------------------------------------------------------------ coarse E
@@ -323,12 +361,8 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
   const LevelHost& Cc = s->lv[1];
   switch (s->d.ekind) {
     case HZ_E_GALERKIN:
-      launch_prolong_z<T>(F.dev(), Cc.dev(), bc, s->d.zkind, x, (C<T>*)s->fz1, 0,
-                          nrhs, done, st);
-      launch_helm<T>(F.dev(), bc, helm1(), vref<T>(s->fz1), vref<T>(nullptr),
-                     (C<T>*)s->fz2, nrhs, done, st);
-      launch_restrict_z<T>(F.dev(), Cc.dev(), bc, s->d.zkind, vref<T>(s->fz2), y,
-                           nrhs, done, st);
+      launch_galerkin_fused<T>(F.dev(), Cc.dev(), bc, s->d.zkind, x, y, nrhs, done,
+                               st);
       break;
     case HZ_E_RED_O2:
       launch_helm<T>(Cc.dev(), bc, helm1(), vref<T>(x), vref<T>(nullptr), y, nrhs,
@@ -391,8 +425,8 @@ inline void prof_mark(hz_solver* s, int kc) {
 // precision); ||w|| of the result lands in ks.hnorm.
 constexpr double kReorthEta = 0.5;
 
-template <class T>
-void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
+template <class T, class SB>
+void cgs2(hz_solver* s, KState& ks, const SB* V, long long vs, long long rs, C<T>* w,
           long long n, int nrhs) {
   cudaStream_t st = s->st;
   KState k = ks;
@@ -402,11 +436,11 @@ void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
   if (s->prof_kc == HZ_KC_MAXPY) ka.abytes = s->prof_bytes;
   for (int pass = 0; pass < 2; ++pass) {
     prof_mark(s, HZ_KC_MDOT);
-    launch_mdot<T>(V, vs, w, n, nrhs, kd, pass, st);
+    launch_mdot<T, SB>(V, vs, rs, w, n, nrhs, kd, pass, st);
     prof_mark(s, HZ_KC_MDOT);
     launch_reduce_cols(k, n, nrhs, pass, st);
     prof_mark(s, HZ_KC_MAXPY);
-    launch_maxpy<T>(V, vs, w, n, nrhs, ka, pass, st);
+    launch_maxpy<T, SB>(V, vs, rs, w, n, nrhs, ka, pass, st);
     prof_mark(s, HZ_KC_MAXPY);
     if (pass == 0) launch_reorth_decide(k, n, nrhs, kReorthEta, st);
   }
@@ -416,14 +450,15 @@ void cgs2(hz_solver* s, KState& ks, const C<T>* V, long long vs, C<T>* w,
 // ------------------------------------------------------------ inner solve
 // E v2 = v1 by right-preconditioned GMRES (V-cycle on the coarse CSLP from
 // level 1), x0 = 0, stopping at |g_{j+1}| <= coarse_tol ||v1||.
-template <class T>
-hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
-                       const int* done_in) {
+template <class T, class SB>
+hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
+                          const int* done_in) {
   cudaStream_t st = s->st;
   KState& ks = s->kin;
   const long long n1 = s->lv[1].n;
-  const long long vs = (long long)s->d.nrhs_max * n1;
-  C<T>* Q = (C<T>*)s->Qb;
+  const long long rs = inner_row(n1);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  SB* Q = (SB*)s->Qb;
   C<T>* sb = (C<T>*)s->sb;
   C<T>* eb = (C<T>*)s->eb;
   const int m = s->d.coarse_maxit;
@@ -431,16 +466,21 @@ hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
   launch_norm2_part<T>(vref<T>(v1), n1, nrhs, ks, nullptr, st);
   launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
   launch_krylov_init(ks, nrhs, done_in, nullptr, tol, st);
-  launch_scale_into<T>(vref<T>(v1), vref<T>(Q), ks.hnorm, n1, nrhs, ks.done, 1, st);
+  launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>(Q), rs, ks.hnorm, n1, nrhs,
+                           ks.done, st);
   int all = 0;
   for (int it = 0; it < m; ++it) {
-    vcycle<T>(s, 1, vref_j<T>(Q, ks.jctr, 0, vs), sb, nrhs, ks.done);
+    // the V-cycle reads the current basis vector, unpadded, in compute
+    // precision
+    launch_basis_load<SB, T>(vrefe_j<SB>(Q, ks.jctr, 0, vs), rs, (C<T>*)s->qf, n1,
+                             nrhs, ks.done, st);
+    vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
     apply_E<T>(s, sb, eb, nrhs, ks.done);
-    cgs2<T>(s, ks, Q, vs, eb, n1, nrhs);
+    cgs2<T, SB>(s, ks, Q, vs, rs, eb, n1, nrhs);
     launch_givens(ks, nrhs, tol, m, st);
     debug_trace(s, ks, "inner");
-    launch_scale_into<T>(vref<T>(eb), vref_j<T>(Q, ks.jctr, 0, vs), ks.hnorm, n1,
-                         nrhs, ks.done, 1, st);
+    launch_scale_into<T, SB>(vref<T>(eb), vrefe_j<SB>(Q, ks.jctr, 0, vs), rs,
+                             ks.hnorm, n1, nrhs, ks.done, st);
     if ((it + 1) % s->check_every == 0 || it + 1 == m) {
       const hz_status e = read_flag(s, ks.alldone, &all);
       if (e != HZ_OK) return e;
@@ -448,10 +488,19 @@ hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
     }
   }
   launch_trisolve(ks, nrhs, st);
-  launch_update<T, T>(Q, vs, ks, eb, 0, n1, nrhs, st);
+  launch_update<SB, T>(Q, vs, rs, ks, eb, 0, n1, nrhs, st);
   vcycle<T>(s, 1, vref<T>(eb), v2, nrhs, done_in);
   launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
   return cuda_check(s, "coarse solve");
+}
+
+template <class T>
+hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
+                       const int* done_in) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (s->basis16) return coarse_solve_sb<T, __half2>(s, v1, v2, nrhs, done_in);
+  }
+  return coarse_solve_sb<T, C<T>>(s, v1, v2, nrhs, done_in);
 }
 
 // ------------------------------------------------------------ A-DEF1
@@ -464,11 +513,8 @@ hz_status precond(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
   const int bc = s->d.bc;
   const long long n0 = s->lv[0].n;
   VRef<T> v;
-  if (std::is_same<T, double>::value) {
-    v.base = (C<T>*)vin.base;
-    v.jidx = vin.jidx;
-    v.jofs = vin.jofs;
-    v.jstride = vin.jstride;
+  if constexpr (std::is_same<T, double>::value) {
+    v = vin;
   } else {
     launch_add_conv<double, T>(vin, nullptr, vref<T>(s->vin), n0, nrhs, done, st);
     v = vref<T>(s->vin);
@@ -525,8 +571,8 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
   launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
   launch_krylov_init(ko, nrhs, nullptr, s->bnorm_o, tol, st);
-  launch_scale_into<double>(vref<double>(s->wo), vref<double>(s->Vo), ko.hnorm, n0,
-                            nrhs, ko.done, 1, st);
+  launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(s->Vo), n0,
+                                    ko.hnorm, n0, nrhs, ko.done, st);
   hz_status e = cuda_check(s, "outer init");
   if (e != HZ_OK) return e;
   int all = 0;
@@ -538,16 +584,17 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
     if (e != HZ_OK) return e;
     launch_helm<double>(F, bc, helm1(), vref_j<double>(s->Zo, ko.jctr, 0, vs),
                         vref<double>(nullptr), s->wo, nrhs, ko.done, st);
-    cgs2<double>(s, ko, s->Vo, vs, s->wo, n0, nrhs);
+    cgs2<double, double2>(s, ko, s->Vo, vs, n0, s->wo, n0, nrhs);
     launch_givens(ko, nrhs, tol, m, st);
     debug_trace(s, ko, "outer");
-    launch_scale_into<double>(vref<double>(s->wo), vref_j<double>(s->Vo, ko.jctr, 0, vs),
-                              ko.hnorm, n0, nrhs, ko.done, 1, st);
+    launch_scale_into<double, double2>(vref<double>(s->wo),
+                                      vref_j<double>(s->Vo, ko.jctr, 0, vs), n0,
+                                      ko.hnorm, n0, nrhs, ko.done, st);
     e = read_flag(s, ko.alldone, &all);
     if (e != HZ_OK) return e;
   }
   launch_trisolve(ko, nrhs, st);
-  launch_update<double, double>(s->Zo, vs, ko, x, 1, n0, nrhs, st);
+  launch_update<double2, double>(s->Zo, vs, n0, ko, x, 1, n0, nrhs, st);
   // true residual
   launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo, nrhs,
                       nullptr, st);

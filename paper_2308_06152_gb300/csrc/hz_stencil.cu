@@ -5,6 +5,7 @@
 // the setup kernels.  Every kernel serves nrhs right-hand sides (blockIdx.z)
 // and skips those flagged done.
 #include "hz_common.cuh"
+#include "hz_stencil_dev.cuh"
 
 namespace hz {
 
@@ -14,48 +15,6 @@ constexpr int BX = 32, BY = 8;
 
 inline dim3 grid2d(int nx, int ny, int nrhs) {
   return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nrhs);
-}
-
-__device__ __forceinline__ bool on_bnd(int i, int j, int nx, int ny) {
-  return i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
-}
-
-// (M x)(i, j) for an unknown node (i, j): centre 4/h^2 - s k^2, Sommerfeld
-// sides add -2 i k / h each, remove the outward neighbour and double the
-// opposite one (ghost elimination); Dirichlet rows drop couplings to the
-// (fixed zero) boundary nodes.
-template <class T>
-__device__ __forceinline__ C<T> helm_point(const LevelDev& L, int bc, T sre,
-                                           T sim, const C<T>* __restrict__ x,
-                                           int i, int j) {
-  const int nx = L.nx, ny = L.ny;
-  const long long id = (long long)j * nx + i;
-  const T ih2 = ih2_of<T>(L);
-  const T k2 = k2_of<T>(L)[id];
-  C<T> cen = mkc(T(4) * ih2 - sre * k2, -sim * k2);
-  T cw = -ih2, ce = -ih2, cs = -ih2, cn = -ih2;
-  if (bc == BC_SOMMERFELD) {
-    const bool x0 = i == 0, x1 = i == nx - 1, y0 = j == 0, y1 = j == ny - 1;
-    const int ns = int(x0) + int(x1) + int(y0) + int(y1);
-    if (ns) {
-      cen.y -= T(ns) * tih_of<T>(L) * sqrt(k2);
-      if (x0) { cw = T(0); ce = T(2) * ce; }
-      if (x1) { ce = T(0); cw = T(2) * cw; }
-      if (y0) { cs = T(0); cn = T(2) * cn; }
-      if (y1) { cn = T(0); cs = T(2) * cs; }
-    }
-  } else {
-    if (i == 1) cw = T(0);
-    if (i == nx - 2) ce = T(0);
-    if (j == 1) cs = T(0);
-    if (j == ny - 2) cn = T(0);
-  }
-  C<T> acc = cmul(cen, x[id]);
-  if (cw != T(0)) acc = rfma(cw, x[id - 1], acc);
-  if (ce != T(0)) acc = rfma(ce, x[id + 1], acc);
-  if (cs != T(0)) acc = rfma(cs, x[id - nx], acc);
-  if (cn != T(0)) acc = rfma(cn, x[id + nx], acc);
-  return acc;
 }
 
 template <class T>
@@ -73,106 +32,6 @@ __global__ void k_helm(LevelDev L, int bc, T sre, T sim, VRef<T> xin,
   }
   const C<T> v = helm_point<T>(L, bc, sre, sim, xin.get() + r * n, i, j);
   yr[id] = bin.base ? bin.get()[r * n + id] - v : v;
-}
-
-template <class T>
-__global__ void k_jacobi0(LevelDev L, int bc, VRef<T> fin, C<T>* __restrict__ x,
-                          const int* __restrict__ done) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const int r = blockIdx.z;
-  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
-  const long long n = (long long)L.nx * L.ny, id = (long long)j * L.nx + i;
-  if (bc == BC_DIRICHLET && on_bnd(i, j, L.nx, L.ny)) {
-    x[r * n + id] = czero<T>();
-    return;
-  }
-  x[r * n + id] = cmul(dinv_of<T>(L)[id], fin.get()[r * n + id]);
-}
-
-// fc(I,J) = sum_{a,b in -1..1} (2-|a|)(2-|b|)/16 * (f - M x)(2I+a, 2J+b)
-template <class T>
-__global__ void k_resid_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
-                                 VRef<T> fin, const C<T>* __restrict__ x,
-                                 C<T>* __restrict__ fc,
-                                 const int* __restrict__ done) {
-  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
-  const int r = blockIdx.z;
-  if (I >= Lc.nx || J >= Lc.ny || (done && done[r])) return;
-  const long long nf = (long long)Lf.nx * Lf.ny, nc = (long long)Lc.nx * Lc.ny;
-  const long long idc = (long long)J * Lc.nx + I;
-  if (bc == BC_DIRICHLET && on_bnd(I, J, Lc.nx, Lc.ny)) {
-    fc[r * nc + idc] = czero<T>();
-    return;
-  }
-  const C<T>* f = fin.get() + r * nf;
-  const C<T>* xr = x + r * nf;
-  C<T> acc = czero<T>();
-  for (int b = -1; b <= 1; ++b) {
-    const int jf = 2 * J + b;
-    if (jf < 0 || jf >= Lf.ny) continue;
-    for (int a = -1; a <= 1; ++a) {
-      const int jf_i = 2 * I + a;
-      if (jf_i < 0 || jf_i >= Lf.nx) continue;
-      if (bc == BC_DIRICHLET && on_bnd(jf_i, jf, Lf.nx, Lf.ny)) continue;
-      const C<T> res = f[(long long)jf * Lf.nx + jf_i] -
-                       helm_point<T>(Lf, bc, sre, sim, xr, jf_i, jf);
-      const T w = T((2 - abs(a)) * (2 - abs(b))) * T(0.0625);
-      acc = rfma(w, res, acc);
-    }
-  }
-  fc[r * nc + idc] = acc;
-}
-
-// bilinear interpolation of xc at fine node (i, j)
-template <class T>
-__device__ __forceinline__ C<T> interp_bilinear(const LevelDev& Lc,
-                                                const C<T>* __restrict__ xc,
-                                                int i, int j) {
-  const int I0 = i >> 1, J0 = j >> 1;
-  const bool ox = i & 1, oy = j & 1;
-  const long long b0 = (long long)J0 * Lc.nx + I0;
-  C<T> v;
-  if (!ox && !oy) return xc[b0];
-  if (ox && !oy) {
-    v = xc[b0] + xc[b0 + 1];
-    return T(0.5) * v;
-  }
-  if (!ox && oy) {
-    v = xc[b0] + xc[b0 + Lc.nx];
-    return T(0.5) * v;
-  }
-  v = (xc[b0] + xc[b0 + 1]) + (xc[b0 + Lc.nx] + xc[b0 + Lc.nx + 1]);
-  return T(0.25) * v;
-}
-
-template <class T>
-__global__ void k_prolong_add(LevelDev Lf, LevelDev Lc, int bc,
-                              const C<T>* __restrict__ xc, C<T>* __restrict__ x,
-                              const int* __restrict__ done) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const int r = blockIdx.z;
-  if (i >= Lf.nx || j >= Lf.ny || (done && done[r])) return;
-  if (bc == BC_DIRICHLET && on_bnd(i, j, Lf.nx, Lf.ny)) return;
-  const long long nf = (long long)Lf.nx * Lf.ny, nc = (long long)Lc.nx * Lc.ny;
-  const long long id = (long long)j * Lf.nx + i;
-  x[r * nf + id] = x[r * nf + id] + interp_bilinear<T>(Lc, xc + r * nc, i, j);
-}
-
-template <class T>
-__global__ void k_smooth(LevelDev L, int bc, T sre, T sim, VRef<T> fin,
-                         const C<T>* __restrict__ x, C<T>* __restrict__ xo,
-                         const int* __restrict__ done) {
-  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
-  const int r = blockIdx.z;
-  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
-  const long long n = (long long)L.nx * L.ny, id = (long long)j * L.nx + i;
-  if (bc == BC_DIRICHLET && on_bnd(i, j, L.nx, L.ny)) {
-    xo[r * n + id] = czero<T>();
-    return;
-  }
-  const C<T>* xr = x + r * n;
-  const C<T> res = fin.get()[r * n + id] - helm_point<T>(L, bc, sre, sim, xr, i, j);
-  xo[r * n + id] = cfma(dinv_of<T>(L)[id], res, xr[id]);
 }
 
 // 1-D weights of Z^T: bilinear [1 2 1]/2 at offsets -1..1, higher-order
@@ -257,6 +116,146 @@ __global__ void k_prolong_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
     }
   }
   fine[r * nf + id] = add ? fine[r * nf + id] + acc : acc;
+}
+
+// str-Glk fused (Sec. 5.2.1): y = R_Z A_h Z x for a TC x TC tile of coarse
+// outputs in one CTA.  The coarse tile with a halo of 2, the interpolated
+// fine values Z x on the 2TC+5 square around it and A_h Z x on the 2TC+3
+// square stay in shared memory, so each launch reads x and k^2 once and
+// writes y once (the three-kernel form moves two fine-grid vectors through
+// HBM twice).  Same boundary rules as k_prolong_z / k_helm / k_restrict_z.
+// Interpolation taps of a fine index g along one dimension: the values at
+// coarse base, base+1, base+2 get weights w0, w1, w2 (Z = bilinear or the
+// higher-order rule; odd g lies between two coarse nodes).
+template <class T>
+__device__ __forceinline__ int ztaps(int zk, int g, T& w0, T& w1, T& w2) {
+  const int K = g >> 1;  // floor(g / 2), also for negative g
+  if (g & 1) {
+    w0 = T(0.5); w1 = T(0.5); w2 = T(0);
+    return K;
+  }
+  if (zk == ZK_HO) {
+    w0 = T(0.125); w1 = T(0.75); w2 = T(0.125);
+  } else {
+    w0 = T(0); w1 = T(1); w2 = T(0);
+  }
+  return K - 1;
+}
+
+// Weight of fine offset a in the restriction R_Z = Z^T / 4 along one
+// dimension (the 1/4 applied once at the end).
+template <class T>
+__device__ __forceinline__ T rtap(int zk, int a) {
+  if (zk == ZK_HO) {
+    switch (a) {
+      case -2: case 2: return T(0.125);
+      case -1: case 1: return T(0.5);
+      default: return T(0.75);
+    }
+  }
+  return (a == 0) ? T(1) : ((a == 1 || a == -1) ? T(0.5) : T(0));
+}
+
+template <class T, int TC>
+__global__ void __launch_bounds__(TC * TC)
+k_galerkin_fused(LevelDev Lf, LevelDev Lc, int bc, int zk,
+                 const C<T>* __restrict__ x, C<T>* __restrict__ y,
+                 const int* __restrict__ done) {
+  constexpr int CX = TC + 5, FZ = 2 * TC + 5, FA = 2 * TC + 3;
+  __shared__ C<T> xs[CX * CX];
+  __shared__ C<T> zs[FZ * FZ];
+  __shared__ C<T> as[FA * FA];
+  const int r = blockIdx.z;
+  if (done && done[r]) return;
+  const int I0 = blockIdx.x * TC, J0 = blockIdx.y * TC;
+  const int nfx = Lf.nx, nfy = Lf.ny, ncx = Lc.nx, ncy = Lc.ny;
+  const long long nc = (long long)ncx * ncy;
+  const C<T>* xr = x + r * nc;
+  const int tid = threadIdx.x, nt = TC * TC;
+  // 1. coarse tile [I0-2, I0+TC+2]^2 (zero outside the grid and on
+  //    Dirichlet boundary nodes, so Z is truncated there)
+  for (int q = tid; q < CX * CX; q += nt) {
+    const int ci = I0 - 2 + q % CX, cj = J0 - 2 + q / CX;
+    C<T> v = czero<T>();
+    if (ci >= 0 && ci < ncx && cj >= 0 && cj < ncy &&
+        !(bc == BC_DIRICHLET && on_bnd(ci, cj, ncx, ncy)))
+      v = xr[(long long)cj * ncx + ci];
+    xs[q] = v;
+  }
+  __syncthreads();
+  // 2. z = Z x on fine nodes [2I0-3, 2I0+2TC+1]^2
+  for (int q = tid; q < FZ * FZ; q += nt) {
+    const int gi = 2 * I0 - 3 + q % FZ, gj = 2 * J0 - 3 + q / FZ;
+    C<T> v = czero<T>();
+    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+      T wx[3], wy[3];
+      const int bx = ztaps<T>(zk, gi, wx[0], wx[1], wx[2]) - (I0 - 2);
+      const int by = ztaps<T>(zk, gj, wy[0], wy[1], wy[2]) - (J0 - 2);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          v = rfma(wx[a] * wy[b], xs[(by + b) * CX + bx + a], v);
+    }
+    zs[q] = v;
+  }
+  __syncthreads();
+  // 3. A_h z on fine nodes [2I0-2, 2I0+2TC]^2
+  const T ih2 = ih2_of<T>(Lf);
+  const T* k2 = k2_of<T>(Lf);
+  for (int q = tid; q < FA * FA; q += nt) {
+    const int ai = q % FA, aj = q / FA;
+    const int gi = 2 * I0 - 2 + ai, gj = 2 * J0 - 2 + aj;
+    C<T> v = czero<T>();
+    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+      const T kk = k2[(long long)gj * nfx + gi];
+      C<T> cen = mkc(T(4) * ih2 - kk, T(0));
+      T cw = -ih2, ce = -ih2, cs = -ih2, cn = -ih2;
+      if (bc == BC_SOMMERFELD) {
+        const bool x0 = gi == 0, x1 = gi == nfx - 1, y0 = gj == 0, y1 = gj == nfy - 1;
+        const int ns = int(x0) + int(x1) + int(y0) + int(y1);
+        if (ns) {
+          cen.y -= T(ns) * tih_of<T>(Lf) * sqrt(kk);
+          if (x0) { cw = T(0); ce = T(2) * ce; }
+          if (x1) { ce = T(0); cw = T(2) * cw; }
+          if (y0) { cs = T(0); cn = T(2) * cn; }
+          if (y1) { cn = T(0); cs = T(2) * cs; }
+        }
+      } else {
+        if (gi == 1) cw = T(0);
+        if (gi == nfx - 2) ce = T(0);
+        if (gj == 1) cs = T(0);
+        if (gj == nfy - 2) cn = T(0);
+      }
+      const int zc = (aj + 1) * FZ + (ai + 1);
+      v = cmul(cen, zs[zc]);
+      v = rfma(cw, zs[zc - 1], v);
+      v = rfma(ce, zs[zc + 1], v);
+      v = rfma(cs, zs[zc - FZ], v);
+      v = rfma(cn, zs[zc + FZ], v);
+    }
+    as[q] = v;
+  }
+  __syncthreads();
+  // 4. y = R_Z (A z) on the coarse tile; fine nodes outside the grid (and
+  //    Dirichlet boundary nodes) hold zero in `as`
+  const int I = I0 + tid % TC, J = J0 + tid / TC;
+  if (I >= ncx || J >= ncy) return;
+  C<T> acc = czero<T>();
+  if (!(bc == BC_DIRICHLET && on_bnd(I, J, ncx, ncy))) {
+    const int ab = 2 * (I - I0), bb = 2 * (J - J0);   // local index of 2I - 2
+#pragma unroll
+    for (int b = -2; b <= 2; ++b) {
+      const T wy = rtap<T>(zk, b);
+#pragma unroll
+      for (int a = -2; a <= 2; ++a)
+        acc = rfma(rtap<T>(zk, a) * wy, as[(bb + 2 + b) * FA + ab + 2 + a], acc);
+    }
+    acc = T(0.25) * acc;
+  }
+  y[r * nc + (long long)J * ncx + I] = acc;
 }
 
 // ReD-Glk (Sec. 5.2.4): printed 5x5 Galerkin Laplacian (scale 1/(256 H^2))
@@ -367,24 +366,6 @@ __global__ void k_mask_dirichlet(LevelDev L, C<T>* __restrict__ x) {
   const int r = blockIdx.z;
   if (i >= L.nx || j >= L.ny || !on_bnd(i, j, L.nx, L.ny)) return;
   x[(long long)r * L.nx * L.ny + (long long)j * L.nx + i] = czero<T>();
-}
-
-template <class T>
-__global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRef<T> fin,
-                           C<T>* __restrict__ x, const int* __restrict__ done) {
-  extern __shared__ unsigned char smraw[];
-  C<T>* fs = reinterpret_cast<C<T>*>(smraw);
-  const int r = blockIdx.y;
-  if (done && done[r]) return;
-  const C<T>* f = fin.get();
-  for (int c = threadIdx.x; c < n; c += blockDim.x) fs[c] = f[(long long)r * n + c];
-  __syncthreads();
-  const int row = blockIdx.x * blockDim.x + threadIdx.x;
-  if (row >= n) return;
-  const C<T>* mr = minv + (long long)row * n;
-  C<T> acc = czero<T>();
-  for (int c = 0; c < n; ++c) acc = cfma(mr[c], fs[c], acc);
-  x[(long long)r * n + row] = acc;
 }
 
 template <class T> __device__ __forceinline__ C<T> cvt(double2 v);
@@ -579,36 +560,6 @@ void launch_helm(const LevelDev& L, int bc, Shift s, VRef<T> x, VRef<T> b,
       L, bc, (T)s.re, (T)s.im, x, b, y, done);
 }
 template <class T>
-void launch_jacobi0(const LevelDev& L, int bc, VRef<T> f, C<T>* x, int nrhs,
-                    const int* done, cudaStream_t st) {
-  HZ_COUNT();
-  k_jacobi0<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, f, x, done);
-}
-template <class T>
-void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc,
-                           Shift s, VRef<T> f, const C<T>* x, C<T>* fc,
-                           int nrhs, const int* done, cudaStream_t st) {
-  HZ_COUNT();
-  k_resid_restrict<T><<<grid2d(Lc.nx, Lc.ny, nrhs), dim3(BX, BY), 0, st>>>(
-      Lf, Lc, bc, (T)s.re, (T)s.im, f, x, fc, done);
-}
-template <class T>
-void launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, int bc,
-                        const C<T>* xc, C<T>* x, int nrhs, const int* done,
-                        cudaStream_t st) {
-  HZ_COUNT();
-  k_prolong_add<T><<<grid2d(Lf.nx, Lf.ny, nrhs), dim3(BX, BY), 0, st>>>(
-      Lf, Lc, bc, xc, x, done);
-}
-template <class T>
-void launch_smooth(const LevelDev& L, int bc, Shift s, VRef<T> f,
-                   const C<T>* x, C<T>* xo, int nrhs, const int* done,
-                   cudaStream_t st) {
-  HZ_COUNT();
-  k_smooth<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(
-      L, bc, (T)s.re, (T)s.im, f, x, xo, done);
-}
-template <class T>
 void launch_restrict_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
                        VRef<T> fine, C<T>* coarse, int nrhs, const int* done,
                        cudaStream_t st) {
@@ -625,19 +576,20 @@ void launch_prolong_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
       Lf, Lc, bc, zk, coarse, fine, add, done);
 }
 template <class T>
+void launch_galerkin_fused(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
+                           const C<T>* x, C<T>* y, int nrhs, const int* done,
+                           cudaStream_t st) {
+  HZ_COUNT();
+  constexpr int TC = 16;
+  k_galerkin_fused<T, TC><<<dim3((Lc.nx + TC - 1) / TC, (Lc.ny + TC - 1) / TC, nrhs),
+                            TC * TC, 0, st>>>(Lf, Lc, bc, zk, x, y, done);
+}
+template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
                 int nrhs, const int* done, cudaStream_t st) {
   HZ_COUNT();
   k_glk<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, variant, x,
                                                                y, done);
-}
-template <class T>
-void launch_dense_mv(int n, const C<T>* minv, VRef<T> f, C<T>* x, int nrhs,
-                     const int* done, cudaStream_t st) {
-  HZ_COUNT();
-  const int nt = 128;
-  k_dense_mv<T><<<dim3((n + nt - 1) / nt, nrhs), nt, n * sizeof(C<T>), st>>>(
-      n, minv, f, x, done);
 }
 template <class T>
 void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
@@ -692,29 +644,20 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
   template void launch_helm<T>(const LevelDev&, int, Shift, VRef<T>,            \
                                VRef<T>, C<T>*, int, const int*,                 \
                                cudaStream_t);                                   \
-  template void launch_jacobi0<T>(const LevelDev&, int, VRef<T>, C<T>*, int,    \
-                                  const int*, cudaStream_t);                    \
-  template void launch_resid_restrict<T>(const LevelDev&, const LevelDev&, int, \
-                                         Shift, VRef<T>, const C<T>*, C<T>*,    \
-                                         int, const int*, cudaStream_t);        \
-  template void launch_prolong_add<T>(const LevelDev&, const LevelDev&, int,    \
-                                      const C<T>*, C<T>*, int, const int*,      \
-                                      cudaStream_t);                            \
-  template void launch_smooth<T>(const LevelDev&, int, Shift, VRef<T>,          \
-                                 const C<T>*, C<T>*, int, const int*,           \
-                                 cudaStream_t);                                 \
   template void launch_restrict_z<T>(const LevelDev&, const LevelDev&, int,     \
                                      int, VRef<T>, C<T>*, int, const int*,      \
                                      cudaStream_t);                             \
   template void launch_prolong_z<T>(const LevelDev&, const LevelDev&, int, int, \
                                     const C<T>*, C<T>*, int, int, const int*,   \
                                     cudaStream_t);                              \
+  template void launch_galerkin_fused<T>(const LevelDev&, const LevelDev&, int, \
+                                         int, const C<T>*, C<T>*, int,          \
+                                         const int*, cudaStream_t);             \
   template void launch_glk<T>(const LevelDev&, int, int, const C<T>*, C<T>*,    \
                               int, const int*, cudaStream_t);                   \
   template void launch_mask_dirichlet<T>(const LevelDev&, int, C<T>*, int,      \
                                          cudaStream_t);                        \
-  template void launch_dense_mv<T>(int, const C<T>*, VRef<T>, C<T>*, int,       \
-                                   const int*, cudaStream_t);
+  /* end */
 
 HZ_INST(double)
 HZ_INST(float)

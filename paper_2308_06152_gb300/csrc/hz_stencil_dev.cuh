@@ -1,0 +1,77 @@
+// Device helpers shared by the stencil and V-cycle translation units: the
+// boundary test, one row of the Helmholtz / CSLP operator and bilinear
+// interpolation, for any storage type of the vector they read.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "hz_common.cuh"
+
+namespace hz {
+
+__device__ __forceinline__ float2 ld2(const __nv_bfloat162* p, long long i) {
+  return __bfloat1622float2(p[i]);
+}
+__device__ __forceinline__ void st2(__nv_bfloat162* p, long long i, float2 v) {
+  p[i] = __float22bfloat162_rn(v);
+}
+
+__device__ __forceinline__ bool on_bnd(int i, int j, int nx, int ny) {
+  return i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
+}
+
+// (M x)(i, j) for an unknown node (i, j): centre 4/h^2 - s k^2, Sommerfeld
+// sides add -2 i k / h each, remove the outward neighbour and double the
+// opposite one (ghost elimination); Dirichlet rows drop couplings to the
+// (fixed zero) boundary nodes.  x is stored as SX, the arithmetic is C<T>.
+template <class T, class SX>
+__device__ __forceinline__ C<T> helm_point(const LevelDev& L, int bc, T sre,
+                                           T sim, const SX* __restrict__ x,
+                                           int i, int j) {
+  const int nx = L.nx, ny = L.ny;
+  const long long id = (long long)j * nx + i;
+  const T ih2 = ih2_of<T>(L);
+  const T k2 = k2_of<T>(L)[id];
+  C<T> cen = mkc(T(4) * ih2 - sre * k2, -sim * k2);
+  T cw = -ih2, ce = -ih2, cs = -ih2, cn = -ih2;
+  if (bc == BC_SOMMERFELD) {
+    const bool x0 = i == 0, x1 = i == nx - 1, y0 = j == 0, y1 = j == ny - 1;
+    const int ns = int(x0) + int(x1) + int(y0) + int(y1);
+    if (ns) {
+      cen.y -= T(ns) * tih_of<T>(L) * sqrt(k2);
+      if (x0) { cw = T(0); ce = T(2) * ce; }
+      if (x1) { ce = T(0); cw = T(2) * cw; }
+      if (y0) { cs = T(0); cn = T(2) * cn; }
+      if (y1) { cn = T(0); cs = T(2) * cs; }
+    }
+  } else {
+    if (i == 1) cw = T(0);
+    if (i == nx - 2) ce = T(0);
+    if (j == 1) cs = T(0);
+    if (j == ny - 2) cn = T(0);
+  }
+  C<T> acc = cmul(cen, ld2(x, id));
+  if (cw != T(0)) acc = rfma(cw, ld2(x, id - 1), acc);
+  if (ce != T(0)) acc = rfma(ce, ld2(x, id + 1), acc);
+  if (cs != T(0)) acc = rfma(cs, ld2(x, id - nx), acc);
+  if (cn != T(0)) acc = rfma(cn, ld2(x, id + nx), acc);
+  return acc;
+}
+
+// bilinear interpolation of the coarse vector xc (stored as SC) at fine
+// node (i, j)
+template <class T, class SC>
+__device__ __forceinline__ C<T> interp_bilinear(const LevelDev& Lc,
+                                                const SC* __restrict__ xc,
+                                                int i, int j) {
+  const int I0 = i >> 1, J0 = j >> 1;
+  const bool ox = i & 1, oy = j & 1;
+  const long long b0 = (long long)J0 * Lc.nx + I0;
+  if (!ox && !oy) return ld2(xc, b0);
+  if (ox && !oy) return T(0.5) * (ld2(xc, b0) + ld2(xc, b0 + 1));
+  if (!ox && oy) return T(0.5) * (ld2(xc, b0) + ld2(xc, b0 + Lc.nx));
+  return T(0.25) * ((ld2(xc, b0) + ld2(xc, b0 + 1)) +
+                    (ld2(xc, b0 + Lc.nx) + ld2(xc, b0 + Lc.nx + 1)));
+}
+
+}  // namespace hz

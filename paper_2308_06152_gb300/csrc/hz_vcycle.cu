@@ -1,0 +1,208 @@
+// Kernels of the CSLP multigrid V-cycle (Sec. 3.1, Sec. 5.1): damped-Jacobi
+// sweeps (w = 0.8) with the residual fused into full-weighting restriction
+// (eq. weight operator), bilinear interpolation of the correction (eq.
+// bilinear operator) and the dense coarsest-level solve.  Vectors of the
+// level hierarchy may be stored in a narrower type than the arithmetic
+// (BF16 pairs for the smoother variant); the arithmetic is C<T>.
+#include "hz_common.cuh"
+#include "hz_stencil_dev.cuh"
+
+namespace hz {
+
+namespace {
+
+constexpr int BX = 32, BY = 8;
+
+inline dim3 grid2d(int nx, int ny, int nrhs) {
+  return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY, nrhs);
+}
+
+// x = dinv .* f (one damped-Jacobi sweep from x = 0)
+template <class T, class SF, class SX>
+__global__ void k_jacobi0(LevelDev L, int bc, VRefE<SF> fin, SX* __restrict__ x,
+                          const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
+  const long long n = (long long)L.nx * L.ny, id = (long long)j * L.nx + i;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, L.nx, L.ny)) {
+    st2(x, r * n + id, czero<T>());
+    return;
+  }
+  st2(x, r * n + id, cmul(dinv_of<T>(L)[id], ld2(fin.get(), r * n + id)));
+}
+
+// fc(I,J) = sum_{a,b in -1..1} (2-|a|)(2-|b|)/16 * (f - M x)(2I+a, 2J+b)
+template <class T, class SF, class SX, class SC>
+__global__ void k_resid_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
+                                 VRefE<SF> fin, const SX* __restrict__ x,
+                                 SC* __restrict__ fc, const int* __restrict__ done) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (I >= Lc.nx || J >= Lc.ny || (done && done[r])) return;
+  const long long nf = (long long)Lf.nx * Lf.ny, nc = (long long)Lc.nx * Lc.ny;
+  const long long idc = (long long)J * Lc.nx + I;
+  if (bc == BC_DIRICHLET && on_bnd(I, J, Lc.nx, Lc.ny)) {
+    st2(fc, r * nc + idc, czero<T>());
+    return;
+  }
+  const SF* f = fin.get() + r * nf;
+  const SX* xr = x + r * nf;
+  C<T> acc = czero<T>();
+  for (int b = -1; b <= 1; ++b) {
+    const int jf = 2 * J + b;
+    if (jf < 0 || jf >= Lf.ny) continue;
+    for (int a = -1; a <= 1; ++a) {
+      const int ifn = 2 * I + a;
+      if (ifn < 0 || ifn >= Lf.nx) continue;
+      if (bc == BC_DIRICHLET && on_bnd(ifn, jf, Lf.nx, Lf.ny)) continue;
+      const C<T> res = ld2(f, (long long)jf * Lf.nx + ifn) -
+                       helm_point<T, SX>(Lf, bc, sre, sim, xr, ifn, jf);
+      const T w = T((2 - abs(a)) * (2 - abs(b))) * T(0.0625);
+      acc = rfma(w, res, acc);
+    }
+  }
+  st2(fc, r * nc + idc, acc);
+}
+
+// x += P_bilinear xc
+template <class T, class SC, class SX>
+__global__ void k_prolong_add(LevelDev Lf, LevelDev Lc, int bc,
+                              const SC* __restrict__ xc, SX* __restrict__ x,
+                              const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= Lf.nx || j >= Lf.ny || (done && done[r])) return;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, Lf.nx, Lf.ny)) return;
+  const long long nf = (long long)Lf.nx * Lf.ny, nc = (long long)Lc.nx * Lc.ny;
+  const long long id = (long long)j * Lf.nx + i;
+  st2(x, r * nf + id, ld2(x, r * nf + id) + interp_bilinear<T, SC>(Lc, xc + r * nc, i, j));
+}
+
+// xo = x + dinv .* (f - M x)
+template <class T, class SF, class SX, class SO>
+__global__ void k_smooth(LevelDev L, int bc, T sre, T sim, VRefE<SF> fin,
+                         const SX* __restrict__ x, SO* __restrict__ xo,
+                         const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
+  const long long n = (long long)L.nx * L.ny, id = (long long)j * L.nx + i;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, L.nx, L.ny)) {
+    st2(xo, r * n + id, czero<T>());
+    return;
+  }
+  const SX* xr = x + r * n;
+  const C<T> res = ld2(fin.get(), r * n + id) - helm_point<T, SX>(L, bc, sre, sim, xr, i, j);
+  st2(xo, r * n + id, cfma(dinv_of<T>(L)[id], res, ld2(xr, id)));
+}
+
+// x = Minv f on the coarsest level (dense inverse built at setup)
+template <class T, class SF, class SO>
+__global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRefE<SF> fin,
+                           SO* __restrict__ x, const int* __restrict__ done) {
+  extern __shared__ unsigned char smraw[];
+  C<T>* fs = reinterpret_cast<C<T>*>(smraw);
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  const SF* f = fin.get();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) fs[c] = ld2(f, (long long)r * n + c);
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const C<T>* mr = minv + (long long)row * n;
+  C<T> acc = czero<T>();
+  for (int c = 0; c < n; ++c) acc = cfma(mr[c], fs[c], acc);
+  st2(x, (long long)r * n + row, acc);
+}
+
+}  // namespace
+
+template <class T, class SF, class SX>
+void launch_jacobi0(const LevelDev& L, int bc, VRefE<SF> f, SX* x, int nrhs,
+                    const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_jacobi0<T, SF, SX><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, f, x,
+                                                                       done);
+}
+template <class T, class SF, class SX, class SC>
+void launch_resid_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
+                           VRefE<SF> f, const SX* x, SC* fc, int nrhs,
+                           const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_resid_restrict<T, SF, SX, SC><<<grid2d(Lc.nx, Lc.ny, nrhs), dim3(BX, BY), 0, st>>>(
+      Lf, Lc, bc, (T)s.re, (T)s.im, f, x, fc, done);
+}
+template <class T, class SC, class SX>
+void launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, int bc, const SC* xc,
+                        SX* x, int nrhs, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_prolong_add<T, SC, SX><<<grid2d(Lf.nx, Lf.ny, nrhs), dim3(BX, BY), 0, st>>>(
+      Lf, Lc, bc, xc, x, done);
+}
+template <class T, class SF, class SX, class SO>
+void launch_smooth(const LevelDev& L, int bc, Shift s, VRefE<SF> f, const SX* x,
+                   SO* xo, int nrhs, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_smooth<T, SF, SX, SO><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(
+      L, bc, (T)s.re, (T)s.im, f, x, xo, done);
+}
+template <class T, class SF, class SO>
+void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
+                     const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  const int nt = 128;
+  k_dense_mv<T, SF, SO><<<dim3((n + nt - 1) / nt, nrhs), nt, n * sizeof(C<T>), st>>>(
+      n, minv, f, x, done);
+}
+
+// Instantiations: the plain FP64 and FP32 hierarchies (one storage type), and
+// the BF16-storage hierarchy under an FP32 V-cycle whose entry vector and
+// result stay FP32.
+#define HZ_VC_SAME(T)                                                           \
+  template void launch_jacobi0<T, C<T>, C<T>>(const LevelDev&, int, VRef<T>,    \
+                                              C<T>*, int, const int*,           \
+                                              cudaStream_t);                    \
+  template void launch_resid_restrict<T, C<T>, C<T>, C<T>>(                     \
+      const LevelDev&, const LevelDev&, int, Shift, VRef<T>, const C<T>*,       \
+      C<T>*, int, const int*, cudaStream_t);                                    \
+  template void launch_prolong_add<T, C<T>, C<T>>(const LevelDev&,              \
+                                                  const LevelDev&, int,         \
+                                                  const C<T>*, C<T>*, int,      \
+                                                  const int*, cudaStream_t);    \
+  template void launch_smooth<T, C<T>, C<T>, C<T>>(const LevelDev&, int, Shift, \
+                                                   VRef<T>, const C<T>*, C<T>*, \
+                                                   int, const int*,             \
+                                                   cudaStream_t);               \
+  template void launch_dense_mv<T, C<T>, C<T>>(int, const C<T>*, VRef<T>,       \
+                                               C<T>*, int, const int*,          \
+                                               cudaStream_t);
+
+HZ_VC_SAME(double)
+HZ_VC_SAME(float)
+
+using bf2 = __nv_bfloat162;
+template void launch_jacobi0<float, float2, bf2>(const LevelDev&, int, VRefE<float2>,
+                                                 bf2*, int, const int*, cudaStream_t);
+template void launch_jacobi0<float, bf2, bf2>(const LevelDev&, int, VRefE<bf2>, bf2*,
+                                              int, const int*, cudaStream_t);
+template void launch_resid_restrict<float, float2, bf2, bf2>(
+    const LevelDev&, const LevelDev&, int, Shift, VRefE<float2>, const bf2*, bf2*, int,
+    const int*, cudaStream_t);
+template void launch_resid_restrict<float, bf2, bf2, bf2>(
+    const LevelDev&, const LevelDev&, int, Shift, VRefE<bf2>, const bf2*, bf2*, int,
+    const int*, cudaStream_t);
+template void launch_prolong_add<float, bf2, bf2>(const LevelDev&, const LevelDev&, int,
+                                                  const bf2*, bf2*, int, const int*,
+                                                  cudaStream_t);
+template void launch_smooth<float, float2, bf2, float2>(const LevelDev&, int, Shift,
+                                                        VRefE<float2>, const bf2*,
+                                                        float2*, int, const int*,
+                                                        cudaStream_t);
+template void launch_smooth<float, bf2, bf2, bf2>(const LevelDev&, int, Shift,
+                                                  VRefE<bf2>, const bf2*, bf2*, int,
+                                                  const int*, cudaStream_t);
+template void launch_dense_mv<float, bf2, bf2>(int, const float2*, VRefE<bf2>, bf2*, int,
+                                               const int*, cudaStream_t);
+
+}  // namespace hz

@@ -116,6 +116,50 @@ def test_vcycle(bc, prec, tol):
         assert rel(y, ref) < tol, (l, rel(y, ref))
 
 
+@pytest.mark.parametrize("bc", BCS)
+def test_vcycle_bf16_storage(bc):
+    """BF16-storage smoother: level vectors rounded to 8-bit mantissas
+    (relative 2^-9 per stored value), FP32 arithmetic; the V-cycle stays
+    within 2e-2 of the FP64 oracle's."""
+    k2 = rk2(NY, NX, 6)
+    s = solver(NX, NY, H, k2, bc, z="ho", prec="mixed_bf16")
+    orc = Oracle(NX, NY, H, k2, bc, z="ho", coarsest="direct")
+    for l in (0, 1, orc.L):
+        lv = orc.levels[l]
+        f = wl.random_complex((1, lv.ny, lv.nx), 30 + l)
+        y = to_np(s.apply("vcycle", f, l))[0]
+        ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[0]), l))
+        assert rel(y, ref) < (2e-2 if l < orc.L else 1e-6), (l, rel(y, ref))
+
+
+@pytest.mark.parametrize("prec,basis16", [("mixed", True), ("mixed_bf16", False),
+                                          ("mixed_bf16", True)])
+def test_reduced_storage_solves_reach_fp64_residual(prec, basis16):
+    """FP16 inner Krylov basis and / or BF16 V-cycle storage inside FP64
+    FGMRES: every RHS still reaches a true FP64 residual <= 1e-6 (checked
+    with the oracle's A); the iteration counts stay near the FP32 ones."""
+    n, k = 129, 80.0
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    nodes = [(64, 64), (30, 90)]
+    b = wl.point_sources(n, n, nodes)
+    ref = solver(n, n, h, k2, "sommerfeld", prec="mixed", nrhs=2,
+                 coarse_tol=1e-1, coarse_maxit=300)
+    _, iref = ref.solve(b, tol=1e-6)
+    s = solver(n, n, h, k2, "sommerfeld", prec=prec, nrhs=2, coarse_tol=1e-1,
+               coarse_maxit=300, inner_basis_fp16=basis16)
+    x, info = s.solve(b, tol=1e-6)
+    orc = Oracle(n, n, h, k2, "sommerfeld", z="ho", coarsest="direct")
+    lv = orc.levels[0]
+    xs = to_np(x)
+    for r in range(2):
+        bu = lv.to_unknowns(b[r])
+        res = np.linalg.norm(bu - orc.A @ lv.to_unknowns(xs[r])) / np.linalg.norm(bu)
+        assert res <= 1e-6 and info[r].status == "HZ_OK", (r, res)
+        assert info[r].outer_iters <= iref[r].outer_iters + 2
+        assert info[r].inner_iters_total <= 1.3 * iref[r].inner_iters_total + 10
+
+
 @pytest.mark.parametrize("bc,z,e", [("sommerfeld", "ho", "galerkin"),
                                     ("dirichlet", "bilinear", "galerkin"),
                                     ("sommerfeld", "ho", "red_glk2")])
@@ -266,6 +310,40 @@ def test_gradient_matches_oracle():
     assert J == pytest.approx(J0, rel=1e-8)
     assert rel(to_np(g), g0) < 1e-7
     assert len(infos) == 6 and all(i.status == "HZ_OK" for i in infos)
+
+
+def test_autograd_gradient_matches_central_differences():
+    """dJ/dm from the library's adjoint (through torch.autograd) against
+    central differences of J computed by GPU forward solves (tol 1e-12),
+    along random directions and single interior / edge / corner nodes."""
+    from paper_2308_06152_gb300.api import Desc
+    from paper_2308_06152_gb300.autograd import misfit
+    nx, ny, h, omega = 17, 13, 1.0 / 16, 25.0
+    rng = np.random.default_rng(21)
+    m = torch.tensor(rng.uniform(0.7, 1.3, size=(ny, nx)), device="cuda",
+                     requires_grad=True)
+    src = wl.point_sources(nx, ny, [(8, 6), (3, 9)])
+    rec = wl.surface_receivers(nx, 0)
+    d = (rng.standard_normal((2, nx)) + 1j * rng.standard_normal((2, nx))) * 1e-3
+    desc = Desc(nx, ny, h, bc="sommerfeld", z="ho", nrhs_max=2,
+                coarse_tol=1e-12, coarse_maxit=400)
+    J = misfit(m, desc, omega, src, rec, d, tol=1e-12)
+    J.backward()
+    g = m.grad.detach()
+    dirs = [torch.tensor(rng.standard_normal((ny, nx)), device="cuda")
+            for _ in range(3)]
+    for (i, j) in ((8, 6), (0, 5), (0, 0)):
+        e = torch.zeros((ny, nx), dtype=torch.float64, device="cuda")
+        e[j, i] = 1.0
+        dirs.append(e)
+    with torch.no_grad():
+        for dm in dirs:
+            eps = 1e-4 * float(m.abs().max()) / float(dm.abs().max())
+            jp = misfit(m + eps * dm, desc, omega, src, rec, d, tol=1e-12)
+            jm = misfit(m - eps * dm, desc, omega, src, rec, d, tol=1e-12)
+            fd = float(jp - jm) / (2 * eps)
+            an = float((g * dm).sum())
+            assert abs(fd - an) <= 1e-5 * abs(fd), (fd, an)
 
 
 @pytest.mark.slow
