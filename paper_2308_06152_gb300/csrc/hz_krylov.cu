@@ -4,7 +4,9 @@
 // norms, Givens updates of the Hessenberg columns and the triangular solve.
 // Each right-hand side owns its basis, Hessenberg matrix and stopping state;
 // all of them live in device memory so that no launch depends on host data.
+#include <mutex>
 #include <type_traits>
+#include <unordered_map>
 
 #include "hz_common.cuh"
 
@@ -108,14 +110,17 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 template <class T, class SB>
 __global__ void __launch_bounds__(NT)
 k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
-       const C<T>* __restrict__ w, long long n, KState ks, int pass) {
+       const C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs,
+       int nblk) {
   constexpr int TILE = 32, NW = NT / 32;
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
   __shared__ double2 wred[NW][TILE];
   __shared__ double red[NW];
-  const int r = blockIdx.y, blk = blockIdx.x;
-  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   const int j = *ks.jctr;
+  // persistent loop over (RHS, chunk) tiles
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
+  const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
+  if (ks.done[r] || (pass && !ks.reorth[r])) continue;
   // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (sizeof(C<T>) + (j + 1) * sizeof(SB)));
@@ -184,6 +189,7 @@ k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
     }
     __syncthreads();
   }
+  }
 }
 
 // hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] = (pass 0) or += (pass 1)
@@ -223,18 +229,19 @@ __global__ void k_reduce_cols(KState ks, int nblk, int pass) {
 template <class T, class SB>
 __global__ void __launch_bounds__(NT)
 k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
-        C<T>* __restrict__ w, long long n, KState ks, int pass) {
+        C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
   constexpr int TILE = 512;
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
   __shared__ C<T> hs[TILE];
   __shared__ double red[NT / 32];
-  const int r = blockIdx.y;
-  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   const int j = *ks.jctr;
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
+  const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
+  if (ks.done[r] || (pass && !ks.reorth[r])) continue;
   // algorithmic bytes of this RHS: read w and basis 0..j, write w
-  if (ks.abytes && blockIdx.x == 0 && threadIdx.x == 0)
+  if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB)));
-  const long long g0 = (long long)blockIdx.x * (CHUNK / W) + threadIdx.x;
+  const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
   C<T>* wr = w + r * n;
   C<T> acc[EPT];
 #pragma unroll
@@ -287,7 +294,8 @@ k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
       }
     }
   const double t = block_sum((double)wn, red);
-  if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blockIdx.x] = t;
+  if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = t;
+  }
 }
 
 // After the first pass: ||w|| (wpart) and ||w - V h|| (npart) per RHS; the
@@ -502,25 +510,37 @@ __global__ void k_givens_finish(KState ks, int nrhs) {
   }
 }
 
-__global__ void k_trisolve(KState ks, int nrhs) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= nrhs) return;
+// Back substitution R y = g for each RHS (R = rotated Hessenberg), one block
+// per RHS: the right-hand side lives in shared memory and each step updates
+// the rows above the pivot in parallel.
+__global__ void k_trisolve(KState ks) {
+  extern __shared__ unsigned char smraw[];
+  double2* gs = reinterpret_cast<double2*>(smraw);   // k entries
+  __shared__ double2 yi_s;
+  const int r = blockIdx.x;
   const int m = ks.m, k = ks.iters[r];
   const double2* H = ks.H + (long long)r * (m + 1) * m;
-  const double2* g = ks.g + (long long)r * (m + 1);
   double2* y = ks.y + (long long)r * m;
+  for (int q = threadIdx.x; q < k; q += blockDim.x) gs[q] = ks.g[(long long)r * (m + 1) + q];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    double2 s = g[i];
-    for (int c = i + 1; c < k; ++c) {
-      const double2 h = H[(long long)i * m + c], yc = y[c];
-      s.x -= h.x * yc.x - h.y * yc.y;
-      s.y -= h.x * yc.y + h.y * yc.x;
+    if (threadIdx.x == 0) {
+      const double2 d = H[(long long)i * m + i], s = gs[i];
+      const double dm = d.x * d.x + d.y * d.y;
+      const double2 v = (dm > 0.0) ? make_double2((s.x * d.x + s.y * d.y) / dm,
+                                                  (s.y * d.x - s.x * d.y) / dm)
+                                   : make_double2(0.0, 0.0);
+      y[i] = v;
+      yi_s = v;
     }
-    const double2 d = H[(long long)i * m + i];
-    const double dm = d.x * d.x + d.y * d.y;
-    y[i] = (dm > 0.0) ? make_double2((s.x * d.x + s.y * d.y) / dm,
-                                     (s.y * d.x - s.x * d.y) / dm)
-                      : make_double2(0.0, 0.0);
+    __syncthreads();
+    const double2 yv = yi_s;
+    for (int q = threadIdx.x; q < i; q += blockDim.x) {
+      const double2 h = H[(long long)q * m + i];
+      gs[q].x -= h.x * yv.x - h.y * yv.y;
+      gs[q].y -= h.x * yv.y + h.y * yv.x;
+    }
+    __syncthreads();
   }
 }
 
@@ -528,13 +548,14 @@ __global__ void k_trisolve(KState ks, int nrhs) {
 template <class SB, class Tx>
 __global__ void __launch_bounds__(NT)
 k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
-         C<Tx>* __restrict__ x, int accumulate, long long n) {
+         C<Tx>* __restrict__ x, int accumulate, long long n, int nrhs, int nblk) {
   constexpr int TILE = 512;
   __shared__ C<Tx> ys[TILE];
-  const int r = blockIdx.y;
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
+  const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
   const int k = ks.iters[r];
-  if (accumulate && k == 0) return;
-  const long long base = (long long)blockIdx.x * CHUNK + threadIdx.x;
+  if (accumulate && k == 0) continue;
+  const long long base = (long long)blk * CHUNK + threadIdx.x;
   C<Tx>* xr = x + r * n;
   C<Tx> acc[EPT];
 #pragma unroll
@@ -567,6 +588,7 @@ k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
     const long long e = base + q * NT;
     if (e < n) xr[e] = acc[q];
   }
+  }
 }
 
 __global__ void k_fill_int(int* p, int v, int count) {
@@ -582,12 +604,42 @@ __global__ void k_copy_int(const int* s, int* d, int count) {
 
 int krylov_nblk(long long n) { return (int)((n + CHUNK - 1) / CHUNK); }
 
+namespace {
+// Blocks of a persistent launch: at most as many as the GPU keeps resident
+// (SMs x resident blocks per SM for this kernel), so the last wave is never
+// a small fraction of the GPU; cached per kernel and device.
+std::mutex g_grid_mu;
+std::unordered_map<long long, int> g_grid_cap;
+
+unsigned persistent_grid(const void* kern, long long tiles) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const long long key = (long long)(uintptr_t)kern * 64 + dev;
+  int cap = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_grid_mu);
+    auto it = g_grid_cap.find(key);
+    if (it != g_grid_cap.end()) cap = it->second;
+  }
+  if (!cap) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, 0);
+    cap = (sms > 0 ? sms : 1) * (per > 0 ? per : 1);
+    std::lock_guard<std::mutex> lock(g_grid_mu);
+    g_grid_cap[key] = cap;
+  }
+  return (unsigned)(tiles < cap ? tiles : cap);
+}
+}  // namespace
+
 template <class T, class SB>
 void launch_mdot(const SB* V, long long vstride, long long rs, const C<T>* w,
                  long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_mdot<T, SB><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, w, n, ks,
-                                                          pass);
+  const int nblk = krylov_nblk(n);
+  const unsigned grid = persistent_grid((const void*)k_mdot<T, SB>, (long long)nblk * nrhs);
+  k_mdot<T, SB><<<grid, NT, 0, st>>>(V, vstride, rs, w, n, ks, pass, nrhs, nblk);
 }
 void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st) {
@@ -600,8 +652,9 @@ template <class T, class SB>
 void launch_maxpy(const SB* V, long long vstride, long long rs, C<T>* w,
                   long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
-  k_maxpy<T, SB><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, w, n, ks,
-                                                           pass);
+  const int nblk = krylov_nblk(n);
+  const unsigned grid = persistent_grid((const void*)k_maxpy<T, SB>, (long long)nblk * nrhs);
+  k_maxpy<T, SB><<<grid, NT, 0, st>>>(V, vstride, rs, w, n, ks, pass, nrhs, nblk);
 }
 void launch_reorth_decide(const KState& ks, long long n, int nrhs, double eta,
                           cudaStream_t st) {
@@ -649,15 +702,16 @@ void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
 }
 void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st) {
   HZ_COUNT();
-  k_trisolve<<<(nrhs + 63) / 64, 64, 0, st>>>(ks, nrhs);
+  k_trisolve<<<nrhs, 128, (size_t)ks.m * sizeof(double2), st>>>(ks);
 }
 template <class SB, class Tx>
 void launch_update(const SB* V, long long vstride, long long rs, const KState& ks,
                    C<Tx>* x, int accumulate, long long n, int nrhs,
                    cudaStream_t st) {
   HZ_COUNT();
-  k_update<SB, Tx><<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(V, vstride, rs, ks, x,
-                                                              accumulate, n);
+  const int nblk = krylov_nblk(n);
+  const unsigned grid = persistent_grid((const void*)k_update<SB, Tx>, (long long)nblk * nrhs);
+  k_update<SB, Tx><<<grid, NT, 0, st>>>(V, vstride, rs, ks, x, accumulate, n, nrhs, nblk);
 }
 void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
   HZ_COUNT();

@@ -156,15 +156,20 @@ __device__ __forceinline__ T rtap(int zk, int a) {
   return (a == 0) ? T(1) : ((a == 1 || a == -1) ? T(0.5) : T(0));
 }
 
-template <class T, int TC>
+// The interpolation and the restriction are tensor products of 1-D rules,
+// so they run as an x pass then a y pass (3 + 3 taps instead of 9, 5 + 5
+// instead of 25).  Shared buffers are reused between passes:
+//   xs: coarse tile;  bufA: x-interpolated rows, then A z;
+//   bufZ: z = Z x, then the x-restricted rows.
+template <class T, int TC, int ZK>
 __global__ void __launch_bounds__(TC * TC)
-k_galerkin_fused(LevelDev Lf, LevelDev Lc, int bc, int zk,
-                 const C<T>* __restrict__ x, C<T>* __restrict__ y,
-                 const int* __restrict__ done) {
+k_galerkin_fused(LevelDev Lf, LevelDev Lc, int bc, const C<T>* __restrict__ x,
+                 C<T>* __restrict__ y, const int* __restrict__ done) {
   constexpr int CX = TC + 5, FZ = 2 * TC + 5, FA = 2 * TC + 3;
   __shared__ C<T> xs[CX * CX];
-  __shared__ C<T> zs[FZ * FZ];
-  __shared__ C<T> as[FA * FA];
+  __shared__ C<T> bufZ[FZ * FZ];
+  __shared__ C<T> bufA[FA * FA];
+  static_assert(CX * FZ <= FA * FA && FA * TC <= FZ * FZ, "buffer reuse");
   const int r = blockIdx.z;
   if (done && done[r]) return;
   const int I0 = blockIdx.x * TC, J0 = blockIdx.y * TC;
@@ -183,25 +188,35 @@ k_galerkin_fused(LevelDev Lf, LevelDev Lc, int bc, int zk,
     xs[q] = v;
   }
   __syncthreads();
-  // 2. z = Z x on fine nodes [2I0-3, 2I0+2TC+1]^2
+  // 2a. interpolate along x: coarse rows x fine columns [2I0-3, 2I0+2TC+1]
+  C<T>* zx = bufA;
+  for (int q = tid; q < CX * FZ; q += nt) {
+    const int cj = q / FZ, fi = q % FZ;
+    T w0, w1, w2;
+    const int bx = ztaps<T>(ZK, 2 * I0 - 3 + fi, w0, w1, w2) - (I0 - 2);
+    const C<T>* row = xs + cj * CX + bx;
+    zx[q] = rfma(w2, row[2], rfma(w1, row[1], w0 * row[0]));
+  }
+  __syncthreads();
+  // 2b. interpolate along y: z on fine nodes [2I0-3, 2I0+2TC+1]^2, zero
+  //     outside the grid and on Dirichlet boundary nodes
   for (int q = tid; q < FZ * FZ; q += nt) {
-    const int gi = 2 * I0 - 3 + q % FZ, gj = 2 * J0 - 3 + q / FZ;
+    const int fj = q / FZ, fi = q % FZ;
+    const int gi = 2 * I0 - 3 + fi, gj = 2 * J0 - 3 + fj;
     C<T> v = czero<T>();
     if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
         !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
-      T wx[3], wy[3];
-      const int bx = ztaps<T>(zk, gi, wx[0], wx[1], wx[2]) - (I0 - 2);
-      const int by = ztaps<T>(zk, gj, wy[0], wy[1], wy[2]) - (J0 - 2);
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          v = rfma(wx[a] * wy[b], xs[(by + b) * CX + bx + a], v);
+      T w0, w1, w2;
+      const int by = ztaps<T>(ZK, gj, w0, w1, w2) - (J0 - 2);
+      const C<T>* col = zx + by * FZ + fi;
+      v = rfma(w2, col[2 * FZ], rfma(w1, col[FZ], w0 * col[0]));
     }
-    zs[q] = v;
+    bufZ[q] = v;
   }
   __syncthreads();
   // 3. A_h z on fine nodes [2I0-2, 2I0+2TC]^2
+  const C<T>* zs = bufZ;
+  C<T>* as = bufA;
   const T ih2 = ih2_of<T>(Lf);
   const T* k2 = k2_of<T>(Lf);
   for (int q = tid; q < FA * FA; q += nt) {
@@ -239,20 +254,27 @@ k_galerkin_fused(LevelDev Lf, LevelDev Lc, int bc, int zk,
     as[q] = v;
   }
   __syncthreads();
-  // 4. y = R_Z (A z) on the coarse tile; fine nodes outside the grid (and
-  //    Dirichlet boundary nodes) hold zero in `as`
-  const int I = I0 + tid % TC, J = J0 + tid / TC;
+  // 4a. restrict along x: fine rows [2J0-2, 2J0+2TC] x the tile's columns;
+  //     fine nodes outside the grid hold zero in `as`
+  C<T>* rx = bufZ;
+  for (int q = tid; q < FA * TC; q += nt) {
+    const int fa = q / TC, ti = q % TC;
+    const C<T>* row = as + fa * FA + 2 * ti;
+    C<T> v = czero<T>();
+#pragma unroll
+    for (int a = 0; a < 5; ++a) v = rfma(rtap<T>(ZK, a - 2), row[a], v);
+    rx[q] = v;
+  }
+  __syncthreads();
+  // 4b. restrict along y and scale by 1/4 (R_Z = Z^T / 4)
+  const int ti = tid % TC, tj = tid / TC;
+  const int I = I0 + ti, J = J0 + tj;
   if (I >= ncx || J >= ncy) return;
   C<T> acc = czero<T>();
   if (!(bc == BC_DIRICHLET && on_bnd(I, J, ncx, ncy))) {
-    const int ab = 2 * (I - I0), bb = 2 * (J - J0);   // local index of 2I - 2
+    const C<T>* col = rx + (2 * tj) * TC + ti;
 #pragma unroll
-    for (int b = -2; b <= 2; ++b) {
-      const T wy = rtap<T>(zk, b);
-#pragma unroll
-      for (int a = -2; a <= 2; ++a)
-        acc = rfma(rtap<T>(zk, a) * wy, as[(bb + 2 + b) * FA + ab + 2 + a], acc);
-    }
+    for (int b = 0; b < 5; ++b) acc = rfma(rtap<T>(ZK, b - 2), col[b * TC], acc);
     acc = T(0.25) * acc;
   }
   y[r * nc + (long long)J * ncx + I] = acc;
@@ -581,8 +603,11 @@ void launch_galerkin_fused(const LevelDev& Lf, const LevelDev& Lc, int bc, int z
                            cudaStream_t st) {
   HZ_COUNT();
   constexpr int TC = 16;
-  k_galerkin_fused<T, TC><<<dim3((Lc.nx + TC - 1) / TC, (Lc.ny + TC - 1) / TC, nrhs),
-                            TC * TC, 0, st>>>(Lf, Lc, bc, zk, x, y, done);
+  const dim3 grid((Lc.nx + TC - 1) / TC, (Lc.ny + TC - 1) / TC, nrhs);
+  if (zk == ZK_HO)
+    k_galerkin_fused<T, TC, ZK_HO><<<grid, TC * TC, 0, st>>>(Lf, Lc, bc, x, y, done);
+  else
+    k_galerkin_fused<T, TC, ZK_BILINEAR><<<grid, TC * TC, 0, st>>>(Lf, Lc, bc, x, y, done);
 }
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
