@@ -59,6 +59,20 @@ WORKLOADS = {
                         z="bilinear", e="galerkin", nrhs=1,
                         sources="centre", coarse_tol=1e-6,
                         coarse_maxit=1000, outer_maxit=100, tol=1e-6),
+    # three-layer wedge, 40 Hz on 289 x 481 (h = 2.08 m, kh = 0.35 at
+    # 1500 m/s), one source on the surface at x = 300 m
+    "wedge_289x481_f40": dict(model=("wedge", 289, 481, 40.0),
+                              bc="sommerfeld", z="ho", e="galerkin", nrhs=1,
+                              sources="surface_mid", coarse_tol=1e-1,
+                              coarse_maxit=200, outer_maxit=60, tol=1e-6),
+    # seeded layered-and-faulted model, 2301 x 751 physical nodes (h = 4 m)
+    # padded to 2305 x 769, 31.25 Hz (kh = 0.52 at 1500 m/s), 64 surface
+    # sources at i = 35 + 35 s
+    "layered_2305x769_b64": dict(model=("layered", 2301, 751, 31.25),
+                                 bc="sommerfeld", z="ho", e="galerkin",
+                                 nrhs=64, sources="surface_line",
+                                 coarse_tol=1e-1, coarse_maxit=160,
+                                 outer_maxit=30, tol=1e-6),
 }
 DEFAULT_WORKLOAD = "mp2b_1281_k800_b16"
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_bench_counts.json")
@@ -86,10 +100,22 @@ def max_over_ranks(value, world, device="cpu"):
 def build_inputs(wl_name, rank=0):
     from paper_2308_06152_gb300 import workloads as wl
     cfg = WORKLOADS[wl_name]
-    kind, n, k = cfg["model"]
-    model = wl.constant_k(n, k)
+    kind = cfg["model"][0]
+    if kind == "constant_k":
+        model = wl.constant_k(*cfg["model"][1:])
+    elif kind == "wedge":
+        _, nx, ny, f = cfg["model"]
+        model = wl.wedge(f, nx, ny)
+    else:
+        _, nx, ny, f = cfg["model"]
+        model = wl.layered_faulted(nx, ny, freq=f)
     if cfg["sources"] == "centre":
         nodes = [wl.centre_node(model.nx, model.ny)] * cfg["nrhs"]
+    elif cfg["sources"] == "surface_mid":
+        nodes = rank_sources([((model.nx - 1) // 2, 0)] * cfg["nrhs"], rank)
+    elif cfg["sources"] == "surface_line":
+        nodes = rank_sources(wl.surface_line(model.physical[0] - 1,
+                                             cfg["nrhs"]), rank)
     else:
         nodes = rank_sources(wl.centre_cluster(model.nx, model.ny,
                                                cfg["nrhs"]), rank)
@@ -98,9 +124,10 @@ def build_inputs(wl_name, rank=0):
 
 
 def unknowns(cfg, model):
+    """Unknowns per solve; a padded model counts its physical nodes only."""
     if cfg["bc"] == "dirichlet":
         return (model.nx - 2) * (model.ny - 2)
-    return model.nx * model.ny
+    return model.physical[0] * model.physical[1]
 
 
 # ------------------------------------------------------------------ clocks
@@ -250,7 +277,8 @@ def run_ours(args):
                 e=cfg["e"], prec=args.prec, nrhs_max=cfg["nrhs"],
                 coarse_tol=cfg["coarse_tol"], coarse_maxit=cfg["coarse_maxit"],
                 outer_maxit=cfg["outer_maxit"],
-                inner_basis_fp16=bool(args.basis16))
+                inner_basis_fp16=bool(args.basis16),
+                cuda_graph=bool(args.cuda_graph))
     solver = Solver(desc, model.k2)
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
@@ -268,8 +296,6 @@ def run_ours(args):
     sampler = ClockSampler(uuid)
     sampler.start()
     time.sleep(0.3)
-    if args.profile_kernel != "none":
-        solver.profile_begin(args.profile_kernel, max_launches=200000)
     l0 = lib.hz_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -281,7 +307,22 @@ def run_ours(args):
     ev1.record(stream)
     torch.cuda.synchronize()
     launches = lib.hz_kernel_launches() - l0
-    prof = solver.profile_end() if args.profile_kernel != "none" else None
+    # per-kernel timing: CUDA events must bracket every launch of the
+    # profiled kernel class, which a replayed graph does not allow, so these
+    # steps issue the same kernels one by one
+    prof = None
+    prof_ms = None
+    if args.profile_kernel != "none":
+        solver.profile_begin(args.profile_kernel, max_launches=200000)
+        pe0 = torch.cuda.Event(enable_timing=True)
+        pe1 = torch.cuda.Event(enable_timing=True)
+        pe0.record(stream)
+        for _ in range(args.profile_steps):
+            solver.solve(b, tol=tol)
+        pe1.record(stream)
+        torch.cuda.synchronize()
+        prof = solver.profile_end()
+        prof_ms = pe0.elapsed_time(pe1) / args.profile_steps
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     if world > 1:
@@ -316,7 +357,11 @@ def run_ours(args):
                 "traffic": None, "launches": int(n_l),
                 "alg_bytes_per_launch": by / n_l,
                 "avg_launch_us": 1e3 * ms_k / n_l,
-                "share_of_step": ms_k / (ms * args.steps)}
+                "timed_over": (f"{args.profile_steps} further step(s) of the "
+                               "same workload with the kernels issued one by "
+                               "one (events around each launch)"),
+                "profiled_step_ms": prof_ms,
+                "share_of_step": ms_k / (prof_ms * args.profile_steps)}
 
     fp64 = None
     if args.compare_fp64 and args.prec != "fp64":
@@ -354,7 +399,9 @@ def run_ours(args):
             "dtype": "c128" if args.prec == "fp64" else "c64",
             "data": "synthetic",
             "config": {"workload": args.workload, "grid": [model.nx, model.ny],
-                       "k": cfg["model"][2], "bc": cfg["bc"],
+                       "physical_grid": list(model.physical),
+                       "velocity_model": model.name,
+                       "kh_max": round(model.kh_max(), 4), "bc": cfg["bc"],
                        "deflation": f"{cfg['z']}/{cfg['e']}",
                        "precision": PREC_TEXT[args.prec],
                        "inner_basis_storage": ("fp16" if args.basis16 and
@@ -364,6 +411,7 @@ def run_ours(args):
                        "nrhs_per_gpu": cfg["nrhs"], "tol": tol,
                        "coarse_tol": cfg["coarse_tol"],
                        "parallelism": f"replicas{world}",
+                       "cuda_graph": bool(args.cuda_graph),
                        "l2": "inputs larger than L2 (each batch vector "
                              f"{b_np.nbytes / 1e6:.0f} MB)"},
             "e2e": {"value": units / e2e_s, "unit": UNIT,
@@ -417,6 +465,11 @@ def main():
                     help="skip the CPU oracle baseline sample")
     ap.add_argument("--compare-fp64", type=int, default=1,
                     help="also time one solve with the FP64 preconditioner")
+    ap.add_argument("--cuda-graph", type=int, default=1,
+                    help="1: outer iterations as CUDA graphs with a device-side "
+                         "inner WHILE loop; 0: kernels issued one by one")
+    ap.add_argument("--profile-steps", type=int, default=1,
+                    help="steps timed per kernel for the roofline entry")
     ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],
                     default="mdot",
                     help="kernel class timed live for the roofline entry")

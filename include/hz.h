@@ -93,6 +93,12 @@ typedef struct {
   int inner_basis_fp16;       /* mixed precisions only: store the inner
                                  coarse-solve Krylov basis as FP16 pairs
                                  (arithmetic stays FP32); 0 = FP32 basis   */
+  int no_cuda_graph;          /* 0 (default): each outer iteration of hz_solve
+                                 runs as one CUDA graph launch whose inner
+                                 coarse-solve loop is a device-side WHILE
+                                 node; 1: the same kernels issued one by one
+                                 with a host completion check every 4 inner
+                                 iterations.  Results are the same.         */
 } hz_desc;
 
 typedef struct {

@@ -22,7 +22,8 @@ class HzDesc(ctypes.Structure):
                 ("jacobi_omega", c_double), ("min_coarse_intervals", c_int),
                 ("coarse_tol", c_double), ("coarse_maxit", c_int),
                 ("outer_maxit", c_int), ("nrhs_max", c_int),
-                ("inner_basis_fp16", c_int)]
+                ("inner_basis_fp16", c_int),
+                ("no_cuda_graph", c_int)]
 
 
 class HzSolveInfo(ctypes.Structure):

@@ -49,6 +49,7 @@ class Desc:
     outer_maxit: int = 100
     nrhs_max: int = 1
     inner_basis_fp16: bool = False
+    cuda_graph: bool = True
 
     def to_c(self):
         d = HzDesc()
@@ -65,6 +66,7 @@ class Desc:
         d.outer_maxit = int(self.outer_maxit)
         d.nrhs_max = int(self.nrhs_max)
         d.inner_basis_fp16 = int(bool(self.inner_basis_fp16))
+        d.no_cuda_graph = int(not self.cuda_graph)
         return d
 
 

@@ -325,4 +325,18 @@ void launch_image(const LevelDev& L, int bc, double omega, const double2* u,
                   const double2* x, double* grad, int nrhs, cudaStream_t st);
 void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st);
 
+// Device-side loop control of an iteration captured as the body of a CUDA
+// graph WHILE node.  loop_begin (upstream of the node) resets the iteration
+// counter *it and runs the body only if *alldone is clear; loop_next (last
+// node of the body) counts the iteration, adds *body_kernels to the device
+// total of graph-executed kernels and repeats while *alldone is clear and
+// fewer than maxit iterations ran.
+void launch_loop_begin(const int* alldone, int* it, cudaGraphConditionalHandle h,
+                       cudaStream_t st);
+void launch_loop_next(const int* alldone, int* it, int maxit, const int* body_kernels,
+                      cudaGraphConditionalHandle h, cudaStream_t st);
+// Kernels run by WHILE-node bodies on the current device so far (0 if the
+// counter cannot be read).
+unsigned long long graph_body_kernels_run();
+
 }  // namespace hz

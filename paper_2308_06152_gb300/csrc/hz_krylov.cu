@@ -591,6 +591,24 @@ k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
   }
 }
 
+// Kernels executed inside WHILE-node bodies (graph launches are counted on
+// the host; the iterations of a device-side loop only here).
+__device__ unsigned long long g_body_kernels_run;
+
+__global__ void k_loop_begin(const int* alldone, int* it,
+                             cudaGraphConditionalHandle h) {
+  *it = 0;
+  cudaGraphSetConditional(h, *alldone ? 0u : 1u);
+}
+
+__global__ void k_loop_next(const int* alldone, int* it, int maxit,
+                            const int* body_kernels, cudaGraphConditionalHandle h) {
+  const int k = *it + 1;
+  *it = k;
+  atomicAdd(&g_body_kernels_run, (unsigned long long)*body_kernels);
+  cudaGraphSetConditional(h, (!*alldone && k < maxit) ? 1u : 0u);
+}
+
 __global__ void k_fill_int(int* p, int v, int count) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < count) p[e] = v;
@@ -716,6 +734,24 @@ void launch_update(const SB* V, long long vstride, long long rs, const KState& k
 void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
   HZ_COUNT();
   k_fill_int<<<(count + 255) / 256, 256, 0, st>>>(p, v, count);
+}
+void launch_loop_begin(const int* alldone, int* it, cudaGraphConditionalHandle h,
+                       cudaStream_t st) {
+  HZ_COUNT();
+  k_loop_begin<<<1, 1, 0, st>>>(alldone, it, h);
+}
+void launch_loop_next(const int* alldone, int* it, int maxit, const int* body_kernels,
+                      cudaGraphConditionalHandle h, cudaStream_t st) {
+  HZ_COUNT();
+  k_loop_next<<<1, 1, 0, st>>>(alldone, it, maxit, body_kernels, h);
+}
+unsigned long long graph_body_kernels_run() {
+  unsigned long long v = 0;
+  if (cudaMemcpyFromSymbol(&v, g_body_kernels_run, sizeof v) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return v;
 }
 void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
   HZ_COUNT();

@@ -150,6 +150,32 @@ struct hz_solver {
   std::vector<cudaEvent_t> prof_ev;
   size_t prof_used = 0;
   long long prof_dropped = 0;
+  // CUDA graphs of one outer iteration, the inner loop as a WHILE node; one
+  // per (nrhs, tol), captured on the library's own streams (stream capture
+  // is not allowed on the legacy default stream) and launched on st
+  struct OuterGraph {
+    int nrhs;
+    double tol;
+    cudaGraph_t g;
+    cudaGraphExec_t ex;
+    long long kernels;   // kernels of one launch outside WHILE bodies
+  };
+  std::vector<OuterGraph> graphs;
+  cudaStream_t cap_main = nullptr, cap_body = nullptr;
+  bool capturing = false;
+  long long body_count = 0;      // kernels of one WHILE body
+  int* loop_it = nullptr;        // device: iterations of the running loop
+  int* body_kernels = nullptr;   // device: body_count
+  int body_kernels_host = 0;
+
+  ~hz_solver() {
+    for (OuterGraph& g : graphs) {
+      cudaGraphExecDestroy(g.ex);
+      cudaGraphDestroy(g.g);
+    }
+    if (cap_main) cudaStreamDestroy(cap_main);
+    if (cap_body) cudaStreamDestroy(cap_body);
+  }
 };
 
 namespace {
@@ -251,6 +277,8 @@ void plan(hz_solver* s, Arena& a) {
   s->io2 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
   s->Jd = (double*)a.take(sizeof(double));
   s->prof_bytes = (unsigned long long*)a.take(sizeof(unsigned long long));
+  s->loop_it = (int*)a.take(sizeof(int));
+  s->body_kernels = (int*)a.take(sizeof(int));
 }
 
 hz_status init_shapes(hz_solver* s) {
@@ -385,11 +413,15 @@ hz_status read_flag(hz_solver* s, const int* dptr, int* out) {
   return HZ_OK;
 }
 
+bool debug_on() {
+  static const bool on = std::getenv("HZ_DEBUG") != nullptr;
+  return on;
+}
+
 // Opt-in trace (environment HZ_DEBUG=1): Arnoldi state of RHS 0 after a
 // Givens step, printed to stderr.  Synchronises the stream.
 void debug_trace(hz_solver* s, const KState& ks, const char* label) {
-  static const bool on = std::getenv("HZ_DEBUG") != nullptr;
-  if (!on) return;
+  if (!debug_on()) return;
   cudaStreamSynchronize(s->st);
   int j = 0, done = 0, it = 0;
   double hn = 0, bn = 0;
@@ -448,6 +480,86 @@ void cgs2(hz_solver* s, KState& ks, const SB* V, long long vs, long long rs, C<T
 }
 
 // ------------------------------------------------------------ inner solve
+// One Arnoldi step of the inner GMRES: basis vector j (selected on the
+// device by the column counter) -> V-cycle -> E -> Gram-Schmidt -> Givens ->
+// new basis vector.  Every launch goes to s->st and every argument is fixed
+// for the solver, so the step can be captured once and replayed.
+template <class T, class SB>
+void inner_step(hz_solver* s, int nrhs) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin;
+  const long long n1 = s->lv[1].n;
+  const long long rs = inner_row(n1);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  SB* Q = (SB*)s->Qb;
+  C<T>* sb = (C<T>*)s->sb;
+  C<T>* eb = (C<T>*)s->eb;
+  // the V-cycle reads the current basis vector, unpadded, in compute
+  // precision
+  launch_basis_load<SB, T>(vrefe_j<SB>(Q, ks.jctr, 0, vs), rs, (C<T>*)s->qf, n1,
+                           nrhs, ks.done, st);
+  vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
+  apply_E<T>(s, sb, eb, nrhs, ks.done);
+  cgs2<T, SB>(s, ks, Q, vs, rs, eb, n1, nrhs);
+  launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, st);
+  debug_trace(s, ks, "inner");
+  launch_scale_into<T, SB>(vref<T>(eb), vrefe_j<SB>(Q, ks.jctr, 0, vs), rs,
+                           ks.hnorm, n1, nrhs, ks.done, st);
+}
+
+// While s->st is being captured: appends to the captured graph a WHILE node
+// whose body is one inner_step plus the loop control, preceded by the kernel
+// that sets the loop condition from the all-converged flag.  The loop ends
+// when every RHS is done or after coarse_maxit iterations (k_givens marks
+// every RHS done at the cap, so the count bound is a second guard).
+template <class T, class SB>
+hz_status capture_inner_loop(hz_solver* s, int nrhs) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaGraph_t G = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, nullptr, nullptr, nullptr) !=
+          cudaSuccess ||
+      cs != cudaStreamCaptureStatusActive)
+    return cuda_check(s, "inner loop capture: stream not capturing");
+  cudaGraphConditionalHandle h;
+  if (cudaGraphConditionalHandleCreate(&h, G, 0, 0) != cudaSuccess)
+    return cuda_check(s, "conditional handle");
+  launch_loop_begin(ks.alldone, s->loop_it, h, st);
+  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, &deps, nullptr, &nd) !=
+      cudaSuccess)
+    return cuda_check(s, "capture info");
+  cudaGraphNodeParams p{};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = cudaGraphCondTypeWhile;
+  p.conditional.size = 1;
+  cudaGraphNode_t node;
+  if (cudaGraphAddNode(&node, G, deps, nullptr, nd, &p) != cudaSuccess)
+    return cuda_check(s, "WHILE node");
+  cudaGraph_t body = p.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(s->cap_body, body, nullptr, nullptr, 0,
+                                    cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return cuda_check(s, "body capture");
+  const long long c0 = launch_counter().load();
+  s->st = s->cap_body;
+  inner_step<T, SB>(s, nrhs);
+  launch_loop_next(ks.alldone, s->loop_it, s->d.coarse_maxit, s->body_kernels, h,
+                   s->st);
+  s->st = st;
+  s->body_count = launch_counter().load() - c0;
+  cudaGraph_t body_out = nullptr;
+  if (cudaStreamEndCapture(s->cap_body, &body_out) != cudaSuccess)
+    return cuda_check(s, "body capture end");
+  if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                          cudaStreamSetCaptureDependencies) !=
+      cudaSuccess)
+    return cuda_check(s, "capture dependencies");
+  return cuda_check(s, "inner loop capture");
+}
+
 // E v2 = v1 by right-preconditioned GMRES (V-cycle on the coarse CSLP from
 // level 1), x0 = 0, stopping at |g_{j+1}| <= coarse_tol ||v1||.
 template <class T, class SB>
@@ -459,7 +571,6 @@ hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
   const long long rs = inner_row(n1);
   const long long vs = (long long)s->d.nrhs_max * rs;
   SB* Q = (SB*)s->Qb;
-  C<T>* sb = (C<T>*)s->sb;
   C<T>* eb = (C<T>*)s->eb;
   const int m = s->d.coarse_maxit;
   const double tol = s->d.coarse_tol;
@@ -468,23 +579,18 @@ hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
   launch_krylov_init(ks, nrhs, done_in, nullptr, tol, st);
   launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>(Q), rs, ks.hnorm, n1, nrhs,
                            ks.done, st);
-  int all = 0;
-  for (int it = 0; it < m; ++it) {
-    // the V-cycle reads the current basis vector, unpadded, in compute
-    // precision
-    launch_basis_load<SB, T>(vrefe_j<SB>(Q, ks.jctr, 0, vs), rs, (C<T>*)s->qf, n1,
-                             nrhs, ks.done, st);
-    vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
-    apply_E<T>(s, sb, eb, nrhs, ks.done);
-    cgs2<T, SB>(s, ks, Q, vs, rs, eb, n1, nrhs);
-    launch_givens(ks, nrhs, tol, m, st);
-    debug_trace(s, ks, "inner");
-    launch_scale_into<T, SB>(vref<T>(eb), vrefe_j<SB>(Q, ks.jctr, 0, vs), rs,
-                             ks.hnorm, n1, nrhs, ks.done, st);
-    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
-      const hz_status e = read_flag(s, ks.alldone, &all);
-      if (e != HZ_OK) return e;
-      if (all) break;
+  if (s->capturing) {
+    const hz_status e = capture_inner_loop<T, SB>(s, nrhs);
+    if (e != HZ_OK) return e;
+  } else {
+    int all = 0;
+    for (int it = 0; it < m; ++it) {
+      inner_step<T, SB>(s, nrhs);
+      if ((it + 1) % s->check_every == 0 || it + 1 == m) {
+        const hz_status e = read_flag(s, ks.alldone, &all);
+        if (e != HZ_OK) return e;
+        if (all) break;
+      }
     }
   }
   launch_trisolve(ks, nrhs, st);
@@ -544,6 +650,109 @@ hz_status precond_any(hz_solver* s, VRef<double> v, VRef<double> z, int nrhs,
 }
 
 // ------------------------------------------------------------ outer FGMRES
+// One outer FGMRES iteration: z_j = P v_j (A-DEF1), w = A z_j, Gram-Schmidt,
+// Givens, v_{j+1}.  Column j is selected on the device.
+hz_status outer_step(hz_solver* s, int nrhs, double tol) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const long long n0 = s->lv[0].n;
+  const long long vs = (long long)s->d.nrhs_max * n0;
+  const LevelDev F = dev64(s, 0);
+  hz_status e = precond_any(s, vref_j<double>(s->Vo, ko.jctr, 0, vs),
+                            vref_j<double>(s->Zo, ko.jctr, 0, vs), nrhs, ko.done);
+  if (e != HZ_OK) return e;
+  launch_helm<double>(F, s->d.bc, helm1(), vref_j<double>(s->Zo, ko.jctr, 0, vs),
+                      vref<double>(nullptr), s->wo, nrhs, ko.done, st);
+  cgs2<double, double2>(s, ko, s->Vo, vs, n0, s->wo, n0, nrhs);
+  launch_givens(ko, nrhs, tol, s->d.outer_maxit, st);
+  debug_trace(s, ko, "outer");
+  launch_scale_into<double, double2>(vref<double>(s->wo),
+                                    vref_j<double>(s->Vo, ko.jctr, 0, vs), n0,
+                                    ko.hnorm, n0, nrhs, ko.done, st);
+  return cuda_check(s, "outer step");
+}
+
+std::atomic<bool> g_graph_launched{false};
+constexpr size_t kMaxGraphs = 4;
+
+void end_failed_capture(hz_solver* s) {
+  cudaGraph_t g = nullptr;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (s->cap_body && cudaStreamIsCapturing(s->cap_body, &cs) == cudaSuccess &&
+      cs != cudaStreamCaptureStatusNone) {
+    cudaStreamEndCapture(s->cap_body, &g);
+    g = nullptr;
+  }
+  if (s->cap_main && cudaStreamIsCapturing(s->cap_main, &cs) == cudaSuccess &&
+      cs != cudaStreamCaptureStatusNone) {
+    if (cudaStreamEndCapture(s->cap_main, &g) == cudaSuccess && g)
+      cudaGraphDestroy(g);
+  }
+  cudaGetLastError();
+}
+
+// The instantiated graph of outer_step for (nrhs, tol), captured on first
+// use.  Returns nullptr (with s->err set) if capture or instantiation fails.
+hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
+  for (hz_solver::OuterGraph& g : s->graphs)
+    if (g.nrhs == nrhs && g.tol == tol) return &g;
+  if (s->graphs.size() >= kMaxGraphs) {
+    cudaStreamSynchronize(s->st);
+    cudaGraphExecDestroy(s->graphs.front().ex);
+    cudaGraphDestroy(s->graphs.front().g);
+    s->graphs.erase(s->graphs.begin());
+  }
+  if ((!s->cap_main &&
+       cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking) != cudaSuccess) ||
+      (!s->cap_body &&
+       cudaStreamCreateWithFlags(&s->cap_body, cudaStreamNonBlocking) != cudaSuccess)) {
+    cuda_check(s, "capture streams");
+    return nullptr;
+  }
+  cudaStream_t st0 = s->st;
+  const long long c0 = launch_counter().load();
+  if (cudaStreamBeginCapture(s->cap_main, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cuda_check(s, "begin capture");
+    return nullptr;
+  }
+  s->st = s->cap_main;
+  s->capturing = true;
+  s->body_count = 0;
+  hz_status e = outer_step(s, nrhs, tol);
+  s->capturing = false;
+  s->st = st0;
+  const long long captured = launch_counter().load() - c0;
+  launch_counter().fetch_sub(captured);   // nothing ran yet
+  if (e != HZ_OK) {
+    const std::string why = s->err;
+    end_failed_capture(s);
+    s->err = why;
+    return nullptr;
+  }
+  hz_solver::OuterGraph og{nrhs, tol, nullptr, nullptr, captured - s->body_count};
+  if (cudaStreamEndCapture(s->cap_main, &og.g) != cudaSuccess) {
+    cuda_check(s, "end capture");
+    end_failed_capture(s);
+    return nullptr;
+  }
+  if (cudaGraphInstantiate(&og.ex, og.g, 0) != cudaSuccess) {
+    cuda_check(s, "graph instantiate");
+    cudaGraphDestroy(og.g);
+    return nullptr;
+  }
+  s->body_kernels_host = (int)s->body_count;
+  if (cudaMemcpyAsync(s->body_kernels, &s->body_kernels_host, sizeof(int),
+                      cudaMemcpyHostToDevice, st0) != cudaSuccess ||
+      cudaStreamSynchronize(st0) != cudaSuccess) {
+    cuda_check(s, "graph counter");
+    cudaGraphExecDestroy(og.ex);
+    cudaGraphDestroy(og.g);
+    return nullptr;
+  }
+  s->graphs.push_back(og);
+  return &s->graphs.back();
+}
+
 hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
                     double tol, int use_x0, hz_solve_info* info) {
   cudaStream_t st = s->st;
@@ -576,20 +785,24 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   hz_status e = cuda_check(s, "outer init");
   if (e != HZ_OK) return e;
   int all = 0;
+  // graphs replay fixed launches: the per-launch events of the profiler
+  // and the trace's host reads need the launches issued one by one
+  hz_solver::OuterGraph* og = nullptr;
+  if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on()) {
+    og = outer_graph(s, nrhs, tol);
+    if (!og) return HZ_CUDA_ERROR;
+  }
   e = read_flag(s, ko.alldone, &all);
   if (e != HZ_OK) return e;
   for (int it = 0; it < m && !all; ++it) {
-    e = precond_any(s, vref_j<double>(s->Vo, ko.jctr, 0, vs),
-                    vref_j<double>(s->Zo, ko.jctr, 0, vs), nrhs, ko.done);
-    if (e != HZ_OK) return e;
-    launch_helm<double>(F, bc, helm1(), vref_j<double>(s->Zo, ko.jctr, 0, vs),
-                        vref<double>(nullptr), s->wo, nrhs, ko.done, st);
-    cgs2<double, double2>(s, ko, s->Vo, vs, n0, s->wo, n0, nrhs);
-    launch_givens(ko, nrhs, tol, m, st);
-    debug_trace(s, ko, "outer");
-    launch_scale_into<double, double2>(vref<double>(s->wo),
-                                      vref_j<double>(s->Vo, ko.jctr, 0, vs), n0,
-                                      ko.hnorm, n0, nrhs, ko.done, st);
+    if (og) {
+      if (cudaGraphLaunch(og->ex, st) != cudaSuccess) return cuda_check(s, "graph launch");
+      launch_counter().fetch_add(og->kernels);
+      g_graph_launched.store(true);
+    } else {
+      e = outer_step(s, nrhs, tol);
+      if (e != HZ_OK) return e;
+    }
     e = read_flag(s, ko.alldone, &all);
     if (e != HZ_OK) return e;
   }
@@ -981,6 +1194,10 @@ const char* hz_status_str(hz_status st) {
 
 const char* hz_last_error(const hz_solver* s) { return s ? s->err.c_str() : ""; }
 
-long long hz_kernel_launches(void) { return hz::launch_counter().load(); }
+long long hz_kernel_launches(void) {
+  long long n = hz::launch_counter().load();
+  if (g_graph_launched.load()) n += (long long)hz::graph_body_kernels_run();
+  return n;
+}
 
 }  // extern "C"

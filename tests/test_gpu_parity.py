@@ -259,6 +259,46 @@ def test_batched_equals_single_and_host_io():
     assert rel(xh.numpy(), to_np(xb)) < 1e-12
 
 
+@pytest.mark.parametrize("bc,prec,basis16", [("sommerfeld", "fp64", False),
+                                             ("dirichlet", "mixed", False),
+                                             ("sommerfeld", "mixed_bf16", True)])
+def test_cuda_graph_loop_equals_host_issued_loop(bc, prec, basis16):
+    """The default path runs each outer iteration as one CUDA graph whose
+    inner loop is a device-side WHILE node; with no_cuda_graph the same
+    kernels are issued one by one.  Both must give the same iteration
+    counts and the same solution (the kernels are deterministic), on two
+    solves in a row (the second replays the cached graph), and the kernel
+    counter must account for the kernels run inside the WHILE bodies."""
+    from paper_2308_06152_gb300 import _lib
+    lib = _lib.load_library()
+    k2 = rk2(NY, NX, 5, lo=10.0, hi=40.0)
+    b = wl.random_complex((2, NY, NX), 77)
+    out = {}
+    for graph in (True, False):
+        s = solver(NX, NY, H, k2, bc, prec=prec, nrhs=2, coarse_tol=1e-3,
+                   coarse_maxit=200, inner_basis_fp16=basis16,
+                   cuda_graph=graph)
+        runs = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            n0 = lib.hz_kernel_launches()
+            x, infos = s.solve(b, tol=1e-8)
+            torch.cuda.synchronize()
+            runs.append((to_np(x), infos, lib.hz_kernel_launches() - n0))
+        s.close()
+        out[graph] = runs
+    for (xg, ig, ng), (xe, ie, ne) in zip(out[True], out[False]):
+        for r in range(2):
+            assert ig[r].status == ie[r].status == "HZ_OK"
+            assert ig[r].outer_iters == ie[r].outer_iters
+            assert ig[r].inner_iters_total == ie[r].inner_iters_total
+            assert rel(xg[r], xe[r]) < 1e-13
+        # the host-issued loop runs up to 3 extra (early-exit) inner steps
+        # per coarse solve; the graph adds two small loop-control kernels
+        assert 0.7 * ne < ng < 1.3 * ne, (ng, ne)
+    assert rel(out[True][0][0], out[True][1][0]) == 0.0
+
+
 def test_edge_cases():
     from paper_2308_06152_gb300.api import Desc, HzError, Solver
     n = 33
