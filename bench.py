@@ -2,7 +2,8 @@
 """Benchmark of the GB300 two-level-deflation Helmholtz solver.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload NAME] [--prec mixed|fp64]
+                    [--workload NAME] [--prec mixed_bf16|mixed|fp64]
+                    [--basis16 0|1] [--autotune 0|1] [--cuda-graph 0|1]
 
 A step is one complete solve of a batch of right-hand sides to relative
 residual 1e-6 through the C ABI (hz_solve): outer FP64 flexible GMRES, the
@@ -11,6 +12,12 @@ is unknowns * solves per second (whole job), device-timed with CUDA events;
 ``e2e`` repeats it through hz_solve_host with host buffers and the copies
 inside the timed region.  Under torchrun every rank solves its own shots
 (replicas, weak scaling; there is no exchange between ranks).
+
+Default variant: complex-FP32 preconditioner with BF16-stored V-cycle
+vectors and an FP16 inner Krylov basis, inside FP64 FGMRES (every solve
+still reaches the FP64 true residual 1e-6, reported per step), with the
+kernel choices of hz_autotune; ``fp64`` in the output line times the same
+workload with the FP64 preconditioner.
 
 ``--impl reference`` times the CPU FP64 oracle (the plain restatement of the
 method used by the tests) on a bounded sample of the same workload.
@@ -280,6 +287,16 @@ def run_ours(args):
                 inner_basis_fp16=bool(args.basis16),
                 cuda_graph=bool(args.cuda_graph))
     solver = Solver(desc, model.k2)
+    tune_ms = None
+    if args.autotune:
+        tune_ms = solver.autotune(cfg["nrhs"])["ms"]
+    if args.mdot_kernel is not None:
+        solver.set_tuning(mdot_kernel=args.mdot_kernel)
+    if args.maxpy_kernel is not None:
+        solver.set_tuning(maxpy_kernel=args.maxpy_kernel)
+    if args.galerkin_apply is not None:
+        solver.set_tuning(galerkin_apply=args.galerkin_apply)
+    tuning = solver.get_tuning()
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
     tol = cfg["tol"]
@@ -412,6 +429,7 @@ def run_ours(args):
                        "coarse_tol": cfg["coarse_tol"],
                        "parallelism": f"replicas{world}",
                        "cuda_graph": bool(args.cuda_graph),
+                       "tuning": tuning, "autotune_ms": tune_ms,
                        "l2": "inputs larger than L2 (each batch vector "
                              f"{b_np.nbytes / 1e6:.0f} MB)"},
             "e2e": {"value": units / e2e_s, "unit": UNIT,
@@ -458,8 +476,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
                     choices=sorted(WORKLOADS))
     ap.add_argument("--prec", choices=["mixed", "mixed_bf16", "fp64"],
-                    default="mixed")
-    ap.add_argument("--basis16", type=int, default=0,
+                    default="mixed_bf16")
+    ap.add_argument("--basis16", type=int, default=1,
                     help="store the inner coarse-solve Krylov basis as FP16")
     ap.add_argument("--no-cpu", action="store_true",
                     help="skip the CPU oracle baseline sample")
@@ -468,6 +486,15 @@ def main():
     ap.add_argument("--cuda-graph", type=int, default=1,
                     help="1: outer iterations as CUDA graphs with a device-side "
                          "inner WHILE loop; 0: kernels issued one by one")
+    ap.add_argument("--autotune", type=int, default=1,
+                    help="time the hz_tuning candidates at setup and keep the "
+                         "fastest (outside the timed region)")
+    ap.add_argument("--mdot-kernel", type=int, choices=[0, 1, 2], default=None,
+                    help="force hz_tuning.mdot_kernel")
+    ap.add_argument("--maxpy-kernel", type=int, choices=[0, 1, 2], default=None,
+                    help="force hz_tuning.maxpy_kernel")
+    ap.add_argument("--galerkin-apply", type=int, choices=[0, 1], default=None,
+                    help="force hz_tuning.galerkin_apply")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
     ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],

@@ -226,6 +226,36 @@ hz_status hz_coarse_galerkin_noalloc(int nx, int ny, double h, hz_bc bc,
                                      const void* x_dev, void* y_dev, int nrhs,
                                      void* cuda_stream);
 
+/* Grids of different sizes solved together (spec batching pattern;
+ * the paper solves one grid at a time and has no counterpart).  Member g of
+ * the group (up to HZ_MAX_GROUP solvers, each set up on its own grid and
+ * workspace) solves nrhs[g] right-hand sides b_dev[g] -> x_dev[g] (layout
+ * and x0 = 0 as hz_solve) to tol.  Every outer and inner Krylov iteration of
+ * all members advances together: each member's stencil, transfer and
+ * coarse-operator kernels run on its own grid, and the Gram-Schmidt kernels
+ * of all members run as one persistent launch over a table of the members'
+ * tiles, so small grids share the GPU instead of taking turns.  A member
+ * that converged only skips its work.  Members must agree in precision class
+ * (FP64 or mixed), inner-basis storage and deflation on/off (HZ_INVALID_ARG
+ * otherwise, and for a repeated member); they run on members[0]'s stream,
+ * eagerly (no CUDA graph).  info[g] (nrhs[g] entries) may be null.  Returns
+ * the worst status over the members. */
+#define HZ_MAX_GROUP 8
+hz_status hz_solve_group(hz_solver* const* members, int count, const void* const* b_dev,
+                         void* const* x_dev, const int* nrhs, double tol,
+                         hz_solve_info* const* info);
+
+/* hz_gradient for a group of grids: member g uses omega[g], nshots[g]
+ * sources src_dev[g], receivers rec_idx_dev[g] (nrec[g]) and data
+ * d_obs_dev[g], and receives J_host[g] and grad_dev[g] (its own grid).  Shot
+ * batches of all members run their forward and adjoint solves together
+ * through hz_solve_group. */
+hz_status hz_gradient_group(hz_solver* const* members, int count, const double* omega,
+                            const void* const* src_dev, const int* nshots,
+                            const int* const* rec_idx_dev, const int* nrec,
+                            const void* const* d_obs_dev, double tol, double* J_host,
+                            double* const* grad_dev, hz_solve_info* const* info);
+
 /* Kernel classes that hz_profile_* can time: the multi-vector dot product
  * and the multi-vector update of the Gram-Schmidt step (Alg. 1 inner loop),
  * which carry the basis traffic of both Krylov solvers. */
@@ -243,8 +273,62 @@ hz_status hz_profile_begin(hz_solver* s, hz_kernel_class kc, int max_launches);
 hz_status hz_profile_end(hz_solver* s, long long* launches, double* ms_total,
                          double* alg_bytes);
 
-/* Kernels launched by this library since it was loaded (all solvers). */
+/* Kernels launched by this library since it was loaded (all solvers),
+ * including the kernels run inside the device-side loops of CUDA graphs
+ * (read from the current device's counter). */
 long long hz_kernel_launches(void);
+
+/* Implementation choices that leave the method's arithmetic unchanged up to
+ * rounding order.  hz_setup starts from hz_tuning_default; hz_autotune
+ * times the candidates on the solver's own workspace and keeps the fastest;
+ * hz_set_tuning sets them directly (e.g. from a cache of an earlier
+ * tuning).  The paper has no counterpart: its CPU code has one kernel per
+ * operation. */
+typedef struct {
+  int mdot_kernel;  /* multi-vector dot product of the Gram-Schmidt step:
+                       0 register-pipelined (each block streams basis rows
+                       through registers), 1 TMA ring (bulk copies into a
+                       6-stage shared-memory ring, 8 consumer warps per SM),
+                       2 TMA ring with 16 consumer warps                   */
+  int maxpy_kernel; /* multi-vector update of the Gram-Schmidt step, the
+                       same three choices                                  */
+  int galerkin_apply; /* HZ_E_GALERKIN only: 0 the product R_Z (A_h (Z x))
+                       on the fly each application (str-Glk, Sec. 5.2.1),
+                       1 the product's 5x5 (higher-order Z) or 3x3 (bilinear
+                       Z) stencil stored per coarse node at setup and applied
+                       as a stencil (stcl-op-Glk, Table 1)                 */
+  int e_rhs_per_block; /* stored-stencil E: right-hand sides that one block
+                       walks through with its coefficients held in registers
+                       (0 = all of them; else 1..1024)                     */
+  int vcycle_fused; /* 0 the V-cycle's smoothing and transfers as separate
+                       kernels; 1 pre-smoothing + residual + restriction and
+                       prolongation + post-smoothing fused into one tiled
+                       kernel each (the intermediate iterate stays in shared
+                       memory)                                             */
+} hz_tuning;
+
+/* Candidates hz_autotune times, in the order of its ms[] output:
+ * mdot_kernel 0, 1, 2; maxpy_kernel 0, 1, 2; galerkin_apply 0, 1;
+ * e_rhs_per_block 0, 8, 4; vcycle_fused 0, 1. */
+#define HZ_TUNE_CANDIDATES 13
+
+void hz_tuning_default(hz_tuning* t);
+
+/* Times the candidates on this solver's workspace and stream and keeps the
+ * fastest of each (as hz_set_tuning; *best receives them if not null).
+ * ms[HZ_TUNE_CANDIDATES], if not null, receives the time of one launch per
+ * candidate (-1 where not applicable), each for nrhs right-hand sides: the
+ * Gram-Schmidt dot and update kernels at Arnoldi column min(maxit - 1, 64)
+ * of the inner solver (of the outer one without deflation) on synthetic
+ * basis rows, then E (Galerkin E only) on the fly and stored, then the
+ * stored stencil's RHS per block, then one V-cycle from level 1 (level 0
+ * without deflation) unfused and fused.
+ * Overwrites the iteration state in the workspace: call it between solves.
+ * HZ_INVALID_ARG for nrhs outside 1..nrhs_max. */
+hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms);
+/* HZ_INVALID_ARG for a null pointer or an out-of-range field. */
+hz_status hz_get_tuning(const hz_solver* s, hz_tuning* t);
+hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t);
 
 const char* hz_status_str(hz_status st);
 const char* hz_last_error(const hz_solver* s);

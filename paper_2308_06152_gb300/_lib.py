@@ -32,6 +32,12 @@ class HzSolveInfo(ctypes.Structure):
                 ("status", c_int)]
 
 
+class HzTuning(ctypes.Structure):
+    _fields_ = [("mdot_kernel", c_int), ("maxpy_kernel", c_int),
+                ("galerkin_apply", c_int), ("e_rhs_per_block", c_int),
+                ("vcycle_fused", c_int)]
+
+
 STATUS = {0: "HZ_OK", 1: "HZ_INVALID_ARG", 2: "HZ_INVALID_GRID",
           3: "HZ_WORKSPACE_TOO_SMALL", 4: "HZ_NOT_CONVERGED",
           5: "HZ_BREAKDOWN", 6: "HZ_NAN", 7: "HZ_TIMEOUT",
@@ -61,6 +67,15 @@ SIGNATURES = {
     "hz_kernel_launches": (ctypes.c_longlong, []),
     "hz_profile_begin": (c_int, [c_void_p, c_int, c_int]),
     "hz_profile_end": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "hz_tuning_default": (None, [c_void_p]),
+    "hz_get_tuning": (c_int, [c_void_p, c_void_p]),
+    "hz_set_tuning": (c_int, [c_void_p, c_void_p]),
+    "hz_autotune": (c_int, [c_void_p, c_int, c_void_p, c_void_p]),
+    "hz_solve_group": (c_int, [c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                               c_double, c_void_p]),
+    "hz_gradient_group": (c_int, [c_void_p, c_int, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_void_p, c_void_p,
+                                  c_double, c_void_p, c_void_p, c_void_p]),
     "hz_status_str": (ctypes.c_char_p, [c_int]),
     "hz_last_error": (ctypes.c_char_p, [c_void_p]),
 }

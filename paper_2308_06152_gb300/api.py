@@ -10,7 +10,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from ._lib import HzDesc, HzSolveInfo, STATUS, load_library
+from ._lib import HzDesc, HzSolveInfo, HzTuning, STATUS, load_library
 
 BC = {"dirichlet": 0, "sommerfeld": 1}
 ZKIND = {None: 0, "none": 0, "bilinear": 1, "ho": 2}
@@ -238,6 +238,72 @@ class Solver:
                     "hz_profile_end")
         return n.value, ms.value, by.value
 
+    def get_tuning(self):
+        """The solver's implementation choices as a dict (see hz_tuning)."""
+        t = HzTuning()
+        self._check(self.lib.hz_get_tuning(self.handle, ctypes.byref(t)),
+                    "hz_get_tuning")
+        return {f: getattr(t, f) for f, _ in HzTuning._fields_}
+
+    def set_tuning(self, **choices):
+        """Set some or all hz_tuning fields; the others keep their values."""
+        t = HzTuning()
+        self._check(self.lib.hz_get_tuning(self.handle, ctypes.byref(t)),
+                    "hz_get_tuning")
+        for k, v in choices.items():
+            if k not in dict(HzTuning._fields_):
+                raise KeyError(f"unknown tuning field {k}")
+            setattr(t, k, int(v))
+        self._check(self.lib.hz_set_tuning(self.handle, ctypes.byref(t)),
+                    "hz_set_tuning")
+
+    TUNE_CANDIDATES = ("mdot_kernel=0", "mdot_kernel=1", "mdot_kernel=2",
+                       "maxpy_kernel=0", "maxpy_kernel=1", "maxpy_kernel=2",
+                       "galerkin_apply=0", "galerkin_apply=1",
+                       "e_rhs_per_block=0", "e_rhs_per_block=8",
+                       "e_rhs_per_block=4", "vcycle_fused=0",
+                       "vcycle_fused=1")
+
+    def tuning_key(self, nrhs):
+        """Cache key of a tuning: the device and every descriptor field
+        that changes the timed kernels' shapes."""
+        d = self.desc
+        name = torch.cuda.get_device_name(self.device)
+        return (f"{name}|{d.nx}x{d.ny}|bc={d.bc}|z={d.z}|e={d.e}|prec={d.prec}"
+                f"|basis16={int(bool(d.inner_basis_fp16))}|nrhs={nrhs}"
+                f"|maxit={d.coarse_maxit},{d.outer_maxit}")
+
+    def autotune(self, nrhs=None, cache=None):
+        """Pick the hz_tuning fields by timing them (hz_autotune) for nrhs
+        right-hand sides (default nrhs_max).  With ``cache`` (a JSON file
+        path) an earlier choice for the same key is reused without timing,
+        and a new one is stored.  Returns {"tuning", "ms", "cached"}."""
+        import json
+        import os
+        nrhs = int(nrhs or self.desc.nrhs_max)
+        key = self.tuning_key(nrhs)
+        data = {}
+        if cache and os.path.exists(cache):
+            with open(cache) as fh:
+                data = json.load(fh)
+            if key in data:
+                self.set_tuning(**data[key]["tuning"])
+                return dict(data[key], cached=True)
+        t = HzTuning()
+        ms = (ctypes.c_double * len(self.TUNE_CANDIDATES))()
+        self._check(self.lib.hz_autotune(self.handle, nrhs, ctypes.byref(t), ms),
+                    "hz_autotune")
+        entry = {"tuning": {f: getattr(t, f) for f, _ in HzTuning._fields_},
+                 "ms": {c: (ms[i] if ms[i] >= 0 else None)
+                        for i, c in enumerate(self.TUNE_CANDIDATES)}}
+        if cache:
+            data[key] = entry
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as fh:
+                json.dump(data, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return dict(entry, cached=False)
+
     def close(self):
         if getattr(self, "handle", None):
             self.lib.hz_destroy(self.handle)
@@ -248,3 +314,60 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def _ptrs(values):
+    arr = (ctypes.c_void_p * len(values))()
+    for i, v in enumerate(values):
+        arr[i] = v
+    return arr
+
+
+def solve_group(solvers, bs, tol=1e-6):
+    """Solve on several solvers (grids of different sizes) together
+    (hz_solve_group).  bs[g]: complex (nrhs_g, ny_g, nx_g).  Returns a list
+    of (x_g, infos_g)."""
+    lib = load_library()
+    K = len(solvers)
+    bs = [s._rhs(b) for s, b in zip(solvers, bs)]
+    xs = [torch.empty_like(b) for b in bs]
+    nrhs = (ctypes.c_int * K)(*[b.shape[0] for b in bs])
+    infos = [(HzSolveInfo * b.shape[0])() for b in bs]
+    st = lib.hz_solve_group(_ptrs([s.handle.value for s in solvers]), K,
+                            _ptrs([b.data_ptr() for b in bs]),
+                            _ptrs([x.data_ptr() for x in xs]), nrhs, float(tol),
+                            _ptrs([ctypes.addressof(i) for i in infos]))
+    if st not in (0, 4, 5, 6):
+        solvers[0]._check(st, "hz_solve_group")
+    return [(x, _infos(i, b.shape[0])) for x, i, b in zip(xs, infos, bs)]
+
+
+def gradient_group(solvers, omegas, srcs, recs, ds, tol=1e-10):
+    """hz_gradient over several grids at once: lists per member of omega,
+    sources (nshots, ny, nx), receiver indices and data (nshots, nrec).
+    Returns a list of (J_g, grad_g, infos_g)."""
+    lib = load_library()
+    K = len(solvers)
+    srcs = [s._rhs(x) for s, x in zip(solvers, srcs)]
+    recs = [torch.as_tensor(r, dtype=torch.int32).to(s.device)
+            for s, r in zip(solvers, recs)]
+    ds = [torch.as_tensor(d).to(device=s.device, dtype=torch.complex128).contiguous()
+          for s, d in zip(solvers, ds)]
+    grads = [torch.empty((s.desc.ny, s.desc.nx), dtype=torch.float64,
+                         device=s.device) for s in solvers]
+    J = (ctypes.c_double * K)()
+    infos = [(HzSolveInfo * (2 * x.shape[0]))() for x in srcs]
+    st = lib.hz_gradient_group(
+        _ptrs([s.handle.value for s in solvers]), K,
+        (ctypes.c_double * K)(*[float(o) for o in omegas]),
+        _ptrs([x.data_ptr() for x in srcs]),
+        (ctypes.c_int * K)(*[x.shape[0] for x in srcs]),
+        _ptrs([r.data_ptr() for r in recs]),
+        (ctypes.c_int * K)(*[r.numel() for r in recs]),
+        _ptrs([d.data_ptr() for d in ds]), float(tol), J,
+        _ptrs([g.data_ptr() for g in grads]),
+        _ptrs([ctypes.addressof(i) for i in infos]))
+    if st not in (0, 4, 5):
+        solvers[0]._check(st, "hz_gradient_group")
+    return [(J[g], grads[g], _infos(infos[g], 2 * srcs[g].shape[0]))
+            for g in range(K)]

@@ -201,6 +201,16 @@ void launch_prolong_add(const LevelDev& Lf, const LevelDev& Lc, int bc,
 template <class T, class SF, class SX, class SO>
 void launch_smooth(const LevelDev& L, int bc, Shift s, VRefE<SF> f, const SX* x,
                    SO* xo, int nrhs, const int* done, cudaStream_t st);
+// fused: x = dinv .* f and fc = R_FW (f - M x) in one pass over a tile
+template <class T, class SF, class SX, class SC>
+void launch_pre_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
+                         VRefE<SF> f, SX* x, SC* fc, int nrhs, const int* done,
+                         cudaStream_t st);
+// fused: xo = x' + dinv .* (f - M x') with x' = x + P xc
+template <class T, class SC, class SX, class SF, class SO>
+void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
+                           const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
+                           const int* done, cudaStream_t st);
 // x = Minv f on the coarsest level (dense)
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
@@ -220,6 +230,17 @@ template <class T>
 void launch_galerkin_fused(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
                            const C<T>* x, C<T>* y, int nrhs, const int* done,
                            cudaStream_t st);
+// stcl-op-Glk: probes (FP64) for extracting the Galerkin stencil, the
+// extraction into (2R+1)^2 coefficient planes S, and y = E x with them
+void launch_probe_fill(const LevelDev& Lc, int P, int c0, int nprobe, double2* out,
+                       cudaStream_t st);
+template <class T>
+void launch_probe_extract(const LevelDev& Lc, int P, int c0, int nprobe,
+                          const double2* ep, C<T>* S, cudaStream_t st);
+// (rpb: right-hand sides per block, 0 = all)
+template <class T>
+void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C<T>* y,
+                      int nrhs, int rpb, const int* done, cudaStream_t st);
 // y = E_glk x on level 1 (variant 1 or 2)
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
@@ -270,6 +291,9 @@ struct KState {
   double* wpart;    // partial ||w||^2 before projection [nrhs_max][nblk_max]
   int* reorth;      // second Gram-Schmidt pass needed [nrhs_max]
   unsigned long long* abytes;  // [1] algorithmic-byte counter or null
+  int* fault;       // [1] set when a pipeline wait of a Krylov kernel timed out
+  int dotk, updk;   // multi-dot / multi-update kernels: 0 register-pipelined,
+                    // 1 / 2 TMA ring with 8 / 16 consumer warps
   int m;            // basis size (max iterations)
   int nblk_max;
 };
@@ -324,6 +348,35 @@ void launch_adjoint_source(int nx, int ny, int bc, const double2* u,
 void launch_image(const LevelDev& L, int bc, double omega, const double2* u,
                   const double2* x, double* grad, int nrhs, cudaStream_t st);
 void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st);
+
+// Grids of different sizes in one launch: the Gram-Schmidt kernels of up to
+// kMaxGroup solvers (each with its own basis, w, n and Krylov state) run as
+// one persistent launch over the concatenation of the members' (RHS, chunk)
+// tiles; start[g] is the first global tile of member g.
+constexpr int kMaxGroup = 8;   // HZ_MAX_GROUP
+struct GroupMember {
+  const void* V;        // basis (SB), vector i of RHS r at V + i*vstride + r*rs
+  long long vstride, rs;
+  void* w;              // C<T> [nrhs][n]
+  long long n;
+  KState ks;
+  int nrhs, nblk;
+};
+struct GroupDesc {
+  int count;
+  long long start[kMaxGroup + 1];
+  GroupMember m[kMaxGroup];
+};
+template <class T, class SB>
+void launch_mdot_group(const GroupDesc& gd, int pass, cudaStream_t st);
+template <class T, class SB>
+void launch_maxpy_group(const GroupDesc& gd, int pass, cudaStream_t st);
+
+// Timing support for the autotuner: synthetic vector contents and an
+// Arnoldi state at column j with RHS 0..nrhs-1 active.
+template <class SB>
+void launch_tune_fill(SB* p, long long count, unsigned seed, cudaStream_t st);
+void launch_tune_state(const KState& ks, int nrhs, int j, cudaStream_t st);
 
 // Device-side loop control of an iteration captured as the body of a CUDA
 // graph WHILE node.  loop_begin (upstream of the node) resets the iteration

@@ -4,6 +4,7 @@
 // norms, Givens updates of the Hessenberg columns and the triangular solve.
 // Each right-hand side owns its basis, Hessenberg matrix and stopping state;
 // all of them live in device memory so that no launch depends on host data.
+#include <cstdlib>
 #include <mutex>
 #include <type_traits>
 #include <unordered_map>
@@ -103,24 +104,19 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
-// Pass `pass` (0 or 1) of classical Gram-Schmidt: partial dot products
-// part[r][i][blk] = sum_{e in blk} conj(V_i[e]) w[e], i = 0..j.  Pass 0 also
-// stores the partial ||w||^2 in wpart; pass 1 runs only for the RHS whose
-// reorth flag the first pass raised.
+constexpr int MDOT_TILE = 32;
+
+// One (RHS r, chunk blk) tile of k_mdot: w's chunk stays in registers while
+// the j+1 basis rows stream through (G rows' loads issued before use).
 template <class T, class SB>
-__global__ void __launch_bounds__(NT)
-k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
-       const C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs,
-       int nblk) {
-  constexpr int TILE = 32, NW = NT / 32;
+__device__ __forceinline__ void mdot_tile(const SB* __restrict__ V, long long vstride,
+                                          long long rs, const C<T>* __restrict__ w,
+                                          long long n, const KState& ks, int pass, int j,
+                                          int r, int blk, double2 (*wred)[MDOT_TILE],
+                                          double* red) {
+  constexpr int TILE = MDOT_TILE, NW = NT / 32;
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
-  __shared__ double2 wred[NW][TILE];
-  __shared__ double red[NW];
-  const int j = *ks.jctr;
-  // persistent loop over (RHS, chunk) tiles
-  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
-  const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
-  if (ks.done[r] || (pass && !ks.reorth[r])) continue;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (sizeof(C<T>) + (j + 1) * sizeof(SB)));
@@ -189,7 +185,24 @@ k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
     }
     __syncthreads();
   }
-  }
+}
+
+// Pass `pass` (0 or 1) of classical Gram-Schmidt: partial dot products
+// part[r][i][blk] = sum_{e in blk} conj(V_i[e]) w[e], i = 0..j.  Pass 0 also
+// stores the partial ||w||^2 in wpart; pass 1 runs only for the RHS whose
+// reorth flag the first pass raised.
+template <class T, class SB>
+__global__ void __launch_bounds__(NT)
+k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
+       const C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs,
+       int nblk) {
+  __shared__ double2 wred[NT / 32][MDOT_TILE];
+  __shared__ double red[NT / 32];
+  const int j = *ks.jctr;
+  // persistent loop over (RHS, chunk) tiles
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
+    mdot_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
+                     (int)(tile % nblk), wred, red);
 }
 
 // hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] = (pass 0) or += (pass 1)
@@ -225,19 +238,18 @@ __global__ void k_reduce_cols(KState ks, int nblk, int pass) {
   }
 }
 
-// w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
+constexpr int MAXPY_TILE = 512;
+
+// One (RHS r, chunk blk) tile of k_maxpy: w's chunk is updated in registers
+// across all j+1 basis rows, written once, and its squared norm reduced.
 template <class T, class SB>
-__global__ void __launch_bounds__(NT)
-k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
-        C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
-  constexpr int TILE = 512;
+__device__ __forceinline__ void maxpy_tile(const SB* __restrict__ V, long long vstride,
+                                           long long rs, C<T>* __restrict__ w, long long n,
+                                           const KState& ks, int pass, int j, int r,
+                                           int blk, C<T>* hs, double* red) {
+  constexpr int TILE = MAXPY_TILE;
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
-  __shared__ C<T> hs[TILE];
-  __shared__ double red[NT / 32];
-  const int j = *ks.jctr;
-  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
-  const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
-  if (ks.done[r] || (pass && !ks.reorth[r])) continue;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return;
   // algorithmic bytes of this RHS: read w and basis 0..j, write w
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB)));
@@ -295,7 +307,597 @@ k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
     }
   const double t = block_sum((double)wn, red);
   if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = t;
+}
+
+// w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
+template <class T, class SB>
+__global__ void __launch_bounds__(NT)
+k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
+        C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
+  __shared__ C<T> hs[MAXPY_TILE];
+  __shared__ double red[NT / 32];
+  const int j = *ks.jctr;
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
+    maxpy_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
+                      (int)(tile % nblk), hs, red);
+}
+
+// The same two kernels over the tiles of several grids (GroupDesc).
+template <class T, class SB>
+__global__ void __launch_bounds__(NT)
+k_mdot_group(const __grid_constant__ GroupDesc gd, int pass) {
+  __shared__ double2 wred[NT / 32][MDOT_TILE];
+  __shared__ double red[NT / 32];
+  const long long total = gd.start[gd.count];
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int g = 0;
+    while (tile >= gd.start[g + 1]) ++g;
+    const GroupMember& M = gd.m[g];
+    const long long lt = tile - gd.start[g];
+    mdot_tile<T, SB>((const SB*)M.V, M.vstride, M.rs, (const C<T>*)M.w, M.n, M.ks, pass,
+                     *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), wred, red);
   }
+}
+
+template <class T, class SB>
+__global__ void __launch_bounds__(NT)
+k_maxpy_group(const __grid_constant__ GroupDesc gd, int pass) {
+  __shared__ C<T> hs[MAXPY_TILE];
+  __shared__ double red[NT / 32];
+  const long long total = gd.start[gd.count];
+  for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
+    int g = 0;
+    while (tile >= gd.start[g + 1]) ++g;
+    const GroupMember& M = gd.m[g];
+    const long long lt = tile - gd.start[g];
+    maxpy_tile<T, SB>((const SB*)M.V, M.vstride, M.rs, (C<T>*)M.w, M.n, M.ks, pass,
+                      *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), hs, red);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// TMA-pipelined Gram-Schmidt kernels.  One producer warp streams chunks of
+// basis rows (CHUNK values of G consecutive basis vectors of one RHS, 32 KB
+// per stage) from HBM into a ring of shared-memory stages with bulk copies
+// (cp.async.bulk) completing on mbarriers; NCW consumer warps read each
+// stage from shared memory.  The bytes in flight per SM are set by the ring
+// (NSTAGE x 32 KB), not by registers, and the next tile's chunk of w is
+// prefetched into registers while the current tile streams.  Every wait is
+// bounded: after kWaitNs the kernel raises ks.fault, stops waiting and
+// still takes part in every block barrier, so the launch always ends; the
+// host reports the flag.
+constexpr int NSTAGE = 6;
+constexpr int STAGE_BYTES = 32768;
+constexpr int RING_BYTES = NSTAGE * STAGE_BYTES;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+template <class SB, int NTC> struct Cgs {
+  static constexpr int W = VW<SB>::w;                          // values per 16 B
+  static constexpr int ROWB = CHUNK * (int)sizeof(SB);         // bytes per row chunk
+  static constexpr int G = STAGE_BYTES / ROWB;                 // vectors per stage
+  static constexpr int VPT = CHUNK / (NTC * W);                // groups per thread
+  static_assert(VPT >= 1 && VPT * NTC * W == CHUNK, "chunk split");
+};
+
+__device__ __forceinline__ unsigned sm_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(b)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(b)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n"
+      " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(sm_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the phase of parity `parity` of barrier b; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+  if (mbar_test(b, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  for (;;) {
+    for (int k = 0; k < 64; ++k)
+      if (mbar_test(b, parity)) return true;
+    if (gtimer() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+      "[%3];" ::"r"(sm_addr(dst)),
+      "l"(src), "r"(bytes), "r"(sm_addr(b))
+      : "memory");
+}
+// named barrier of the NTC consumer threads only
+template <int NTC>
+__device__ __forceinline__ void consumers_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(NTC) : "memory");
+}
+
+// Warp sum of NV values at once (NV a power of two <= 8): log2(NV) halving
+// exchanges leave each lane one value, then plain xor steps finish the sum.
+// Returns the sum of value *idx; every lane of a group of 32/NV lanes holds
+// the same value.
+template <int CNT, class T>
+__device__ __forceinline__ void halve(T* v, int lane, int o) {
+  const bool up = (lane & o) != 0;
+#pragma unroll
+  for (int k = 0; k < CNT / 2; ++k) {
+    const T send = up ? v[k] : v[k + CNT / 2];
+    const T keep = up ? v[k + CNT / 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+template <int NV, class T>
+__device__ __forceinline__ T multi_reduce(T* v, int lane, int* idx) {
+  int o = 16, id = 0;
+  if constexpr (NV >= 2) {
+    halve<NV>(v, lane, 16);
+    id += ((lane >> 4) & 1) * (NV / 2);
+    o = 8;
+  }
+  if constexpr (NV >= 4) {
+    halve<NV / 2>(v, lane, 8);
+    id += ((lane >> 3) & 1) * (NV / 4);
+    o = 4;
+  }
+  if constexpr (NV >= 8) {
+    halve<NV / 4>(v, lane, 4);
+    id += ((lane >> 2) & 1) * (NV / 8);
+    o = 2;
+  }
+  T s = v[0];
+  for (; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  *idx = id;
+  return s;
+}
+
+// RHS that take part in this pass, compacted into act[] by warp 0.
+__device__ __forceinline__ void active_rhs(const KState& ks, int pass, int nrhs,
+                                           int* act, int* nact) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  int cnt = 0;
+  for (int base = 0; base < nrhs; base += 32) {
+    const int r = base + lane;
+    const bool a = r < nrhs && !ks.done[r] && (!pass || ks.reorth[r]);
+    const unsigned m = __ballot_sync(0xffffffffu, a);
+    if (a) act[cnt + __popc(m & ((1u << lane) - 1u))] = r;
+    cnt += __popc(m);
+  }
+  if (lane == 0) *nact = cnt;
+}
+
+// Producer side of one stage: row chunk blk of vectors i0 .. i0+nv-1 of RHS r.
+template <class SB>
+__device__ __forceinline__ void produce(unsigned char* stage, unsigned long long* full,
+                                        const SB* V, long long vstride, long long rs,
+                                        int r, int blk, int i0, int nv) {
+  constexpr int ROWB = CHUNK * (int)sizeof(SB);
+  const long long off = (long long)blk * CHUNK;
+  const long long cnt = (rs - off < CHUNK) ? (rs - off) : CHUNK;
+  const unsigned bytes = (unsigned)(cnt * (long long)sizeof(SB));
+  mbar_expect_tx(full, bytes * (unsigned)nv);
+  for (int q = 0; q < nv; ++q)
+    bulk_g2s(stage + q * ROWB, V + (long long)(i0 + q) * vstride + r * rs + off, bytes,
+             full);
+}
+
+// Chunk blk of RHS row w_r into registers: value k*W+u of this consumer
+// thread is element blk*CHUNK + (k*NTC + tid)*W + u (zero beyond n).
+template <class T, int W, int VPT, int NTC>
+__device__ __forceinline__ void load_chunk(C<T>* dst, const C<T>* wr, long long off,
+                                           long long n) {
+#pragma unroll
+  for (int k = 0; k < VPT; ++k)
+#pragma unroll
+    for (int u = 0; u < W; ++u) {
+      const long long e = off + (long long)(k * NTC + threadIdx.x) * W + u;
+      dst[k * W + u] = (e < n) ? wr[e] : czero<T>();
+    }
+}
+
+// Ring slot of one item: stage s (0 .. NSTAGE-1) and the parity of its use.
+struct Slot {
+  int s = 0;
+  unsigned ph = 0;
+  __device__ __forceinline__ void next() {
+    if (++s == NSTAGE) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
+
+// Producer lane: wait until the consumers released the stage of slot q.
+__device__ __forceinline__ bool producer_acquire(unsigned long long* empty, Slot q,
+                                                 volatile int* s_abort, int* fault) {
+  if (*s_abort || !mbar_wait(&empty[q.s], q.ph ^ 1u)) {
+    *s_abort = 1;
+    atomicExch(fault, 1);
+    return false;
+  }
+  return true;
+}
+// No bulk copy may still be landing when the block exits: wait for the last
+// min(issued, NSTAGE) stages (slot `at` is the one after the last issued).
+__device__ __forceinline__ void producer_drain(unsigned long long* full, long long issued,
+                                               Slot at, int* fault) {
+  const int cnt = issued < NSTAGE ? (int)issued : NSTAGE;
+  for (int u = 0; u < cnt; ++u) {
+    // step back one slot
+    if (at.s == 0) {
+      at.s = NSTAGE - 1;
+      at.ph ^= 1u;
+    } else {
+      --at.s;
+    }
+    if (!mbar_wait(&full[at.s], at.ph)) atomicExch(fault, 1);
+  }
+}
+__device__ __forceinline__ bool consumer_acquire(unsigned long long* full, Slot q,
+                                                 volatile int* s_abort, int* fault) {
+  if (*s_abort || !mbar_wait(&full[q.s], q.ph)) {
+    *s_abort = 1;
+    atomicExch(fault, 1);
+    return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void consumer_release(unsigned long long* empty, Slot q) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[q.s]);
+}
+
+template <int NCW>
+__device__ __forceinline__ void ring_init(unsigned long long* full,
+                                          unsigned long long* empty,
+                                          volatile int* s_abort) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NCW);
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+// Position of a work item of k_mdot_tma: active RHS a, row chunk blk,
+// vector group grp; advanced without divisions.
+struct Item {
+  int a, blk, grp;
+  __device__ __forceinline__ void next(int nblk, int ngrp) {
+    if (++grp == ngrp) {
+      grp = 0;
+      if (++blk == nblk) {
+        blk = 0;
+        ++a;
+      }
+    }
+  }
+};
+
+// Pass `pass` of classical Gram-Schmidt (same contract as k_mdot).  The
+// work items (RHS, row chunk, group of G vectors) of all active RHS are
+// split evenly over the blocks, so every block streams the same number of
+// bytes whatever j and the number of converged RHS.
+template <class T, class SB, int NCW>
+__global__ void __launch_bounds__(32 * NCW + 32, 1)
+k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
+           const C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs,
+           int nblk) {
+  constexpr int NTC = 32 * NCW;
+  using P = Cgs<SB, NTC>;
+  constexpr int W = P::W, G = P::G, VPT = P::VPT, NV = 2 * G, E = VPT * W;
+  constexpr int FLUSH = 32 / G;   // items per reduction flush
+  extern __shared__ __align__(128) unsigned char stages[];
+  __shared__ unsigned long long full[NSTAGE], empty[NSTAGE];
+  __shared__ int act[1024];
+  __shared__ int s_nact;
+  __shared__ volatile int s_abort;
+  __shared__ double wred[NCW][2 * 32];
+  __shared__ double wnred[NCW][32];
+  __shared__ int3 pitem[32];     // (RHS, chunk, group) of the pending items
+  const int j = *ks.jctr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  active_rhs(ks, pass, nrhs, act, &s_nact);
+  ring_init<NCW>(full, empty, &s_abort);
+  __syncthreads();
+  const int ngrp = (j + 1 + G - 1) / G;
+  const long long items = (long long)s_nact * nblk * ngrp;
+  const long long lo = items * blockIdx.x / gridDim.x;
+  const long long hi = items * (blockIdx.x + 1) / gridDim.x;
+  const int nitems = (int)(hi - lo);
+  Item it0;
+  {
+    const long long tile = lo / ngrp;
+    it0.grp = (int)(lo - tile * ngrp);
+    it0.a = (int)(tile / nblk);
+    it0.blk = (int)(tile - (long long)it0.a * nblk);
+  }
+
+  if (warp == NCW) {  // producer
+    if (lane == 0) {
+      Slot sl;
+      Item it = it0;
+      int t = 0;
+      for (; t < nitems; ++t) {
+        if (!producer_acquire(empty, sl, &s_abort, ks.fault)) break;
+        const int i0 = it.grp * G, nv = min(G, j + 1 - i0);
+        produce<SB>(stages + sl.s * STAGE_BYTES, &full[sl.s], V, vstride, rs, act[it.a],
+                    it.blk, i0, nv);
+        sl.next();
+        it.next(nblk, ngrp);
+      }
+      producer_drain(full, t, sl, ks.fault);
+    }
+  } else {  // consumers
+    int cur_a = -1, cur_blk = -1;
+    bool have_next = false;
+    C<T> wv[E], wq[E];
+    int pend = 0;
+    Slot sl;
+    Item it = it0;
+    for (int t = 0; t < nitems; ++t) {
+      const long long off = (long long)it.blk * CHUNK;
+      if (it.a != cur_a || it.blk != cur_blk) {
+        if (have_next) {
+#pragma unroll
+          for (int e = 0; e < E; ++e) wv[e] = wq[e];
+        } else {
+          load_chunk<T, W, VPT, NTC>(wv, w + act[it.a] * n, off, n);
+        }
+        cur_a = it.a;
+        cur_blk = it.blk;
+        // prefetch the chunk of w of the next tile if this block reaches it
+        const int left = nitems - t - (ngrp - it.grp);   // items after this tile
+        int na = it.a, nb = it.blk + 1;
+        if (nb == nblk) {
+          nb = 0;
+          ++na;
+        }
+        have_next = left > 0;
+        if (have_next)
+          load_chunk<T, W, VPT, NTC>(wq, w + act[na] * n, (long long)nb * CHUNK, n);
+        if (pass == 0 && it.grp == 0) {
+          T wn = T(0);
+#pragma unroll
+          for (int e = 0; e < E; ++e) wn += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
+          for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
+          if (lane == 0) wnred[warp][pend] = (double)wn;
+        }
+      }
+      if (threadIdx.x == 0) pitem[pend] = make_int3(it.a, it.blk, it.grp);
+      T acc[NV];
+#pragma unroll
+      for (int c = 0; c < NV; ++c) acc[c] = T(0);
+      if (consumer_acquire(full, sl, &s_abort, ks.fault)) {
+        const int nv = min(G, j + 1 - it.grp * G);
+        const long long valid = n - off;   // values of this chunk inside the row
+        const unsigned char* sb = stages + sl.s * STAGE_BYTES;
+#pragma unroll
+        for (int qq = 0; qq < G; ++qq) {
+          if (qq < nv) {
+#pragma unroll
+            for (int k = 0; k < VPT; ++k) {
+              const int g = k * NTC + threadIdx.x;
+              if ((long long)g * W < valid) {
+                const uint4 raw =
+                    *reinterpret_cast<const uint4*>(sb + qq * P::ROWB + g * 16);
+                static_for<W>([&](auto U) {
+                  const C<T> v = unpk<U.value>(raw, (const SB*)nullptr);
+                  const C<T> wk = wv[k * W + U.value];
+                  acc[2 * qq] += v.x * wk.x + v.y * wk.y;
+                  acc[2 * qq + 1] += v.x * wk.y - v.y * wk.x;
+                });
+              }
+            }
+          }
+        }
+      }
+      consumer_release(empty, sl);
+      sl.next();
+      int idx = 0;
+      const T sum = multi_reduce<NV>(acc, lane, &idx);
+      if ((lane & (32 / NV - 1)) == 0) wred[warp][pend * NV + idx] = (double)sum;
+      ++pend;
+      it.next(nblk, ngrp);
+      if (pend == FLUSH || t + 1 == nitems) {
+        consumers_sync<NTC>();
+        const int v = threadIdx.x;
+        if (v < pend * G) {
+          const int3 pi = pitem[v / G];
+          const int i = pi.z * G + v % G;
+          if (i <= j) {
+            double2 sm = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int ww = 0; ww < NCW; ++ww) {
+              sm.x += wred[ww][2 * v];
+              sm.y += wred[ww][2 * v + 1];
+            }
+            ks.part[((long long)act[pi.x] * (ks.m + 1) + i) * ks.nblk_max + pi.y] = sm;
+          }
+        }
+        if (pass == 0 && v < pend) {
+          const int3 pi = pitem[v];
+          if (pi.z == 0) {
+            double tw = 0.0;
+#pragma unroll
+            for (int ww = 0; ww < NCW; ++ww) tw += wnred[ww][v];
+            ks.wpart[(long long)act[pi.x] * ks.nblk_max + pi.y] = tw;
+          }
+        }
+        consumers_sync<NTC>();
+        pend = 0;
+      }
+    }
+    if (ks.abytes && threadIdx.x == 0 && nitems > 0) {
+      // algorithmic bytes: each basis row chunk once, w once per chunk
+      // (counted by the block that holds the chunk's first group)
+      unsigned long long b = 0;
+      Item q = it0;
+      for (int t = 0; t < nitems; ++t) {
+        const long long off = (long long)q.blk * CHUNK;
+        const long long vals = (n - off < CHUNK) ? (n - off) : CHUNK;
+        b += (unsigned long long)vals * (min(G, j + 1 - q.grp * G) * sizeof(SB) +
+                                         (q.grp == 0 ? sizeof(C<T>) : 0));
+        q.next(nblk, ngrp);
+      }
+      atomicAdd(ks.abytes, b);
+    }
+  }
+  __syncthreads();
+}
+
+// w -= sum_{i<=j} V_i hcol_i and the partial ||w||^2 (same contract as
+// k_maxpy).  Blocks take whole (RHS, chunk) tiles round-robin, since the
+// chunk of w is updated in registers across all j+1 vectors.
+template <class T, class SB, int NCW>
+__global__ void __launch_bounds__(32 * NCW + 32, 1)
+k_maxpy_tma(const SB* __restrict__ V, long long vstride, long long rs,
+            C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
+  constexpr int NTC = 32 * NCW;
+  using P = Cgs<SB, NTC>;
+  constexpr int W = P::W, G = P::G, VPT = P::VPT, E = VPT * W;
+  extern __shared__ __align__(128) unsigned char stages[];
+  __shared__ unsigned long long full[NSTAGE], empty[NSTAGE];
+  __shared__ int act[1024];
+  __shared__ int s_nact;
+  __shared__ volatile int s_abort;
+  __shared__ double red[NCW];
+  const int j = *ks.jctr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  active_rhs(ks, pass, nrhs, act, &s_nact);
+  ring_init<NCW>(full, empty, &s_abort);
+  __syncthreads();
+  const int ngrp = (j + 1 + G - 1) / G;
+  const int tiles = s_nact * nblk;
+
+  if (warp == NCW) {  // producer
+    if (lane == 0) {
+      Slot sl;
+      long long t = 0;
+      bool stop = false;
+      for (int tile = blockIdx.x; tile < tiles && !stop; tile += gridDim.x) {
+        const int a = tile / nblk, blk = tile - a * nblk;
+        for (int grp = 0; grp < ngrp; ++grp, ++t) {
+          if (!producer_acquire(empty, sl, &s_abort, ks.fault)) {
+            stop = true;
+            break;
+          }
+          produce<SB>(stages + sl.s * STAGE_BYTES, &full[sl.s], V, vstride, rs, act[a],
+                      blk, grp * G, min(G, j + 1 - grp * G));
+          sl.next();
+        }
+      }
+      producer_drain(full, t, sl, ks.fault);
+    }
+  } else {  // consumers
+    Slot sl;
+    unsigned long long bytes = 0;
+    C<T> acc[E], nxt[E];
+    bool have_next = false;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+      const int a = tile / nblk, blk = tile - a * nblk;
+      const int r = act[a];
+      const long long off = (long long)blk * CHUNK;
+      const long long valid = n - off;
+      C<T>* wr = w + r * n;
+      if (have_next) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) acc[e] = nxt[e];
+      } else {
+        load_chunk<T, W, VPT, NTC>(acc, wr, off, n);
+      }
+      // prefetch the next tile's chunk of w (a different chunk: no overlap
+      // with the stores of this tile)
+      const int nt = tile + gridDim.x;
+      have_next = nt < tiles;
+      if (have_next) {
+        const int na = nt / nblk;
+        load_chunk<T, W, VPT, NTC>(nxt, w + act[na] * n, (long long)(nt - na * nblk) * CHUNK,
+                                   n);
+      }
+      const double2* hc = ks.hcol + (long long)r * (ks.m + 1);
+      for (int grp = 0; grp < ngrp; ++grp) {
+        const int nv = min(G, j + 1 - grp * G);
+        C<T> h[G];
+#pragma unroll
+        for (int qq = 0; qq < G; ++qq)
+          h[qq] = (qq < nv) ? cvt_to<T>(hc[grp * G + qq]) : czero<T>();
+        if (consumer_acquire(full, sl, &s_abort, ks.fault)) {
+          const unsigned char* sb = stages + sl.s * STAGE_BYTES;
+#pragma unroll
+          for (int qq = 0; qq < G; ++qq) {
+            if (qq < nv) {
+#pragma unroll
+              for (int k = 0; k < VPT; ++k) {
+                const int g = k * NTC + threadIdx.x;
+                if ((long long)g * W < valid) {
+                  const uint4 raw =
+                      *reinterpret_cast<const uint4*>(sb + qq * P::ROWB + g * 16);
+                  static_for<W>([&](auto U) {
+                    const C<T> v = unpk<U.value>(raw, (const SB*)nullptr);
+                    acc[k * W + U.value].x -= v.x * h[qq].x - v.y * h[qq].y;
+                    acc[k * W + U.value].y -= v.x * h[qq].y + v.y * h[qq].x;
+                  });
+                }
+              }
+            }
+          }
+        }
+        consumer_release(empty, sl);
+        sl.next();
+      }
+      T wn = T(0);
+#pragma unroll
+      for (int k = 0; k < VPT; ++k)
+#pragma unroll
+        for (int u = 0; u < W; ++u) {
+          const long long e = off + (long long)(k * NTC + threadIdx.x) * W + u;
+          if (e < n) {
+            wr[e] = acc[k * W + u];
+            wn += acc[k * W + u].x * acc[k * W + u].x + acc[k * W + u].y * acc[k * W + u].y;
+          }
+        }
+      double d = (double)wn;
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) red[warp] = d;
+      consumers_sync<NTC>();
+      if (threadIdx.x == 0) {
+        double tsum = 0.0;
+#pragma unroll
+        for (int ww = 0; ww < NCW; ++ww) tsum += red[ww];
+        ks.npart[(long long)r * ks.nblk_max + blk] = tsum;
+      }
+      consumers_sync<NTC>();
+      const long long vals = valid < CHUNK ? valid : CHUNK;
+      bytes += (unsigned long long)vals * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB));
+    }
+    if (ks.abytes && threadIdx.x == 0 && bytes) atomicAdd(ks.abytes, bytes);
+  }
+  __syncthreads();
 }
 
 // After the first pass: ||w|| (wpart) and ||w - V h|| (npart) per RHS; the
@@ -404,8 +1006,14 @@ __global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
                              const int* __restrict__ done) {
   const int r = blockIdx.y;
   if (done && done[r]) return;
-  const double sv = s[r];
-  const T f = (sv != 0.0) ? T(1.0 / sv) : T(0);
+  // one FP64 reciprocal per block (FP64 division is slow on this GPU)
+  __shared__ T f_s;
+  if (threadIdx.x == 0) {
+    const double sv = s[r];
+    f_s = (sv != 0.0) ? T(1.0 / sv) : T(0);
+  }
+  __syncthreads();
+  const T f = f_s;
   const C<T>* wr = w.get() + r * n;
   SB* orow = out.get() + r * rs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
@@ -609,6 +1217,34 @@ __global__ void k_loop_next(const int* alldone, int* it, int maxit,
   cudaGraphSetConditional(h, (!*alldone && k < maxit) ? 1u : 0u);
 }
 
+// Synthetic vectors for timing (values in [-1/2, 1/2) from an integer hash
+// of the index); no result of the method depends on them.
+template <class SB>
+__global__ void k_tune_fill(SB* __restrict__ p, long long count, unsigned seed) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < count;
+       e += (long long)gridDim.x * blockDim.x) {
+    unsigned h = (unsigned)e * 2654435761u ^ seed;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const float a = (float)(h & 0xffffu) * (1.0f / 65536.0f) - 0.5f;
+    const float b = (float)(h >> 16) * (1.0f / 65536.0f) - 0.5f;
+    if constexpr (std::is_same<SB, double2>::value)
+      p[e] = make_double2(a, b);
+    else
+      st2(p, e, make_float2(a, b));
+  }
+}
+// Arnoldi state of a timing run: column j, every RHS below nrhs active.
+__global__ void k_tune_state(KState ks, int nrhs, int j) {
+  const int r = threadIdx.x;
+  if (r == 0) *ks.jctr = j;
+  if (r < nrhs) {
+    ks.done[r] = 0;
+    ks.reorth[r] = 0;
+  }
+}
+
 __global__ void k_fill_int(int* p, int v, int count) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < count) p[e] = v;
@@ -651,13 +1287,65 @@ unsigned persistent_grid(const void* kern, long long tiles) {
 }
 }  // namespace
 
+namespace {
+int sm_count() {
+  static std::mutex mu;
+  static std::unordered_map<int, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms <= 0) sms = 1;
+  cache[dev] = sms;
+  return sms;
+}
+// opt a kernel in to the stage ring's dynamic shared memory (once per kernel)
+void allow_stages(const void* kern) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, bool> done;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[kern]) return;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RING_BYTES);
+  done[kern] = true;
+}
+}  // namespace
+
 template <class T, class SB>
 void launch_mdot(const SB* V, long long vstride, long long rs, const C<T>* w,
                  long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
   const int nblk = krylov_nblk(n);
+  if (ks.dotk == 1 || ks.dotk == 2) {
+    const void* kern = ks.dotk == 1 ? (const void*)k_mdot_tma<T, SB, 8>
+                                   : (const void*)k_mdot_tma<T, SB, 16>;
+    allow_stages(kern);
+    if (ks.dotk == 1)
+      k_mdot_tma<T, SB, 8><<<sm_count(), 288, RING_BYTES, st>>>(V, vstride, rs, w, n, ks,
+                                                               pass, nrhs, nblk);
+    else
+      k_mdot_tma<T, SB, 16><<<sm_count(), 544, RING_BYTES, st>>>(V, vstride, rs, w, n, ks,
+                                                                pass, nrhs, nblk);
+    return;
+  }
   const unsigned grid = persistent_grid((const void*)k_mdot<T, SB>, (long long)nblk * nrhs);
   k_mdot<T, SB><<<grid, NT, 0, st>>>(V, vstride, rs, w, n, ks, pass, nrhs, nblk);
+}
+template <class T, class SB>
+void launch_mdot_group(const GroupDesc& gd, int pass, cudaStream_t st) {
+  HZ_COUNT();
+  const unsigned grid =
+      persistent_grid((const void*)k_mdot_group<T, SB>, gd.start[gd.count]);
+  k_mdot_group<T, SB><<<grid, NT, 0, st>>>(gd, pass);
+}
+template <class T, class SB>
+void launch_maxpy_group(const GroupDesc& gd, int pass, cudaStream_t st) {
+  HZ_COUNT();
+  const unsigned grid =
+      persistent_grid((const void*)k_maxpy_group<T, SB>, gd.start[gd.count]);
+  k_maxpy_group<T, SB><<<grid, NT, 0, st>>>(gd, pass);
 }
 void launch_reduce_cols(const KState& ks, long long n, int nrhs, int pass,
                         cudaStream_t st) {
@@ -671,6 +1359,20 @@ void launch_maxpy(const SB* V, long long vstride, long long rs, C<T>* w,
                   long long n, int nrhs, const KState& ks, int pass, cudaStream_t st) {
   HZ_COUNT();
   const int nblk = krylov_nblk(n);
+  if (ks.updk == 1 || ks.updk == 2) {
+    const void* kern = ks.updk == 1 ? (const void*)k_maxpy_tma<T, SB, 8>
+                                   : (const void*)k_maxpy_tma<T, SB, 16>;
+    allow_stages(kern);
+    const long long tiles = (long long)nblk * nrhs;
+    const unsigned grid = (unsigned)(tiles < sm_count() ? tiles : sm_count());
+    if (ks.updk == 1)
+      k_maxpy_tma<T, SB, 8><<<grid, 288, RING_BYTES, st>>>(V, vstride, rs, w, n, ks, pass,
+                                                          nrhs, nblk);
+    else
+      k_maxpy_tma<T, SB, 16><<<grid, 544, RING_BYTES, st>>>(V, vstride, rs, w, n, ks, pass,
+                                                           nrhs, nblk);
+    return;
+  }
   const unsigned grid = persistent_grid((const void*)k_maxpy<T, SB>, (long long)nblk * nrhs);
   k_maxpy<T, SB><<<grid, NT, 0, st>>>(V, vstride, rs, w, n, ks, pass, nrhs, nblk);
 }
@@ -735,6 +1437,20 @@ void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
   HZ_COUNT();
   k_fill_int<<<(count + 255) / 256, 256, 0, st>>>(p, v, count);
 }
+template <class SB>
+void launch_tune_fill(SB* p, long long count, unsigned seed, cudaStream_t st) {
+  HZ_COUNT();
+  long long nb = (count + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_tune_fill<SB><<<(unsigned)nb, 256, 0, st>>>(p, count, seed);
+}
+template void launch_tune_fill<double2>(double2*, long long, unsigned, cudaStream_t);
+template void launch_tune_fill<float2>(float2*, long long, unsigned, cudaStream_t);
+template void launch_tune_fill<__half2>(__half2*, long long, unsigned, cudaStream_t);
+void launch_tune_state(const KState& ks, int nrhs, int j, cudaStream_t st) {
+  HZ_COUNT();
+  k_tune_state<<<1, 1024, 0, st>>>(ks, nrhs, j);
+}
 void launch_loop_begin(const int* alldone, int* it, cudaGraphConditionalHandle h,
                        cudaStream_t st) {
   HZ_COUNT();
@@ -772,7 +1488,9 @@ void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
                                          int, const int*, cudaStream_t);        \
   template void launch_update<SB, T>(const SB*, long long, long long,           \
                                      const KState&, C<T>*, int, long long, int, \
-                                     cudaStream_t);
+                                     cudaStream_t);                             \
+  template void launch_mdot_group<T, SB>(const GroupDesc&, int, cudaStream_t);  \
+  template void launch_maxpy_group<T, SB>(const GroupDesc&, int, cudaStream_t);
 
 template void launch_norm2_part<double>(VRef<double>, long long, int, const KState&,
                                         const int*, cudaStream_t);

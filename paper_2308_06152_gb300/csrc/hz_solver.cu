@@ -130,6 +130,7 @@ struct hz_solver {
   // coarse level (level 1)
   void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
   void* qf = nullptr;      // current basis vector in compute precision (FP16 basis)
+  void* Sglk = nullptr;    // stcl-op-Glk coefficient planes [P*P][n1] (Galerkin E)
   bool basis16 = false;    // inner Krylov basis stored as FP16 pairs
   KState kin{}, kout{};
   int* in_total = nullptr;
@@ -166,6 +167,8 @@ struct hz_solver {
   long long body_count = 0;      // kernels of one WHILE body
   int* loop_it = nullptr;        // device: iterations of the running loop
   int* body_kernels = nullptr;   // device: body_count
+  int* fault = nullptr;          // device: a Krylov pipeline wait timed out
+  hz_tuning tune{};
   int body_kernels_host = 0;
 
   ~hz_solver() {
@@ -224,6 +227,9 @@ KState plan_kstate(Arena& a, int B, int m, long long n) {
   k.npart = (double*)a.take(sizeof(double) * (size_t)B * k.nblk_max);
   k.wpart = (double*)a.take(sizeof(double) * (size_t)B * k.nblk_max);
   k.reorth = (int*)a.take(sizeof(int) * B);
+  k.fault = nullptr;   // set by plan(): one flag per solver
+  k.dotk = 0;
+  k.updk = 0;
   return k;
 }
 
@@ -263,6 +269,10 @@ void plan(hz_solver* s, Arena& a) {
     s->Qb = a.take(bes * (size_t)B * inner_row(n1) * (d.coarse_maxit + 1));
     s->qf = a.take(es * B * n1);
     s->kin = plan_kstate(a, B, d.coarse_maxit, n1);
+    if (d.ekind == HZ_E_GALERKIN) {
+      const int P = d.zkind == HZ_Z_HO ? 5 : 3;
+      s->Sglk = a.take(es * (size_t)P * P * n1);
+    }
   }
   s->in_total = (int*)a.take(sizeof(int) * B);
   s->in_max = (int*)a.take(sizeof(int) * B);
@@ -279,6 +289,11 @@ void plan(hz_solver* s, Arena& a) {
   s->prof_bytes = (unsigned long long*)a.take(sizeof(unsigned long long));
   s->loop_it = (int*)a.take(sizeof(int));
   s->body_kernels = (int*)a.take(sizeof(int));
+  s->fault = (int*)a.take(sizeof(int));
+  s->kin.fault = s->fault;
+  s->kout.fault = s->fault;
+  s->kin.dotk = s->kout.dotk = s->tune.mdot_kernel;
+  s->kin.updk = s->kout.updk = s->tune.maxpy_kernel;
 }
 
 hz_status init_shapes(hz_solver* s) {
@@ -337,9 +352,19 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
     launch_dense_mv<T, C<T>, C<T>>(s->nL, minv, f, xout, nrhs, done, st);
     return;
   }
+  const bool fused = s->tune.vcycle_fused != 0;
   for (int l = l0; l < s->L; ++l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
+    if (fused) {
+      if (l == l0)
+        launch_pre_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f, (SL*)A.xa,
+                                             (SL*)Bc.f, nrhs, done, st);
+      else
+        launch_pre_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, vrefe<SL>(A.f),
+                                           (SL*)A.xa, (SL*)Bc.f, nrhs, done, st);
+      continue;
+    }
     if (l == l0) {
       launch_jacobi0<T, C<T>, SL>(A.dev(), bc, f, (SL*)A.xa, nrhs, done, st);
       launch_resid_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f,
@@ -358,6 +383,17 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
   for (int l = s->L - 1; l >= l0; --l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
+    if (fused) {
+      if (l == l0)
+        launch_prolong_smooth<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, sh,
+                                                     (const SL*)Bc.x, (const SL*)A.xa, f,
+                                                     xout, nrhs, done, st);
+      else
+        launch_prolong_smooth<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh,
+                                                 (const SL*)Bc.x, (const SL*)A.xa,
+                                                 vrefe<SL>(A.f), (SL*)A.x, nrhs, done, st);
+      continue;
+    }
     launch_prolong_add<T, SL, SL>(A.dev(), Bc.dev(), bc, (const SL*)Bc.x, (SL*)A.xa,
                                   nrhs, done, st);
     if (l == l0)
@@ -389,8 +425,13 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
   const LevelHost& Cc = s->lv[1];
   switch (s->d.ekind) {
     case HZ_E_GALERKIN:
-      launch_galerkin_fused<T>(F.dev(), Cc.dev(), bc, s->d.zkind, x, y, nrhs, done,
-                               st);
+      if (s->tune.galerkin_apply == 1)
+        launch_stencil_e<T>(Cc.dev(), s->d.zkind == HZ_Z_HO ? 2 : 1,
+                            (const C<T>*)s->Sglk, x, y, nrhs, s->tune.e_rhs_per_block,
+                            done, st);
+      else
+        launch_galerkin_fused<T>(F.dev(), Cc.dev(), bc, s->d.zkind, x, y, nrhs, done,
+                                 st);
       break;
     case HZ_E_RED_O2:
       launch_helm<T>(Cc.dev(), bc, helm1(), vref<T>(x), vref<T>(nullptr), y, nrhs,
@@ -402,6 +443,31 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
     default:
       launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st);
       break;
+  }
+}
+
+// stcl-op-Glk set-up: the coefficients of E = R_Z A_h Z by FP64 probing of
+// the on-the-fly product (the outer basis, unused until a solve, holds the
+// probes and their images).
+void extract_galerkin_stencil(hz_solver* s) {
+  cudaStream_t st = s->st;
+  const int P = s->d.zkind == HZ_Z_HO ? 5 : 3, K = P * P;
+  const long long n1 = s->lv[1].n;
+  const size_t scratch = sizeof(double2) * (size_t)s->d.nrhs_max * s->lv[0].n *
+                         (s->d.outer_maxit + 1);
+  long long pb = (long long)(scratch / (2 * sizeof(double2) * (size_t)n1));
+  if (pb > K) pb = K;
+  double2* pin = s->Vo;
+  double2* pout = s->Vo + pb * n1;
+  const LevelDev F = dev64(s, 0), Cc = dev64(s, 1);
+  for (int c0 = 0; c0 < K; c0 += (int)pb) {
+    const int nb = (int)(K - c0 < pb ? K - c0 : pb);
+    launch_probe_fill(Cc, P, c0, nb, pin, st);
+    launch_galerkin_fused<double>(F, Cc, s->d.bc, s->d.zkind, pin, pout, nb, nullptr, st);
+    if (s->mixed)
+      launch_probe_extract<float>(Cc, P, c0, nb, pout, (float2*)s->Sglk, st);
+    else
+      launch_probe_extract<double>(Cc, P, c0, nb, pout, (double2*)s->Sglk, st);
   }
 }
 
@@ -484,27 +550,41 @@ void cgs2(hz_solver* s, KState& ks, const SB* V, long long vs, long long rs, C<T
 // device by the column counter) -> V-cycle -> E -> Gram-Schmidt -> Givens ->
 // new basis vector.  Every launch goes to s->st and every argument is fixed
 // for the solver, so the step can be captured once and replayed.
+// (the part before the Gram-Schmidt step: w = E M_2h^-1 v_j into eb)
 template <class T, class SB>
-void inner_step(hz_solver* s, int nrhs) {
-  cudaStream_t st = s->st;
+void inner_pre(hz_solver* s, int nrhs) {
   KState& ks = s->kin;
   const long long n1 = s->lv[1].n;
   const long long rs = inner_row(n1);
   const long long vs = (long long)s->d.nrhs_max * rs;
-  SB* Q = (SB*)s->Qb;
   C<T>* sb = (C<T>*)s->sb;
-  C<T>* eb = (C<T>*)s->eb;
   // the V-cycle reads the current basis vector, unpadded, in compute
   // precision
-  launch_basis_load<SB, T>(vrefe_j<SB>(Q, ks.jctr, 0, vs), rs, (C<T>*)s->qf, n1,
-                           nrhs, ks.done, st);
+  launch_basis_load<SB, T>(vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs), rs, (C<T>*)s->qf,
+                           n1, nrhs, ks.done, s->st);
   vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
-  apply_E<T>(s, sb, eb, nrhs, ks.done);
-  cgs2<T, SB>(s, ks, Q, vs, rs, eb, n1, nrhs);
-  launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, st);
+  apply_E<T>(s, sb, (C<T>*)s->eb, nrhs, ks.done);
+}
+// (the part after it: Givens update and v_{j+1} = w / ||w||)
+template <class T, class SB>
+void inner_post(hz_solver* s, int nrhs) {
+  KState& ks = s->kin;
+  const long long n1 = s->lv[1].n;
+  const long long rs = inner_row(n1);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, s->st);
   debug_trace(s, ks, "inner");
-  launch_scale_into<T, SB>(vref<T>(eb), vrefe_j<SB>(Q, ks.jctr, 0, vs), rs,
-                           ks.hnorm, n1, nrhs, ks.done, st);
+  launch_scale_into<T, SB>(vref<T>((C<T>*)s->eb), vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs),
+                           rs, ks.hnorm, n1, nrhs, ks.done, s->st);
+}
+template <class T, class SB>
+void inner_step(hz_solver* s, int nrhs) {
+  const long long n1 = s->lv[1].n;
+  const long long rs = inner_row(n1);
+  inner_pre<T, SB>(s, nrhs);
+  cgs2<T, SB>(s, s->kin, (SB*)s->Qb, (long long)s->d.nrhs_max * rs, rs, (C<T>*)s->eb, n1,
+              nrhs);
+  inner_post<T, SB>(s, nrhs);
 }
 
 // While s->st is being captured: appends to the captured graph a WHILE node
@@ -563,22 +643,37 @@ hz_status capture_inner_loop(hz_solver* s, int nrhs) {
 // E v2 = v1 by right-preconditioned GMRES (V-cycle on the coarse CSLP from
 // level 1), x0 = 0, stopping at |g_{j+1}| <= coarse_tol ||v1||.
 template <class T, class SB>
-hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
-                          const int* done_in) {
+void coarse_begin(hz_solver* s, const C<T>* v1, int nrhs, const int* done_in) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin;
+  const long long n1 = s->lv[1].n;
+  launch_norm2_part<T>(vref<T>(v1), n1, nrhs, ks, nullptr, st);
+  launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
+  launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, st);
+  launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>((SB*)s->Qb), inner_row(n1), ks.hnorm,
+                           n1, nrhs, ks.done, st);
+}
+// x = Q_k y (k the iterations taken), then v2 = M_2h^-1 x (right
+// preconditioning)
+template <class T, class SB>
+void coarse_finish(hz_solver* s, C<T>* v2, int nrhs, const int* done_in) {
   cudaStream_t st = s->st;
   KState& ks = s->kin;
   const long long n1 = s->lv[1].n;
   const long long rs = inner_row(n1);
-  const long long vs = (long long)s->d.nrhs_max * rs;
-  SB* Q = (SB*)s->Qb;
-  C<T>* eb = (C<T>*)s->eb;
+  launch_trisolve(ks, nrhs, st);
+  launch_update<SB, T>((const SB*)s->Qb, (long long)s->d.nrhs_max * rs, rs, ks,
+                       (C<T>*)s->eb, 0, n1, nrhs, st);
+  vcycle<T>(s, 1, vref<T>((C<T>*)s->eb), v2, nrhs, done_in);
+  launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
+}
+
+template <class T, class SB>
+hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
+                          const int* done_in) {
+  KState& ks = s->kin;
   const int m = s->d.coarse_maxit;
-  const double tol = s->d.coarse_tol;
-  launch_norm2_part<T>(vref<T>(v1), n1, nrhs, ks, nullptr, st);
-  launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
-  launch_krylov_init(ks, nrhs, done_in, nullptr, tol, st);
-  launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>(Q), rs, ks.hnorm, n1, nrhs,
-                           ks.done, st);
+  coarse_begin<T, SB>(s, v1, nrhs, done_in);
   if (s->capturing) {
     const hz_status e = capture_inner_loop<T, SB>(s, nrhs);
     if (e != HZ_OK) return e;
@@ -593,10 +688,7 @@ hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
       }
     }
   }
-  launch_trisolve(ks, nrhs, st);
-  launch_update<SB, T>(Q, vs, rs, ks, eb, 0, n1, nrhs, st);
-  vcycle<T>(s, 1, vref<T>(eb), v2, nrhs, done_in);
-  launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
+  coarse_finish<T, SB>(s, v2, nrhs, done_in);
   return cuda_check(s, "coarse solve");
 }
 
@@ -612,34 +704,52 @@ hz_status coarse_solve(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
 // ------------------------------------------------------------ A-DEF1
 // z = M^-1 (v - A q) + q, q = Z E^-1 R v; v, z FP64 (possibly indexed by the
 // outer Arnoldi counter), the preconditioner in precision T.
+// (first part: v in precision T, and v1 = R_Z v with deflation)
 template <class T>
-hz_status precond(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
-                  const int* done) {
-  cudaStream_t st = s->st;
-  const int bc = s->d.bc;
+VRef<T> precond_begin(hz_solver* s, VRef<double> vin, int nrhs, const int* done) {
   const long long n0 = s->lv[0].n;
   VRef<T> v;
   if constexpr (std::is_same<T, double>::value) {
     v = vin;
   } else {
-    launch_add_conv<double, T>(vin, nullptr, vref<T>(s->vin), n0, nrhs, done, st);
+    launch_add_conv<double, T>(vin, nullptr, vref<T>(s->vin), n0, nrhs, done, s->st);
     v = vref<T>(s->vin);
   }
+  if (s->d.zkind != HZ_Z_NONE)
+    launch_restrict_z<T>(s->lv[0].dev(), s->lv[1].dev(), s->d.bc, s->d.zkind, v,
+                         (C<T>*)s->v1, nrhs, done, s->st);
+  return v;
+}
+// (last part, after v2 = E^-1 v1: q = Z v2, z = M^-1 (v - A q) + q)
+template <class T>
+void precond_finish(hz_solver* s, VRef<T> v, VRef<double> zout, int nrhs,
+                    const int* done) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const long long n0 = s->lv[0].n;
   C<T>* yv = (C<T>*)s->yv;
   if (s->d.zkind == HZ_Z_NONE) {
     vcycle<T>(s, 0, v, yv, nrhs, done);
     launch_add_conv<T, double>(vref<T>(yv), nullptr, zout, n0, nrhs, done, st);
-    return cuda_check(s, "precond");
+    return;
   }
   const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
-  launch_restrict_z<T>(F, Cc, bc, s->d.zkind, v, (C<T>*)s->v1, nrhs, done, st);
-  hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
-  if (e != HZ_OK) return e;
   launch_prolong_z<T>(F, Cc, bc, s->d.zkind, (const C<T>*)s->v2, (C<T>*)s->q, 0, nrhs,
                       done, st);
   launch_helm<T>(F, bc, helm1(), vref<T>(s->q), v, (C<T>*)s->t, nrhs, done, st);
   vcycle<T>(s, 0, vref<T>(s->t), yv, nrhs, done);
   launch_add_conv<T, double>(vref<T>(yv), (const C<T>*)s->q, zout, n0, nrhs, done, st);
+}
+
+template <class T>
+hz_status precond(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
+                  const int* done) {
+  const VRef<T> v = precond_begin<T>(s, vin, nrhs, done);
+  if (s->d.zkind != HZ_Z_NONE) {
+    const hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
+    if (e != HZ_OK) return e;
+  }
+  precond_finish<T>(s, v, zout, nrhs, done);
   return cuda_check(s, "precond");
 }
 
@@ -753,13 +863,12 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
   return &s->graphs.back();
 }
 
-hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
-                    double tol, int use_x0, hz_solve_info* info) {
+// Outer FGMRES start: ||b||, r0 = b - A x0 (or b), Krylov state, v_0.
+hz_status outer_begin(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
+                      int use_x0) {
   cudaStream_t st = s->st;
   KState& ko = s->kout;
   const long long n0 = s->lv[0].n;
-  const long long vs = (long long)s->d.nrhs_max * n0;
-  const int m = s->d.outer_maxit;
   const int bc = s->d.bc;
   const LevelDev F = dev64(s, 0);
   cudaMemsetAsync(s->in_total, 0, sizeof(int) * nrhs, st);
@@ -782,7 +891,165 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   launch_krylov_init(ko, nrhs, nullptr, s->bnorm_o, tol, st);
   launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(s->Vo), n0,
                                     ko.hnorm, n0, nrhs, ko.done, st);
-  hz_status e = cuda_check(s, "outer init");
+  return cuda_check(s, "outer init");
+}
+
+// Outer FGMRES end: x += Z_k y, the true residual and the per-RHS report.
+hz_status outer_end(hz_solver* s, const double2* b, double2* x, int nrhs,
+                    hz_solve_info* info) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const long long n0 = s->lv[0].n;
+  const long long vs = (long long)s->d.nrhs_max * n0;
+  const int bc = s->d.bc;
+  const LevelDev F = dev64(s, 0);
+  hz_status e = HZ_OK;
+  launch_trisolve(ko, nrhs, st);
+  launch_update<double2, double>(s->Zo, vs, n0, ko, x, 1, n0, nrhs, st);
+  // true residual
+  launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo, nrhs,
+                      nullptr, st);
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, s->relres, 1, st);
+  e = cuda_check(s, "outer finish");
+  if (e != HZ_OK) return e;
+  std::vector<int> it(nrhs), stt(nrhs), itot(nrhs), imax(nrhs);
+  std::vector<double> rr(nrhs), bn(nrhs);
+  int fault = 0;
+  cudaMemcpyAsync(&fault, s->fault, sizeof(int), cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(it.data(), ko.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(stt.data(), ko.stat, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(itot.data(), s->in_total, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(imax.data(), s->in_max, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(rr.data(), s->relres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(bn.data(), s->bnorm_o, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(s, "outer sync");
+  if (fault) {
+    set_err(s, "a Krylov kernel gave up waiting for its staged basis rows");
+    cudaMemsetAsync(s->fault, 0, sizeof(int), st);
+    return HZ_TIMEOUT;
+  }
+  hz_status worst = HZ_OK;
+  for (int r = 0; r < nrhs; ++r) {
+    hz_status sr = (hz_status)stt[r];
+    const double rel = bn[r] > 0 ? rr[r] / bn[r] : 0.0;
+    if (sr == HZ_OK && !std::isfinite(rel)) sr = HZ_NAN;
+    if (info) {
+      info[r].outer_iters = it[r];
+      info[r].inner_iters_total = itot[r];
+      info[r].inner_iters_max = imax[r];
+      info[r].relres = rel;
+      info[r].status = sr;
+    }
+    if (worst == HZ_OK && sr != HZ_OK) worst = sr;
+  }
+  return worst;
+}
+
+// ------------------------------------------------------------ autotuning
+// Mean ms of `reps` calls of f() on the solver's stream (after one warm-up).
+template <class F>
+double time_ms(hz_solver* s, int reps, F&& f) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  f();
+  cudaEventRecord(e0, s->st);
+  for (int k = 0; k < reps; ++k) f();
+  cudaEventRecord(e1, s->st);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return (double)ms / reps;
+}
+
+// One launch of the Gram-Schmidt dot (upd = false) or update kernel of the
+// inner solver at column j on synthetic basis rows (of the outer solver
+// when there is no deflation), with the given kernel variant.
+template <class T, class SB>
+double time_cgs(hz_solver* s, int nrhs, bool upd, int variant) {
+  const bool inner = s->d.zkind != HZ_Z_NONE;
+  KState& ks = inner ? s->kin : s->kout;
+  const long long n = inner ? s->lv[1].n : s->lv[0].n;
+  const long long rs = inner ? inner_row(n) : n;
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  const int m = inner ? s->d.coarse_maxit : s->d.outer_maxit;
+  const int j = m - 1 < 64 ? m - 1 : 64;
+  SB* V = inner ? (SB*)s->Qb : (SB*)s->Vo;
+  C<T>* w = inner ? (C<T>*)s->eb : (C<T>*)s->wo;
+  launch_tune_fill<SB>(V, vs * (j + 1), 0x9e3779b9u, s->st);
+  launch_tune_fill<C<T>>(w, n * nrhs, 0x85ebca6bu, s->st);
+  launch_tune_state(ks, nrhs, j, s->st);
+  // the update's coefficients: a first dot pass
+  launch_mdot<T, SB>(V, vs, rs, w, n, nrhs, ks, 0, s->st);
+  launch_reduce_cols(ks, n, nrhs, 0, s->st);
+  KState k = ks;
+  k.abytes = nullptr;
+  (upd ? k.updk : k.dotk) = variant;
+  return time_ms(s, 5, [&]() {
+    if (upd)
+      launch_maxpy<T, SB>(V, vs, rs, w, n, nrhs, k, 0, s->st);
+    else
+      launch_mdot<T, SB>(V, vs, rs, w, n, nrhs, k, 0, s->st);
+  });
+}
+
+double time_cgs_any(hz_solver* s, int nrhs, bool upd, int variant) {
+  if (s->d.zkind == HZ_Z_NONE || !s->mixed)
+    return time_cgs<double, double2>(s, nrhs, upd, variant);
+  if (s->basis16) return time_cgs<float, __half2>(s, nrhs, upd, variant);
+  return time_cgs<float, float2>(s, nrhs, upd, variant);
+}
+
+// One V-cycle from level 1 (level 0 without deflation) on synthetic data.
+template <class T>
+double time_vcycle(hz_solver* s, int nrhs, int fused) {
+  const hz_tuning saved = s->tune;
+  s->tune.vcycle_fused = fused;
+  const int l0 = (s->d.zkind != HZ_Z_NONE && s->L >= 1) ? 1 : 0;
+  const long long n = s->lv[l0].n;
+  C<T>* in = (C<T>*)(l0 == 1 ? s->sb : s->t);
+  C<T>* out = (C<T>*)(l0 == 1 ? s->eb : s->yv);
+  launch_tune_fill<C<T>>(in, n * nrhs, 0x165667b1u, s->st);
+  const double ms =
+      time_ms(s, 5, [&]() { vcycle<T>(s, l0, vref<T>(in), out, nrhs, nullptr); });
+  s->tune = saved;
+  return ms;
+}
+
+template <class T>
+double time_e(hz_solver* s, int nrhs, int apply, int rpb) {
+  const hz_tuning saved = s->tune;
+  s->tune.galerkin_apply = apply;
+  s->tune.e_rhs_per_block = rpb;
+  const long long n1 = s->lv[1].n;
+  launch_tune_fill<C<T>>((C<T>*)s->sb, n1 * nrhs, 0x27d4eb2fu, s->st);
+  const double ms = time_ms(s, 8, [&]() {
+    apply_E<T>(s, (const C<T>*)s->sb, (C<T>*)s->eb, nrhs, nullptr);
+  });
+  s->tune = saved;
+  return ms;
+}
+
+// HZ_TIMEOUT (and the flag cleared) if a Krylov kernel's bounded wait ran out.
+hz_status take_fault(hz_solver* s) {
+  int f = 0;
+  const hz_status e = read_flag(s, s->fault, &f);
+  if (e != HZ_OK) return e;
+  if (!f) return HZ_OK;
+  set_err(s, "a Krylov kernel gave up waiting for its staged basis rows");
+  cudaMemsetAsync(s->fault, 0, sizeof(int), s->st);
+  return HZ_TIMEOUT;
+}
+
+hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
+                    double tol, int use_x0, hz_solve_info* info) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const int m = s->d.outer_maxit;
+  hz_status e = outer_begin(s, b, x, nrhs, tol, use_x0);
   if (e != HZ_OK) return e;
   int all = 0;
   // graphs replay fixed launches: the per-launch events of the profiler
@@ -806,40 +1073,204 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
     e = read_flag(s, ko.alldone, &all);
     if (e != HZ_OK) return e;
   }
-  launch_trisolve(ko, nrhs, st);
-  launch_update<double2, double>(s->Zo, vs, n0, ko, x, 1, n0, nrhs, st);
-  // true residual
-  launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo, nrhs,
-                      nullptr, st);
-  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
-  launch_reduce_norm(ko, n0, nrhs, s->relres, 1, st);
-  e = cuda_check(s, "outer finish");
-  if (e != HZ_OK) return e;
-  std::vector<int> it(nrhs), stt(nrhs), itot(nrhs), imax(nrhs);
-  std::vector<double> rr(nrhs), bn(nrhs);
-  cudaMemcpyAsync(it.data(), ko.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(stt.data(), ko.stat, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(itot.data(), s->in_total, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(imax.data(), s->in_max, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(rr.data(), s->relres, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
-  cudaMemcpyAsync(bn.data(), s->bnorm_o, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(s, "outer sync");
-  hz_status worst = HZ_OK;
-  for (int r = 0; r < nrhs; ++r) {
-    hz_status sr = (hz_status)stt[r];
-    const double rel = bn[r] > 0 ? rr[r] / bn[r] : 0.0;
-    if (sr == HZ_OK && !std::isfinite(rel)) sr = HZ_NAN;
-    if (info) {
-      info[r].outer_iters = it[r];
-      info[r].inner_iters_total = itot[r];
-      info[r].inner_iters_max = imax[r];
-      info[r].relres = rel;
-      info[r].status = sr;
+  return outer_end(s, b, x, nrhs, info);
+}
+
+// ------------------------------------------------------------ uneven grids
+// Solvers on grids of different sizes advanced together: every Krylov
+// iteration of all members runs in lockstep, each member's stencil work is
+// launched for its own grid, and the Gram-Schmidt kernels of all members run
+// as one persistent launch over a table of their tiles (k_*_group).
+struct Member {
+  hz_solver* s;
+  int nrhs;
+};
+
+template <class T, class SB>
+void cgs2_group(const std::vector<Member>& M, bool inner, cudaStream_t st) {
+  GroupDesc gd{};
+  gd.count = (int)M.size();
+  long long start = 0;
+  for (int g = 0; g < gd.count; ++g) {
+    hz_solver* s = M[g].s;
+    GroupMember& m = gd.m[g];
+    const long long n = inner ? s->lv[1].n : s->lv[0].n;
+    m.rs = inner ? inner_row(n) : n;
+    m.vstride = (long long)s->d.nrhs_max * m.rs;
+    m.V = inner ? s->Qb : (const void*)s->Vo;
+    m.w = inner ? s->eb : (void*)s->wo;
+    m.n = n;
+    m.ks = inner ? s->kin : s->kout;
+    m.ks.abytes = nullptr;
+    m.nrhs = M[g].nrhs;
+    m.nblk = krylov_nblk(n);
+    gd.start[g] = start;
+    start += (long long)m.nrhs * m.nblk;
+  }
+  gd.start[gd.count] = start;
+  for (int pass = 0; pass < 2; ++pass) {
+    launch_mdot_group<T, SB>(gd, pass, st);
+    for (int g = 0; g < gd.count; ++g)
+      launch_reduce_cols(gd.m[g].ks, gd.m[g].n, gd.m[g].nrhs, pass, st);
+    launch_maxpy_group<T, SB>(gd, pass, st);
+    if (pass == 0)
+      for (int g = 0; g < gd.count; ++g)
+        launch_reorth_decide(gd.m[g].ks, gd.m[g].n, gd.m[g].nrhs, kReorthEta, st);
+  }
+  for (int g = 0; g < gd.count; ++g)
+    launch_reduce_norm(gd.m[g].ks, gd.m[g].n, gd.m[g].nrhs, gd.m[g].ks.hnorm, 1, st);
+}
+
+// all[g] = the all-converged flag of member g's inner or outer solver
+hz_status read_flags(const std::vector<Member>& M, bool inner, std::vector<int>& all,
+                     cudaStream_t st) {
+  all.assign(M.size(), 0);
+  for (size_t g = 0; g < M.size(); ++g)
+    cudaMemcpyAsync(&all[g], inner ? M[g].s->kin.alldone : M[g].s->kout.alldone,
+                    sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(M[0].s, "group flags");
+  return HZ_OK;
+}
+
+template <class T, class SB>
+hz_status coarse_solve_group(const std::vector<Member>& M, cudaStream_t st) {
+  int m = 0;
+  for (const Member& g : M) {
+    coarse_begin<T, SB>(g.s, (const C<T>*)g.s->v1, g.nrhs, g.s->kout.done);
+    m = g.s->d.coarse_maxit > m ? g.s->d.coarse_maxit : m;
+  }
+  const int every = M[0].s->check_every;
+  std::vector<int> all;
+  for (int it = 0; it < m; ++it) {
+    for (const Member& g : M) inner_pre<T, SB>(g.s, g.nrhs);
+    cgs2_group<T, SB>(M, true, st);
+    for (const Member& g : M) inner_post<T, SB>(g.s, g.nrhs);
+    if ((it + 1) % every == 0 || it + 1 == m) {
+      const hz_status e = read_flags(M, true, all, st);
+      if (e != HZ_OK) return e;
+      bool done = true;
+      for (int a : all) done = done && a;
+      if (done) break;
     }
-    if (worst == HZ_OK && sr != HZ_OK) worst = sr;
+  }
+  for (const Member& g : M) coarse_finish<T, SB>(g.s, (C<T>*)g.s->v2, g.nrhs, g.s->kout.done);
+  return cuda_check(M[0].s, "group coarse solve");
+}
+
+template <class T>
+hz_status outer_step_group(const std::vector<Member>& M, double tol, cudaStream_t st) {
+  std::vector<VRef<T>> v(M.size());
+  for (size_t g = 0; g < M.size(); ++g) {
+    hz_solver* s = M[g].s;
+    const long long vs = (long long)s->d.nrhs_max * s->lv[0].n;
+    v[g] = precond_begin<T>(s, vref_j<double>(s->Vo, s->kout.jctr, 0, vs), M[g].nrhs,
+                            s->kout.done);
+  }
+  if (M[0].s->d.zkind != HZ_Z_NONE) {
+    hz_status e;
+    if constexpr (std::is_same<T, float>::value) {
+      e = M[0].s->basis16 ? coarse_solve_group<T, __half2>(M, st)
+                          : coarse_solve_group<T, C<T>>(M, st);
+    } else {
+      e = coarse_solve_group<T, C<T>>(M, st);
+    }
+    if (e != HZ_OK) return e;
+  }
+  for (size_t g = 0; g < M.size(); ++g) {
+    hz_solver* s = M[g].s;
+    const long long vs = (long long)s->d.nrhs_max * s->lv[0].n;
+    precond_finish<T>(s, v[g], vref_j<double>(s->Zo, s->kout.jctr, 0, vs), M[g].nrhs,
+                      s->kout.done);
+    launch_helm<double>(dev64(s, 0), s->d.bc, helm1(),
+                        vref_j<double>(s->Zo, s->kout.jctr, 0, vs), vref<double>(nullptr),
+                        s->wo, M[g].nrhs, s->kout.done, st);
+  }
+  cgs2_group<double, double2>(M, false, st);
+  for (const Member& g : M) {
+    hz_solver* s = g.s;
+    const long long n0 = s->lv[0].n;
+    const long long vs = (long long)s->d.nrhs_max * n0;
+    launch_givens(s->kout, g.nrhs, tol, s->d.outer_maxit, st);
+    launch_scale_into<double, double2>(vref<double>(s->wo),
+                                      vref_j<double>(s->Vo, s->kout.jctr, 0, vs), n0,
+                                      s->kout.hnorm, n0, g.nrhs, s->kout.done, st);
+  }
+  return cuda_check(M[0].s, "group outer step");
+}
+
+// Member g solves b[g] -> x[g] (x0 = 0); all members already run on st.
+hz_status solve_group_dev(const std::vector<Member>& M, const double2* const* b,
+                          double2* const* x, double tol, hz_solve_info* const* info,
+                          cudaStream_t st) {
+  const int K = (int)M.size();
+  int m = 0;
+  for (int g = 0; g < K; ++g) {
+    const hz_status e = outer_begin(M[g].s, b[g], x[g], M[g].nrhs, tol, 0);
+    if (e != HZ_OK) return e;
+    m = M[g].s->d.outer_maxit > m ? M[g].s->d.outer_maxit : m;
+  }
+  std::vector<int> all;
+  hz_status e = read_flags(M, false, all, st);
+  if (e != HZ_OK) return e;
+  for (int it = 0; it < m; ++it) {
+    std::vector<Member> act;
+    for (int g = 0; g < K; ++g)
+      if (!all[g]) act.push_back(M[g]);
+    if (act.empty()) break;
+    e = M[0].s->mixed ? outer_step_group<float>(act, tol, st)
+                      : outer_step_group<double>(act, tol, st);
+    if (e != HZ_OK) return e;
+    std::vector<int> now;
+    e = read_flags(act, false, now, st);
+    if (e != HZ_OK) return e;
+    for (size_t a = 0, g = 0; g < (size_t)K; ++g)
+      if (!all[g]) all[g] = now[a++];
+  }
+  hz_status worst = HZ_OK;
+  for (int g = 0; g < K; ++g) {
+    e = outer_end(M[g].s, b[g], x[g], M[g].nrhs, info ? info[g] : nullptr);
+    if (e == HZ_CUDA_ERROR || e == HZ_TIMEOUT) return e;
+    if (worst == HZ_OK) worst = e;
   }
   return worst;
 }
+
+// Checks a group and runs every member on members[0]'s stream while alive.
+struct GroupScope {
+  std::vector<hz_solver*> S;
+  std::vector<cudaStream_t> saved;
+  hz_status status = HZ_OK;
+  GroupScope(hz_solver* const* members, int count) {
+    if (!members || count < 1 || count > kMaxGroup) {
+      status = HZ_INVALID_ARG;
+      return;
+    }
+    for (int g = 0; g < count; ++g) {
+      hz_solver* s = members[g];
+      if (!s) {
+        status = HZ_INVALID_ARG;
+        return;
+      }
+      for (hz_solver* t : S)
+        if (t == s) status = HZ_INVALID_ARG;
+      if (g > 0 && (s->mixed != S[0]->mixed || s->basis16 != S[0]->basis16 ||
+                    (s->d.zkind == HZ_Z_NONE) != (S[0]->d.zkind == HZ_Z_NONE))) {
+        set_err(S[0], "group members differ in precision, inner-basis storage or "
+                      "deflation");
+        status = HZ_INVALID_ARG;
+      }
+      S.push_back(s);
+    }
+    if (status != HZ_OK) return;
+    for (hz_solver* s : S) {
+      saved.push_back(s->st);
+      s->st = S[0]->st;
+    }
+  }
+  ~GroupScope() {
+    for (size_t g = 0; g < saved.size(); ++g) S[g]->st = saved[g];
+  }
+};
 
 template <class T>
 hz_status apply_op(hz_solver* s, hz_op op, int level, const double2* x, double2* y,
@@ -926,10 +1357,13 @@ hz_status apply_op(hz_solver* s, hz_op op, int level, const double2* x, double2*
       hz_status e = coarse_solve<T>(s, tin, yout, nrhs, nullptr);
       if (e != HZ_OK) return e;
       conv_out(s->lv[1].n);
-      return cuda_check(s, "apply coarse solve");
+      e = cuda_check(s, "apply coarse solve");
+      return e == HZ_OK ? take_fault(s) : e;
     }
-    case HZ_OP_PRECOND:
-      return precond<T>(s, vref<double>(x), vref<double>(y), nrhs, nullptr);
+    case HZ_OP_PRECOND: {
+      const hz_status e = precond<T>(s, vref<double>(x), vref<double>(y), nrhs, nullptr);
+      return e == HZ_OK ? take_fault(s) : e;
+    }
     default:
       break;
   }
@@ -984,6 +1418,7 @@ hz_status hz_setup(const hz_desc* d, const double* k2_dev, void* ws, size_t ws_b
   if (((uintptr_t)ws) & 255) return HZ_INVALID_ARG;
   hz_solver* s = new hz_solver();
   s->d = *d;
+  hz_tuning_default(&s->tune);
   s->st = (cudaStream_t)stream;
   if (const char* ce = std::getenv("HZ_CHECK_EVERY")) {
     const int v = std::atoi(ce);
@@ -1017,6 +1452,8 @@ hz_status hz_setup(const hz_desc* d, const double* k2_dev, void* ws, size_t ws_b
                 s->lv[l].dinv_f, st);
   }
   cudaMemsetAsync(s->gj_err, 0, sizeof(int), st);
+  cudaMemsetAsync(s->fault, 0, sizeof(int), st);
+  if (s->Sglk) extract_galerkin_stencil(s);
   launch_dense_assemble(dev64(s, s->L), s->d.bc, sh, s->aug, st);
   launch_gauss_jordan(s->nL, s->aug, s->gj_err, st);
   launch_extract_inverse(dev64(s, s->L), s->d.bc, s->aug,
@@ -1129,6 +1566,105 @@ hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev, int nshot
   return e != HZ_OK ? e : worst;
 }
 
+hz_status hz_solve_group(hz_solver* const* members, int count, const void* const* b_dev,
+                         void* const* x_dev, const int* nrhs, double tol,
+                         hz_solve_info* const* info) {
+  GroupScope G(members, count);
+  if (G.status != HZ_OK) return G.status;
+  if (!b_dev || !x_dev || !nrhs || !(tol > 0)) return HZ_INVALID_ARG;
+  std::vector<Member> M;
+  std::vector<const double2*> b;
+  std::vector<double2*> x;
+  for (int g = 0; g < count; ++g) {
+    if (!b_dev[g] || !x_dev[g] || nrhs[g] < 1 || nrhs[g] > G.S[g]->d.nrhs_max)
+      return HZ_INVALID_ARG;
+    M.push_back({G.S[g], nrhs[g]});
+    b.push_back((const double2*)b_dev[g]);
+    x.push_back((double2*)x_dev[g]);
+  }
+  return solve_group_dev(M, b.data(), x.data(), tol, info, G.S[0]->st);
+}
+
+hz_status hz_gradient_group(hz_solver* const* members, int count, const double* omega,
+                            const void* const* src_dev, const int* nshots,
+                            const int* const* rec_idx_dev, const int* nrec,
+                            const void* const* d_obs_dev, double tol, double* J_host,
+                            double* const* grad_dev, hz_solve_info* const* info) {
+  GroupScope G(members, count);
+  if (G.status != HZ_OK) return G.status;
+  if (!omega || !src_dev || !nshots || !rec_idx_dev || !nrec || !d_obs_dev || !J_host ||
+      !grad_dev || !(tol > 0))
+    return HZ_INVALID_ARG;
+  for (int g = 0; g < count; ++g)
+    if (!(omega[g] > 0) || !src_dev[g] || nshots[g] < 1 || !rec_idx_dev[g] || nrec[g] < 1 ||
+        !d_obs_dev[g] || !grad_dev[g])
+      return HZ_INVALID_ARG;
+  cudaStream_t st = G.S[0]->st;
+  for (int g = 0; g < count; ++g) {
+    cudaMemsetAsync(grad_dev[g], 0, sizeof(double) * G.S[g]->lv[0].n, st);
+    cudaMemsetAsync(G.S[g]->Jd, 0, sizeof(double), st);
+  }
+  hz_status worst = HZ_OK;
+  std::vector<std::vector<hz_solve_info>> inf(count);
+  for (int k = 0;; ++k) {
+    // batch k: shots k*B .. of every member that has any left
+    std::vector<Member> M;
+    std::vector<int> gi, s0;
+    std::vector<const double2*> b;
+    std::vector<double2*> x;
+    std::vector<hz_solve_info*> ip;
+    for (int g = 0; g < count; ++g) {
+      hz_solver* s = G.S[g];
+      const int B = s->d.nrhs_max, first = k * B;
+      if (first >= nshots[g]) continue;
+      const int nb = nshots[g] - first < B ? nshots[g] - first : B;
+      M.push_back({s, nb});
+      gi.push_back(g);
+      s0.push_back(first);
+      inf[g].resize(B);
+    }
+    if (M.empty()) break;
+    for (size_t a = 0; a < M.size(); ++a) {
+      hz_solver* s = M[a].s;
+      b.push_back((const double2*)src_dev[gi[a]] + (long long)s0[a] * s->lv[0].n);
+      x.push_back(s->io2);
+      ip.push_back(inf[gi[a]].data());
+    }
+    hz_status e = solve_group_dev(M, b.data(), x.data(), tol, ip.data(), st);
+    if (e != HZ_OK && e != HZ_NOT_CONVERGED && e != HZ_BREAKDOWN) return e;
+    if (worst == HZ_OK) worst = e;
+    for (size_t a = 0; a < M.size(); ++a) {
+      hz_solver* s = M[a].s;
+      const int g = gi[a];
+      if (info && info[g])
+        for (int r = 0; r < M[a].nrhs; ++r) info[g][2 * (s0[a] + r)] = inf[g][r];
+      const long long n0 = s->lv[0].n;
+      cudaMemsetAsync(s->io0, 0, sizeof(double2) * n0 * M[a].nrhs, st);
+      launch_adjoint_source(s->lv[0].nx, s->lv[0].ny, s->d.bc, s->io2, rec_idx_dev[g],
+                            nrec[g], (const double2*)d_obs_dev[g] + (long long)s0[a] * nrec[g],
+                            s->io0, s->Jd, M[a].nrhs, st);
+      b[a] = s->io0;
+      x[a] = s->io1;
+    }
+    e = solve_group_dev(M, b.data(), x.data(), tol, ip.data(), st);
+    if (e != HZ_OK && e != HZ_NOT_CONVERGED && e != HZ_BREAKDOWN) return e;
+    if (worst == HZ_OK) worst = e;
+    for (size_t a = 0; a < M.size(); ++a) {
+      hz_solver* s = M[a].s;
+      const int g = gi[a];
+      if (info && info[g])
+        for (int r = 0; r < M[a].nrhs; ++r) info[g][2 * (s0[a] + r) + 1] = inf[g][r];
+      launch_image(dev64(s, 0), s->d.bc, omega[g], s->io2, s->io1, grad_dev[g], M[a].nrhs,
+                   st);
+    }
+  }
+  for (int g = 0; g < count; ++g)
+    cudaMemcpyAsync(&J_host[g], G.S[g]->Jd, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return cuda_check(G.S[0], "gradient group");
+  const hz_status e = cuda_check(G.S[0], "gradient group");
+  return e != HZ_OK ? e : worst;
+}
+
 hz_status hz_profile_begin(hz_solver* s, hz_kernel_class kc, int max_launches) {
   if (!s || kc < HZ_KC_NONE || kc > HZ_KC_MAXPY || max_launches < 0)
     return HZ_INVALID_ARG;
@@ -1193,6 +1729,92 @@ const char* hz_status_str(hz_status st) {
 }
 
 const char* hz_last_error(const hz_solver* s) { return s ? s->err.c_str() : ""; }
+
+void hz_tuning_default(hz_tuning* t) {
+  if (!t) return;
+  std::memset(t, 0, sizeof(*t));
+  t->mdot_kernel = 0;
+  t->maxpy_kernel = 0;
+  t->galerkin_apply = 0;
+  t->e_rhs_per_block = 0;
+  t->vcycle_fused = 0;
+}
+
+hz_status hz_get_tuning(const hz_solver* s, hz_tuning* t) {
+  if (!s || !t) return HZ_INVALID_ARG;
+  *t = s->tune;
+  return HZ_OK;
+}
+
+hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
+  if (!s || !t || t->mdot_kernel < 0 || t->mdot_kernel > 2 || t->maxpy_kernel < 0 ||
+      t->maxpy_kernel > 2 || t->galerkin_apply < 0 || t->galerkin_apply > 1 ||
+      t->e_rhs_per_block < 0 || t->e_rhs_per_block > kMaxRhs || t->vcycle_fused < 0 ||
+      t->vcycle_fused > 1)
+    return HZ_INVALID_ARG;
+  if (t->galerkin_apply == 1 && !s->Sglk) {
+    set_err(s, "galerkin_apply = 1 needs the Galerkin coarse operator (HZ_E_GALERKIN)");
+    return HZ_INVALID_ARG;
+  }
+  // captured graphs hold the launches of the previous choice
+  if (!s->graphs.empty()) {
+    cudaStreamSynchronize(s->st);
+    for (hz_solver::OuterGraph& g : s->graphs) {
+      cudaGraphExecDestroy(g.ex);
+      cudaGraphDestroy(g.g);
+    }
+    s->graphs.clear();
+  }
+  s->tune = *t;
+  s->kin.dotk = s->kout.dotk = t->mdot_kernel;
+  s->kin.updk = s->kout.updk = t->maxpy_kernel;
+  return HZ_OK;
+}
+
+hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
+  if (!s || nrhs < 1 || nrhs > s->d.nrhs_max) return HZ_INVALID_ARG;
+  const int saved_prof = s->prof_kc;
+  s->prof_kc = HZ_KC_NONE;
+  hz_tuning t = s->tune;
+  double tm[HZ_TUNE_CANDIDATES];
+  for (double& v : tm) v = -1.0;
+  for (int upd = 0; upd <= 1; ++upd) {
+    int pick = 0;
+    for (int v = 0; v <= 2; ++v) {
+      tm[3 * upd + v] = time_cgs_any(s, nrhs, upd != 0, v);
+      if (tm[3 * upd + v] < tm[3 * upd + pick]) pick = v;
+    }
+    (upd ? t.maxpy_kernel : t.mdot_kernel) = pick;
+  }
+  if (s->Sglk) {
+    const int rpb[3] = {0, 8, 4};
+    int pick = 0;
+    for (int k = 0; k < 3; ++k) {
+      tm[8 + k] = s->mixed ? time_e<float>(s, nrhs, 1, rpb[k])
+                           : time_e<double>(s, nrhs, 1, rpb[k]);
+      if (tm[8 + k] < tm[8 + pick]) pick = k;
+    }
+    t.e_rhs_per_block = rpb[pick];
+    tm[6] = s->mixed ? time_e<float>(s, nrhs, 0, 0) : time_e<double>(s, nrhs, 0, 0);
+    tm[7] = tm[8 + pick];
+    t.galerkin_apply = tm[7] < tm[6] ? 1 : 0;
+  }
+  if (s->L >= 1) {
+    for (int f = 0; f <= 1; ++f)
+      tm[11 + f] = s->mixed ? time_vcycle<float>(s, nrhs, f) : time_vcycle<double>(s, nrhs, f);
+    t.vcycle_fused = tm[12] < tm[11] ? 1 : 0;
+  }
+  s->prof_kc = saved_prof;
+  hz_status e = take_fault(s);
+  if (e == HZ_OK) e = cuda_check(s, "autotune");
+  if (e != HZ_OK) return e;
+  e = hz_set_tuning(s, &t);
+  if (e != HZ_OK) return e;
+  if (best) *best = t;
+  if (ms)
+    for (int k = 0; k < HZ_TUNE_CANDIDATES; ++k) ms[k] = tm[k];
+  return HZ_OK;
+}
 
 long long hz_kernel_launches(void) {
   long long n = hz::launch_counter().load();

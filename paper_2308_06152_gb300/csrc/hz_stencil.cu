@@ -401,6 +401,105 @@ template <> __device__ __forceinline__ double2 widen<float>(float2 v) {
   return make_double2(v.x, v.y);
 }
 
+// ---------------------------------------------------------------------------
+// stcl-op-Glk (Sec. 5.2.1, Table 1): the Galerkin operator E = R_Z A_h Z
+// stored as one (2R+1) x (2R+1) stencil per coarse node (R = 2 for the
+// higher-order Z, 1 for bilinear Z) and applied as a stencil.  The
+// coefficients are extracted at setup by applying the on-the-fly product to
+// P^2 probe vectors (P = 2R+1), probe c = (cx, cy) holding 1 on the coarse
+// nodes J with J mod P = c: since E couples nodes at most R apart, (E p_c)(I)
+// is the single coefficient E(I, J) of the J of probe c within R of I.
+
+// out[b] = probe c0 + b (FP64), b < nprobe
+__global__ void k_probe_fill(LevelDev Lc, int P, int c0, double2* __restrict__ out) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+  const int b = blockIdx.z;
+  if (I >= Lc.nx || J >= Lc.ny) return;
+  const int c = c0 + b, cx = c % P, cy = c / P;
+  const long long nc = (long long)Lc.nx * Lc.ny;
+  out[b * nc + (long long)J * Lc.nx + I] =
+      make_double2((I % P == cx && J % P == cy) ? 1.0 : 0.0, 0.0);
+}
+
+// S[k][I] = (E p_c)(I) for the stencil slot k of the offset from I to the
+// probe node of c; S holds (2R+1)^2 coefficient planes of nc values
+template <class T>
+__global__ void k_probe_extract(LevelDev Lc, int P, int c0,
+                                const double2* __restrict__ ep, C<T>* __restrict__ S) {
+  const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
+  const int b = blockIdx.z;
+  if (I >= Lc.nx || J >= Lc.ny) return;
+  const int R = P / 2, c = c0 + b, cx = c % P, cy = c / P;
+  int dx = ((cx - I) % P + P) % P, dy = ((cy - J) % P + P) % P;
+  if (dx > R) dx -= P;
+  if (dy > R) dy -= P;
+  const long long nc = (long long)Lc.nx * Lc.ny, id = (long long)J * Lc.nx + I;
+  S[(long long)((dy + R) * P + (dx + R)) * nc + id] = cvt<T>(ep[b * nc + id]);
+}
+
+// y = E x with the stored stencil; one thread per coarse node keeps its
+// coefficients in registers while the block walks over its right-hand sides
+// (blockIdx.z selects a group of rpb of them), each x tile with its halo
+// staged in shared memory; the next right-hand side's tile is loaded into
+// registers while the current one is applied.
+template <class T, int R>
+__global__ void __launch_bounds__(BX * BY)
+k_stencil_e(LevelDev Lc, const C<T>* __restrict__ S, const C<T>* __restrict__ x,
+            C<T>* __restrict__ y, int nrhs, int rpb, const int* __restrict__ done) {
+  constexpr int P = 2 * R + 1, K = P * P, TX = BX + 2 * R, TY = BY + 2 * R;
+  constexpr int NT = BX * BY, NPT = (TY * TX + NT - 1) / NT;
+  __shared__ C<T> xs[TY * TX];
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+  const int I = I0 + tx, J = J0 + ty;
+  const int ncx = Lc.nx, ncy = Lc.ny;
+  const long long nc = (long long)ncx * ncy;
+  const bool in = I < ncx && J < ncy;
+  const long long id = (long long)J * ncx + I;
+  const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  C<T> cf[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) cf[k] = in ? S[(long long)k * nc + id] : czero<T>();
+  // tile values of right-hand side r held by this thread
+  auto fetch = [&](int r, C<T>* v) {
+    const C<T>* xr = x + r * nc;
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+      const int q = tid + u * NT;
+      const int gi = I0 - R + q % TX, gj = J0 - R + q / TX;
+      v[u] = (q < TY * TX && gi >= 0 && gi < ncx && gj >= 0 && gj < ncy)
+                 ? xr[(long long)gj * ncx + gi]
+                 : czero<T>();
+    }
+  };
+  auto next_active = [&](int r) {
+    while (r < r1 && done && done[r]) ++r;
+    return r;
+  };
+  C<T> pv[NPT];
+  int r = next_active(r0);
+  if (r < r1) fetch(r, pv);
+  while (r < r1) {
+#pragma unroll
+    for (int u = 0; u < NPT; ++u)
+      if (tid + u * NT < TY * TX) xs[tid + u * NT] = pv[u];
+    __syncthreads();
+    const int rn = next_active(r + 1);
+    if (rn < r1) fetch(rn, pv);
+    if (in) {
+      C<T> acc = czero<T>();
+#pragma unroll
+      for (int b = 0; b < P; ++b)
+#pragma unroll
+        for (int a = 0; a < P; ++a) acc = cfma(cf[b * P + a], xs[(ty + b) * TX + tx + a], acc);
+      y[r * nc + id] = acc;
+    }
+    __syncthreads();
+    r = rn;
+  }
+}
+
+
 template <class Ti, class To>
 __global__ void k_add_conv(VRef<Ti> a, const C<Ti>* __restrict__ b, VRef<To> out,
                            long long n, const int* __restrict__ done) {
@@ -609,6 +708,29 @@ void launch_galerkin_fused(const LevelDev& Lf, const LevelDev& Lc, int bc, int z
   else
     k_galerkin_fused<T, TC, ZK_BILINEAR><<<grid, TC * TC, 0, st>>>(Lf, Lc, bc, x, y, done);
 }
+void launch_probe_fill(const LevelDev& Lc, int P, int c0, int nprobe, double2* out,
+                       cudaStream_t st) {
+  HZ_COUNT();
+  k_probe_fill<<<grid2d(Lc.nx, Lc.ny, nprobe), dim3(BX, BY), 0, st>>>(Lc, P, c0, out);
+}
+template <class T>
+void launch_probe_extract(const LevelDev& Lc, int P, int c0, int nprobe,
+                          const double2* ep, C<T>* S, cudaStream_t st) {
+  HZ_COUNT();
+  k_probe_extract<T><<<grid2d(Lc.nx, Lc.ny, nprobe), dim3(BX, BY), 0, st>>>(Lc, P, c0, ep,
+                                                                          S);
+}
+template <class T>
+void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C<T>* y,
+                      int nrhs, int rpb, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  if (rpb <= 0 || rpb > nrhs) rpb = nrhs;
+  const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  if (R == 2)
+    k_stencil_e<T, 2><<<grid, dim3(BX, BY), 0, st>>>(Lc, S, x, y, nrhs, rpb, done);
+  else
+    k_stencil_e<T, 1><<<grid, dim3(BX, BY), 0, st>>>(Lc, S, x, y, nrhs, rpb, done);
+}
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
                 int nrhs, const int* done, cudaStream_t st) {
@@ -682,6 +804,11 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                               int, const int*, cudaStream_t);                   \
   template void launch_mask_dirichlet<T>(const LevelDev&, int, C<T>*, int,      \
                                          cudaStream_t);                        \
+  template void launch_probe_extract<T>(const LevelDev&, int, int, int,         \
+                                        const double2*, C<T>*, cudaStream_t);   \
+  template void launch_stencil_e<T>(const LevelDev&, int, const C<T>*,          \
+                                    const C<T>*, C<T>*, int, int, const int*,   \
+                                    cudaStream_t);                              \
   /* end */
 
 HZ_INST(double)

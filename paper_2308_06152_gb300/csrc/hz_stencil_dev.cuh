@@ -20,6 +20,38 @@ __device__ __forceinline__ bool on_bnd(int i, int j, int nx, int ny) {
   return i == 0 || j == 0 || i == nx - 1 || j == ny - 1;
 }
 
+// Row (i, j) of M = -Lap - (sre + i sim) k^2 with the boundary rules of
+// helm_point below: centre and the four neighbour weights (0 where the
+// neighbour is outside the grid or a Dirichlet boundary node).
+template <class T>
+__device__ __forceinline__ void helm_row(const LevelDev& L, int bc, T sre, T sim, int i,
+                                         int j, C<T>& cen, T& cw, T& ce, T& cs, T& cn) {
+  const int nx = L.nx, ny = L.ny;
+  const T ih2 = ih2_of<T>(L);
+  const T k2 = k2_of<T>(L)[(long long)j * nx + i];
+  cen = mkc(T(4) * ih2 - sre * k2, -sim * k2);
+  cw = -ih2;
+  ce = -ih2;
+  cs = -ih2;
+  cn = -ih2;
+  if (bc == BC_SOMMERFELD) {
+    const bool x0 = i == 0, x1 = i == nx - 1, y0 = j == 0, y1 = j == ny - 1;
+    const int ns = int(x0) + int(x1) + int(y0) + int(y1);
+    if (ns) {
+      cen.y -= T(ns) * tih_of<T>(L) * sqrt(k2);
+      if (x0) { cw = T(0); ce = T(2) * ce; }
+      if (x1) { ce = T(0); cw = T(2) * cw; }
+      if (y0) { cs = T(0); cn = T(2) * cn; }
+      if (y1) { cn = T(0); cs = T(2) * cs; }
+    }
+  } else {
+    if (i == 1) cw = T(0);
+    if (i == nx - 2) ce = T(0);
+    if (j == 1) cs = T(0);
+    if (j == ny - 2) cn = T(0);
+  }
+}
+
 // (M x)(i, j) for an unknown node (i, j): centre 4/h^2 - s k^2, Sommerfeld
 // sides add -2 i k / h each, remove the outward neighbour and double the
 // opposite one (ghost elimination); Dirichlet rows drop couplings to the

@@ -97,6 +97,124 @@ __global__ void k_smooth(LevelDev L, int bc, T sre, T sim, VRefE<SF> fin,
   st2(xo, r * n + id, cfma(dinv_of<T>(L)[id], res, ld2(xr, id)));
 }
 
+// Fused pre-smoothing, residual and restriction for one BX x BY tile of
+// coarse nodes: x = dinv .* f on the fine nodes [2I0-2, 2I0+2BX] (+1) held
+// in shared memory (the tile's own fine nodes are also written out), then
+// f - M x on [2I0-1, 2I0+2BX-1] and its full weighting.  x is computed
+// from f where it is needed instead of being read back, so the pair reads
+// f once and writes x and the coarse right-hand side once.
+template <class T, class SF, class SX, class SC>
+__global__ void __launch_bounds__(BX * BY)
+k_pre_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim, VRefE<SF> fin,
+               SX* __restrict__ x, SC* __restrict__ fc, const int* __restrict__ done) {
+  constexpr int XW = 2 * BX + 3, XH = 2 * BY + 3, RW = 2 * BX + 1, RH = 2 * BY + 1;
+  constexpr int NT = BX * BY;
+  __shared__ C<T> xs[XH * XW];
+  __shared__ C<T> rsd[RH * RW];
+  const int r = blockIdx.z;
+  if (done && done[r]) return;
+  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int nfx = Lf.nx, nfy = Lf.ny;
+  const long long nf = (long long)nfx * nfy, nc = (long long)Lc.nx * Lc.ny;
+  const SF* f = fin.get() + r * nf;
+  SX* xr = x + r * nf;
+  const C<T>* dinv = dinv_of<T>(Lf);
+  for (int q = tid; q < XH * XW; q += NT) {
+    const int gi = 2 * I0 - 2 + q % XW, gj = 2 * J0 - 2 + q / XW;
+    C<T> v = czero<T>();
+    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+      const long long id = (long long)gj * nfx + gi;
+      if (!(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) v = cmul(dinv[id], ld2(f, id));
+      if (gi >= 2 * I0 && gi < 2 * I0 + 2 * BX && gj >= 2 * J0 && gj < 2 * J0 + 2 * BY)
+        st2(xr, id, v);
+    }
+    xs[q] = v;
+  }
+  __syncthreads();
+  for (int q = tid; q < RH * RW; q += NT) {
+    const int ri = q % RW, rj = q / RW;
+    const int gi = 2 * I0 - 1 + ri, gj = 2 * J0 - 1 + rj;
+    C<T> v = czero<T>();
+    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+      C<T> cen;
+      T cw, ce, cs, cn;
+      helm_row<T>(Lf, bc, sre, sim, gi, gj, cen, cw, ce, cs, cn);
+      const int c = (rj + 1) * XW + (ri + 1);
+      C<T> acc = cmul(cen, xs[c]);
+      if (cw != T(0)) acc = rfma(cw, xs[c - 1], acc);
+      if (ce != T(0)) acc = rfma(ce, xs[c + 1], acc);
+      if (cs != T(0)) acc = rfma(cs, xs[c - XW], acc);
+      if (cn != T(0)) acc = rfma(cn, xs[c + XW], acc);
+      v = ld2(f, (long long)gj * nfx + gi) - acc;
+    }
+    rsd[q] = v;
+  }
+  __syncthreads();
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  if (I >= Lc.nx || J >= Lc.ny) return;
+  C<T> acc = czero<T>();
+  if (!(bc == BC_DIRICHLET && on_bnd(I, J, Lc.nx, Lc.ny))) {
+    for (int b = -1; b <= 1; ++b)
+      for (int a = -1; a <= 1; ++a) {
+        const T w = T((2 - abs(a)) * (2 - abs(b))) * T(0.0625);
+        acc = rfma(w, rsd[(2 * threadIdx.y + 1 + b) * RW + 2 * threadIdx.x + 1 + a], acc);
+      }
+  }
+  st2(fc, r * nc + (long long)J * Lc.nx + I, acc);
+}
+
+// Fused coarse-grid correction and post-smoothing for one BX x BY tile of
+// fine nodes: x' = x + P xc on the tile and its 1-node halo in shared
+// memory, then xo = x' + dinv .* (f - M x').  x' is never stored.
+template <class T, class SC, class SX, class SF, class SO>
+__global__ void __launch_bounds__(BX * BY)
+k_prolong_smooth(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
+                 const SC* __restrict__ xc, const SX* __restrict__ x, VRefE<SF> fin,
+                 SO* __restrict__ xo, const int* __restrict__ done) {
+  constexpr int PW = BX + 2, PH = BY + 2, NT = BX * BY;
+  __shared__ C<T> xp[PH * PW];
+  const int r = blockIdx.z;
+  if (done && done[r]) return;
+  const int i0 = blockIdx.x * BX, j0 = blockIdx.y * BY;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int nfx = Lf.nx, nfy = Lf.ny;
+  const long long nf = (long long)nfx * nfy, nc = (long long)Lc.nx * Lc.ny;
+  const SX* xr = x + r * nf;
+  const SC* xcr = xc + r * nc;
+  for (int q = tid; q < PH * PW; q += NT) {
+    const int gi = i0 - 1 + q % PW, gj = j0 - 1 + q / PW;
+    C<T> v = czero<T>();
+    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+      const long long id = (long long)gj * nfx + gi;
+      v = ld2(xr, id);
+      if (!(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy)))
+        v = v + interp_bilinear<T, SC>(Lc, xcr, gi, gj);
+    }
+    xp[q] = v;
+  }
+  __syncthreads();
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  if (i >= nfx || j >= nfy) return;
+  const long long id = (long long)j * nfx + i;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, nfx, nfy)) {
+    st2(xo, r * nf + id, czero<T>());
+    return;
+  }
+  C<T> cen;
+  T cw, ce, cs, cn;
+  helm_row<T>(Lf, bc, sre, sim, i, j, cen, cw, ce, cs, cn);
+  const int c = (threadIdx.y + 1) * PW + (threadIdx.x + 1);
+  C<T> acc = cmul(cen, xp[c]);
+  if (cw != T(0)) acc = rfma(cw, xp[c - 1], acc);
+  if (ce != T(0)) acc = rfma(ce, xp[c + 1], acc);
+  if (cs != T(0)) acc = rfma(cs, xp[c - PW], acc);
+  if (cn != T(0)) acc = rfma(cn, xp[c + PW], acc);
+  const C<T> res = ld2(fin.get(), r * nf + id) - acc;
+  st2(xo, r * nf + id, cfma(dinv_of<T>(Lf)[id], res, xp[c]));
+}
+
 // x = Minv f on the coarsest level (dense inverse built at setup)
 template <class T, class SF, class SO>
 __global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRefE<SF> fin,
@@ -146,6 +264,22 @@ void launch_smooth(const LevelDev& L, int bc, Shift s, VRefE<SF> f, const SX* x,
   HZ_COUNT();
   k_smooth<T, SF, SX, SO><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(
       L, bc, (T)s.re, (T)s.im, f, x, xo, done);
+}
+template <class T, class SF, class SX, class SC>
+void launch_pre_restrict(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
+                         VRefE<SF> f, SX* x, SC* fc, int nrhs, const int* done,
+                         cudaStream_t st) {
+  HZ_COUNT();
+  k_pre_restrict<T, SF, SX, SC><<<grid2d(Lc.nx, Lc.ny, nrhs), dim3(BX, BY), 0, st>>>(
+      Lf, Lc, bc, (T)s.re, (T)s.im, f, x, fc, done);
+}
+template <class T, class SC, class SX, class SF, class SO>
+void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
+                           const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
+                           const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_prolong_smooth<T, SC, SX, SF, SO><<<grid2d(Lf.nx, Lf.ny, nrhs), dim3(BX, BY), 0, st>>>(
+      Lf, Lc, bc, (T)s.re, (T)s.im, xc, x, f, xo, done);
 }
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
@@ -204,5 +338,17 @@ template void launch_smooth<float, bf2, bf2, bf2>(const LevelDev&, int, Shift,
                                                   const int*, cudaStream_t);
 template void launch_dense_mv<float, bf2, bf2>(int, const float2*, VRefE<bf2>, bf2*, int,
                                                const int*, cudaStream_t);
+
+#define HZ_VC_FUSED(T, SF, SX, SC, SO)                                          \
+  template void launch_pre_restrict<T, SF, SX, SC>(                             \
+      const LevelDev&, const LevelDev&, int, Shift, VRefE<SF>, SX*, SC*, int,   \
+      const int*, cudaStream_t);                                                \
+  template void launch_prolong_smooth<T, SC, SX, SF, SO>(                       \
+      const LevelDev&, const LevelDev&, int, Shift, const SC*, const SX*,       \
+      VRefE<SF>, SO*, int, const int*, cudaStream_t);
+HZ_VC_FUSED(double, double2, double2, double2, double2)
+HZ_VC_FUSED(float, float2, float2, float2, float2)
+HZ_VC_FUSED(float, float2, bf2, bf2, float2)
+HZ_VC_FUSED(float, bf2, bf2, bf2, bf2)
 
 }  // namespace hz

@@ -44,19 +44,20 @@ def test_library_exports_every_declared_symbol(lib):
     assert set(declared_functions()) <= set(_lib.SIGNATURES)
 
 
+STRUCTS = [(_lib.HzDesc, "hz_desc"), (_lib.HzSolveInfo, "hz_solve_info"),
+           (_lib.HzTuning, "hz_tuning")]
+
+
 def test_struct_layout_matches_header(tmp_path):
     if shutil.which("gcc") is None:
         pytest.skip("no gcc")
     src = tmp_path / "layout.c"
-    fields = [f[0] for f in _lib.HzDesc._fields_]
-    ifields = [f[0] for f in _lib.HzSolveInfo._fields_]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hz.h"',
-             "int main(void){",
-             'printf("%zu\\n", sizeof(hz_desc));',
-             'printf("%zu\\n", sizeof(hz_solve_info));']
-    lines += [f'printf("%zu\\n", offsetof(hz_desc, {f}));' for f in fields]
-    lines += [f'printf("%zu\\n", offsetof(hz_solve_info, {f}));'
-              for f in ifields]
+             "int main(void){"]
+    for cls, cname in STRUCTS:
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        lines += [f'printf("%zu\\n", offsetof({cname}, {f}));'
+                  for f, _ in cls._fields_]
     lines += ["return 0;}"]
     src.write_text("\n".join(lines))
     exe = tmp_path / "layout"
@@ -64,15 +65,13 @@ def test_struct_layout_matches_header(tmp_path):
                     str(exe)], check=True)
     out = [int(v) for v in subprocess.run([str(exe)], capture_output=True,
                                           text=True).stdout.split()]
-    assert out[0] == ctypes.sizeof(_lib.HzDesc)
-    assert out[1] == ctypes.sizeof(_lib.HzSolveInfo)
-    k = 2
-    for f in fields:
-        assert out[k] == getattr(_lib.HzDesc, f).offset, f
+    k = 0
+    for cls, cname in STRUCTS:
+        assert out[k] == ctypes.sizeof(cls), cname
         k += 1
-    for f in ifields:
-        assert out[k] == getattr(_lib.HzSolveInfo, f).offset, f
-        k += 1
+        for f, _ in cls._fields_:
+            assert out[k] == getattr(cls, f).offset, (cname, f)
+            k += 1
 
 
 def _ws(lib, **kw):

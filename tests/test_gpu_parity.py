@@ -103,6 +103,36 @@ def test_deflation_operators(bc, z, e):
 
 
 @pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("z", ["bilinear", "ho"])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("mixed", 2e-6)])
+def test_stored_galerkin_stencil(bc, z, prec, tol):
+    """stcl-op-Glk: the Galerkin product's per-node stencil, extracted at
+    setup by FP64 probing, applied to several right-hand sides against the
+    oracle's explicit R_Z A Z (FP64 to 1e-12; FP32-stored coefficients and
+    FP32 arithmetic to 2e-6, below the on-the-fly FP32 product's error)."""
+    k2 = rk2(NY, NX, 2)
+    s = solver(NX, NY, H, k2, bc, z=z, e="galerkin", prec=prec, nrhs=3)
+    orc = Oracle(NX, NY, H, k2, bc, z=z, e="galerkin", coarsest="direct")
+    lc = orc.levels[1]
+    xc = wl.random_complex((3, lc.ny, lc.nx), 15)
+    for rpb in (0, 2, 1):
+        s.set_tuning(galerkin_apply=1, e_rhs_per_block=rpb)
+        y = to_np(s.apply("coarse_e", xc))
+        for r in range(3):
+            assert rel(y[r], oapply(orc, orc.E, 1, 1, xc[r])) < tol, (rpb, r)
+    s.set_tuning(galerkin_apply=0)
+    y0 = to_np(s.apply("coarse_e", xc))
+    assert rel(y0[0], oapply(orc, orc.E, 1, 1, xc[0])) < max(tol, 2e-5)
+
+
+def test_stored_galerkin_stencil_rejected_without_galerkin_e():
+    from paper_2308_06152_gb300.api import HzError
+    s = solver(NX, NY, H, rk2(NY, NX, 2), "sommerfeld", z="ho", e="red_glk2")
+    with pytest.raises(HzError):
+        s.set_tuning(galerkin_apply=1)
+
+
+@pytest.mark.parametrize("bc", BCS)
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 5e-5)])
 def test_vcycle(bc, prec, tol):
     k2 = rk2(NY, NX, 6)
@@ -114,6 +144,31 @@ def test_vcycle(bc, prec, tol):
         y = to_np(s.apply("vcycle", f, l))[0]
         ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[0]), l))
         assert rel(y, ref) < tol, (l, rel(y, ref))
+
+
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 5e-5),
+                                      ("mixed_bf16", 2e-2)])
+def test_fused_vcycle_matches_oracle(bc, prec, tol):
+    """The fused smoothing/transfer kernels (vcycle_fused = 1) give the same
+    V-cycle as the oracle from levels 0, 1 and L, and as the unfused
+    kernels to rounding."""
+    k2 = rk2(NY, NX, 6)
+    s = solver(NX, NY, H, k2, bc, z="ho", prec=prec, nrhs=2)
+    orc = Oracle(NX, NY, H, k2, bc, z="ho", coarsest="direct")
+    for l in (0, 1, orc.L):
+        lv = orc.levels[l]
+        f = wl.random_complex((2, lv.ny, lv.nx), 30 + l)
+        s.set_tuning(vcycle_fused=0)
+        y0 = to_np(s.apply("vcycle", f, l))
+        s.set_tuning(vcycle_fused=1)
+        y1 = to_np(s.apply("vcycle", f, l))
+        for r in range(2):
+            ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[r]), l))
+            assert rel(y1[r], ref) < tol, (l, r, rel(y1[r], ref))
+            # unfused BF16 storage rounds x + P xc once more
+            bound = {"fp64": 1e-13, "mixed": 1e-6, "mixed_bf16": 2e-2}[prec]
+            assert rel(y1[r], y0[r]) < bound
 
 
 @pytest.mark.parametrize("bc", BCS)
@@ -227,6 +282,24 @@ def test_solve_parity_tight(bc, z, e):
     assert abs(info[0].outer_iters - io.outer_iters) <= 1
 
 
+def test_solve_with_stored_galerkin_stencil_matches_oracle():
+    """The whole solve with stcl-op-Glk: same operator as str-Glk, so the
+    tight solution matches the oracle's to 1e-8 and the outer count +-1."""
+    n, k = 65, 30
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), float(k) ** 2)
+    b = wl.point_sources(n, n, [wl.centre_node(n, n)])
+    s = solver(n, n, h, k2, "sommerfeld", z="ho", e="galerkin",
+               coarse_tol=1e-11, coarse_maxit=1500, outer_maxit=200)
+    s.set_tuning(galerkin_apply=1)
+    x, info = s.solve(b, tol=1e-11)
+    orc = Oracle(n, n, h, k2, "sommerfeld", z="ho", e="galerkin",
+                 coarse_tol=1e-11, coarse_maxit=1500)
+    xo, io = orc.solve(b[0], tol=1e-11)
+    assert rel(to_np(x)[0], xo) < 1e-8
+    assert abs(info[0].outer_iters - io.outer_iters) <= 1
+
+
 def test_mixed_precision_reaches_fp64_residual():
     n, k = 129, 80
     orc, b, x, info = _solve_pair(n, k, "sommerfeld", "ho", "galerkin", 1e-6,
@@ -297,6 +370,138 @@ def test_cuda_graph_loop_equals_host_issued_loop(bc, prec, basis16):
         # per coarse solve; the graph adds two small loop-control kernels
         assert 0.7 * ne < ng < 1.3 * ne, (ng, ne)
     assert rel(out[True][0][0], out[True][1][0]) == 0.0
+
+
+@pytest.mark.parametrize("prec,basis16", [("fp64", False), ("mixed", True)])
+def test_gram_schmidt_kernel_variants_agree(prec, basis16):
+    """The register-pipelined and the two TMA-ring Gram-Schmidt kernels sum
+    in different orders only: the same iteration counts (+-1) and solutions
+    within rounding of each other (FP64 1e-9; mixed 1e-5, the FP32
+    preconditioner's reach)."""
+    k2 = rk2(NY, NX, 6, lo=10.0, hi=40.0)
+    b = wl.random_complex((3, NY, NX), 78)
+    res = {}
+    for v in (0, 1, 2):
+        s = solver(NX, NY, H, k2, "sommerfeld", prec=prec, nrhs=3,
+                   coarse_tol=1e-3, coarse_maxit=200, inner_basis_fp16=basis16)
+        s.set_tuning(mdot_kernel=v, maxpy_kernel=(v + 1) % 3)
+        t = s.get_tuning()
+        assert t["mdot_kernel"] == v and t["maxpy_kernel"] == (v + 1) % 3
+        x, infos = s.solve(b, tol=1e-9)
+        s.close()
+        res[v] = (to_np(x), infos)
+    tol = 1e-9 if prec == "fp64" else 1e-5
+    x0, i0 = res[0]
+    for v in (1, 2):
+        xv, iv = res[v]
+        for r in range(3):
+            assert iv[r].status == "HZ_OK"
+            assert abs(iv[r].outer_iters - i0[r].outer_iters) <= 1
+            assert rel(xv[r], x0[r]) < tol, (v, r)
+
+
+def test_autotune_picks_valid_choices_and_caches(tmp_path):
+    """hz_autotune times every candidate, keeps the fastest of each, and a
+    solve with the tuned choices still matches the default choices'; the
+    JSON cache returns the same choice without timing."""
+    k2 = rk2(NY, NX, 7, lo=10.0, hi=40.0)
+    b = wl.random_complex((2, NY, NX), 79)
+    s = solver(NX, NY, H, k2, "sommerfeld", prec="mixed", nrhs=2,
+               coarse_tol=1e-3, coarse_maxit=100)
+    x0, i0 = s.solve(b, tol=1e-8)
+    cache = str(tmp_path / "tune.json")
+    out = s.autotune(2, cache=cache)
+    assert not out["cached"]
+    ms = out["ms"]
+    assert all(ms[c] > 0 for c in s.TUNE_CANDIDATES), ms
+    t = out["tuning"]
+    assert t == s.get_tuning()
+    for cls in ("mdot_kernel", "maxpy_kernel"):
+        assert t[cls] == min(range(3), key=lambda v: ms[f"{cls}={v}"])
+    rpb = min((0, 8, 4), key=lambda v: ms[f"e_rhs_per_block={v}"])
+    assert t["e_rhs_per_block"] == rpb
+    assert ms["galerkin_apply=1"] == ms[f"e_rhs_per_block={rpb}"]
+    ga = 1 if ms["galerkin_apply=1"] < ms["galerkin_apply=0"] else 0
+    assert t["galerkin_apply"] == ga
+    vf = 1 if ms["vcycle_fused=1"] < ms["vcycle_fused=0"] else 0
+    assert t["vcycle_fused"] == vf
+    x1, i1 = s.solve(b, tol=1e-8)
+    for r in range(2):
+        assert i1[r].status == "HZ_OK"
+        assert abs(i1[r].outer_iters - i0[r].outer_iters) <= 1
+        assert rel(to_np(x1)[r], to_np(x0)[r]) < 1e-5
+    s2 = solver(NX, NY, H, k2, "sommerfeld", prec="mixed", nrhs=2,
+                coarse_tol=1e-3, coarse_maxit=100)
+    again = s2.autotune(2, cache=cache)
+    assert again["cached"] and again["tuning"] == t
+    assert s2.get_tuning() == t
+
+
+def test_group_of_uneven_grids_equals_separate_solves():
+    """hz_solve_group on three grids of different shapes, boundary types and
+    coarse operators, with different RHS counts: each member gets the same
+    iteration counts and the same solution (the same kernels in the same
+    order per member; FP64 to 1e-13) as its own separate solve."""
+    from paper_2308_06152_gb300.api import solve_group
+    specs = [(97, 73, 1.0 / 96, "sommerfeld", "ho", "galerkin", 2, 11),
+             (65, 129, 1.0 / 64, "dirichlet", "bilinear", "galerkin", 1, 12),
+             (129, 65, 1.0 / 128, "sommerfeld", "ho", "red_glk2", 3, 13)]
+    for prec in ("fp64", "mixed"):
+        solvers, bs = [], []
+        for nx, ny, h, bc, z, e, nr, seed in specs:
+            k2 = rk2(ny, nx, seed, lo=8.0, hi=30.0)
+            solvers.append(solver(nx, ny, h, k2, bc, z=z, e=e, prec=prec,
+                                  nrhs=nr, coarse_tol=1e-3, coarse_maxit=200,
+                                  inner_basis_fp16=(prec == "mixed"),
+                                  cuda_graph=False))
+            bs.append(wl.random_complex((nr, ny, nx), seed + 100))
+        out = solve_group(solvers, bs, tol=1e-8)
+        for s, b, (xg, ig) in zip(solvers, bs, out):
+            xs, is_ = s.solve(b, tol=1e-8)
+            for r in range(b.shape[0]):
+                assert ig[r].status == "HZ_OK"
+                assert ig[r].outer_iters == is_[r].outer_iters
+                assert ig[r].inner_iters_total == is_[r].inner_iters_total
+                assert rel(to_np(xg)[r], to_np(xs)[r]) < 1e-13, (prec, r)
+    # members must agree in precision class
+    from paper_2308_06152_gb300.api import HzError
+    a = solver(33, 33, 1 / 32, rk2(33, 33, 1), "sommerfeld", prec="fp64")
+    c = solver(33, 33, 1 / 32, rk2(33, 33, 1), "sommerfeld", prec="mixed")
+    with pytest.raises(HzError):
+        solve_group([a, c], [wl.random_complex((1, 33, 33), 1)] * 2)
+
+
+def test_gradient_group_equals_separate_gradients():
+    """hz_gradient_group over two uneven grids (different shot counts,
+    batches of 2 shots) equals each member's own hz_gradient (1e-12) and the
+    oracle's sparse-LU gradient (1e-7)."""
+    from paper_2308_06152_gb300.api import gradient_group
+    cases = []
+    for (nx, ny, h, omega, nsh, seed) in ((17, 13, 1 / 16, 25.0, 3, 31),
+                                          (25, 33, 1 / 24, 30.0, 5, 32)):
+        rng = np.random.default_rng(seed)
+        m = rng.uniform(0.7, 1.3, size=(ny, nx))
+        nodes = [(1 + (3 * s) % (nx - 2), 1 + s % 3) for s in range(nsh)]
+        src = wl.point_sources(nx, ny, nodes)
+        rec = wl.surface_receivers(nx, 0)
+        d = (rng.standard_normal((nsh, nx))
+             + 1j * rng.standard_normal((nsh, nx))) * 1e-3
+        s = solver(nx, ny, h, omega ** 2 * m, "sommerfeld", z="ho", nrhs=2,
+                   coarse_tol=1e-12, coarse_maxit=400)
+        cases.append((s, omega, src, rec, d, m, nx, ny, h))
+    out = gradient_group([c[0] for c in cases], [c[1] for c in cases],
+                         [c[2] for c in cases], [c[3] for c in cases],
+                         [c[4] for c in cases], tol=1e-12)
+    for (s, omega, src, rec, d, m, nx, ny, h), (Jg, gg, ig) in zip(cases, out):
+        J1, g1, _ = s.gradient(omega, src, rec, d, tol=1e-12)
+        assert Jg == pytest.approx(J1, rel=1e-12)
+        assert rel(to_np(gg), to_np(g1)) < 1e-12
+        assert len(ig) == 2 * src.shape[0]
+        assert all(i.status == "HZ_OK" for i in ig)
+        J0, g0 = grd.misfit_and_gradient(nx, ny, h, m, omega, "sommerfeld", src,
+                                         rec, d)
+        assert Jg == pytest.approx(J0, rel=1e-8)
+        assert rel(to_np(gg), g0) < 1e-7
 
 
 def test_edge_cases():
