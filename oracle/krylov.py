@@ -7,6 +7,10 @@ FP64 (Sec. 3.3, Algorithm 1).  Test infrastructure only.
                  tolerances), otherwise the iterate is x0 + M^{-1} V y.
 ``gmres_left``   Algorithm 1: GMRES on the preconditioned operator,
                  stopping on the preconditioned relative residual.
+``gcr_flexible`` the preconditioned Generalized Conjugate Residual method
+                 with a variable right preconditioner (Sec. 3.3 names it,
+                 after Eisenstat et al.; Sec. 6.3 uses it as the outer
+                 iteration with a loose coarse tolerance).
 
 Stopping rule of ``gmres_right``: after iteration j the Givens-updated
 least-squares residual |g_{j+1}| is compared with ``tol * ||b||``.
@@ -119,3 +123,40 @@ def gmres_left(matvec, prec, b, tol, maxit, x0=None):
     V, _, y, k, res = _arnoldi_lsq(op, r0 / beta, beta, tol * beta, maxit)
     return Result(x0 + sum(y[i] * V[i] for i in range(k)), k, res,
                   res <= tol * beta)
+
+
+def gcr_flexible(matvec, b, tol, maxit, x0=None, prec=None):
+    """Flexible GCR: each step preconditions the current residual,
+    u = P(r), c = A u, makes c orthogonal to the previous A-images by
+    modified Gram-Schmidt (applying the same coefficients to u),
+    normalises both by ||c||, and takes the step that minimises the
+    residual along c: x += (c, r) u, r -= (c, r) c.  Stops when the
+    recursively updated ||r|| <= tol ||b||."""
+    x = np.zeros_like(b, dtype=np.complex128) if x0 is None else x0.astype(np.complex128)
+    r = b - matvec(x) if x0 is not None else b.astype(np.complex128).copy()
+    bn = np.linalg.norm(b)
+    if bn == 0.0:
+        return Result(np.zeros_like(x), 0, 0.0, True)
+    U, Cs = [], []
+    res = np.linalg.norm(r)
+    k = 0
+    while k < maxit and res > tol * bn:
+        u = prec(r) if prec is not None else r.copy()
+        c = matvec(u)
+        for ci, ui in zip(Cs, U):
+            beta = np.vdot(ci, c)
+            c = c - beta * ci
+            u = u - beta * ui
+        a = np.linalg.norm(c)
+        if a == 0.0:
+            break
+        c = c / a
+        u = u / a
+        gamma = np.vdot(c, r)
+        x = x + gamma * u
+        r = r - gamma * c
+        Cs.append(c)
+        U.append(u)
+        res = np.linalg.norm(r)
+        k += 1
+    return Result(x, k, res, res <= tol * bn)

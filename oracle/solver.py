@@ -14,7 +14,7 @@ import numpy as np
 import scipy.sparse.linalg as spla
 
 from . import operators as ops
-from .krylov import gmres_right, gmres_left
+from .krylov import gcr_flexible, gmres_right, gmres_left
 
 
 class SolveInfo:
@@ -139,6 +139,22 @@ class Oracle:
         self.inner_log = []
         res = gmres_right(lambda v: self.A @ v, b, tol, maxit, x0=x0,
                           prec=self.adef1, flexible=True)
+        info = SolveInfo()
+        info.outer_iters = res.iters
+        info.inner_iters = list(self.inner_log)
+        bn = np.linalg.norm(b)
+        info.relres = (np.linalg.norm(b - self.A @ res.x) / bn) if bn else 0.0
+        info.converged = res.converged
+        return lv.to_full(res.x), info
+
+    def solve_gcr(self, b_full, tol=1e-6, maxit=500):
+        """Flexible GCR on A x = b right-preconditioned by A-DEF1 (the
+        outer iteration of Sec. 6.3).  Returns the full-grid solution and a
+        SolveInfo with the true relative residual."""
+        lv = self.levels[0]
+        b = lv.to_unknowns(b_full)
+        self.inner_log = []
+        res = gcr_flexible(lambda v: self.A @ v, b, tol, maxit, prec=self.adef1)
         info = SolveInfo()
         info.outer_iters = res.iters
         info.inner_iters = list(self.inner_log)

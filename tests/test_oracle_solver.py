@@ -117,6 +117,49 @@ def test_fgmres_warm_start_and_zero_rhs():
     assert i2.outer_iters <= 1 and i2.relres < 1e-9
 
 
+@pytest.mark.parametrize("nx,ny,bc,z,e", CASES[:3])
+def test_gcr_matches_direct_solve(nx, ny, bc, z, e):
+    """Flexible GCR with A-DEF1 (Sec. 6.3's outer iteration) converges to
+    the sparse-LU solution."""
+    h = 1.0 / (max(nx, ny) - 1)
+    k2 = _k2(ny, nx, 5, lo=8, hi=20)
+    orc = Oracle(nx, ny, h, k2, bc, z=z, e=e, coarse_tol=1e-10)
+    rng = np.random.default_rng(6)
+    b = rng.standard_normal((ny, nx)) + 1j * rng.standard_normal((ny, nx))
+    x, info = orc.solve_gcr(b, tol=1e-12, maxit=200)
+    lv = orc.levels[0]
+    xd = lv.to_full(spla.spsolve(orc.A.tocsc(), lv.to_unknowns(b)))
+    assert info.converged and info.relres < 1e-11
+    assert np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_gcr_equals_gmres_for_a_fixed_preconditioner():
+    """With a fixed linear preconditioner P, GCR's directions span
+    P K_k(A P, r0) and it minimises the residual over that space, as
+    right-preconditioned GMRES does: the residual norms after k steps agree
+    for every k (a property of the two methods, not of this code)."""
+    from oracle.krylov import gcr_flexible
+    n = 33
+    orc = Oracle(n, n, 1 / 32, _k2(n, n, 9, lo=8, hi=20), ops.SOMMERFELD,
+                 z="ho", coarsest="direct")
+    lv = orc.levels[0]
+    rng = np.random.default_rng(3)
+    b = lv.to_unknowns(rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n)))
+
+    def prec(v):
+        return orc.vcycle(v, 0)
+
+    def matvec(v):
+        return orc.A @ v
+
+    for k in (1, 3, 6, 10):
+        xg = gcr_flexible(matvec, b, 0.0, k, prec=prec).x
+        xm = gmres_right(matvec, b, 0.0, k, prec=prec).x
+        rg = np.linalg.norm(b - matvec(xg))
+        rm = np.linalg.norm(b - matvec(xm))
+        assert abs(rg - rm) <= 1e-9 * np.linalg.norm(b), (k, rg, rm)
+
+
 def test_gmres_lucky_breakdown_identity():
     b = np.arange(1, 6) + 0j
     res = gmres_right(lambda v: 3.0 * v, b, 1e-14, 10)
