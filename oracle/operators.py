@@ -301,14 +301,15 @@ def ghost_values(level):
     return g
 
 
-def stencil_with_ghosts(level, rows_mask, coef_fn, radius):
+def stencil_with_ghosts(level, rows_mask, coef_fn, radius, ghosts=None):
     """Assemble rows (full-grid) for nodes in ``rows_mask`` from a stencil of
     the given radius; neighbours one layer outside the grid are replaced by
-    their ghost combination.  ``coef_fn(i, j, di, dj, k2_nb)`` gives the
-    coefficient of offset (di, dj), with k2_nb the squared wavenumber of
-    that neighbour (zero at a ghost node)."""
+    their ghost combination (``ghosts``, default ``ghost_values(level)``).
+    ``coef_fn(i, j, di, dj, k2_nb)`` gives the coefficient of offset
+    (di, dj), with k2_nb the squared wavenumber of that neighbour (zero at a
+    ghost node)."""
     nx, ny = level.nx, level.ny
-    g = ghost_values(level)
+    g = ghost_values(level) if ghosts is None else ghosts
     rows, cols, vals = [], [], []
     for j in range(ny):
         for i in range(nx):
@@ -362,4 +363,95 @@ def red_glk(coarse, variant=2):
     full_o2 = five_point_full(nx, ny, H, coarse.k2, coarse.bc, 1.0)
     keep = sp.diags(o2_rows.ravel().astype(np.float64))
     full = (keep @ full_o2 + full_glk).tocsr()
+    return _restrict_to_unknowns(full, coarse, coarse)
+
+
+def _dist_to_boundary(nx, ny):
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    return np.minimum(np.minimum(ii, nx - 1 - ii), np.minimum(jj, ny - 1 - jj))
+
+
+def red_o4(coarse):
+    """ReD-O4 (Sec. 5.2.3): coarse nodes whose 4th-order cross stays inside
+    the grid use eq. (Helmstencil Oh4): the Laplacian
+    [-1 16 -30 16 -1] / (12 H^2) along x and along y, minus k^2 of the node
+    (the printed centre writes k^2 (2h)^2 inside the 1/(12 (2h)^2) factor,
+    which would scale the wavenumber by 1/12; it is read as the plain -k^2
+    of every other stencil of the paper).  Nodes within one node of the
+    boundary, where the cross would leave the grid, use the ReD-O2 row with
+    its boundary rules, as the paper does for its boundary points."""
+    nx, ny, H = coarse.nx, coarse.ny, coarse.h
+    o2_rows = _dist_to_boundary(nx, ny) <= 1
+    s = 1.0 / (12.0 * H * H)
+    side = {1: -16.0 * s, 2: 1.0 * s}
+
+    def coef(i, j, di, dj, k2nb):
+        if di == 0 and dj == 0:
+            return 60.0 * s - k2nb
+        if di != 0 and dj != 0:
+            return 0.0
+        return side[abs(di) + abs(dj)]
+
+    full_o4 = stencil_with_ghosts(coarse, ~o2_rows, coef, 2)
+    full_o2 = five_point_full(nx, ny, H, coarse.k2, coarse.bc, 1.0)
+    keep = sp.diags(o2_rows.ravel().astype(np.float64))
+    return _restrict_to_unknowns((keep @ full_o2 + full_o4).tocsr(), coarse, coarse)
+
+
+# eq. (GeneralFormReD) with the Singer-Turkel coefficients (gamma = 1),
+# Sec. 5.2.5: [A_2h] = [a] / H^2 - [b] k^2, rows y = -1..1, columns x.
+def cmp_o4_weights(gamma=1.0):
+    a0, a_s, a_c = 10.0 / 3.0, -2.0 / 3.0, -1.0 / 6.0
+    b0 = 2.0 / 3.0 + gamma / 36.0
+    b_s = 1.0 / 12.0 - gamma / 72.0
+    b_c = gamma / 144.0
+    a = np.array([[a_c, a_s, a_c], [a_s, a0, a_s], [a_c, a_s, a_c]])
+    b = np.array([[b_c, b_s, b_c], [b_s, b0, b_s], [b_c, b_s, b_c]])
+    return a, b
+
+
+def ghost_values_cmp(level):
+    """Ghost nodes one layer outside a Sommerfeld boundary for ReD-cmpO4
+    (Sec. 5.2.5): the 4th-order rule u_ghost = 2 i k H (1 - k^2 H^2 / 6)
+    u_bnd + u_in with k of the boundary node; a corner ghost is the average
+    of its two neighbouring edge ghosts."""
+    nx, ny, H = level.nx, level.ny, level.h
+    k = np.sqrt(level.k2)
+
+    def rule(kb, b_node, in_node):
+        return {b_node: 2j * kb * H * (1.0 - kb * kb * H * H / 6.0), in_node: 1.0}
+
+    g = {}
+    for j in range(ny):
+        g[(-1, j)] = rule(k[j, 0], j * nx, j * nx + 1)
+        g[(nx, j)] = rule(k[j, nx - 1], j * nx + nx - 1, j * nx + nx - 2)
+    for i in range(nx):
+        g[(i, -1)] = rule(k[0, i], i, nx + i)
+        g[(i, ny)] = rule(k[ny - 1, i], (ny - 1) * nx + i, (ny - 2) * nx + i)
+    for gi, bi in ((-1, 0), (nx, nx - 1)):
+        for gj, bj in ((-1, 0), (ny, ny - 1)):
+            avg = {}
+            for d in (g[(bi, gj)], g[(gi, bj)]):
+                for key, c in d.items():
+                    avg[key] = avg.get(key, 0) + 0.5 * c
+            g[(gi, gj)] = avg
+    return g
+
+
+def red_cmpo4(coarse, gamma=1.0):
+    """ReD-cmpO4 (Sec. 5.2.5): the compact 3x3 fourth-order stencil of
+    eq. (GeneralFormReD), [a] / H^2 - [b] k^2, at every unknown.  Each entry
+    of the mass part takes k^2 of its own node (zero at a ghost node, as for
+    ReD-Glk); Sommerfeld boundary rows eliminate the ghost layer with
+    ghost_values_cmp; Dirichlet rows only meet boundary nodes, which hold
+    zero."""
+    a, b = cmp_o4_weights(gamma)
+    H = coarse.h
+    ih2 = 1.0 / (H * H)
+
+    def coef(i, j, di, dj, k2nb):
+        return a[dj + 1, di + 1] * ih2 - b[dj + 1, di + 1] * k2nb
+
+    ghosts = ghost_values_cmp(coarse) if coarse.bc == SOMMERFELD else {}
+    full = stencil_with_ghosts(coarse, coarse.mask, coef, 1, ghosts=ghosts)
     return _restrict_to_unknowns(full, coarse, coarse)

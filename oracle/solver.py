@@ -38,15 +38,18 @@ class Oracle:
     coarsest-level GMRES to 1e-8 (Sec. 6), coarse tolerance 1e-6 (Sec. 6.3).
 
     ``z``: None (plain CSLP), 'bilinear' (A-DEF1) or 'ho' (APD).
-    ``e``: 'galerkin' (str-Glk), 'red_o2', 'red_glk1' or 'red_glk2'.
+    ``e``: 'galerkin' (str-Glk), 'red_o2', 'red_glk1', 'red_glk2',
+    'red_o4' or 'red_cmpo4'.
     ``coarsest``: 'gmres' (paper) or 'direct' (sparse LU; used where an
     exact coarsest solve is wanted for tight comparisons).
+    ``precond``: 'adef1' (A-DEF1 / APD, eq. ADEF1) or 'tlkm' (the practical
+    TLKM preconditioner of Sec. 3.2.2 with the coarse system of Sec. 5.2).
     """
 
     def __init__(self, nx, ny, h, k2, bc, z="ho", e="galerkin",
                  beta=(1.0, -0.5), omega=0.8, min_coarse_intervals=2,
                  coarsest="gmres", coarsest_tol=1e-8, coarse_tol=1e-6,
-                 coarse_maxit=3000):
+                 coarse_maxit=3000, precond="adef1"):
         self.levels = ops.build_levels(nx, ny, h, k2, bc,
                                        min_coarse_intervals)
         self.L = len(self.levels) - 1
@@ -65,6 +68,9 @@ class Oracle:
         if coarsest == "direct":
             self._lu = spla.splu(self.M[self.L].tocsc())
         self.zkind, self.ekind = z, e
+        if precond not in ("adef1", "tlkm") or (precond == "tlkm" and z is None):
+            raise ValueError(precond)
+        self.precond = self.adef1 if precond == "adef1" else self.tlkm
         self.coarse_tol, self.coarse_maxit = coarse_tol, coarse_maxit
         self.inner_log = []
         if z is not None:
@@ -80,6 +86,10 @@ class Oracle:
                 self.E = ops.red_glk(self.levels[1], 1)
             elif e == "red_glk2":
                 self.E = ops.red_glk(self.levels[1], 2)
+            elif e == "red_o4":
+                self.E = ops.red_o4(self.levels[1])
+            elif e == "red_cmpo4":
+                self.E = ops.red_cmpo4(self.levels[1])
             else:
                 raise ValueError(e)
 
@@ -128,6 +138,28 @@ class Oracle:
         q = self.deflation_Q(v)
         return self.vcycle(v - self.A @ q, 0) + q
 
+    def coarse_solve_tlkm(self, v1, tol=None, maxit=None):
+        """The practical TLKM coarse system (Sec. 5.2, eq. TLKM CGP):
+        I_h^2h I_2h^h M_2h^-1 A_2h v2 = v1 with I_h^2h I_2h^h = R_Z Z, M_2h^-1
+        one V-cycle on the coarse CSLP from level 1 and A_2h = E, by GMRES on
+        that operator (it already carries M_2h^-1), x0 = 0."""
+        tol = self.coarse_tol if tol is None else tol
+        maxit = self.coarse_maxit if maxit is None else maxit
+        RZZ = self.RZ @ self.Z
+        res = gmres_right(lambda v: RZZ @ self.vcycle(self.E @ v, 1), v1, tol,
+                          maxit)
+        self.inner_log.append(res.iters)
+        return res.x
+
+    def tlkm(self, v, gamma=1.0):
+        """Practical TLKM preconditioner (Sec. 3.2.2):
+        P v = (I - A~ Q~ + gamma Q~) M^-1 v with A~ = M^-1 A and
+        Q~ = Z A~_2h^-1 R_Z, A~_2h replaced by the practical coarse operator
+        of coarse_solve_tlkm; gamma = 1."""
+        w = self.vcycle(v, 0)
+        q = self.Z @ self.coarse_solve_tlkm(self.RZ @ w)
+        return w - self.vcycle(self.A @ q, 0) + gamma * q
+
     # ---- outer solve (Sec. 6.3) -------------------------------------------
     def solve(self, b_full, tol=1e-6, maxit=500, x0_full=None):
         """Flexible GMRES on A x = b right-preconditioned by A-DEF1.  Returns
@@ -138,7 +170,7 @@ class Oracle:
         x0 = None if x0_full is None else lv.to_unknowns(x0_full)
         self.inner_log = []
         res = gmres_right(lambda v: self.A @ v, b, tol, maxit, x0=x0,
-                          prec=self.adef1, flexible=True)
+                          prec=self.precond, flexible=True)
         info = SolveInfo()
         info.outer_iters = res.iters
         info.inner_iters = list(self.inner_log)
@@ -154,7 +186,7 @@ class Oracle:
         lv = self.levels[0]
         b = lv.to_unknowns(b_full)
         self.inner_log = []
-        res = gcr_flexible(lambda v: self.A @ v, b, tol, maxit, prec=self.adef1)
+        res = gcr_flexible(lambda v: self.A @ v, b, tol, maxit, prec=self.precond)
         info = SolveInfo()
         info.outer_iters = res.iters
         info.inner_iters = list(self.inner_log)

@@ -291,3 +291,118 @@ def test_red_o2_is_coarse_helmholtz():
     E = ops.red_o2(lv[1])
     direct = ops.five_point_full(9, 9, 0.2, lv[1].k2, ops.SOMMERFELD)
     np.testing.assert_allclose(E.toarray(), direct.toarray())
+
+
+# ---------------------------------------------------------------- ReD-O4 / ReD-cmpO4
+def _const_level(n, k, bc):
+    H = 1.0 / (n - 1)
+    return ops.Level(n, n, H, np.full((n, n), float(k) ** 2), bc)
+
+
+def _full_row(mat, lv, i, j):
+    """Row of node (i, j) of an operator over the unknowns, as a full-grid
+    (ny, nx) array."""
+    pos = {u: p for p, u in enumerate(lv.unk)}
+    row = mat.getrow(pos[j * lv.nx + i]).toarray().ravel()
+    return lv.to_full(row)
+
+
+def test_red_o4_interior_row_is_the_printed_stencil():
+    g = load_golden("red_o4_cmpo4_stencils.txt")
+    w = g["o4_1d"][0] / g["o4_1d_scale"][0, 0]
+    # the printed cross is -1 x the 1-D weights along x plus along y
+    cross = np.zeros((5, 5))
+    cross[2, :] -= w
+    cross[:, 2] -= w
+    np.testing.assert_allclose(cross * 12.0, g["o4_cross"], atol=1e-13)
+    for bc in (ops.SOMMERFELD, ops.DIRICHLET):
+        lv = _const_level(17, 7.0, bc)
+        E = ops.red_o4(lv)
+        row = _full_row(E, lv, 8, 8)
+        H = lv.h
+        want = np.zeros((17, 17), complex)
+        want[6:11, 6:11] = g["o4_cross"] / (12.0 * H * H)
+        want[8, 8] -= 49.0
+        np.testing.assert_allclose(row, want, atol=1e-9 * np.abs(want).max())
+        # rows within one node of the boundary are the ReD-O2 rows
+        o2 = ops.five_point(lv)
+        for (i, j) in ((1, 8), (8, 15), (1, 1)):
+            np.testing.assert_allclose(_full_row(E, lv, i, j),
+                                       _full_row(o2, lv, i, j), atol=1e-9)
+
+
+def test_red_o4_is_fourth_order_on_a_smooth_function():
+    """(-Lap - k^2) u for u = sin(pi x) sin(2 pi y) is (5 pi^2 - k^2) u; the
+    O4 rows' error shrinks 16x per halving of H (the O2 rows' 4x)."""
+    errs = []
+    for n in (33, 65, 129):
+        lv = _const_level(n, 5.0, ops.DIRICHLET)
+        x = np.linspace(0.0, 1.0, n)
+        u = np.sin(np.pi * x)[None, :] * np.sin(2 * np.pi * x)[:, None]
+        got = lv.to_full(ops.red_o4(lv) @ lv.to_unknowns(u))
+        exact = (5 * np.pi ** 2 - 25.0) * u
+        inner = np.zeros((n, n), bool)
+        inner[2:-2, 2:-2] = True
+        errs.append(np.abs(got - exact)[inner].max())
+    assert errs[0] / errs[1] > 14 and errs[1] / errs[2] > 14, errs
+
+
+def test_red_cmpo4_coefficients_and_symbol():
+    """The Singer-Turkel weights of Sec. 5.2.5 (fixture), their sums
+    (sum a = 0: a Laplacian; sum b = 1: a mass average), and the operator
+    on Dirichlet sine modes equals its closed-form symbol."""
+    g = load_golden("red_o4_cmpo4_stencils.txt")
+    a, b = ops.cmp_o4_weights(1.0)
+    np.testing.assert_allclose(a, g["cmp_a"], atol=1e-15)
+    np.testing.assert_allclose(b, g["cmp_b"], atol=1e-15)
+    assert abs(a.sum()) < 1e-14 and abs(b.sum() - 1.0) < 1e-14
+    n, k = 33, 9.0
+    lv = _const_level(n, k, ops.DIRICHLET)
+    E = ops.red_cmpo4(lv)
+    H = lv.h
+    x = np.linspace(0.0, 1.0, n)
+    for p, q in ((1, 1), (3, 2), (7, 11)):
+        u = np.sin(p * np.pi * x)[None, :] * np.sin(q * np.pi * x)[:, None]
+        cx, cy = np.cos(p * np.pi * H), np.cos(q * np.pi * H)
+        sa = a[1, 1] + 2 * a[1, 0] * (cx + cy) + 4 * a[0, 0] * cx * cy
+        sb = b[1, 1] + 2 * b[1, 0] * (cx + cy) + 4 * b[0, 0] * cx * cy
+        sym = sa / H ** 2 - sb * k * k
+        got = E @ lv.to_unknowns(u)
+        np.testing.assert_allclose(got, sym * lv.to_unknowns(u),
+                                   atol=1e-9 * abs(sym))
+
+
+def test_red_cmpo4_sommerfeld_ghost_rule():
+    """At a left-edge Sommerfeld node the ghost column is eliminated with
+    u_g = 2 i k H (1 - k^2 H^2 / 6) u_b + u_in (Sec. 5.2.5): the row acting
+    on a vector equals the stencil applied to the vector extended by that
+    rule, corner ghosts being the average of their two neighbouring edge
+    ghosts."""
+    n, kk = 9, 6.0
+    lv = _const_level(n, kk, ops.SOMMERFELD)
+    E = ops.red_cmpo4(lv)
+    a, b = ops.cmp_o4_weights(1.0)
+    H = lv.h
+    rng = np.random.default_rng(4)
+    u = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    ext = np.zeros((n + 2, n + 2), complex)
+    ext[1:-1, 1:-1] = u
+    c = 2j * kk * H * (1 - kk * kk * H * H / 6)
+    ext[1:-1, 0] = c * u[:, 0] + u[:, 1]
+    ext[1:-1, -1] = c * u[:, -1] + u[:, -2]
+    ext[0, 1:-1] = c * u[0, :] + u[1, :]
+    ext[-1, 1:-1] = c * u[-1, :] + u[-2, :]
+    for (gj, gi, bj, bi) in ((0, 0, 1, 1), (0, -1, 1, -2), (-1, 0, -2, 1),
+                             (-1, -1, -2, -2)):
+        ext[gj, gi] = 0.5 * (ext[gj, bi] + ext[bj, gi])
+    k2 = np.zeros((n + 2, n + 2))
+    k2[1:-1, 1:-1] = kk * kk
+    got = lv.to_full(E @ lv.to_unknowns(u))
+    for (i, j) in ((0, 4), (0, 0), (4, 8), (8, 8)):
+        want = 0.0
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                v = ext[j + 1 + dj, i + 1 + di]
+                want += (a[dj + 1, di + 1] / H ** 2
+                         - b[dj + 1, di + 1] * k2[j + 1 + dj, i + 1 + di]) * v
+        assert abs(got[j, i] - want) <= 1e-10 * abs(want), (i, j)

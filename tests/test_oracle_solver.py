@@ -89,6 +89,9 @@ CASES = [
     (17, 17, ops.DIRICHLET, "ho", "red_glk1"),
     (33, 17, ops.SOMMERFELD, "bilinear", "red_o2"),
     (17, 17, ops.SOMMERFELD, None, "galerkin"),
+    (33, 33, ops.SOMMERFELD, "ho", "red_o4"),
+    (33, 17, ops.DIRICHLET, "bilinear", "red_cmpo4"),
+    (33, 33, ops.SOMMERFELD, "ho", "red_cmpo4"),
 ]
 
 
@@ -158,6 +161,42 @@ def test_gcr_equals_gmres_for_a_fixed_preconditioner():
         rg = np.linalg.norm(b - matvec(xg))
         rm = np.linalg.norm(b - matvec(xm))
         assert abs(rg - rm) <= 1e-9 * np.linalg.norm(b), (k, rg, rm)
+
+
+def test_tlkm_converges_to_the_direct_solution():
+    """FGMRES with the practical TLKM preconditioner converges to the
+    sparse-LU solution (TLKM changes the convergence, not the system)."""
+    n = 33
+    k2 = _k2(n, n, 5, lo=8, hi=20)
+    for bc, z in ((ops.SOMMERFELD, "ho"), (ops.DIRICHLET, "bilinear")):
+        orc = Oracle(n, n, 1 / 32, k2, bc, z=z, coarse_tol=1e-10, precond="tlkm")
+        rng = np.random.default_rng(8)
+        b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        x, info = orc.solve(b, tol=1e-11, maxit=200)
+        lv = orc.levels[0]
+        xd = lv.to_full(spla.spsolve(orc.A.tocsc(), lv.to_unknowns(b)))
+        assert info.converged and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
+def test_tlkm_with_exact_pieces_deflates_the_coarse_space():
+    """With the exact pieces it approximates -- M~^-1 = M^-1 exactly and the
+    coarse operator R_Z M^-1 A Z solved exactly -- TLKM with gamma = 1 maps
+    the coarse space onto itself: P_TLKM A Z = Z (Sec. 3.2.2: P~ A~ Z =
+    A~ Z - A~ Z + gamma Z).  Exercises the composition order of tlkm()."""
+    n = 17
+    orc = Oracle(n, n, 1 / 16, _k2(n, n, 2, lo=6, hi=12), ops.SOMMERFELD,
+                 z="ho", coarsest="direct", precond="tlkm")
+    lu = spla.splu(orc.M[0].tocsc())
+    Minv = lambda v: lu.solve(v)  # noqa: E731
+    Z = orc.Z.tocsc()
+    coarse = orc.RZ @ np.column_stack(
+        [Minv(orc.A @ Z[:, j].toarray().ravel()) for j in range(Z.shape[1])])
+    orc.vcycle = lambda v, level=0: Minv(v)
+    orc.coarse_solve_tlkm = lambda v1: np.linalg.solve(coarse, v1)
+    for j in (0, 7, Z.shape[1] // 2, Z.shape[1] - 1):
+        zj = Z[:, j].toarray().ravel().astype(complex)
+        out = orc.tlkm(orc.A @ zj)
+        assert np.linalg.norm(out - zj) <= 1e-9 * np.linalg.norm(zj), j
 
 
 def test_gmres_lucky_breakdown_identity():
