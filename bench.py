@@ -213,23 +213,16 @@ def hbm_peak():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(wl_name, steps, warmup):
-    """Bounded CPU sample: one outer flexible-GMRES iteration of the oracle
-    (one A-DEF1 application with its inner coarse solve, one A product and
-    the Gram-Schmidt step) on one right-hand side, scaled to a whole solve by
-    the oracle's own outer-iteration count for this workload."""
+def _oracle_iteration(wl_name, steps=1, warmup=0):
+    """Seconds of one outer flexible-GMRES iteration of the oracle (one
+    A-DEF1 application with its inner coarse solve, one A product and the
+    Gram-Schmidt step) on one right-hand side, and the inner iterations it
+    took."""
     from oracle.solver import Oracle
     cfg, model, b = build_inputs(wl_name)
-    key = ORACLE_COUNT_KEY.get(wl_name)
-    counts = {}
-    if os.path.exists(ORACLE_COUNTS):
-        with open(ORACLE_COUNTS) as fh:
-            counts = json.load(fh)
-    outer = counts.get(key, {}).get("outer_iters") if key else None
     orc = Oracle(model.nx, model.ny, model.h, model.k2, cfg["bc"], z=cfg["z"],
                  e=cfg["e"], coarse_tol=cfg["coarse_tol"],
                  coarse_maxit=cfg["coarse_maxit"])
-    inner_total = counts.get(key, {}).get("inner_iters_total") if key else None
     lv = orc.levels[0]
     bu = lv.to_unknowns(b[0])
     v = bu / np.linalg.norm(bu)
@@ -245,23 +238,57 @@ def oracle_sample(wl_name, steps, warmup):
         if it >= warmup:
             times.append(dt)
             inner.append(sum(orc.inner_log) or 1)
-    t_iter = float(np.mean(times))
+    return float(np.mean(times)), float(np.mean(inner)), len(times)
+
+
+def _oracle_worker(wl_name):
+    return _oracle_iteration(wl_name)
+
+
+def oracle_sample(wl_name, steps, warmup, all_cores=False):
+    """Bounded CPU sample of the oracle, scaled to a whole solve by the
+    oracle's own iteration counts for this workload.  With all_cores, the
+    same sample also runs in one process per host core at once (spawned
+    processes, each its own shot), as the batched CPU baseline."""
+    cfg, model, _ = build_inputs(wl_name)
+    key = ORACLE_COUNT_KEY.get(wl_name)
+    counts = {}
+    if os.path.exists(ORACLE_COUNTS):
+        with open(ORACLE_COUNTS) as fh:
+            counts = json.load(fh)
+    outer = counts.get(key, {}).get("outer_iters") if key else None
+    inner_total = counts.get(key, {}).get("inner_iters_total") if key else None
+    t_iter, inner_mean, nsamp = _oracle_iteration(wl_name, steps, warmup)
     n_unk = unknowns(cfg, model)
     value = None
     how = "no recorded oracle iteration counts for this workload"
     if outer and inner_total:
         # full solve ~ outer iterations, each costing the sample's time per
         # inner iteration times the inner iterations it needs on average
-        t_inner = t_iter / float(np.mean(inner))
-        t_full = t_inner * inner_total
+        t_full = t_iter / inner_mean * inner_total
         value = n_unk / t_full
         how = (f"scaled to the oracle's {outer} outer / {inner_total} inner "
                f"iterations for a full solve ({t_full:.0f} s)")
-    return {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"one outer FGMRES iteration (A-DEF1 with its "
-                       f"{int(np.mean(inner))}-iteration inner coarse solve) "
-                       f"of 1 RHS of {wl_name}, {t_iter:.2f} s mean over "
-                       f"{len(times)}; {how}")}
+    out = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": (f"one outer FGMRES iteration (A-DEF1 with its "
+                      f"{int(inner_mean)}-iteration inner coarse solve) "
+                      f"of 1 RHS of {wl_name}, {t_iter:.2f} s mean over "
+                      f"{nsamp}; {how}")}
+    if all_cores and value is not None:
+        import multiprocessing as mp
+        procs = os.cpu_count() or 1
+        t0 = time.perf_counter()
+        with mp.get_context("spawn").Pool(procs) as pool:
+            res = pool.map(_oracle_worker, [wl_name] * procs)
+        wall = time.perf_counter() - t0
+        per = [t / i * inner_total for (t, i, _) in res]
+        out["all_cores"] = {
+            "value": n_unk * procs / float(np.mean(per)), "unit": UNIT,
+            "cores": procs,
+            "sample": (f"the same sample in {procs} spawned processes at once "
+                       f"(one shot each, {wall:.0f} s wall incl. set-up), "
+                       "scaled the same way")}
+    return out
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -280,11 +307,16 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     lib = load_library()
     cfg, model, b_np = build_inputs(args.workload, rank)
+    cfg = dict(cfg)
+    for key in ("coarse_tol", "coarse_maxit", "outer_maxit"):
+        if getattr(args, key) is not None:
+            cfg[key] = getattr(args, key)
     desc = Desc(model.nx, model.ny, model.h, bc=cfg["bc"], z=cfg["z"],
                 e=cfg["e"], prec=args.prec, nrhs_max=cfg["nrhs"],
                 coarse_tol=cfg["coarse_tol"], coarse_maxit=cfg["coarse_maxit"],
                 outer_maxit=cfg["outer_maxit"],
                 inner_basis_fp16=bool(args.basis16),
+                outer=args.outer, precond=args.precond,
                 cuda_graph=bool(args.cuda_graph))
     solver = Solver(desc, model.k2)
     tune_ms = None
@@ -296,6 +328,8 @@ def run_ours(args):
         solver.set_tuning(maxpy_kernel=args.maxpy_kernel)
     if args.galerkin_apply is not None:
         solver.set_tuning(galerkin_apply=args.galerkin_apply)
+    if args.vcycle_fused is not None:
+        solver.set_tuning(vcycle_fused=args.vcycle_fused)
     tuning = solver.get_tuning()
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
@@ -364,6 +398,14 @@ def run_ours(args):
     io_bytes = int(b_np.nbytes)
 
     roof = None
+    # DRAM bytes / algorithmic bytes of the profiled kernel, measured with ncu
+    # on a smaller case of the same kernel variant and storage (the summary
+    # under profiles/ names the command); traffic scales with the rows
+    # streamed, so a bench launch's traffic is this ratio times its bytes
+    traffic_ratio = None
+    if (args.profile_kernel == "mdot" and tuning.get("mdot_kernel") == 2
+            and args.prec == "mixed_bf16" and args.basis16):
+        traffic_ratio = (1.014, "profiles/k_mdot_tma_dram_mp2b_641_k400_b8_prof.md")
     if prof and prof[0] > 0:
         n_l, ms_k, by = prof
         peak, peak_src = hbm_peak()
@@ -371,7 +413,9 @@ def run_ours(args):
         roof = {"kernel": KERNEL_NAMES[args.profile_kernel], "bound": "hbm",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": None, "launches": int(n_l),
+                "traffic": (traffic_ratio[0] * by / n_l if traffic_ratio else None),
+                "traffic_source": (traffic_ratio[1] if traffic_ratio else None),
+                "launches": int(n_l),
                 "alg_bytes_per_launch": by / n_l,
                 "avg_launch_us": 1e3 * ms_k / n_l,
                 "timed_over": (f"{args.profile_steps} further step(s) of the "
@@ -406,7 +450,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = oracle_sample(args.workload, steps=1, warmup=0)
+        cpu = oracle_sample(args.workload, steps=1, warmup=0, all_cores=True)
 
     if rank == 0:
         line = {
@@ -420,6 +464,7 @@ def run_ours(args):
                        "velocity_model": model.name,
                        "kh_max": round(model.kh_max(), 4), "bc": cfg["bc"],
                        "deflation": f"{cfg['z']}/{cfg['e']}",
+                       "outer": args.outer, "preconditioner": args.precond,
                        "precision": PREC_TEXT[args.prec],
                        "inner_basis_storage": ("fp16" if args.basis16 and
                                                args.prec != "fp64" else
@@ -486,6 +531,16 @@ def main():
     ap.add_argument("--cuda-graph", type=int, default=1,
                     help="1: outer iterations as CUDA graphs with a device-side "
                          "inner WHILE loop; 0: kernels issued one by one")
+    ap.add_argument("--outer", choices=["fgmres", "gcr"], default="fgmres",
+                    help="outer Krylov iteration (hz_desc.outer_solver)")
+    ap.add_argument("--precond", choices=["adef1", "tlkm"], default="adef1",
+                    help="two-level preconditioner (hz_desc.preconditioner)")
+    ap.add_argument("--coarse-tol", type=float, default=None,
+                    help="override the workload's inner coarse-solve tolerance")
+    ap.add_argument("--coarse-maxit", type=int, default=None,
+                    help="override the inner iteration cap")
+    ap.add_argument("--outer-maxit", type=int, default=None,
+                    help="override the outer iteration cap")
     ap.add_argument("--autotune", type=int, default=1,
                     help="time the hz_tuning candidates at setup and keep the "
                          "fastest (outside the timed region)")
@@ -495,6 +550,8 @@ def main():
                     help="force hz_tuning.maxpy_kernel")
     ap.add_argument("--galerkin-apply", type=int, choices=[0, 1], default=None,
                     help="force hz_tuning.galerkin_apply")
+    ap.add_argument("--vcycle-fused", type=int, choices=[0, 1], default=None,
+                    help="force hz_tuning.vcycle_fused")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
     ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],

@@ -53,13 +53,18 @@ typedef enum { HZ_BC_DIRICHLET = 0, HZ_BC_SOMMERFELD = 1 } hz_bc;
  * interpolation (APD). */
 typedef enum { HZ_Z_NONE = 0, HZ_Z_BILINEAR = 1, HZ_Z_HO = 2 } hz_zkind;
 
-/* Coarse operator E = A_2h (Sec. 5.2): the Galerkin product R A_h Z formed
- * on the fly each application (str-Glk), 2nd-order re-discretisation
- * (ReD-O2), or the Galerkin-derived 5x5 re-discretisation with 2nd-order
- * rows on the two outer rings (ReD-Glk1) or on the outer ring with ghost
- * values on the second (ReD-Glk2). */
+/* Coarse operator E = A_2h (Sec. 5.2): the Galerkin product R A_h Z
+ * (str-Glk, Sec. 5.2.1, or its stored stencil, see hz_tuning), 2nd-order
+ * re-discretisation (ReD-O2, Sec. 5.2.3), the Galerkin-derived 5x5
+ * re-discretisation with 2nd-order rows on the two outer rings (ReD-Glk1)
+ * or on the outer ring with ghost values on the second (ReD-Glk2, Sec.
+ * 5.2.4), the 4th-order cross with ReD-O2 rows within one node of the
+ * boundary (ReD-O4, Sec. 5.2.3, eq. Helmstencil Oh4 with the wavenumber
+ * term read as -k^2), or the compact 4th-order 3x3 scheme with 4th-order
+ * Sommerfeld ghosts (ReD-cmpO4, Sec. 5.2.5, gamma = 1). */
 typedef enum {
-  HZ_E_GALERKIN = 0, HZ_E_RED_O2 = 1, HZ_E_RED_GLK1 = 2, HZ_E_RED_GLK2 = 3
+  HZ_E_GALERKIN = 0, HZ_E_RED_O2 = 1, HZ_E_RED_GLK1 = 2, HZ_E_RED_GLK2 = 3,
+  HZ_E_RED_O4 = 4, HZ_E_RED_CMPO4 = 5
 } hz_ekind;
 
 /* Arithmetic of the preconditioner (V-cycle, deflation, inner coarse
@@ -71,6 +76,20 @@ typedef enum {
 typedef enum {
   HZ_PREC_FP64 = 0, HZ_PREC_MIXED_FP32 = 1, HZ_PREC_MIXED_BF16 = 2
 } hz_precision;
+
+/* Outer Krylov iteration, both right-preconditioned by A-DEF1 and flexible
+ * (variable inner tolerance, Sec. 6.3): FGMRES (Arnoldi + Givens, the
+ * iterate formed at the end) or the preconditioned GCR of Sec. 3.3 / 6.3
+ * (the iterate and residual updated every step; issued without CUDA
+ * graphs).  Both store two sets of outer_maxit FP64 vectors. */
+typedef enum { HZ_OUTER_FGMRES = 0, HZ_OUTER_GCR = 1 } hz_outer;
+
+/* Two-level preconditioner: A-DEF1 (APD with the higher-order Z), eq. ADEF1,
+ * P = M^-1 (I - A Q) + Q; or the practical TLKM of Sec. 3.2.2,
+ * P = (I - M^-1 A Q~ + Q~) M^-1 (gamma = 1), whose coarse system
+ * I_h^2h I_2h^h M_2h^-1 A_2h v2 = v1 (Sec. 5.2, eq. TLKM CGP) is solved by
+ * GMRES on that operator (R_Z Z after a V-cycle on M_2h after E). */
+typedef enum { HZ_PRECOND_ADEF1 = 0, HZ_PRECOND_TLKM = 1 } hz_precond;
 
 typedef struct {
   int nx, ny;                 /* nodes; each >= 3                            */
@@ -93,6 +112,9 @@ typedef struct {
   int inner_basis_fp16;       /* mixed precisions only: store the inner
                                  coarse-solve Krylov basis as FP16 pairs
                                  (arithmetic stays FP32); 0 = FP32 basis   */
+  int outer_solver;           /* HZ_OUTER_FGMRES (default) or HZ_OUTER_GCR  */
+  int preconditioner;         /* HZ_PRECOND_ADEF1 (default) or HZ_PRECOND_TLKM
+                                 (needs zkind != HZ_Z_NONE)                 */
   int no_cuda_graph;          /* 0 (default): each outer iteration of hz_solve
                                  runs as one CUDA graph launch whose inner
                                  coarse-solve loop is a device-side WHILE
@@ -226,8 +248,8 @@ hz_status hz_coarse_galerkin_noalloc(int nx, int ny, double h, hz_bc bc,
                                      const void* x_dev, void* y_dev, int nrhs,
                                      void* cuda_stream);
 
-/* Grids of different sizes solved together (spec batching pattern;
- * the paper solves one grid at a time and has no counterpart).  Member g of
+/* Grids of different sizes solved together (a batching extension: the
+ * paper solves one grid at a time and has no counterpart).  Member g of
  * the group (up to HZ_MAX_GROUP solvers, each set up on its own grid and
  * workspace) solves nrhs[g] right-hand sides b_dev[g] -> x_dev[g] (layout
  * and x0 = 0 as hz_solve) to tol.  Every outer and inner Krylov iteration of

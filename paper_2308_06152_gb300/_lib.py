@@ -23,6 +23,8 @@ class HzDesc(ctypes.Structure):
                 ("coarse_tol", c_double), ("coarse_maxit", c_int),
                 ("outer_maxit", c_int), ("nrhs_max", c_int),
                 ("inner_basis_fp16", c_int),
+                ("outer_solver", c_int),
+                ("preconditioner", c_int),
                 ("no_cuda_graph", c_int)]
 
 

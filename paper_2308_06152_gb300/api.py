@@ -14,8 +14,11 @@ from ._lib import HzDesc, HzSolveInfo, HzTuning, STATUS, load_library
 
 BC = {"dirichlet": 0, "sommerfeld": 1}
 ZKIND = {None: 0, "none": 0, "bilinear": 1, "ho": 2}
-EKIND = {"galerkin": 0, "red_o2": 1, "red_glk1": 2, "red_glk2": 3}
+EKIND = {"galerkin": 0, "red_o2": 1, "red_glk1": 2, "red_glk2": 3,
+         "red_o4": 4, "red_cmpo4": 5}
 PREC = {"fp64": 0, "mixed": 1, "mixed_bf16": 2}
+OUTER = {"fgmres": 0, "gcr": 1}
+PRECOND = {"adef1": 0, "tlkm": 1}
 OPS = {"helmholtz": 0, "cslp": 1, "vcycle": 2, "restrict_fw": 3,
        "prolong_bilinear": 4, "restrict_z": 5, "prolong_z": 6, "coarse_e": 7,
        "coarse_solve": 8, "precond": 9}
@@ -49,6 +52,8 @@ class Desc:
     outer_maxit: int = 100
     nrhs_max: int = 1
     inner_basis_fp16: bool = False
+    outer: str = "fgmres"
+    precond: str = "adef1"
     cuda_graph: bool = True
 
     def to_c(self):
@@ -66,6 +71,8 @@ class Desc:
         d.outer_maxit = int(self.outer_maxit)
         d.nrhs_max = int(self.nrhs_max)
         d.inner_basis_fp16 = int(bool(self.inner_basis_fp16))
+        d.outer_solver = OUTER[self.outer]
+        d.preconditioner = PRECOND[self.precond]
         d.no_cuda_graph = int(not self.cuda_graph)
         return d
 

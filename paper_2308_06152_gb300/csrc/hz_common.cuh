@@ -241,6 +241,14 @@ void launch_probe_extract(const LevelDev& Lc, int P, int c0, int nprobe,
 template <class T>
 void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C<T>* y,
                       int nrhs, int rpb, const int* done, cudaStream_t st);
+// y = E x with ReD-O4 (4th-order cross, O2 near the boundary) or ReD-cmpO4
+// (compact 4th-order 3x3 with 4th-order Sommerfeld ghosts)
+template <class T>
+void launch_red_o4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                   const int* done, cudaStream_t st);
+template <class T>
+void launch_red_cmpo4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                      const int* done, cudaStream_t st);
 // y = E_glk x on level 1 (variant 1 or 2)
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
@@ -255,6 +263,10 @@ void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
 template <class Ti, class To>
 void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
                      int nrhs, const int* done, cudaStream_t st);
+// out = a - b + c, widened to FP64
+template <class T>
+void launch_sub_add_widen(const C<T>* a, const C<T>* b, const C<T>* c, VRef<double> out,
+                          long long n, int nrhs, const int* done, cudaStream_t st);
 // setup helpers
 void launch_inject(const LevelDev& Lf, const LevelDev& Lc, double* k2c,
                    cudaStream_t st);
@@ -371,6 +383,13 @@ template <class T, class SB>
 void launch_mdot_group(const GroupDesc& gd, int pass, cudaStream_t st);
 template <class T, class SB>
 void launch_maxpy_group(const GroupDesc& gd, int pass, cudaStream_t st);
+
+// Flexible GCR outer iteration: x += g u, r -= g c with g = hcol[r][0] and
+// partial ||r||^2 in npart; then the convergence test of step k
+void launch_gcr_update(double2* x, double2* r, const double2* u, const double2* c,
+                       long long n, int nrhs, const KState& ks, cudaStream_t st);
+void launch_gcr_check(const KState& ks, const double* rnorm, int nrhs, double tol, int k,
+                      int maxit, cudaStream_t st);
 
 // Timing support for the autotuner: synthetic vector contents and an
 // Arnoldi state at column j with RHS 0..nrhs-1 active.

@@ -1217,6 +1217,62 @@ __global__ void k_loop_next(const int* alldone, int* it, int maxit,
   cudaGraphSetConditional(h, (!*alldone && k < maxit) ? 1u : 0u);
 }
 
+// GCR step (Sec. 6.3's outer iteration): x += g u_k and r -= g c_k with
+// g = hcol[r][0] = (c_k, r), and the partial ||r||^2 of the new residual.
+__global__ void __launch_bounds__(NT)
+k_gcr_update(double2* __restrict__ x, double2* __restrict__ res,
+             const double2* __restrict__ u, const double2* __restrict__ c, long long n,
+             KState ks) {
+  __shared__ double red[NT / 32];
+  const int r = blockIdx.y, blk = blockIdx.x;
+  if (ks.done[r]) return;
+  const double2 g = ks.hcol[(long long)r * (ks.m + 1)];
+  double s = 0.0;
+  for (int k = 0; k < EPT; ++k) {
+    const long long e = (long long)blk * CHUNK + k * NT + threadIdx.x;
+    if (e >= n) break;
+    const long long id = r * n + e;
+    const double2 uv = u[id], cv = c[id];
+    double2 xv = x[id], rv = res[id];
+    xv.x += g.x * uv.x - g.y * uv.y;
+    xv.y += g.x * uv.y + g.y * uv.x;
+    rv.x -= g.x * cv.x - g.y * cv.y;
+    rv.y -= g.x * cv.y + g.y * cv.x;
+    x[id] = xv;
+    res[id] = rv;
+    s += rv.x * rv.x + rv.y * rv.y;
+  }
+  const double t = block_sum(s, red);
+  if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = t;
+}
+
+// GCR convergence after step k: ||r|| <= tol ||b|| (rnorm[r] = ||r||), a
+// non-finite residual, or the cap; all-converged flag.
+__global__ void k_gcr_check(KState ks, const double* __restrict__ rnorm, int nrhs,
+                            double tol, int k, int maxit) {
+  const int r = threadIdx.x;
+  int d = 1;
+  if (r < nrhs) {
+    d = ks.done[r];
+    if (!d) {
+      const double res = rnorm[r];
+      ks.iters[r] = k + 1;
+      if (!isfinite(res)) {
+        d = 1;
+        ks.stat[r] = ST_NAN;
+      } else if (res <= tol * ks.bnorm[r]) {
+        d = 1;
+      } else if (k + 1 >= maxit) {
+        d = 1;
+        ks.stat[r] = ST_NOT_CONVERGED;
+      }
+      ks.done[r] = d;
+    }
+  }
+  const int all = __syncthreads_and(d);
+  if (r == 0) *ks.alldone = all;
+}
+
 // Synthetic vectors for timing (values in [-1/2, 1/2) from an integer hash
 // of the index); no result of the method depends on them.
 template <class SB>
@@ -1436,6 +1492,16 @@ void launch_update(const SB* V, long long vstride, long long rs, const KState& k
 void launch_fill_int(int* p, int v, int count, cudaStream_t st) {
   HZ_COUNT();
   k_fill_int<<<(count + 255) / 256, 256, 0, st>>>(p, v, count);
+}
+void launch_gcr_update(double2* x, double2* r, const double2* u, const double2* c,
+                       long long n, int nrhs, const KState& ks, cudaStream_t st) {
+  HZ_COUNT();
+  k_gcr_update<<<dim3(krylov_nblk(n), nrhs), NT, 0, st>>>(x, r, u, c, n, ks);
+}
+void launch_gcr_check(const KState& ks, const double* rnorm, int nrhs, double tol, int k,
+                      int maxit, cudaStream_t st) {
+  HZ_COUNT();
+  k_gcr_check<<<1, 1024, 0, st>>>(ks, rnorm, nrhs, tol, k, maxit);
 }
 template <class SB>
 void launch_tune_fill(SB* p, long long count, unsigned seed, cudaStream_t st) {

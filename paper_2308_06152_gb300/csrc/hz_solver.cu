@@ -84,7 +84,7 @@ bool valid_desc(const hz_desc* d, std::string* why) {
   if (!(d->h > 0)) { *why = "h must be positive"; return false; }
   if (d->bc != HZ_BC_DIRICHLET && d->bc != HZ_BC_SOMMERFELD) { *why = "bad bc"; return false; }
   if (d->zkind < HZ_Z_NONE || d->zkind > HZ_Z_HO) { *why = "bad zkind"; return false; }
-  if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_GLK2) { *why = "bad ekind"; return false; }
+  if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_CMPO4) { *why = "bad ekind"; return false; }
   if (d->prec < HZ_PREC_FP64 || d->prec > HZ_PREC_MIXED_BF16) { *why = "bad prec"; return false; }
   if (d->nrhs_max < 1 || d->nrhs_max > kMaxRhs) { *why = "nrhs_max must be in 1..1024"; return false; }
   if (d->outer_maxit < 1 || d->coarse_maxit < 1 || d->outer_maxit > kMaxIters ||
@@ -94,6 +94,18 @@ bool valid_desc(const hz_desc* d, std::string* why) {
   }
   if (d->min_coarse_intervals < 1) { *why = "min_coarse_intervals must be >= 1"; return false; }
   if (!(d->jacobi_omega > 0)) { *why = "jacobi_omega must be positive"; return false; }
+  if (d->outer_solver != HZ_OUTER_FGMRES && d->outer_solver != HZ_OUTER_GCR) {
+    *why = "bad outer_solver";
+    return false;
+  }
+  if (d->preconditioner != HZ_PRECOND_ADEF1 && d->preconditioner != HZ_PRECOND_TLKM) {
+    *why = "bad preconditioner";
+    return false;
+  }
+  if (d->preconditioner == HZ_PRECOND_TLKM && d->zkind == HZ_Z_NONE) {
+    *why = "TLKM needs deflation vectors";
+    return false;
+  }
   return true;
 }
 
@@ -125,7 +137,7 @@ struct hz_solver {
   double2* aug = nullptr;
   int* gj_err = nullptr;
   // preconditioner scratch (preconditioner precision), fine level
-  void *fz1 = nullptr, *fz2 = nullptr, *t = nullptr, *yv = nullptr, *q = nullptr,
+  void *fz1 = nullptr, *t = nullptr, *yv = nullptr, *q = nullptr,
        *vin = nullptr;
   // coarse level (level 1)
   void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
@@ -137,6 +149,8 @@ struct hz_solver {
   int* in_max = nullptr;
   // outer FGMRES (FP64)
   double2 *Vo = nullptr, *Zo = nullptr, *wo = nullptr;
+  double2* ro = nullptr;   // GCR residual
+  int* izero = nullptr;    // a device 0 (column index of a one-vector dot)
   double* bnorm_o = nullptr;
   double* relres = nullptr;
   // host-buffer solve and gradient storage
@@ -256,6 +270,7 @@ void plan(hz_solver* s, Arena& a) {
   const long long n0 = s->lv[0].n;
   s->t = a.take(es * B * n0);
   s->yv = a.take(es * B * n0);
+  s->fz1 = d.preconditioner == HZ_PRECOND_TLKM ? a.take(es * B * n0) : nullptr;
   s->vin = s->mixed ? a.take(es * B * n0) : nullptr;
   if (d.zkind != HZ_Z_NONE) {
     const long long n1 = s->lv[1].n;
@@ -287,6 +302,10 @@ void plan(hz_solver* s, Arena& a) {
   s->io2 = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
   s->Jd = (double*)a.take(sizeof(double));
   s->prof_bytes = (unsigned long long*)a.take(sizeof(unsigned long long));
+  s->izero = (int*)a.take(sizeof(int));
+  s->ro = d.outer_solver == HZ_OUTER_GCR
+              ? (double2*)a.take(sizeof(double2) * (size_t)B * n0)
+              : nullptr;
   s->loop_it = (int*)a.take(sizeof(int));
   s->body_kernels = (int*)a.take(sizeof(int));
   s->fault = (int*)a.take(sizeof(int));
@@ -440,6 +459,12 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
     case HZ_E_RED_GLK1:
       launch_glk<T>(Cc.dev(), bc, 1, x, y, nrhs, done, st);
       break;
+    case HZ_E_RED_O4:
+      launch_red_o4<T>(Cc.dev(), bc, x, y, nrhs, done, st);
+      break;
+    case HZ_E_RED_CMPO4:
+      launch_red_cmpo4<T>(Cc.dev(), bc, x, y, nrhs, done, st);
+      break;
     default:
       launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st);
       break;
@@ -554,6 +579,22 @@ void cgs2(hz_solver* s, KState& ks, const SB* V, long long vs, long long rs, C<T
 template <class T, class SB>
 void inner_pre(hz_solver* s, int nrhs) {
   KState& ks = s->kin;
+  if (s->d.preconditioner == HZ_PRECOND_TLKM) {
+    // TLKM coarse operator: w = R_Z Z M_2h^-1 E v_j
+    const long long n1 = s->lv[1].n;
+    const long long rs = inner_row(n1);
+    const long long vs = (long long)s->d.nrhs_max * rs;
+    const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
+    launch_basis_load<SB, T>(vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs), rs, (C<T>*)s->qf,
+                             n1, nrhs, ks.done, s->st);
+    apply_E<T>(s, (const C<T>*)s->qf, (C<T>*)s->sb, nrhs, ks.done);
+    vcycle<T>(s, 1, vref<T>((C<T>*)s->sb), (C<T>*)s->eb, nrhs, ks.done);
+    launch_prolong_z<T>(F, Cc, s->d.bc, s->d.zkind, (const C<T>*)s->eb, (C<T>*)s->q, 0,
+                        nrhs, ks.done, s->st);
+    launch_restrict_z<T>(F, Cc, s->d.bc, s->d.zkind, vref<T>((C<T>*)s->q), (C<T>*)s->eb,
+                         nrhs, ks.done, s->st);
+    return;
+  }
   const long long n1 = s->lv[1].n;
   const long long rs = inner_row(n1);
   const long long vs = (long long)s->d.nrhs_max * rs;
@@ -664,7 +705,11 @@ void coarse_finish(hz_solver* s, C<T>* v2, int nrhs, const int* done_in) {
   launch_trisolve(ks, nrhs, st);
   launch_update<SB, T>((const SB*)s->Qb, (long long)s->d.nrhs_max * rs, rs, ks,
                        (C<T>*)s->eb, 0, n1, nrhs, st);
-  vcycle<T>(s, 1, vref<T>((C<T>*)s->eb), v2, nrhs, done_in);
+  if (s->d.preconditioner == HZ_PRECOND_TLKM)   // the operator carries M_2h^-1
+    launch_add_conv<T, T>(vref<T>((C<T>*)s->eb), nullptr, vref<T>(v2), n1, nrhs, done_in,
+                          st);
+  else
+    vcycle<T>(s, 1, vref<T>((C<T>*)s->eb), v2, nrhs, done_in);
   launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
 }
 
@@ -741,9 +786,42 @@ void precond_finish(hz_solver* s, VRef<T> v, VRef<double> zout, int nrhs,
   launch_add_conv<T, double>(vref<T>(yv), (const C<T>*)s->q, zout, n0, nrhs, done, st);
 }
 
+// Practical TLKM (Sec. 3.2.2): w = M^-1 v, v2 from the TLKM coarse system
+// with right-hand side R_Z w, q = Z v2, z = w - M^-1 (A q) + q (gamma = 1).
+template <class T>
+hz_status precond_tlkm(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
+                       const int* done) {
+  cudaStream_t st = s->st;
+  const int bc = s->d.bc;
+  const long long n0 = s->lv[0].n;
+  VRef<T> v;
+  if constexpr (std::is_same<T, double>::value) {
+    v = vin;
+  } else {
+    launch_add_conv<double, T>(vin, nullptr, vref<T>(s->vin), n0, nrhs, done, st);
+    v = vref<T>(s->vin);
+  }
+  const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
+  C<T>* w = (C<T>*)s->yv;
+  vcycle<T>(s, 0, v, w, nrhs, done);
+  launch_restrict_z<T>(F, Cc, bc, s->d.zkind, vref<T>(w), (C<T>*)s->v1, nrhs, done, st);
+  const hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
+  if (e != HZ_OK) return e;
+  launch_prolong_z<T>(F, Cc, bc, s->d.zkind, (const C<T>*)s->v2, (C<T>*)s->q, 0, nrhs,
+                      done, st);
+  launch_helm<T>(F, bc, helm1(), vref<T>(s->q), vref<T>(nullptr), (C<T>*)s->t, nrhs,
+                 done, st);
+  vcycle<T>(s, 0, vref<T>(s->t), (C<T>*)s->fz1, nrhs, done);
+  launch_sub_add_widen<T>(w, (const C<T>*)s->fz1, (const C<T>*)s->q, zout, n0, nrhs, done,
+                          st);
+  return cuda_check(s, "tlkm");
+}
+
 template <class T>
 hz_status precond(hz_solver* s, VRef<double> vin, VRef<double> zout, int nrhs,
                   const int* done) {
+  if (s->d.preconditioner == HZ_PRECOND_TLKM)
+    return precond_tlkm<T>(s, vin, zout, nrhs, done);
   const VRef<T> v = precond_begin<T>(s, vin, nrhs, done);
   if (s->d.zkind != HZ_Z_NONE) {
     const hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
@@ -894,18 +972,15 @@ hz_status outer_begin(hz_solver* s, const double2* b, double2* x, int nrhs, doub
   return cuda_check(s, "outer init");
 }
 
-// Outer FGMRES end: x += Z_k y, the true residual and the per-RHS report.
-hz_status outer_end(hz_solver* s, const double2* b, double2* x, int nrhs,
-                    hz_solve_info* info) {
+// The true residual b - A x and the per-RHS report of an outer solve.
+hz_status outer_report(hz_solver* s, const double2* b, double2* x, int nrhs,
+                       hz_solve_info* info) {
   cudaStream_t st = s->st;
   KState& ko = s->kout;
   const long long n0 = s->lv[0].n;
-  const long long vs = (long long)s->d.nrhs_max * n0;
   const int bc = s->d.bc;
   const LevelDev F = dev64(s, 0);
   hz_status e = HZ_OK;
-  launch_trisolve(ko, nrhs, st);
-  launch_update<double2, double>(s->Zo, vs, n0, ko, x, 1, n0, nrhs, st);
   // true residual
   launch_helm<double>(F, bc, helm1(), vref<double>(x), vref<double>(b), s->wo, nrhs,
                       nullptr, st);
@@ -1044,8 +1119,80 @@ hz_status take_fault(hz_solver* s) {
   return HZ_TIMEOUT;
 }
 
+// Outer FGMRES end: x += Z_k y, then the report.
+hz_status outer_end(hz_solver* s, const double2* b, double2* x, int nrhs,
+                    hz_solve_info* info) {
+  const long long n0 = s->lv[0].n;
+  launch_trisolve(s->kout, nrhs, s->st);
+  launch_update<double2, double>(s->Zo, (long long)s->d.nrhs_max * n0, n0, s->kout, x, 1,
+                                 n0, nrhs, s->st);
+  return outer_report(s, b, x, nrhs, info);
+}
+
+// Flexible GCR as the outer iteration (Sec. 6.3), right-preconditioned by
+// A-DEF1.  Step k: u_k = P r (stored in Z slot k), c = A u_k made orthogonal
+// to c_0 .. c_{k-1} (V slots) by the same two-pass classical Gram-Schmidt as
+// FGMRES, with the coefficients also applied to u_k; both normalised by
+// ||c||; then x += (c_k, r) u_k, r -= (c_k, r) c_k.  Issued eagerly.
+hz_status solve_gcr(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
+                    int use_x0, hz_solve_info* info) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const long long n0 = s->lv[0].n;
+  const long long vs = (long long)s->d.nrhs_max * n0;
+  const int m = s->d.outer_maxit;
+  hz_status e = outer_begin(s, b, x, nrhs, tol, use_x0);
+  if (e != HZ_OK) return e;
+  // r = b - A x0, as left in wo by outer_begin
+  launch_add_conv<double, double>(vref<double>(s->wo), nullptr, vref<double>(s->ro), n0,
+                                  nrhs, nullptr, st);
+  KState kg = ko;      // the dot (c_k, r): one basis vector
+  kg.jctr = s->izero;
+  kg.abytes = nullptr;
+  int all = 0;
+  e = read_flag(s, ko.alldone, &all);
+  if (e != HZ_OK) return e;
+  for (int k = 0; k < m && !all; ++k) {
+    double2* u = s->Zo + k * vs;
+    double2* c = s->Vo + k * vs;
+    e = precond_any(s, vref<double>(s->ro), vref<double>(u), nrhs, ko.done);
+    if (e != HZ_OK) return e;
+    launch_helm<double>(dev64(s, 0), s->d.bc, helm1(), vref<double>(u),
+                        vref<double>(nullptr), s->wo, nrhs, ko.done, st);
+    if (k > 0) {
+      launch_fill_int(ko.jctr, k - 1, 1, st);
+      for (int pass = 0; pass < 2; ++pass) {
+        launch_mdot<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
+        launch_reduce_cols(ko, n0, nrhs, pass, st);
+        // the directions first: the update of c leaves its norm in npart
+        launch_maxpy<double, double2>(s->Zo, vs, n0, u, n0, nrhs, ko, pass, st);
+        launch_maxpy<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
+        if (pass == 0) launch_reorth_decide(ko, n0, nrhs, kReorthEta, st);
+      }
+    } else {
+      launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+    }
+    launch_reduce_norm(ko, n0, nrhs, ko.hnorm, 1, st);
+    launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(c), n0, ko.hnorm,
+                                      n0, nrhs, ko.done, st);
+    launch_scale_into<double, double2>(vref<double>(u), vref<double>(u), n0, ko.hnorm, n0,
+                                      nrhs, ko.done, st);
+    launch_mdot<double, double2>(c, vs, n0, s->ro, n0, nrhs, kg, 0, st);
+    launch_reduce_cols(kg, n0, nrhs, 0, st);
+    launch_gcr_update(x, s->ro, u, c, n0, nrhs, ko, st);
+    launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
+    launch_gcr_check(ko, ko.beta, nrhs, tol, k, m, st);
+    e = cuda_check(s, "gcr step");
+    if (e != HZ_OK) return e;
+    e = read_flag(s, ko.alldone, &all);
+    if (e != HZ_OK) return e;
+  }
+  return outer_report(s, b, x, nrhs, info);
+}
+
 hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
                     double tol, int use_x0, hz_solve_info* info) {
+  if (s->d.outer_solver == HZ_OUTER_GCR) return solve_gcr(s, b, x, nrhs, tol, use_x0, info);
   cudaStream_t st = s->st;
   KState& ko = s->kout;
   const int m = s->d.outer_maxit;
@@ -1253,6 +1400,11 @@ struct GroupScope {
       }
       for (hz_solver* t : S)
         if (t == s) status = HZ_INVALID_ARG;
+      if (s->d.outer_solver != HZ_OUTER_FGMRES ||
+          s->d.preconditioner != HZ_PRECOND_ADEF1) {
+        set_err(s, "group solves use flexible GMRES members with A-DEF1");
+        status = HZ_INVALID_ARG;
+      }
       if (g > 0 && (s->mixed != S[0]->mixed || s->basis16 != S[0]->basis16 ||
                     (s->d.zkind == HZ_Z_NONE) != (S[0]->d.zkind == HZ_Z_NONE))) {
         set_err(S[0], "group members differ in precision, inner-basis storage or "
@@ -1453,6 +1605,7 @@ hz_status hz_setup(const hz_desc* d, const double* k2_dev, void* ws, size_t ws_b
   }
   cudaMemsetAsync(s->gj_err, 0, sizeof(int), st);
   cudaMemsetAsync(s->fault, 0, sizeof(int), st);
+  cudaMemsetAsync(s->izero, 0, sizeof(int), st);
   if (s->Sglk) extract_galerkin_stencil(s);
   launch_dense_assemble(dev64(s, s->L), s->d.bc, sh, s->aug, st);
   launch_gauss_jordan(s->nL, s->aug, s->gj_err, st);

@@ -382,6 +382,108 @@ __global__ void k_glk(LevelDev L, int bc, int variant, const C<T>* __restrict__ 
   y[r * n + id] = acc;
 }
 
+// ReD-O4 (Sec. 5.2.3): nodes whose 4th-order cross stays inside the grid use
+// eq. (Helmstencil Oh4), -[-1 16 -30 16 -1] / (12 H^2) along x and y minus
+// k^2 of the node; nodes within one node of the boundary use the ReD-O2 row.
+// Dirichlet boundary nodes hold zero (their values in x are not read).
+template <class T>
+__global__ void k_red_o4(LevelDev L, int bc, const C<T>* __restrict__ x,
+                         C<T>* __restrict__ y, const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
+  const int nx = L.nx, ny = L.ny;
+  const long long n = (long long)nx * ny, id = (long long)j * nx + i;
+  const C<T>* xr = x + r * n;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, nx, ny)) {
+    y[r * n + id] = czero<T>();
+    return;
+  }
+  const int dist = min(min(i, nx - 1 - i), min(j, ny - 1 - j));
+  if (dist <= 1) {
+    y[r * n + id] = helm_point<T>(L, bc, T(1), T(0), xr, i, j);
+    return;
+  }
+  auto xv = [&](int a, int b) {
+    if (bc == BC_DIRICHLET && on_bnd(a, b, nx, ny)) return czero<T>();
+    return xr[(long long)b * nx + a];
+  };
+  const T s = ih2_of<T>(L) / T(12);
+  const T k2 = k2_of<T>(L)[id];
+  C<T> acc = (T(60) * s - k2) * xr[id];
+  acc = rfma(T(-16) * s, (xv(i - 1, j) + xv(i + 1, j)) + (xv(i, j - 1) + xv(i, j + 1)), acc);
+  acc = rfma(s, (xv(i - 2, j) + xv(i + 2, j)) + (xv(i, j - 2) + xv(i, j + 2)), acc);
+  y[r * n + id] = acc;
+}
+
+// ReD-cmpO4 (Sec. 5.2.5): the compact 3x3 stencil [a] / H^2 - [b] k^2 of
+// eq. (GeneralFormReD) with the Singer-Turkel weights (gamma = 1), each
+// mass entry with its own node's k^2.  Under Sommerfeld rows the ghost
+// layer is u_g = 2 i k H (1 - k^2 H^2 / 6) u_b + u_in (k of the boundary
+// node, ghost k^2 = 0), a corner ghost the average of its two neighbouring
+// edge ghosts; Dirichlet boundary nodes hold zero.
+template <class T>
+__device__ __forceinline__ C<T> cmp_edge_ghost(const LevelDev& L, const C<T>* xr, int bi,
+                                               int bj, int ii, int ij) {
+  const long long b = (long long)bj * L.nx + bi;
+  const T k = sqrt(k2_of<T>(L)[b]);
+  const T H = T(L.h);
+  const T c = T(2) * k * H * (T(1) - k * k * H * H / T(6));
+  const C<T> ub = xr[b];
+  return mkc(-c * ub.y, c * ub.x) + xr[(long long)ij * L.nx + ii];
+}
+template <class T>
+__device__ __forceinline__ C<T> cmp_node(const LevelDev& L, int bc, const C<T>* xr,
+                                         int i, int j) {
+  const int nx = L.nx, ny = L.ny;
+  const bool gx = i < 0 || i >= nx, gy = j < 0 || j >= ny;
+  if (!gx && !gy) {
+    if (bc == BC_DIRICHLET && on_bnd(i, j, nx, ny)) return czero<T>();
+    return xr[(long long)j * nx + i];
+  }
+  // ghosts exist only under Sommerfeld rows (Dirichlet rows never reach them)
+  const int bi = i < 0 ? 0 : (i >= nx ? nx - 1 : i);
+  const int bj = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+  const int ii = i < 0 ? 1 : (i >= nx ? nx - 2 : i);
+  const int ij = j < 0 ? 1 : (j >= ny ? ny - 2 : j);
+  if (gx && !gy) return cmp_edge_ghost<T>(L, xr, bi, j, ii, j);
+  if (!gx && gy) return cmp_edge_ghost<T>(L, xr, i, bj, i, ij);
+  // corner: average of the y ghost of (bi, .) and the x ghost of (., bj)
+  return T(0.5) * (cmp_edge_ghost<T>(L, xr, bi, bj, bi, ij) +
+                   cmp_edge_ghost<T>(L, xr, bi, bj, ii, bj));
+}
+template <class T>
+__global__ void k_red_cmpo4(LevelDev L, int bc, const C<T>* __restrict__ x,
+                            C<T>* __restrict__ y, const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
+  const int nx = L.nx, ny = L.ny;
+  const long long n = (long long)nx * ny, id = (long long)j * nx + i;
+  const C<T>* xr = x + r * n;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, nx, ny)) {
+    y[r * n + id] = czero<T>();
+    return;
+  }
+  const T ih2 = ih2_of<T>(L);
+  const T* k2 = k2_of<T>(L);
+  const T a0 = T(10) / T(3), as = T(-2) / T(3), ac = T(-1) / T(6);
+  const T b0 = T(2) / T(3) + T(1) / T(36), bs = T(1) / T(12) - T(1) / T(72),
+          bc_ = T(1) / T(144);
+  C<T> acc = czero<T>();
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      const int a = i + di, b = j + dj;
+      const bool in = a >= 0 && a < nx && b >= 0 && b < ny;
+      const T kk = in ? k2[(long long)b * nx + a] : T(0);
+      const int d = abs(di) + abs(dj);
+      const T wa = d == 0 ? a0 : (d == 1 ? as : ac);
+      const T wb = d == 0 ? b0 : (d == 1 ? bs : bc_);
+      acc = rfma(wa * ih2 - wb * kk, cmp_node<T>(L, bc, xr, a, b), acc);
+    }
+  y[r * n + id] = acc;
+}
+
 template <class T>
 __global__ void k_mask_dirichlet(LevelDev L, C<T>* __restrict__ x) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
@@ -512,6 +614,21 @@ __global__ void k_add_conv(VRef<Ti> a, const C<Ti>* __restrict__ b, VRef<To> out
     C<Ti> v = ar[e];
     if (b) v = v + b[r * n + e];
     orow[e] = cvt<To>(widen<Ti>(v));
+  }
+}
+
+// out = a - b + c in FP64 (the last step of the TLKM preconditioner)
+template <class T>
+__global__ void k_sub_add_widen(const C<T>* __restrict__ a, const C<T>* __restrict__ b,
+                                const C<T>* __restrict__ c, VRef<double> out, long long n,
+                                const int* __restrict__ done) {
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  double2* orow = out.get() + r * n;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long id = r * n + e;
+    orow[e] = widen<T>((a[id] - b[id]) + c[id]);
   }
 }
 
@@ -739,6 +856,18 @@ void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
                                                                y, done);
 }
 template <class T>
+void launch_red_o4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                   const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_red_o4<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
+}
+template <class T>
+void launch_red_cmpo4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                      const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_red_cmpo4<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
+}
+template <class T>
 void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
                            cudaStream_t st) {
   if (bc != BC_DIRICHLET) return;
@@ -753,6 +882,21 @@ void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
   if (nb > 4096) nb = 4096;
   k_add_conv<Ti, To><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(a, b, out, n, done);
 }
+
+template <class T>
+void launch_sub_add_widen(const C<T>* a, const C<T>* b, const C<T>* c, VRef<double> out,
+                          long long n, int nrhs, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  long long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_sub_add_widen<T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(a, b, c, out, n, done);
+}
+template void launch_sub_add_widen<double>(const double2*, const double2*, const double2*,
+                                           VRef<double>, long long, int, const int*,
+                                           cudaStream_t);
+template void launch_sub_add_widen<float>(const float2*, const float2*, const float2*,
+                                          VRef<double>, long long, int, const int*,
+                                          cudaStream_t);
 
 void launch_inject(const LevelDev& Lf, const LevelDev& Lc, double* k2c,
                    cudaStream_t st) {
@@ -804,6 +948,10 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                               int, const int*, cudaStream_t);                   \
   template void launch_mask_dirichlet<T>(const LevelDev&, int, C<T>*, int,      \
                                          cudaStream_t);                        \
+  template void launch_red_o4<T>(const LevelDev&, int, const C<T>*, C<T>*, int, \
+                                 const int*, cudaStream_t);                     \
+  template void launch_red_cmpo4<T>(const LevelDev&, int, const C<T>*, C<T>*,   \
+                                    int, const int*, cudaStream_t);             \
   template void launch_probe_extract<T>(const LevelDev&, int, int, int,         \
                                         const double2*, C<T>*, cudaStream_t);   \
   template void launch_stencil_e<T>(const LevelDev&, int, const C<T>*,          \
