@@ -371,6 +371,37 @@ def _dist_to_boundary(nx, ny):
     return np.minimum(np.minimum(ii, nx - 1 - ii), np.minimum(jj, ny - 1 - jj))
 
 
+def _red_cross(coarse, weights, ring):
+    """Re-discretised operator: the 1-D second-difference weights
+    ``weights`` (offsets -R..R, times 1/H^2) negated along x and y, minus
+    k^2 of the node, on nodes at least ``ring`` nodes inside the grid; the
+    others use the ReD-O2 row with its boundary rules."""
+    nx, ny, H = coarse.nx, coarse.ny, coarse.h
+    R = len(weights) // 2
+    o2_rows = _dist_to_boundary(nx, ny) < ring
+    w = -np.asarray(weights, dtype=np.float64) / (H * H)
+
+    def coef(i, j, di, dj, k2nb):
+        if di == 0 and dj == 0:
+            return 2.0 * w[R] - k2nb
+        if di != 0 and dj != 0:
+            return 0.0
+        return w[R + di + dj]
+
+    full = stencil_with_ghosts(coarse, ~o2_rows, coef, R)
+    full_o2 = five_point_full(nx, ny, H, coarse.k2, coarse.bc, 1.0)
+    keep = sp.diags(o2_rows.ravel().astype(np.float64))
+    return _restrict_to_unknowns((keep @ full_o2 + full).tocsr(), coarse, coarse)
+
+
+def red_o6(coarse):
+    """ReD-O6 (Sec. 5.2.3): the sixth-order second difference
+    (2, -27, 270, -490, 270, -27, 2) / (180 H^2) along x and y minus k^2,
+    on nodes whose 7-point cross stays inside the grid (at least 3 nodes
+    from the boundary); the others use ReD-O2 (as for ReD-O4)."""
+    return _red_cross(coarse, np.array([2, -27, 270, -490, 270, -27, 2]) / 180.0, 3)
+
+
 def red_o4(coarse):
     """ReD-O4 (Sec. 5.2.3): coarse nodes whose 4th-order cross stays inside
     the grid use eq. (Helmstencil Oh4): the Laplacian
@@ -410,16 +441,19 @@ def cmp_o4_weights(gamma=1.0):
     return a, b
 
 
-def ghost_values_cmp(level):
-    """Ghost nodes one layer outside a Sommerfeld boundary for ReD-cmpO4
-    (Sec. 5.2.5): the 4th-order rule u_ghost = 2 i k H (1 - k^2 H^2 / 6)
-    u_bnd + u_in with k of the boundary node; a corner ghost is the average
-    of its two neighbouring edge ghosts."""
+def ghost_values_cmp(level, fourth_order=True):
+    """Ghost nodes one layer outside a Sommerfeld boundary for the compact
+    3x3 schemes: ReD-cmpO4's 4th-order rule (Sec. 5.2.5)
+    u_ghost = 2 i k H (1 - k^2 H^2 / 6) u_bnd + u_in, or (fourth_order
+    False) the 2nd-order eq. (GhostPoint) u_ghost = 2 i k H u_bnd + u_in,
+    with k of the boundary node; a corner ghost is the average of its two
+    neighbouring edge ghosts."""
     nx, ny, H = level.nx, level.ny, level.h
     k = np.sqrt(level.k2)
 
     def rule(kb, b_node, in_node):
-        return {b_node: 2j * kb * H * (1.0 - kb * kb * H * H / 6.0), in_node: 1.0}
+        corr = (1.0 - kb * kb * H * H / 6.0) if fourth_order else 1.0
+        return {b_node: 2j * kb * H * corr, in_node: 1.0}
 
     g = {}
     for j in range(ny):
@@ -436,6 +470,33 @@ def ghost_values_cmp(level):
                     avg[key] = avg.get(key, 0) + 0.5 * c
             g[(gi, gj)] = avg
     return g
+
+
+# ReD-9ptO2 (Appendix B): eq. (GeneralFormReD) with the coefficients the
+# appendix fits at k = 80 (eq. optstcl_k80) and b0 = 1, b_s = b_c = 0.
+def nine_point_o2_weights():
+    a = np.array([[0.158, -1.316, 0.158], [-1.316, 4.632, -1.316],
+                  [0.158, -1.316, 0.158]])
+    b = np.array([[0.0, 0.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 0.0]])
+    return a, b
+
+
+def red_9pt(coarse):
+    """ReD-9ptO2 (Appendix B): [a] / H^2 - [b] k^2 with the appendix's
+    coefficients; a second-order scheme, so Sommerfeld rows eliminate the
+    ghost layer with eq. (GhostPoint), u_g = u_in + 2 i k H u_b (a corner
+    ghost the average of its two neighbouring edge ghosts); Dirichlet rows
+    only meet boundary nodes, which hold zero."""
+    a, b = nine_point_o2_weights()
+    ih2 = 1.0 / (coarse.h * coarse.h)
+
+    def coef(i, j, di, dj, k2nb):
+        return a[dj + 1, di + 1] * ih2 - b[dj + 1, di + 1] * k2nb
+
+    ghosts = (ghost_values_cmp(coarse, fourth_order=False)
+              if coarse.bc == SOMMERFELD else {})
+    full = stencil_with_ghosts(coarse, coarse.mask, coef, 1, ghosts=ghosts)
+    return _restrict_to_unknowns(full, coarse, coarse)
 
 
 def red_cmpo4(coarse, gamma=1.0):

@@ -39,7 +39,7 @@ class Oracle:
 
     ``z``: None (plain CSLP), 'bilinear' (A-DEF1) or 'ho' (APD).
     ``e``: 'galerkin' (str-Glk), 'red_o2', 'red_glk1', 'red_glk2',
-    'red_o4' or 'red_cmpo4'.
+    'red_o4', 'red_o6', 'red_cmpo4' or 'red_9pt'.
     ``coarsest``: 'gmres' (paper) or 'direct' (sparse LU; used where an
     exact coarsest solve is wanted for tight comparisons).
     ``precond``: 'adef1' (A-DEF1 / APD, eq. ADEF1) or 'tlkm' (the practical
@@ -90,6 +90,10 @@ class Oracle:
                 self.E = ops.red_o4(self.levels[1])
             elif e == "red_cmpo4":
                 self.E = ops.red_cmpo4(self.levels[1])
+            elif e == "red_o6":
+                self.E = ops.red_o6(self.levels[1])
+            elif e == "red_9pt":
+                self.E = ops.red_9pt(self.levels[1])
             else:
                 raise ValueError(e)
 

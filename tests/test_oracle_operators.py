@@ -406,3 +406,88 @@ def test_red_cmpo4_sommerfeld_ghost_rule():
                 want += (a[dj + 1, di + 1] / H ** 2
                          - b[dj + 1, di + 1] * k2[j + 1 + dj, i + 1 + di]) * v
         assert abs(got[j, i] - want) <= 1e-10 * abs(want), (i, j)
+
+
+def test_red_o6_weights_and_sixth_order():
+    """ReD-O6 (Sec. 5.2.3): the printed weights, and on a smooth function
+    the rows at least three nodes inside converge at sixth order (error
+    ratio ~64 per halving of H; nodes nearer the boundary use ReD-O2)."""
+    g = load_golden("red_o4_cmpo4_stencils.txt")
+    w = g["o6_1d"][0] / g["o6_1d_scale"][0, 0]
+    assert abs(w.sum()) < 1e-14
+    # second moment of a second difference is 2 (d2/dx2 of x^2 / 2 ... = 1)
+    x = np.arange(-3, 4)
+    assert abs((w * x ** 2).sum() - 2.0) < 1e-13
+    assert abs((w * x ** 4).sum()) < 1e-12 and abs((w * x ** 6).sum()) < 1e-11
+    errs = []
+    for n in (33, 65, 129):
+        lv = _const_level(n, 5.0, ops.DIRICHLET)
+        xs = np.linspace(0.0, 1.0, n)
+        u = np.sin(np.pi * xs)[None, :] * np.sin(2 * np.pi * xs)[:, None]
+        got = lv.to_full(ops.red_o6(lv) @ lv.to_unknowns(u))
+        exact = (5 * np.pi ** 2 - 25.0) * u
+        inner = np.zeros((n, n), bool)
+        inner[3:-3, 3:-3] = True
+        errs.append(np.abs(got - exact)[inner].max())
+        # rows within two nodes of the boundary are the ReD-O2 rows
+        o2 = ops.five_point(lv)
+        for (i, j) in ((2, n // 2), (1, 1)):
+            np.testing.assert_allclose(_full_row(ops.red_o6(lv), lv, i, j),
+                                       _full_row(o2, lv, i, j), atol=1e-9)
+    assert errs[0] / errs[1] > 50 and errs[1] / errs[2] > 50, errs
+
+
+def test_red_9pt_coefficients_constraints_and_symbol():
+    """ReD-9ptO2 (Appendix B): the printed coefficients meet the appendix's
+    consistency constraints (a0 + 4 a_s + 4 a_c = 0, a_s + 2 a_c = -1,
+    b0 + 4 b_s + 4 b_c = 1) to the printed digits, and the operator on
+    Dirichlet sine modes equals the appendix's eigenvalue formula."""
+    g = load_golden("red_o4_cmpo4_stencils.txt")
+    a, b = ops.nine_point_o2_weights()
+    np.testing.assert_allclose(a, g["ninept_a"], atol=1e-15)
+    assert abs(a[1, 1] + 4 * a[1, 0] + 4 * a[0, 0]) < 1e-12
+    assert abs(a[1, 0] + 2 * a[0, 0] + 1.0) < 1e-12
+    assert abs(b.sum() - 1.0) < 1e-15
+    n, k = 33, 9.0
+    lv = _const_level(n, k, ops.DIRICHLET)
+    E = ops.red_9pt(lv)
+    H = lv.h
+    xs = np.linspace(0.0, 1.0, n)
+    for p, q in ((1, 2), (5, 5), (9, 14)):
+        u = np.sin(p * np.pi * xs)[None, :] * np.sin(q * np.pi * xs)[:, None]
+        cp, cq = np.cos(p * np.pi * H), np.cos(q * np.pi * H)
+        lam = ((a[1, 1] - b[1, 1] * k * k * H * H)
+               + 2 * (a[1, 0] - b[1, 0] * k * k * H * H) * (cp + cq)
+               + 4 * (a[0, 0] - b[0, 0] * k * k * H * H) * cp * cq) / H ** 2
+        np.testing.assert_allclose(E @ lv.to_unknowns(u), lam * lv.to_unknowns(u),
+                                   atol=1e-9 * abs(lam))
+
+
+def test_red_9pt_sommerfeld_uses_the_second_order_ghost_rule():
+    n, kk = 9, 6.0
+    lv = _const_level(n, kk, ops.SOMMERFELD)
+    E = ops.red_9pt(lv)
+    a, b = ops.nine_point_o2_weights()
+    H = lv.h
+    rng = np.random.default_rng(6)
+    u = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    ext = np.zeros((n + 2, n + 2), complex)
+    ext[1:-1, 1:-1] = u
+    c = 2j * kk * H
+    ext[1:-1, 0] = c * u[:, 0] + u[:, 1]
+    ext[1:-1, -1] = c * u[:, -1] + u[:, -2]
+    ext[0, 1:-1] = c * u[0, :] + u[1, :]
+    ext[-1, 1:-1] = c * u[-1, :] + u[-2, :]
+    for (gj, gi, bj, bi) in ((0, 0, 1, 1), (0, -1, 1, -2), (-1, 0, -2, 1),
+                             (-1, -1, -2, -2)):
+        ext[gj, gi] = 0.5 * (ext[gj, bi] + ext[bj, gi])
+    got = lv.to_full(E @ lv.to_unknowns(u))
+    for (i, j) in ((0, 4), (0, 0), (8, 8), (4, 4)):
+        want = 0.0
+        for dj in (-1, 0, 1):
+            for di in (-1, 0, 1):
+                inside = 0 <= i + di < n and 0 <= j + dj < n
+                k2nb = kk * kk if inside else 0.0
+                want += (a[dj + 1, di + 1] / H ** 2 - b[dj + 1, di + 1] * k2nb) \
+                    * ext[j + 1 + dj, i + 1 + di]
+        assert abs(got[j, i] - want) <= 1e-10 * abs(want), (i, j)
