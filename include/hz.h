@@ -64,7 +64,11 @@ typedef enum { HZ_Z_NONE = 0, HZ_Z_BILINEAR = 1, HZ_Z_HO = 2 } hz_zkind;
  * Sommerfeld ghosts (ReD-cmpO4, Sec. 5.2.5, gamma = 1). */
 typedef enum {
   HZ_E_GALERKIN = 0, HZ_E_RED_O2 = 1, HZ_E_RED_GLK1 = 2, HZ_E_RED_GLK2 = 3,
-  HZ_E_RED_O4 = 4, HZ_E_RED_CMPO4 = 5
+  HZ_E_RED_O4 = 4, HZ_E_RED_CMPO4 = 5,
+  HZ_E_RED_O6 = 6,  /* sixth-order cross (Sec. 5.2.3), ReD-O2 rows within two
+                       nodes of the boundary                                */
+  HZ_E_RED_9PT = 7  /* ReD-9ptO2 (Appendix B): the fitted compact 3x3
+                       scheme, 2nd-order Sommerfeld ghosts                 */
 } hz_ekind;
 
 /* Arithmetic of the preconditioner (V-cycle, deflation, inner coarse

@@ -15,7 +15,7 @@ from ._lib import HzDesc, HzSolveInfo, HzTuning, STATUS, load_library
 BC = {"dirichlet": 0, "sommerfeld": 1}
 ZKIND = {None: 0, "none": 0, "bilinear": 1, "ho": 2}
 EKIND = {"galerkin": 0, "red_o2": 1, "red_glk1": 2, "red_glk2": 3,
-         "red_o4": 4, "red_cmpo4": 5}
+         "red_o4": 4, "red_cmpo4": 5, "red_o6": 6, "red_9pt": 7}
 PREC = {"fp64": 0, "mixed": 1, "mixed_bf16": 2}
 OUTER = {"fgmres": 0, "gcr": 1}
 PRECOND = {"adef1": 0, "tlkm": 1}

@@ -249,6 +249,13 @@ void launch_red_o4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
 template <class T>
 void launch_red_cmpo4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
                       const int* done, cudaStream_t st);
+// ReD-O6 (sixth-order cross) and ReD-9ptO2 (Appendix B compact scheme)
+template <class T>
+void launch_red_o6(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                   const int* done, cudaStream_t st);
+template <class T>
+void launch_red_9pt(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                    const int* done, cudaStream_t st);
 // y = E_glk x on level 1 (variant 1 or 2)
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
@@ -331,14 +338,12 @@ void launch_reduce_norm(const KState& ks, long long n, int nrhs, double* out,
                         int sqrt_it, cudaStream_t st);
 void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
                         const double* bnorm_src, double tol, cudaStream_t st);
-// out = w / s[r], stored as SB
+// out = w / s[r], stored as SB (and, if copy is not null, also as C<T> in
+// copy [nrhs][n])
 template <class T, class SB>
 void launch_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* s,
-                       long long n, int nrhs, const int* done, cudaStream_t st);
-// out = basis vector v (stored as SB) in compute type T
-template <class SB, class T>
-void launch_basis_load(VRefE<SB> v, long long rs, C<T>* out, long long n, int nrhs,
-                       const int* done, cudaStream_t st);
+                       long long n, int nrhs, const int* done, cudaStream_t st,
+                       C<T>* copy = nullptr);
 void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
                    cudaStream_t st);
 void launch_trisolve(const KState& ks, int nrhs, cudaStream_t st);

@@ -1003,7 +1003,7 @@ __global__ void k_krylov_init(KState ks, int nrhs, const int* done_in,
 template <class T, class SB>
 __global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
                              const double* __restrict__ s, long long n,
-                             const int* __restrict__ done) {
+                             const int* __restrict__ done, C<T>* __restrict__ copy) {
   const int r = blockIdx.y;
   if (done && done[r]) return;
   // one FP64 reciprocal per block (FP64 division is slow on this GPU)
@@ -1018,21 +1018,16 @@ __global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
   SB* orow = out.get() + r * rs;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
        e += (long long)gridDim.x * blockDim.x)
-    st2(orow, e, f * wr[e]);
+  {
+    // the stored (rounded) value, also kept in compute precision as the
+    // V-cycle's input of the next step
+    SB sv;
+    st2(&sv, 0, f * wr[e]);
+    orow[e] = sv;
+    if (copy) copy[r * n + e] = ld2(&sv, 0);
+  }
   // the padding of the row reads as zero in the group loads
   if (blockIdx.x == 0 && threadIdx.x < rs - n) st2(orow, n + threadIdx.x, czero<T>());
-}
-
-template <class SB, class T>
-__global__ void k_basis_load(VRefE<SB> v, long long rs, C<T>* __restrict__ out,
-                             long long n, const int* __restrict__ done) {
-  const int r = blockIdx.y;
-  if (done && done[r]) return;
-  const SB* vr = v.get() + r * rs;
-  C<T>* orow = out + r * n;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x)
-    orow[e] = ld2(vr, e);
 }
 
 // Apply the previous rotations to column j, build the rotation that
@@ -1048,11 +1043,17 @@ __global__ void k_givens(KState ks, double tol, int maxit) {
   const int j = *ks.jctr;
   const int m = ks.m;
   double2* Hc = ks.H + (long long)r * (m + 1) * m + j;  // H[r][i][j] = Hc[i*m]
+  // the previous rotations are staged too, so the sequential chain below
+  // reads shared memory only
+  double2* sn = col + (m + 2);                                  // j entries
+  double* cs = reinterpret_cast<double*>(sn + m);               // j entries
   for (int i = threadIdx.x; i <= j; i += blockDim.x) col[i] = Hc[(long long)i * m];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    cs[i] = ks.cs[(long long)r * m + i];
+    sn[i] = ks.sn[(long long)r * m + i];
+  }
   __syncthreads();
   if (threadIdx.x != 0) return;
-  const double* cs = ks.cs + (long long)r * m;
-  const double2* sn = ks.sn + (long long)r * m;
   double2 a = col[0];
   for (int i = 0; i < j; ++i) {
     const double2 b = col[i + 1];
@@ -1455,24 +1456,26 @@ void launch_krylov_init(const KState& ks, int nrhs, const int* done_in,
 }
 template <class T, class SB>
 void launch_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* s,
-                       long long n, int nrhs, const int* done, cudaStream_t st) {
+                       long long n, int nrhs, const int* done, cudaStream_t st,
+                       C<T>* copy) {
   HZ_COUNT();
   long long nb = (n + 255) / 256;
   if (nb > 2048) nb = 2048;
-  k_scale_into<T, SB><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, rs, s, n, done);
-}
-template <class SB, class T>
-void launch_basis_load(VRefE<SB> v, long long rs, C<T>* out, long long n, int nrhs,
-                       const int* done, cudaStream_t st) {
-  HZ_COUNT();
-  long long nb = (n + 255) / 256;
-  if (nb > 2048) nb = 2048;
-  k_basis_load<SB, T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(v, rs, out, n, done);
+  k_scale_into<T, SB><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, rs, s, n, done,
+                                                                copy);
 }
 void launch_givens(const KState& ks, int nrhs, double tol, int maxit,
                    cudaStream_t st) {
   HZ_COUNT();
-  k_givens<<<nrhs, 128, (size_t)(ks.m + 2) * sizeof(double2), st>>>(ks, tol, maxit);
+  const size_t smem = (size_t)(ks.m + 2) * sizeof(double2) +
+                      (size_t)ks.m * (sizeof(double2) + sizeof(double));
+  static std::once_flag once;
+  std::call_once(once, [] {
+    // the largest basis (3000 columns) needs 120 KB
+    cudaFuncSetAttribute((const void*)k_givens, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(3002 * sizeof(double2) + 3000 * (sizeof(double2) + sizeof(double))));
+  });
+  k_givens<<<nrhs, 128, smem, st>>>(ks, tol, maxit);
   HZ_COUNT();
   k_givens_finish<<<1, 1024, 0, st>>>(ks, nrhs);
 }
@@ -1549,9 +1552,7 @@ void launch_copy_int(const int* src, int* dst, int count, cudaStream_t st) {
                                     cudaStream_t);                              \
   template void launch_scale_into<T, SB>(VRef<T>, VRefE<SB>, long long,         \
                                          const double*, long long, int,         \
-                                         const int*, cudaStream_t);             \
-  template void launch_basis_load<SB, T>(VRefE<SB>, long long, C<T>*, long long, \
-                                         int, const int*, cudaStream_t);        \
+                                         const int*, cudaStream_t, C<T>*);      \
   template void launch_update<SB, T>(const SB*, long long, long long,           \
                                      const KState&, C<T>*, int, long long, int, \
                                      cudaStream_t);                             \

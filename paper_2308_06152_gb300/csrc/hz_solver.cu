@@ -84,7 +84,7 @@ bool valid_desc(const hz_desc* d, std::string* why) {
   if (!(d->h > 0)) { *why = "h must be positive"; return false; }
   if (d->bc != HZ_BC_DIRICHLET && d->bc != HZ_BC_SOMMERFELD) { *why = "bad bc"; return false; }
   if (d->zkind < HZ_Z_NONE || d->zkind > HZ_Z_HO) { *why = "bad zkind"; return false; }
-  if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_CMPO4) { *why = "bad ekind"; return false; }
+  if (d->ekind < HZ_E_GALERKIN || d->ekind > HZ_E_RED_9PT) { *why = "bad ekind"; return false; }
   if (d->prec < HZ_PREC_FP64 || d->prec > HZ_PREC_MIXED_BF16) { *why = "bad prec"; return false; }
   if (d->nrhs_max < 1 || d->nrhs_max > kMaxRhs) { *why = "nrhs_max must be in 1..1024"; return false; }
   if (d->outer_maxit < 1 || d->coarse_maxit < 1 || d->outer_maxit > kMaxIters ||
@@ -465,6 +465,12 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
     case HZ_E_RED_CMPO4:
       launch_red_cmpo4<T>(Cc.dev(), bc, x, y, nrhs, done, st);
       break;
+    case HZ_E_RED_O6:
+      launch_red_o6<T>(Cc.dev(), bc, x, y, nrhs, done, st);
+      break;
+    case HZ_E_RED_9PT:
+      launch_red_9pt<T>(Cc.dev(), bc, x, y, nrhs, done, st);
+      break;
     default:
       launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st);
       break;
@@ -585,8 +591,7 @@ void inner_pre(hz_solver* s, int nrhs) {
     const long long rs = inner_row(n1);
     const long long vs = (long long)s->d.nrhs_max * rs;
     const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
-    launch_basis_load<SB, T>(vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs), rs, (C<T>*)s->qf,
-                             n1, nrhs, ks.done, s->st);
+    // s->qf holds v_j in compute precision (written with the basis vector)
     apply_E<T>(s, (const C<T>*)s->qf, (C<T>*)s->sb, nrhs, ks.done);
     vcycle<T>(s, 1, vref<T>((C<T>*)s->sb), (C<T>*)s->eb, nrhs, ks.done);
     launch_prolong_z<T>(F, Cc, s->d.bc, s->d.zkind, (const C<T>*)s->eb, (C<T>*)s->q, 0,
@@ -599,10 +604,8 @@ void inner_pre(hz_solver* s, int nrhs) {
   const long long rs = inner_row(n1);
   const long long vs = (long long)s->d.nrhs_max * rs;
   C<T>* sb = (C<T>*)s->sb;
-  // the V-cycle reads the current basis vector, unpadded, in compute
-  // precision
-  launch_basis_load<SB, T>(vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs), rs, (C<T>*)s->qf,
-                           n1, nrhs, ks.done, s->st);
+  // the V-cycle reads the current basis vector in compute precision, which
+  // the scaling step left in s->qf next to its stored copy
   vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
   apply_E<T>(s, sb, (C<T>*)s->eb, nrhs, ks.done);
 }
@@ -616,7 +619,7 @@ void inner_post(hz_solver* s, int nrhs) {
   launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, s->st);
   debug_trace(s, ks, "inner");
   launch_scale_into<T, SB>(vref<T>((C<T>*)s->eb), vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs),
-                           rs, ks.hnorm, n1, nrhs, ks.done, s->st);
+                           rs, ks.hnorm, n1, nrhs, ks.done, s->st, (C<T>*)s->qf);
 }
 template <class T, class SB>
 void inner_step(hz_solver* s, int nrhs) {
@@ -692,7 +695,7 @@ void coarse_begin(hz_solver* s, const C<T>* v1, int nrhs, const int* done_in) {
   launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
   launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, st);
   launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>((SB*)s->Qb), inner_row(n1), ks.hnorm,
-                           n1, nrhs, ks.done, st);
+                           n1, nrhs, ks.done, st, (C<T>*)s->qf);
 }
 // x = Q_k y (k the iterations taken), then v2 = M_2h^-1 x (right
 // preconditioning)

@@ -416,23 +416,59 @@ __global__ void k_red_o4(LevelDev L, int bc, const C<T>* __restrict__ x,
   y[r * n + id] = acc;
 }
 
+// ReD-O6 (Sec. 5.2.3): the sixth-order cross (2 -27 270 -490 270 -27 2) /
+// (180 H^2) along x and y, negated, minus k^2 of the node, where the cross
+// stays inside the grid; nodes within two nodes of the boundary use ReD-O2.
+template <class T>
+__global__ void k_red_o6(LevelDev L, int bc, const C<T>* __restrict__ x,
+                         C<T>* __restrict__ y, const int* __restrict__ done) {
+  const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
+  const int r = blockIdx.z;
+  if (i >= L.nx || j >= L.ny || (done && done[r])) return;
+  const int nx = L.nx, ny = L.ny;
+  const long long n = (long long)nx * ny, id = (long long)j * nx + i;
+  const C<T>* xr = x + r * n;
+  if (bc == BC_DIRICHLET && on_bnd(i, j, nx, ny)) {
+    y[r * n + id] = czero<T>();
+    return;
+  }
+  if (min(min(i, nx - 1 - i), min(j, ny - 1 - j)) <= 2) {
+    y[r * n + id] = helm_point<T>(L, bc, T(1), T(0), xr, i, j);
+    return;
+  }
+  auto xv = [&](int a, int b) {
+    if (bc == BC_DIRICHLET && on_bnd(a, b, nx, ny)) return czero<T>();
+    return xr[(long long)b * nx + a];
+  };
+  const T s = ih2_of<T>(L) / T(180);
+  const T k2 = k2_of<T>(L)[id];
+  C<T> acc = (T(980) * s - k2) * xr[id];
+  acc = rfma(T(-270) * s, (xv(i - 1, j) + xv(i + 1, j)) + (xv(i, j - 1) + xv(i, j + 1)), acc);
+  acc = rfma(T(27) * s, (xv(i - 2, j) + xv(i + 2, j)) + (xv(i, j - 2) + xv(i, j + 2)), acc);
+  acc = rfma(T(-2) * s, (xv(i - 3, j) + xv(i + 3, j)) + (xv(i, j - 3) + xv(i, j + 3)), acc);
+  y[r * n + id] = acc;
+}
+
 // ReD-cmpO4 (Sec. 5.2.5): the compact 3x3 stencil [a] / H^2 - [b] k^2 of
 // eq. (GeneralFormReD) with the Singer-Turkel weights (gamma = 1), each
 // mass entry with its own node's k^2.  Under Sommerfeld rows the ghost
 // layer is u_g = 2 i k H (1 - k^2 H^2 / 6) u_b + u_in (k of the boundary
 // node, ghost k^2 = 0), a corner ghost the average of its two neighbouring
 // edge ghosts; Dirichlet boundary nodes hold zero.
-template <class T>
+// The same kernel serves ReD-9ptO2 (Appendix B; SCHEME 1): a = (4.632,
+// -1.316, 0.158), b = (1, 0, 0), with the 2nd-order ghost rule of eq.
+// (GhostPoint), u_g = 2 i k H u_b + u_in.
+template <class T, int SCHEME>
 __device__ __forceinline__ C<T> cmp_edge_ghost(const LevelDev& L, const C<T>* xr, int bi,
                                                int bj, int ii, int ij) {
   const long long b = (long long)bj * L.nx + bi;
   const T k = sqrt(k2_of<T>(L)[b]);
   const T H = T(L.h);
-  const T c = T(2) * k * H * (T(1) - k * k * H * H / T(6));
+  const T c = SCHEME == 0 ? T(2) * k * H * (T(1) - k * k * H * H / T(6)) : T(2) * k * H;
   const C<T> ub = xr[b];
   return mkc(-c * ub.y, c * ub.x) + xr[(long long)ij * L.nx + ii];
 }
-template <class T>
+template <class T, int SCHEME>
 __device__ __forceinline__ C<T> cmp_node(const LevelDev& L, int bc, const C<T>* xr,
                                          int i, int j) {
   const int nx = L.nx, ny = L.ny;
@@ -446,13 +482,13 @@ __device__ __forceinline__ C<T> cmp_node(const LevelDev& L, int bc, const C<T>* 
   const int bj = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
   const int ii = i < 0 ? 1 : (i >= nx ? nx - 2 : i);
   const int ij = j < 0 ? 1 : (j >= ny ? ny - 2 : j);
-  if (gx && !gy) return cmp_edge_ghost<T>(L, xr, bi, j, ii, j);
-  if (!gx && gy) return cmp_edge_ghost<T>(L, xr, i, bj, i, ij);
+  if (gx && !gy) return cmp_edge_ghost<T, SCHEME>(L, xr, bi, j, ii, j);
+  if (!gx && gy) return cmp_edge_ghost<T, SCHEME>(L, xr, i, bj, i, ij);
   // corner: average of the y ghost of (bi, .) and the x ghost of (., bj)
-  return T(0.5) * (cmp_edge_ghost<T>(L, xr, bi, bj, bi, ij) +
-                   cmp_edge_ghost<T>(L, xr, bi, bj, ii, bj));
+  return T(0.5) * (cmp_edge_ghost<T, SCHEME>(L, xr, bi, bj, bi, ij) +
+                   cmp_edge_ghost<T, SCHEME>(L, xr, bi, bj, ii, bj));
 }
-template <class T>
+template <class T, int SCHEME>
 __global__ void k_red_cmpo4(LevelDev L, int bc, const C<T>* __restrict__ x,
                             C<T>* __restrict__ y, const int* __restrict__ done) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
@@ -467,9 +503,12 @@ __global__ void k_red_cmpo4(LevelDev L, int bc, const C<T>* __restrict__ x,
   }
   const T ih2 = ih2_of<T>(L);
   const T* k2 = k2_of<T>(L);
-  const T a0 = T(10) / T(3), as = T(-2) / T(3), ac = T(-1) / T(6);
-  const T b0 = T(2) / T(3) + T(1) / T(36), bs = T(1) / T(12) - T(1) / T(72),
-          bc_ = T(1) / T(144);
+  const T a0 = SCHEME == 0 ? T(10) / T(3) : T(4.632);
+  const T as = SCHEME == 0 ? T(-2) / T(3) : T(-1.316);
+  const T ac = SCHEME == 0 ? T(-1) / T(6) : T(0.158);
+  const T b0 = SCHEME == 0 ? T(2) / T(3) + T(1) / T(36) : T(1);
+  const T bs = SCHEME == 0 ? T(1) / T(12) - T(1) / T(72) : T(0);
+  const T bc_ = SCHEME == 0 ? T(1) / T(144) : T(0);
   C<T> acc = czero<T>();
   for (int dj = -1; dj <= 1; ++dj)
     for (int di = -1; di <= 1; ++di) {
@@ -479,7 +518,7 @@ __global__ void k_red_cmpo4(LevelDev L, int bc, const C<T>* __restrict__ x,
       const int d = abs(di) + abs(dj);
       const T wa = d == 0 ? a0 : (d == 1 ? as : ac);
       const T wb = d == 0 ? b0 : (d == 1 ? bs : bc_);
-      acc = rfma(wa * ih2 - wb * kk, cmp_node<T>(L, bc, xr, a, b), acc);
+      acc = rfma(wa * ih2 - wb * kk, cmp_node<T, SCHEME>(L, bc, xr, a, b), acc);
     }
   y[r * n + id] = acc;
 }
@@ -865,7 +904,19 @@ template <class T>
 void launch_red_cmpo4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
                       const int* done, cudaStream_t st) {
   HZ_COUNT();
-  k_red_cmpo4<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
+  k_red_cmpo4<T, 0><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
+}
+template <class T>
+void launch_red_9pt(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                    const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_red_cmpo4<T, 1><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
+}
+template <class T>
+void launch_red_o6(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
+                   const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  k_red_o6<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, x, y, done);
 }
 template <class T>
 void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
@@ -952,6 +1003,10 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                                  const int*, cudaStream_t);                     \
   template void launch_red_cmpo4<T>(const LevelDev&, int, const C<T>*, C<T>*,   \
                                     int, const int*, cudaStream_t);             \
+  template void launch_red_9pt<T>(const LevelDev&, int, const C<T>*, C<T>*,     \
+                                  int, const int*, cudaStream_t);               \
+  template void launch_red_o6<T>(const LevelDev&, int, const C<T>*, C<T>*, int, \
+                                 const int*, cudaStream_t);                     \
   template void launch_probe_extract<T>(const LevelDev&, int, int, int,         \
                                         const double2*, C<T>*, cudaStream_t);   \
   template void launch_stencil_e<T>(const LevelDev&, int, const C<T>*,          \

@@ -107,6 +107,34 @@ def test_workspace_bytes_host_logic(lib):
     assert _ws(lib, nx=2305, ny=769, h=4.0)[0] == 0
 
 
+def test_workspace_bytes_checks_method_choices(lib):
+    """The coarse operator, outer iteration and preconditioner fields are
+    validated on the host; TLKM needs deflation vectors, and each optional
+    buffer only costs workspace when its choice is made."""
+    _, base = _ws(lib)
+    for ek in range(8):
+        assert _ws(lib, ekind=ek)[0] == 0, ek
+    assert _ws(lib, ekind=8)[0] == 1
+    assert _ws(lib, outer_solver=1)[0] == 0
+    assert _ws(lib, outer_solver=2)[0] == 1
+    assert _ws(lib, preconditioner=1)[0] == 0
+    assert _ws(lib, preconditioner=2)[0] == 1
+    assert _ws(lib, preconditioner=1, zkind=0)[0] == 1
+    # GCR keeps a residual vector; TLKM a fine-grid scratch vector;
+    # the stored Galerkin stencil is only planned for the Galerkin E
+    assert _ws(lib, outer_solver=1)[1] > base
+    assert _ws(lib, preconditioner=1)[1] > base
+    assert _ws(lib, ekind=1)[1] < base
+
+
+def test_tuning_defaults(lib):
+    t = _lib.HzTuning()
+    lib.hz_tuning_default(ctypes.byref(t))
+    assert [getattr(t, f) for f, _ in t._fields_] == [0] * len(t._fields_)
+    assert lib.hz_set_tuning(None, ctypes.byref(t)) == 1
+    assert lib.hz_get_tuning(None, ctypes.byref(t)) == 1
+
+
 def test_status_strings(lib):
     for code in range(9):
         assert lib.hz_status_str(code)

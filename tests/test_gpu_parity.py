@@ -87,7 +87,7 @@ def test_level_operators(bc, prec, tol):
 @pytest.mark.parametrize("bc", BCS)
 @pytest.mark.parametrize("z", ["bilinear", "ho"])
 @pytest.mark.parametrize("e", ["galerkin", "red_o2", "red_glk1", "red_glk2",
-                               "red_o4", "red_cmpo4"])
+                               "red_o4", "red_cmpo4", "red_o6", "red_9pt"])
 def test_deflation_operators(bc, z, e):
     k2 = rk2(NY, NX, 2)
     s = solver(NX, NY, H, k2, bc, z=z, e=e)
@@ -277,6 +277,8 @@ def test_config1_fp64_iterations_and_residual():
                                     ("sommerfeld", "ho", "red_o4"),
                                     ("sommerfeld", "ho", "red_cmpo4"),
                                     ("dirichlet", "bilinear", "red_cmpo4"),
+                                    ("sommerfeld", "ho", "red_o6"),
+                                    ("sommerfeld", "ho", "red_9pt"),
                                     ("sommerfeld", None, "galerkin")])
 def test_solve_parity_tight(bc, z, e):
     """At tight tolerances GPU and oracle solutions agree to 1e-8."""
@@ -553,8 +555,10 @@ def test_gradient_group_equals_separate_gradients():
     oracle's sparse-LU gradient (1e-7)."""
     from paper_2308_06152_gb300.api import gradient_group
     cases = []
-    for (nx, ny, h, omega, nsh, seed) in ((17, 13, 1 / 16, 25.0, 3, 31),
-                                          (25, 33, 1 / 24, 30.0, 5, 32)):
+    # kh <= 0.8: the resolved regime of the method (an under-resolved
+    # problem would need ~70 outer iterations per solve)
+    for (nx, ny, h, omega, nsh, seed) in ((17, 13, 1 / 16, 10.0, 3, 31),
+                                          (25, 33, 1 / 24, 14.0, 5, 32)):
         rng = np.random.default_rng(seed)
         m = rng.uniform(0.7, 1.3, size=(ny, nx))
         nodes = [(1 + (3 * s) % (nx - 2), 1 + s % 3) for s in range(nsh)]
@@ -646,7 +650,7 @@ def test_autograd_gradient_matches_central_differences():
     along random directions and single interior / edge / corner nodes."""
     from paper_2308_06152_gb300.api import Desc
     from paper_2308_06152_gb300.autograd import misfit
-    nx, ny, h, omega = 17, 13, 1.0 / 16, 25.0
+    nx, ny, h, omega = 17, 13, 1.0 / 16, 10.0
     rng = np.random.default_rng(21)
     m = torch.tensor(rng.uniform(0.7, 1.3, size=(ny, nx)), device="cuda",
                      requires_grad=True)
