@@ -44,12 +44,17 @@ class Oracle:
     exact coarsest solve is wanted for tight comparisons).
     ``precond``: 'adef1' (A-DEF1 / APD, eq. ADEF1) or 'tlkm' (the practical
     TLKM preconditioner of Sec. 3.2.2 with the coarse system of Sec. 5.2).
+    ``deflation_levels``: 1 (the paper's two-level method) or 2 (the
+    level-1 coarse system solved by flexible GMRES with A-DEF1 built from
+    it, deflating to level 2 with ``e2``: 'red_glk2' (default), 'red_o2' or
+    'galerkin' = R_1 E Z_1; the multilevel direction of Sec. 1 / Sec. 7).
     """
 
     def __init__(self, nx, ny, h, k2, bc, z="ho", e="galerkin",
                  beta=(1.0, -0.5), omega=0.8, min_coarse_intervals=2,
                  coarsest="gmres", coarsest_tol=1e-8, coarse_tol=1e-6,
-                 coarse_maxit=3000, precond="adef1"):
+                 coarse_maxit=3000, precond="adef1", deflation_levels=1,
+                 e2="red_glk2"):
         self.levels = ops.build_levels(nx, ny, h, k2, bc,
                                        min_coarse_intervals)
         self.L = len(self.levels) - 1
@@ -96,6 +101,25 @@ class Oracle:
                 self.E = ops.red_9pt(self.levels[1])
             else:
                 raise ValueError(e)
+        # multilevel deflation: the level-1 coarse system deflated again
+        self.deflation_levels = deflation_levels
+        if deflation_levels not in (1, 2):
+            raise ValueError("deflation_levels must be 1 or 2")
+        if deflation_levels == 2:
+            if z is None or self.L < 2 or precond != "adef1":
+                raise ValueError("three-level deflation needs Z, A-DEF1 and "
+                                 "two coarsenings")
+            l1, l2 = self.levels[1], self.levels[2]
+            self.Z1 = ops.prolongation(l1, l2, z)
+            self.R1 = ops.restriction(self.Z1)
+            if e2 == "galerkin":
+                self.E2 = (self.R1 @ self.E @ self.Z1).tocsr()
+            elif e2 == "red_glk2":
+                self.E2 = ops.red_glk(l2, 2)
+            elif e2 == "red_o2":
+                self.E2 = ops.red_o2(l2)
+            else:
+                raise ValueError(e2)
 
     # ---- CSLP multigrid V-cycle (Sec. 3.1) -------------------------------
     def coarsest_solve(self, f):
@@ -122,13 +146,32 @@ class Oracle:
     # ---- deflation (Sec. 3.2, 5.2) ----------------------------------------
     def coarse_solve(self, v1, tol=None, maxit=None):
         """E v2 = v1 by GMRES right-preconditioned with the V-cycle on the
-        coarse CSLP (levels 1..L), x0 = 0."""
+        coarse CSLP (levels 1..L), x0 = 0.  With three-level deflation the
+        preconditioner is A-DEF1 of the coarse system itself (adef1_level1),
+        which contains an inexact solve, so the GMRES is flexible."""
         tol = self.coarse_tol if tol is None else tol
         maxit = self.coarse_maxit if maxit is None else maxit
-        res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
-                          prec=lambda v: self.vcycle(v, 1))
+        if self.deflation_levels == 2:
+            res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
+                              prec=self.adef1_level1, flexible=True)
+        else:
+            res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
+                              prec=lambda v: self.vcycle(v, 1))
         self.inner_log.append(res.iters)
         return res.x
+
+    def coarse_solve_level2(self, v):
+        """E_2 v2 = v (level 2) by GMRES right-preconditioned with the
+        V-cycle on the CSLP from level 2, x0 = 0, to the coarse tolerance."""
+        res = gmres_right(lambda u: self.E2 @ u, v, self.coarse_tol,
+                          self.coarse_maxit, prec=lambda u: self.vcycle(u, 2))
+        return res.x
+
+    def adef1_level1(self, v):
+        """A-DEF1 for the level-1 coarse system E (eq. ADEF1 one level
+        down): M_1^-1 (v - E q) + q with q = Z_1 E_2^-1 R_1 v."""
+        q = self.Z1 @ self.coarse_solve_level2(self.R1 @ v)
+        return self.vcycle(v - self.E @ q, 1) + q
 
     def deflation_Q(self, v):
         """Q v = Z E^{-1} R v with the inexact coarse solve (Sec. 5.2)."""

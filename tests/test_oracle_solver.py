@@ -222,6 +222,35 @@ def test_table_b1_ordering_of_re_discretised_coarse_operators():
     assert its["red_o4"] <= its["red_9pt"] < its["red_o2"], its
 
 
+def test_three_level_deflation_invariant_and_direct_solution():
+    """Three-level deflation: with the Galerkin level-2 operator and an
+    exact level-2 solve, A-DEF1 of the level-1 system deflates its coarse
+    space exactly (P_1 E Z_1 = Z_1, the eq. ADEF1 identity one level down);
+    with ReD-Glk2 at level 2 the whole solve still reaches the direct
+    solution."""
+    n = 17
+    k2 = _k2(n, n, 5, lo=6, hi=12)
+    orc = Oracle(n, n, 1 / 16, k2, ops.SOMMERFELD, z="ho", coarsest="direct",
+                 coarse_tol=1e-13, coarse_maxit=200, deflation_levels=2,
+                 e2="galerkin")
+    Z1 = orc.Z1.tocsc()
+    for j in (0, Z1.shape[1] // 2, Z1.shape[1] - 1):
+        zj = Z1[:, j].toarray().ravel().astype(complex)
+        out = orc.adef1_level1(orc.E @ zj)
+        assert np.linalg.norm(out - zj) <= 1e-9 * np.linalg.norm(zj), j
+    for n, bc, z, kmax in ((17, ops.SOMMERFELD, "ho", 8.0),
+                           (33, ops.DIRICHLET, "bilinear", 20.0)):
+        k2 = _k2(n, n, 5, lo=0.4 * kmax, hi=kmax)
+        orc = Oracle(n, n, 1.0 / (n - 1), k2, bc, z=z, coarse_tol=1e-8,
+                     deflation_levels=2)
+        rng = np.random.default_rng(12)
+        b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        x, info = orc.solve(b, tol=1e-11, maxit=200)
+        lv = orc.levels[0]
+        xd = lv.to_full(spla.spsolve(orc.A.tocsc(), lv.to_unknowns(b)))
+        assert info.converged and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
 def test_gmres_lucky_breakdown_identity():
     b = np.arange(1, 6) + 0j
     res = gmres_right(lambda v: 3.0 * v, b, 1e-14, 10)
