@@ -119,6 +119,16 @@ typedef struct {
   int outer_solver;           /* HZ_OUTER_FGMRES (default) or HZ_OUTER_GCR  */
   int preconditioner;         /* HZ_PRECOND_ADEF1 (default) or HZ_PRECOND_TLKM
                                  (needs zkind != HZ_Z_NONE)                 */
+  int deflation_levels;       /* 0 or 1 (default): the paper's two-level
+                                 method.  2: three-level deflation (the
+                                 multilevel direction of Sec. 1 / 7, our
+                                 reading): the level-1 coarse system is
+                                 solved by flexible GMRES preconditioned by
+                                 A-DEF1 built from it, with ReD-Glk2 at level
+                                 2 solved by V-cycle-preconditioned GMRES to
+                                 coarse_tol; needs deflation vectors, A-DEF1
+                                 and two coarsenings; issued without CUDA
+                                 graphs; not in groups.                     */
   int no_cuda_graph;          /* 0 (default): each outer iteration of hz_solve
                                  runs as one CUDA graph launch whose inner
                                  coarse-solve loop is a device-side WHILE

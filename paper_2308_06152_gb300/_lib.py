@@ -25,6 +25,7 @@ class HzDesc(ctypes.Structure):
                 ("inner_basis_fp16", c_int),
                 ("outer_solver", c_int),
                 ("preconditioner", c_int),
+                ("deflation_levels", c_int),
                 ("no_cuda_graph", c_int)]
 
 

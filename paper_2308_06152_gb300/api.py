@@ -54,6 +54,7 @@ class Desc:
     inner_basis_fp16: bool = False
     outer: str = "fgmres"
     precond: str = "adef1"
+    deflation_levels: int = 1
     cuda_graph: bool = True
 
     def to_c(self):
@@ -73,6 +74,7 @@ class Desc:
         d.inner_basis_fp16 = int(bool(self.inner_basis_fp16))
         d.outer_solver = OUTER[self.outer]
         d.preconditioner = PRECOND[self.precond]
+        d.deflation_levels = int(self.deflation_levels)
         d.no_cuda_graph = int(not self.cuda_graph)
         return d
 

@@ -270,6 +270,10 @@ void launch_mask_dirichlet(const LevelDev& L, int bc, C<T>* x, int nrhs,
 template <class Ti, class To>
 void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
                      int nrhs, const int* done, cudaStream_t st);
+// out = a - b
+template <class T>
+void launch_sub(const C<T>* a, const C<T>* b, C<T>* out, long long n, int nrhs,
+                const int* done, cudaStream_t st);
 // out = a - b + c, widened to FP64
 template <class T>
 void launch_sub_add_widen(const C<T>* a, const C<T>* b, const C<T>* c, VRef<double> out,

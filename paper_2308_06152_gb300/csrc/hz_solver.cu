@@ -106,6 +106,12 @@ bool valid_desc(const hz_desc* d, std::string* why) {
     *why = "TLKM needs deflation vectors";
     return false;
   }
+  if (d->deflation_levels < 0 || d->deflation_levels > 2 ||
+      (d->deflation_levels == 2 &&
+       (d->zkind == HZ_Z_NONE || d->preconditioner != HZ_PRECOND_ADEF1))) {
+    *why = "deflation_levels must be 0/1, or 2 with deflation vectors and A-DEF1";
+    return false;
+  }
   return true;
 }
 
@@ -143,6 +149,13 @@ struct hz_solver {
   void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
   void* qf = nullptr;      // current basis vector in compute precision (FP16 basis)
   void* Sglk = nullptr;    // stcl-op-Glk coefficient planes [P*P][n1] (Galerkin E)
+  // three-level deflation: level-1 flexible directions and work vectors,
+  // the level-2 Krylov state, basis and vectors (all compute precision)
+  bool ml = false;
+  void *Z1b = nullptr, *zj = nullptr, *q1 = nullptr, *u1 = nullptr;
+  void *v1_2 = nullptr, *v2_2 = nullptr, *sb2 = nullptr, *eb2 = nullptr, *qf2 = nullptr,
+       *Q2 = nullptr;
+  KState kin2{};
   bool basis16 = false;    // inner Krylov basis stored as FP16 pairs
   KState kin{}, kout{};
   int* in_total = nullptr;
@@ -288,6 +301,20 @@ void plan(hz_solver* s, Arena& a) {
       const int P = d.zkind == HZ_Z_HO ? 5 : 3;
       s->Sglk = a.take(es * (size_t)P * P * n1);
     }
+    if (s->ml) {
+      const long long n2 = s->lv[2].n;
+      s->Z1b = a.take(es * (size_t)B * n1 * d.coarse_maxit);
+      s->zj = a.take(es * B * n1);
+      s->q1 = a.take(es * B * n1);
+      s->u1 = a.take(es * B * n1);
+      s->v1_2 = a.take(es * B * n2);
+      s->v2_2 = a.take(es * B * n2);
+      s->sb2 = a.take(es * B * n2);
+      s->eb2 = a.take(es * B * n2);
+      s->qf2 = a.take(es * B * n2);
+      s->Q2 = a.take(es * (size_t)B * inner_row(n2) * (d.coarse_maxit + 1));
+      s->kin2 = plan_kstate(a, B, d.coarse_maxit, n2);
+    }
   }
   s->in_total = (int*)a.take(sizeof(int) * B);
   s->in_max = (int*)a.take(sizeof(int) * B);
@@ -311,6 +338,9 @@ void plan(hz_solver* s, Arena& a) {
   s->fault = (int*)a.take(sizeof(int));
   s->kin.fault = s->fault;
   s->kout.fault = s->fault;
+  s->kin2.fault = s->fault;
+  s->kin2.dotk = s->tune.mdot_kernel;
+  s->kin2.updk = s->tune.maxpy_kernel;
   s->kin.dotk = s->kout.dotk = s->tune.mdot_kernel;
   s->kin.updk = s->kout.updk = s->tune.maxpy_kernel;
 }
@@ -344,6 +374,11 @@ hz_status init_shapes(hz_solver* s) {
   s->esz = s->mixed ? sizeof(float2) : sizeof(double2);
   s->lsz = s->lvbf16 ? sizeof(__nv_bfloat162) : s->esz;
   s->basis16 = s->mixed && d.inner_basis_fp16;
+  s->ml = d.deflation_levels == 2;
+  if (s->ml && s->L < 2) {
+    set_err(s, "three-level deflation needs a grid that coarsens twice");
+    return HZ_INVALID_GRID;
+  }
   return HZ_OK;
 }
 
@@ -716,9 +751,100 @@ void coarse_finish(hz_solver* s, C<T>* v2, int nrhs, const int* done_in) {
   launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
 }
 
+// ------------------------------------------------------------ three levels
+// Level-2 coarse system E_2 v2 = v1 (E_2 = ReD-Glk2 at level 2) by GMRES
+// right-preconditioned with the V-cycle from level 2, x0 = 0, to the coarse
+// tolerance; RHS done at level 1 (done_in) are skipped.  Buffers: v1_2 in,
+// v2_2 out.
+template <class T>
+hz_status coarse_solve_level2(hz_solver* s, int nrhs, const int* done_in) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin2;
+  const LevelDev L2 = s->lv[2].dev();
+  const long long n2 = s->lv[2].n;
+  const long long rs = inner_row(n2);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  C<T>* Q = (C<T>*)s->Q2;
+  const int m = s->d.coarse_maxit;
+  launch_norm2_part<T>(vref<T>((C<T>*)s->v1_2), n2, nrhs, ks, nullptr, st);
+  launch_reduce_norm(ks, n2, nrhs, ks.beta, 1, st);
+  launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, st);
+  launch_scale_into<T, C<T>>(vref<T>((C<T>*)s->v1_2), vrefe<C<T>>(Q), rs, ks.hnorm, n2,
+                             nrhs, ks.done, st, (C<T>*)s->qf2);
+  int all = 0;
+  for (int it = 0; it < m; ++it) {
+    vcycle<T>(s, 2, vref<T>((C<T>*)s->qf2), (C<T>*)s->sb2, nrhs, ks.done);
+    launch_glk<T>(L2, s->d.bc, 2, (const C<T>*)s->sb2, (C<T>*)s->eb2, nrhs, ks.done, st);
+    cgs2<T, C<T>>(s, ks, Q, vs, rs, (C<T>*)s->eb2, n2, nrhs);
+    launch_givens(ks, nrhs, s->d.coarse_tol, m, st);
+    launch_scale_into<T, C<T>>(vref<T>((C<T>*)s->eb2), vrefe_j<C<T>>(Q, ks.jctr, 0, vs), rs,
+                               ks.hnorm, n2, nrhs, ks.done, st, (C<T>*)s->qf2);
+    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
+      const hz_status e = read_flag(s, ks.alldone, &all);
+      if (e != HZ_OK) return e;
+      if (all) break;
+    }
+  }
+  launch_trisolve(ks, nrhs, st);
+  launch_update<C<T>, T>(Q, vs, rs, ks, (C<T>*)s->eb2, 0, n2, nrhs, st);
+  vcycle<T>(s, 2, vref<T>((C<T>*)s->eb2), (C<T>*)s->v2_2, nrhs, done_in);
+  return cuda_check(s, "level-2 coarse solve");
+}
+
+// The level-1 coarse system with three-level deflation: flexible GMRES on
+// E right-preconditioned by A-DEF1 one level down,
+// z_j = M_1^-1 (v_j - E q) + q, q = Z_1 E_2^-1 R_1 v_j; the directions z_j
+// are kept (Z1b) and v2 = Z1 y at the end.
+template <class T, class SB>
+hz_status coarse_solve_ml(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
+                          const int* done_in) {
+  cudaStream_t st = s->st;
+  KState& ks = s->kin;
+  const int bc = s->d.bc, zk = s->d.zkind;
+  const LevelDev L1 = s->lv[1].dev(), L2 = s->lv[2].dev();
+  const long long n1 = s->lv[1].n;
+  const long long rs = inner_row(n1);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  const long long zs = (long long)s->d.nrhs_max * n1;
+  const int m = s->d.coarse_maxit;
+  C<T>* zj = (C<T>*)s->zj;
+  coarse_begin<T, SB>(s, v1, nrhs, done_in);
+  int all = 0;
+  for (int it = 0; it < m; ++it) {
+    // z_j = P_1 v_j (v_j in compute precision in s->qf)
+    launch_restrict_z<T>(L1, L2, bc, zk, vref<T>((C<T>*)s->qf), (C<T>*)s->v1_2, nrhs,
+                         ks.done, st);
+    hz_status e = coarse_solve_level2<T>(s, nrhs, ks.done);
+    if (e != HZ_OK) return e;
+    launch_prolong_z<T>(L1, L2, bc, zk, (const C<T>*)s->v2_2, (C<T>*)s->q1, 0, nrhs,
+                        ks.done, st);
+    apply_E<T>(s, (const C<T>*)s->q1, (C<T>*)s->u1, nrhs, ks.done);
+    launch_sub<T>((const C<T>*)s->qf, (const C<T>*)s->u1, (C<T>*)s->u1, n1, nrhs, ks.done,
+                  st);
+    vcycle<T>(s, 1, vref<T>((C<T>*)s->u1), (C<T>*)s->sb, nrhs, ks.done);
+    launch_add_conv<T, T>(vref<T>((C<T>*)s->sb), (const C<T>*)s->q1, vref<T>(zj), n1, nrhs,
+                          ks.done, st);
+    launch_add_conv<T, T>(vref<T>(zj), nullptr, vref_j<T>((C<T>*)s->Z1b, ks.jctr, 0, zs),
+                          n1, nrhs, ks.done, st);
+    apply_E<T>(s, zj, (C<T>*)s->eb, nrhs, ks.done);
+    cgs2<T, SB>(s, ks, (SB*)s->Qb, vs, rs, (C<T>*)s->eb, n1, nrhs);
+    inner_post<T, SB>(s, nrhs);
+    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
+      e = read_flag(s, ks.alldone, &all);
+      if (e != HZ_OK) return e;
+      if (all) break;
+    }
+  }
+  launch_trisolve(ks, nrhs, st);
+  launch_update<C<T>, T>((const C<T>*)s->Z1b, zs, n1, ks, v2, 0, n1, nrhs, st);
+  launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
+  return cuda_check(s, "three-level coarse solve");
+}
+
 template <class T, class SB>
 hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
                           const int* done_in) {
+  if (s->ml) return coarse_solve_ml<T, SB>(s, v1, v2, nrhs, done_in);
   KState& ks = s->kin;
   const int m = s->d.coarse_maxit;
   coarse_begin<T, SB>(s, v1, nrhs, done_in);
@@ -1205,7 +1331,7 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   // graphs replay fixed launches: the per-launch events of the profiler
   // and the trace's host reads need the launches issued one by one
   hz_solver::OuterGraph* og = nullptr;
-  if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on()) {
+  if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on() && !s->ml) {
     og = outer_graph(s, nrhs, tol);
     if (!og) return HZ_CUDA_ERROR;
   }
@@ -1404,7 +1530,7 @@ struct GroupScope {
       for (hz_solver* t : S)
         if (t == s) status = HZ_INVALID_ARG;
       if (s->d.outer_solver != HZ_OUTER_FGMRES ||
-          s->d.preconditioner != HZ_PRECOND_ADEF1) {
+          s->d.preconditioner != HZ_PRECOND_ADEF1 || s->ml) {
         set_err(s, "group solves use flexible GMRES members with A-DEF1");
         status = HZ_INVALID_ARG;
       }
@@ -1922,8 +2048,8 @@ hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
     s->graphs.clear();
   }
   s->tune = *t;
-  s->kin.dotk = s->kout.dotk = t->mdot_kernel;
-  s->kin.updk = s->kout.updk = t->maxpy_kernel;
+  s->kin.dotk = s->kout.dotk = s->kin2.dotk = t->mdot_kernel;
+  s->kin.updk = s->kout.updk = s->kin2.updk = t->maxpy_kernel;
   return HZ_OK;
 }
 

@@ -656,6 +656,17 @@ __global__ void k_add_conv(VRef<Ti> a, const C<Ti>* __restrict__ b, VRef<To> out
   }
 }
 
+// out = a - b (same precision)
+template <class T>
+__global__ void k_sub(const C<T>* __restrict__ a, const C<T>* __restrict__ b,
+                      C<T>* __restrict__ out, long long n, const int* __restrict__ done) {
+  const int r = blockIdx.y;
+  if (done && done[r]) return;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[r * n + e] = a[r * n + e] - b[r * n + e];
+}
+
 // out = a - b + c in FP64 (the last step of the TLKM preconditioner)
 template <class T>
 __global__ void k_sub_add_widen(const C<T>* __restrict__ a, const C<T>* __restrict__ b,
@@ -934,6 +945,18 @@ void launch_add_conv(VRef<Ti> a, const C<Ti>* b, VRef<To> out, long long n,
   k_add_conv<Ti, To><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(a, b, out, n, done);
 }
 
+template <class T>
+void launch_sub(const C<T>* a, const C<T>* b, C<T>* out, long long n, int nrhs,
+                const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  long long nb = (n + 255) / 256;
+  if (nb > 4096) nb = 4096;
+  k_sub<T><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(a, b, out, n, done);
+}
+template void launch_sub<double>(const double2*, const double2*, double2*, long long, int,
+                                 const int*, cudaStream_t);
+template void launch_sub<float>(const float2*, const float2*, float2*, long long, int,
+                                const int*, cudaStream_t);
 template <class T>
 void launch_sub_add_widen(const C<T>* a, const C<T>* b, const C<T>* c, VRef<double> out,
                           long long n, int nrhs, const int* done, cudaStream_t st) {

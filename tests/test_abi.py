@@ -120,6 +120,12 @@ def test_workspace_bytes_checks_method_choices(lib):
     assert _ws(lib, preconditioner=1)[0] == 0
     assert _ws(lib, preconditioner=2)[0] == 1
     assert _ws(lib, preconditioner=1, zkind=0)[0] == 1
+    assert _ws(lib, deflation_levels=2)[0] == 0
+    assert _ws(lib, deflation_levels=2)[1] > base
+    assert _ws(lib, deflation_levels=2, zkind=0)[0] == 1
+    assert _ws(lib, deflation_levels=2, preconditioner=1)[0] == 1
+    assert _ws(lib, deflation_levels=3)[0] == 1
+    assert _ws(lib, nx=5, ny=5, deflation_levels=2)[0] == 2   # one coarsening
     # GCR keeps a residual vector; TLKM a fine-grid scratch vector;
     # the stored Galerkin stencil is only planned for the Galerkin E
     assert _ws(lib, outer_solver=1)[1] > base

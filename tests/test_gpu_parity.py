@@ -378,6 +378,41 @@ def test_tlkm_preconditioner_and_solve_match_oracle(bc, z):
     assert rel(to_np(x)[0], xo) < 1e-8
 
 
+@pytest.mark.parametrize("bc,z", [("sommerfeld", "ho"), ("dirichlet", "bilinear")])
+def test_three_level_deflation_matches_oracle(bc, z):
+    """Three-level deflation (the level-1 coarse system solved by flexible
+    GMRES with A-DEF1 deflating to level 2, ReD-Glk2 there): one coarse
+    solve and a tight whole solve against the oracle (1e-8; outer +-1), and
+    the mixed-precision form reaches the FP64 residual target."""
+    n, k = 33, 15
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), float(k) ** 2)
+    s = solver(n, n, h, k2, bc, z=z, coarse_tol=1e-10, coarse_maxit=400,
+               outer_maxit=200, deflation_levels=2)
+    orc = Oracle(n, n, h, k2, bc, z=z, coarsest="direct", coarse_tol=1e-10,
+                 coarse_maxit=400, deflation_levels=2)
+    lc = orc.levels[1]
+    v1 = wl.random_complex((1, lc.ny, lc.nx), 17)
+    v2 = to_np(s.apply("coarse_solve", v1))[0]
+    ref = lc.to_full(orc.coarse_solve(lc.to_unknowns(v1[0])))
+    assert rel(v2, ref) < 1e-8
+    b = wl.point_sources(n, n, [wl.centre_node(n, n)])
+    x, info = s.solve(b, tol=1e-11)
+    orc2 = Oracle(n, n, h, k2, bc, z=z, coarse_tol=1e-10, coarse_maxit=400,
+                  deflation_levels=2)
+    xo, io = orc2.solve(b[0], tol=1e-11)
+    assert info[0].status == "HZ_OK"
+    assert abs(info[0].outer_iters - io.outer_iters) <= 1
+    assert rel(to_np(x)[0], xo) < 1e-8
+    sm = solver(n, n, h, k2, bc, z=z, prec="mixed", coarse_tol=1e-2,
+                coarse_maxit=200, outer_maxit=100, deflation_levels=2)
+    xm, im = sm.solve(b, tol=1e-6)
+    lv = orc2.levels[0]
+    bu = lv.to_unknowns(b[0])
+    res = np.linalg.norm(bu - orc2.A @ lv.to_unknowns(to_np(xm)[0])) / np.linalg.norm(bu)
+    assert im[0].status == "HZ_OK" and res <= 1e-6
+
+
 def test_mixed_precision_reaches_fp64_residual():
     n, k = 129, 80
     orc, b, x, info = _solve_pair(n, k, "sommerfeld", "ho", "galerkin", 1e-6,
