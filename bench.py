@@ -291,6 +291,25 @@ def oracle_sample(wl_name, steps, warmup, all_cores=False):
     return out
 
 
+def workload_config(args, cfg, model, world, b_np):
+    """The "config" of the output line shared by both arms: what the
+    workload is and how it is solved."""
+    return {"workload": args.workload, "grid": [model.nx, model.ny],
+            "physical_grid": list(model.physical),
+            "velocity_model": model.name,
+            "kh_max": round(model.kh_max(), 4), "bc": cfg["bc"],
+            "deflation": f"{cfg['z']}/{cfg['e']}",
+            "outer": args.outer, "preconditioner": args.precond,
+            "precision": PREC_TEXT[args.prec],
+            "inner_basis_storage": ("fp16" if args.basis16 and args.prec != "fp64"
+                                    else ("c64" if args.prec != "fp64" else "c128")),
+            "nrhs_per_gpu": cfg["nrhs"], "tol": cfg["tol"],
+            "coarse_tol": cfg["coarse_tol"],
+            "parallelism": f"replicas{world}",
+            "l2": ("inputs larger than L2 (each batch vector "
+                   f"{b_np.nbytes / 1e6:.0f} MB)")}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_ours(args):
     import torch
@@ -459,24 +478,9 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "c128" if args.prec == "fp64" else "c64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "grid": [model.nx, model.ny],
-                       "physical_grid": list(model.physical),
-                       "velocity_model": model.name,
-                       "kh_max": round(model.kh_max(), 4), "bc": cfg["bc"],
-                       "deflation": f"{cfg['z']}/{cfg['e']}",
-                       "outer": args.outer, "preconditioner": args.precond,
-                       "precision": PREC_TEXT[args.prec],
-                       "inner_basis_storage": ("fp16" if args.basis16 and
-                                               args.prec != "fp64" else
-                                               ("c64" if args.prec != "fp64"
-                                                else "c128")),
-                       "nrhs_per_gpu": cfg["nrhs"], "tol": tol,
-                       "coarse_tol": cfg["coarse_tol"],
-                       "parallelism": f"replicas{world}",
-                       "cuda_graph": bool(args.cuda_graph),
-                       "tuning": tuning, "autotune_ms": tune_ms,
-                       "l2": "inputs larger than L2 (each batch vector "
-                             f"{b_np.nbytes / 1e6:.0f} MB)"},
+            "config": dict(workload_config(args, cfg, model, world, b_np),
+                           cuda_graph=bool(args.cuda_graph), tuning=tuning,
+                           autotune_ms=tune_ms),
             "e2e": {"value": units / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": io_bytes,
                     "d2h_bytes_per_step": io_bytes},
@@ -499,12 +503,13 @@ def run_reference(args):
     if rank != 0:
         return
     cpu = oracle_sample(args.workload, steps=args.steps, warmup=args.warmup)
+    cfg, model, b_np = build_inputs(args.workload)
     line = {
         "impl": "reference", "metric": METRIC, "value": cpu["value"],
         "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-        "config": {"workload": args.workload},
+        "config": workload_config(args, cfg, model, world, b_np),
         "cpu_baseline": cpu,
         "e2e": {"value": cpu["value"], "unit": UNIT,
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
