@@ -418,13 +418,21 @@ def run_ours(args):
 
     roof = None
     # DRAM bytes / algorithmic bytes of the profiled kernel, measured with ncu
-    # on a smaller case of the same kernel variant and storage (the summary
-    # under profiles/ names the command); traffic scales with the rows
-    # streamed, so a bench launch's traffic is this ratio times its bytes
+    # on a smaller case of the same kernel and storage (the summary under
+    # profiles/ names the command); traffic scales with the rows streamed,
+    # so a bench launch's traffic is this ratio times its bytes.  The two
+    # TMA-ring widths (8 or 16 consumer warps) issue the same bulk copies,
+    # w loads and partial-sum stores; only the split of a stage among the
+    # consumer warps differs, so the ratio taken on the 16-warp one holds
+    # for both.
     traffic_ratio = None
-    if (args.profile_kernel == "mdot" and tuning.get("mdot_kernel") == 2
+    if (args.profile_kernel == "mdot" and tuning.get("mdot_kernel") in (1, 2)
             and args.prec == "mixed_bf16" and args.basis16):
-        traffic_ratio = (1.014, "profiles/k_mdot_tma_dram_mp2b_641_k400_b8_prof.md")
+        src = "profiles/k_mdot_tma_dram_mp2b_641_k400_b8_prof.md"
+        if tuning.get("mdot_kernel") == 1:
+            src += (" (captured on the 16-consumer-warp instantiation; this "
+                    "8-warp one issues the same copies and loads)")
+        traffic_ratio = (1.013, src)
     if prof and prof[0] > 0:
         n_l, ms_k, by = prof
         peak, peak_src = hbm_peak()

@@ -601,7 +601,11 @@ struct Item {
 // Pass `pass` of classical Gram-Schmidt (same contract as k_mdot).  The
 // work items (RHS, row chunk, group of G vectors) of all active RHS are
 // split evenly over the blocks, so every block streams the same number of
-// bytes whatever j and the number of converged RHS.
+// bytes whatever j and the number of converged RHS.  The per-warp sums of
+// FLUSH items are combined across warps after one consumer barrier; the
+// staging buffers alternate between two halves, so the next items' sums go
+// to the other half while this half is read, and the barrier of the next
+// flush orders this half's reads before its next writes.
 template <class T, class SB, int NCW>
 __global__ void __launch_bounds__(32 * NCW + 32, 1)
 k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
@@ -616,9 +620,9 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
   __shared__ int act[1024];
   __shared__ int s_nact;
   __shared__ volatile int s_abort;
-  __shared__ double wred[NCW][2 * 32];
-  __shared__ double wnred[NCW][32];
-  __shared__ int3 pitem[32];     // (RHS, chunk, group) of the pending items
+  __shared__ double wred[2][NCW][2 * 32];
+  __shared__ double wnred[2][NCW][FLUSH];
+  __shared__ int3 pitem[2][FLUSH];   // (RHS, chunk, group) of the pending items
   const int j = *ks.jctr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   active_rhs(ks, pass, nrhs, act, &s_nact);
@@ -656,7 +660,7 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
     int cur_a = -1, cur_blk = -1;
     bool have_next = false;
     C<T> wv[E], wq[E];
-    int pend = 0;
+    int pend = 0, buf = 0;
     Slot sl;
     Item it = it0;
     for (int t = 0; t < nitems; ++t) {
@@ -685,10 +689,10 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
 #pragma unroll
           for (int e = 0; e < E; ++e) wn += wv[e].x * wv[e].x + wv[e].y * wv[e].y;
           for (int o = 16; o > 0; o >>= 1) wn += __shfl_xor_sync(0xffffffffu, wn, o);
-          if (lane == 0) wnred[warp][pend] = (double)wn;
+          if (lane == 0) wnred[buf][warp][pend] = (double)wn;
         }
       }
-      if (threadIdx.x == 0) pitem[pend] = make_int3(it.a, it.blk, it.grp);
+      if (threadIdx.x == 0) pitem[buf][pend] = make_int3(it.a, it.blk, it.grp);
       T acc[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) acc[c] = T(0);
@@ -696,59 +700,67 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
         const int nv = min(G, j + 1 - it.grp * G);
         const long long valid = n - off;   // values of this chunk inside the row
         const unsigned char* sb = stages + sl.s * STAGE_BYTES;
+        // FULL: all G vectors of the group exist and the chunk lies inside
+        // the row, so no value needs a bounds test
+        auto dot = [&](auto FULL) {
 #pragma unroll
-        for (int qq = 0; qq < G; ++qq) {
-          if (qq < nv) {
+          for (int qq = 0; qq < G; ++qq) {
+            if (FULL.value || qq < nv) {
 #pragma unroll
-            for (int k = 0; k < VPT; ++k) {
-              const int g = k * NTC + threadIdx.x;
-              if ((long long)g * W < valid) {
-                const uint4 raw =
-                    *reinterpret_cast<const uint4*>(sb + qq * P::ROWB + g * 16);
-                static_for<W>([&](auto U) {
-                  const C<T> v = unpk<U.value>(raw, (const SB*)nullptr);
-                  const C<T> wk = wv[k * W + U.value];
-                  acc[2 * qq] += v.x * wk.x + v.y * wk.y;
-                  acc[2 * qq + 1] += v.x * wk.y - v.y * wk.x;
-                });
+              for (int k = 0; k < VPT; ++k) {
+                const int g = k * NTC + threadIdx.x;
+                if (FULL.value || (long long)g * W < valid) {
+                  const uint4 raw =
+                      *reinterpret_cast<const uint4*>(sb + qq * P::ROWB + g * 16);
+                  static_for<W>([&](auto U) {
+                    const C<T> v = unpk<U.value>(raw, (const SB*)nullptr);
+                    const C<T> wk = wv[k * W + U.value];
+                    acc[2 * qq] += v.x * wk.x + v.y * wk.y;
+                    acc[2 * qq + 1] += v.x * wk.y - v.y * wk.x;
+                  });
+                }
               }
             }
           }
-        }
+        };
+        if (nv == G && valid >= CHUNK)
+          dot(std::true_type{});
+        else
+          dot(std::false_type{});
       }
       consumer_release(empty, sl);
       sl.next();
       int idx = 0;
       const T sum = multi_reduce<NV>(acc, lane, &idx);
-      if ((lane & (32 / NV - 1)) == 0) wred[warp][pend * NV + idx] = (double)sum;
+      if ((lane & (32 / NV - 1)) == 0) wred[buf][warp][pend * NV + idx] = (double)sum;
       ++pend;
       it.next(nblk, ngrp);
       if (pend == FLUSH || t + 1 == nitems) {
         consumers_sync<NTC>();
         const int v = threadIdx.x;
         if (v < pend * G) {
-          const int3 pi = pitem[v / G];
+          const int3 pi = pitem[buf][v / G];
           const int i = pi.z * G + v % G;
           if (i <= j) {
             double2 sm = make_double2(0.0, 0.0);
 #pragma unroll
             for (int ww = 0; ww < NCW; ++ww) {
-              sm.x += wred[ww][2 * v];
-              sm.y += wred[ww][2 * v + 1];
+              sm.x += wred[buf][ww][2 * v];
+              sm.y += wred[buf][ww][2 * v + 1];
             }
             ks.part[((long long)act[pi.x] * (ks.m + 1) + i) * ks.nblk_max + pi.y] = sm;
           }
         }
         if (pass == 0 && v < pend) {
-          const int3 pi = pitem[v];
+          const int3 pi = pitem[buf][v];
           if (pi.z == 0) {
             double tw = 0.0;
 #pragma unroll
-            for (int ww = 0; ww < NCW; ++ww) tw += wnred[ww][v];
+            for (int ww = 0; ww < NCW; ++ww) tw += wnred[buf][ww][v];
             ks.wpart[(long long)act[pi.x] * ks.nblk_max + pi.y] = tw;
           }
         }
-        consumers_sync<NTC>();
+        buf ^= 1;
         pend = 0;
       }
     }
