@@ -284,6 +284,31 @@ def test_glk2_dirichlet_laplacian_sine_modes():
                                    atol=1e-9 * abs(S).max())
 
 
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("bc", [ops.DIRICHLET, ops.SOMMERFELD])
+def test_red_glk_mass_part_takes_each_nodes_own_wavenumber(variant, bc):
+    """Sec. 5.2.4 derives the ReD-Glk mass stencil for a constant k; with a
+    variable k each of its entries takes k^2 of its own coarse node (our
+    reading).  The stencil sums to 1 (it is R_Z Z for the higher-order Z,
+    which reproduces constants), so on rows whose 5x5 stencil reaches only
+    unknowns the mass part E(0) - E(k) maps u = 1/k^2 to exactly 1; taking
+    the centre node's k^2 for every entry would not."""
+    n, H = 17, 1.0 / 16
+    rng = np.random.default_rng(11)
+    k2 = 30.0 + 20.0 * rng.random((n, n))
+    lv_k = ops.Level(n, n, H, k2, bc)
+    lv_0 = ops.Level(n, n, H, np.zeros((n, n)), bc)
+    mass = ops.red_glk(lv_0, variant) - ops.red_glk(lv_k, variant)
+    u = lv_k.to_unknowns(1.0 / k2)
+    out = lv_k.to_full(mass @ u)
+    np.testing.assert_allclose(out[3:-3, 3:-3], 1.0, atol=1e-12)
+    # the same rows of the constant-k operator: mass part = k^2 * (sum 1)
+    lv_c = ops.Level(n, n, H, np.full((n, n), 40.0), bc)
+    mc = ops.red_glk(lv_0, variant) - ops.red_glk(lv_c, variant)
+    np.testing.assert_allclose(lv_c.to_full(mc @ lv_c.to_unknowns(np.ones((n, n))))[3:-3, 3:-3],
+                               40.0, atol=1e-10)
+
+
 def test_red_o2_is_coarse_helmholtz():
     k2 = _rng_k2(9, 9, 6)
     lv = ops.build_levels(17, 17, 0.1, np.kron(k2, np.ones((2, 2)))[:17, :17],
