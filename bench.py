@@ -270,6 +270,8 @@ def oracle_sample(wl_name, steps, warmup, all_cores=False):
         how = (f"scaled to the oracle's {outer} outer / {inner_total} inner "
                f"iterations for a full solve ({t_full:.0f} s)")
     out = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "arithmetic": ("FP64 throughout (SciPy CSR), the oracle's own "
+                          "iteration counts"),
            "sample": (f"one outer FGMRES iteration (A-DEF1 with its "
                       f"{int(inner_mean)}-iteration inner coarse solve) "
                       f"of 1 RHS of {wl_name}, {t_iter:.2f} s mean over "
