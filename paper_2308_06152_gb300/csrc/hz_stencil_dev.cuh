@@ -22,13 +22,15 @@ __device__ __forceinline__ bool on_bnd(int i, int j, int nx, int ny) {
 
 // Row (i, j) of M = -Lap - (sre + i sim) k^2 with the boundary rules of
 // helm_point below: centre and the four neighbour weights (0 where the
-// neighbour is outside the grid or a Dirichlet boundary node).
+// neighbour is outside the grid or a Dirichlet boundary node).  k2 is the
+// node's squared wavenumber, loaded by the caller (so that the load can be
+// issued ahead of its use).
 template <class T>
 __device__ __forceinline__ void helm_row(const LevelDev& L, int bc, T sre, T sim, int i,
-                                         int j, C<T>& cen, T& cw, T& ce, T& cs, T& cn) {
+                                         int j, T k2, C<T>& cen, T& cw, T& ce, T& cs,
+                                         T& cn) {
   const int nx = L.nx, ny = L.ny;
   const T ih2 = ih2_of<T>(L);
-  const T k2 = k2_of<T>(L)[(long long)j * nx + i];
   cen = mkc(T(4) * ih2 - sre * k2, -sim * k2);
   cw = -ih2;
   ce = -ih2;

@@ -102,13 +102,18 @@ __global__ void k_smooth(LevelDev L, int bc, T sre, T sim, VRefE<SF> fin,
 // in shared memory (the tile's own fine nodes are also written out), then
 // f - M x on [2I0-1, 2I0+2BX-1] and its full weighting.  x is computed
 // from f where it is needed instead of being read back, so the pair reads
-// f once and writes x and the coarse right-hand side once.
+// f once and writes x and the coarse right-hand side once.  Every global
+// load a thread needs (D^-1 and f of its x nodes, f and k^2 of its
+// residual nodes) is issued up front into registers, so each thread has
+// all its loads in flight at once instead of one per loop trip, and the
+// residual's operands arrive while the x tile is being built.
 template <class T, class SF, class SX, class SC>
 __global__ void __launch_bounds__(BX * BY)
 k_pre_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim, VRefE<SF> fin,
                SX* __restrict__ x, SC* __restrict__ fc, const int* __restrict__ done) {
   constexpr int XW = 2 * BX + 3, XH = 2 * BY + 3, RW = 2 * BX + 1, RH = 2 * BY + 1;
   constexpr int NT = BX * BY;
+  constexpr int N1 = (XH * XW + NT - 1) / NT, N2 = (RH * RW + NT - 1) / NT;
   __shared__ C<T> xs[XH * XW];
   __shared__ C<T> rsd[RH * RW];
   const int r = blockIdx.z;
@@ -120,36 +125,74 @@ k_pre_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim, VRefE<SF> fin,
   const SF* f = fin.get() + r * nf;
   SX* xr = x + r * nf;
   const C<T>* dinv = dinv_of<T>(Lf);
-  for (int q = tid; q < XH * XW; q += NT) {
+  const T* k2f = k2_of<T>(Lf);
+  // operands of the x tile (zero outside the grid and on Dirichlet
+  // boundary nodes, where x = 0)
+  C<T> dv[N1], fv[N1];
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
     const int gi = 2 * I0 - 2 + q % XW, gj = 2 * J0 - 2 + q / XW;
-    C<T> v = czero<T>();
-    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+    dv[u] = czero<T>();
+    fv[u] = czero<T>();
+    if (q < XH * XW && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
       const long long id = (long long)gj * nfx + gi;
-      if (!(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) v = cmul(dinv[id], ld2(f, id));
-      if (gi >= 2 * I0 && gi < 2 * I0 + 2 * BX && gj >= 2 * J0 && gj < 2 * J0 + 2 * BY)
-        st2(xr, id, v);
+      dv[u] = dinv[id];
+      fv[u] = ld2(f, id);
     }
-    xs[q] = v;
+  }
+  // operands of the residual nodes
+  C<T> f2[N2];
+  T k2v[N2];
+#pragma unroll
+  for (int u = 0; u < N2; ++u) {
+    const int q = tid + u * NT;
+    const int gi = 2 * I0 - 1 + q % RW, gj = 2 * J0 - 1 + q / RW;
+    f2[u] = czero<T>();
+    k2v[u] = T(0);
+    if (q < RH * RW && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+      const long long id = (long long)gj * nfx + gi;
+      f2[u] = ld2(f, id);
+      k2v[u] = k2f[id];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
+    if (q < XH * XW) {
+      const int gi = 2 * I0 - 2 + q % XW, gj = 2 * J0 - 2 + q / XW;
+      const C<T> v = cmul(dv[u], fv[u]);
+      if (gi >= 2 * I0 && gi < 2 * I0 + 2 * BX && gi < nfx && gj >= 2 * J0 &&
+          gj < 2 * J0 + 2 * BY && gj < nfy)
+        st2(xr, (long long)gj * nfx + gi, v);
+      xs[q] = v;
+    }
   }
   __syncthreads();
-  for (int q = tid; q < RH * RW; q += NT) {
-    const int ri = q % RW, rj = q / RW;
-    const int gi = 2 * I0 - 1 + ri, gj = 2 * J0 - 1 + rj;
-    C<T> v = czero<T>();
-    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
-        !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
-      C<T> cen;
-      T cw, ce, cs, cn;
-      helm_row<T>(Lf, bc, sre, sim, gi, gj, cen, cw, ce, cs, cn);
-      const int c = (rj + 1) * XW + (ri + 1);
-      C<T> acc = cmul(cen, xs[c]);
-      if (cw != T(0)) acc = rfma(cw, xs[c - 1], acc);
-      if (ce != T(0)) acc = rfma(ce, xs[c + 1], acc);
-      if (cs != T(0)) acc = rfma(cs, xs[c - XW], acc);
-      if (cn != T(0)) acc = rfma(cn, xs[c + XW], acc);
-      v = ld2(f, (long long)gj * nfx + gi) - acc;
+#pragma unroll
+  for (int u = 0; u < N2; ++u) {
+    const int q = tid + u * NT;
+    if (q < RH * RW) {
+      const int ri = q % RW, rj = q / RW;
+      const int gi = 2 * I0 - 1 + ri, gj = 2 * J0 - 1 + rj;
+      C<T> v = czero<T>();
+      if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+          !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+        C<T> cen;
+        T cw, ce, cs, cn;
+        helm_row<T>(Lf, bc, sre, sim, gi, gj, k2v[u], cen, cw, ce, cs, cn);
+        const int c = (rj + 1) * XW + (ri + 1);
+        C<T> acc = cmul(cen, xs[c]);
+        if (cw != T(0)) acc = rfma(cw, xs[c - 1], acc);
+        if (ce != T(0)) acc = rfma(ce, xs[c + 1], acc);
+        if (cs != T(0)) acc = rfma(cs, xs[c - XW], acc);
+        if (cn != T(0)) acc = rfma(cn, xs[c + XW], acc);
+        v = f2[u] - acc;
+      }
+      rsd[q] = v;
     }
-    rsd[q] = v;
   }
   __syncthreads();
   const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
@@ -167,13 +210,16 @@ k_pre_restrict(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim, VRefE<SF> fin,
 
 // Fused coarse-grid correction and post-smoothing for one BX x BY tile of
 // fine nodes: x' = x + P xc on the tile and its 1-node halo in shared
-// memory, then xo = x' + dinv .* (f - M x').  x' is never stored.
+// memory, then xo = x' + dinv .* (f - M x').  x' is never stored.  The
+// thread's own f, D^-1 and k^2 are loaded before the tile is built, so
+// they arrive while the x' loads are in flight.
 template <class T, class SC, class SX, class SF, class SO>
 __global__ void __launch_bounds__(BX * BY)
 k_prolong_smooth(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
                  const SC* __restrict__ xc, const SX* __restrict__ x, VRefE<SF> fin,
                  SO* __restrict__ xo, const int* __restrict__ done) {
   constexpr int PW = BX + 2, PH = BY + 2, NT = BX * BY;
+  constexpr int N1 = (PH * PW + NT - 1) / NT;
   __shared__ C<T> xp[PH * PW];
   const int r = blockIdx.z;
   if (done && done[r]) return;
@@ -183,36 +229,50 @@ k_prolong_smooth(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
   const long long nf = (long long)nfx * nfy, nc = (long long)Lc.nx * Lc.ny;
   const SX* xr = x + r * nf;
   const SC* xcr = xc + r * nc;
-  for (int q = tid; q < PH * PW; q += NT) {
+  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+  const bool mine = i < nfx && j < nfy;
+  const long long id = (long long)j * nfx + i;
+  C<T> fown = czero<T>(), down = czero<T>();
+  T k2own = T(0);
+  if (mine) {
+    fown = ld2(fin.get(), r * nf + id);
+    down = dinv_of<T>(Lf)[id];
+    k2own = k2_of<T>(Lf)[id];
+  }
+  C<T> xv[N1];
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
     const int gi = i0 - 1 + q % PW, gj = j0 - 1 + q / PW;
-    C<T> v = czero<T>();
-    if (gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
-      const long long id = (long long)gj * nfx + gi;
-      v = ld2(xr, id);
+    xv[u] = czero<T>();
+    if (q < PH * PW && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+      xv[u] = ld2(xr, (long long)gj * nfx + gi);
       if (!(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy)))
-        v = v + interp_bilinear<T, SC>(Lc, xcr, gi, gj);
+        xv[u] = xv[u] + interp_bilinear<T, SC>(Lc, xcr, gi, gj);
     }
-    xp[q] = v;
+  }
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
+    if (q < PH * PW) xp[q] = xv[u];
   }
   __syncthreads();
-  const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-  if (i >= nfx || j >= nfy) return;
-  const long long id = (long long)j * nfx + i;
+  if (!mine) return;
   if (bc == BC_DIRICHLET && on_bnd(i, j, nfx, nfy)) {
     st2(xo, r * nf + id, czero<T>());
     return;
   }
   C<T> cen;
   T cw, ce, cs, cn;
-  helm_row<T>(Lf, bc, sre, sim, i, j, cen, cw, ce, cs, cn);
+  helm_row<T>(Lf, bc, sre, sim, i, j, k2own, cen, cw, ce, cs, cn);
   const int c = (threadIdx.y + 1) * PW + (threadIdx.x + 1);
   C<T> acc = cmul(cen, xp[c]);
   if (cw != T(0)) acc = rfma(cw, xp[c - 1], acc);
   if (ce != T(0)) acc = rfma(ce, xp[c + 1], acc);
   if (cs != T(0)) acc = rfma(cs, xp[c - PW], acc);
   if (cn != T(0)) acc = rfma(cn, xp[c + PW], acc);
-  const C<T> res = ld2(fin.get(), r * nf + id) - acc;
-  st2(xo, r * nf + id, cfma(dinv_of<T>(Lf)[id], res, xp[c]));
+  const C<T> res = fown - acc;
+  st2(xo, r * nf + id, cfma(down, res, xp[c]));
 }
 
 // x = Minv f on the coarsest level (dense inverse built at setup)
