@@ -277,6 +277,49 @@ def test_table5_comparisons_of_coarse_operators():
             assert abs(o65[e] - o129[e]) <= 1, (who, e)
 
 
+def test_coarse_tolerance_study_sec63():
+    """Sec. 6.3 / Table 9 on MP-2b 65^2, k = 40 (APD, ReD-Glk2):
+    - the outer count of left-preconditioned GMRES does not depend on the
+      coarse tolerance (Table 9's rows vary by at most one; so must ours);
+    - its final true residual grows once the coarse tolerance is looser
+      than the outer one, and stays put below it;
+    - GCR keeps its count and reaches the 1e-6 residual at any coarse
+      tolerance;
+    - at tau_c = 0.1 the standard right-preconditioned GMRES, which assumes
+      a fixed preconditioner, misses the residual target while flexible
+      GMRES and GCR meet it."""
+    rows = load_golden("iteration_tables.txt")["table9"]
+    assert all(r.max() - r.min() <= 1 for r in rows)
+    n, k = 65, 40.0
+    k2 = np.full((n, n), k * k)
+    b = np.zeros((n, n), complex)
+    b[n // 2, n // 2] = 1.0
+
+    def orc(tc):
+        return Oracle(n, n, 1.0 / (n - 1), k2, ops.SOMMERFELD, z="ho",
+                      e="red_glk2", coarse_tol=tc)
+
+    left, gcr = {}, {}
+    for tc in (1e-2, 1e-4, 1e-6, 1e-8):
+        o = orc(tc)
+        left[tc] = o.solve_left(b, tol=1e-6)[1]
+        gcr[tc] = o.solve_gcr(b, tol=1e-6)[1]
+    its = [i.outer_iters for i in left.values()]
+    assert max(its) - min(its) <= 1, its
+    assert left[1e-2].relres > 10 * left[1e-4].relres > 10 * left[1e-6].relres
+    assert abs(left[1e-8].relres - left[1e-6].relres) <= 0.1 * left[1e-6].relres
+    its = [i.outer_iters for i in gcr.values()]
+    assert max(its) - min(its) <= 1 and all(i.relres <= 1e-6 for i in gcr.values())
+    o = orc(1e-1)
+    lv = o.levels[0]
+    bu = lv.to_unknowns(b)
+    std = gmres_right(lambda v: o.A @ v, bu, 1e-6, 200, prec=o.precond)
+    assert std.converged
+    assert np.linalg.norm(bu - o.A @ std.x) / np.linalg.norm(bu) > 1e-4
+    assert o.solve(b, tol=1e-6)[1].relres <= 1e-6
+    assert o.solve_gcr(b, tol=1e-6)[1].relres <= 1e-6
+
+
 def test_three_level_deflation_invariant_and_direct_solution():
     """Three-level deflation: with the Galerkin level-2 operator and an
     exact level-2 solve, A-DEF1 of the level-1 system deflates its coarse
