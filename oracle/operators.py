@@ -339,7 +339,7 @@ def stencil_with_ghosts(level, rows_mask, coef_fn, radius, ghosts=None):
                           (rows, cols)), shape=(n, n))
 
 
-def red_glk(coarse, variant=2):
+def red_glk(coarse, variant=2, glk_scale=1.0):
     """ReD-Glk1 / ReD-Glk2 (Sec. 5.2.4).
 
     Interior coarse nodes use the Galerkin-derived 5x5 stencil
@@ -347,7 +347,9 @@ def red_glk(coarse, variant=2):
     of the mass part taking k^2 of its own coarse node, divided by 4 to
     match R = Z^T / 4.  Glk1: the two outermost rings of nodes use ReD-O2.
     Glk2: the outermost ring uses ReD-O2, the second ring the 5x5 stencil
-    with ghost values (wavenumber zero at ghost nodes).
+    with ghost values (wavenumber zero at ghost nodes).  ``glk_scale``
+    multiplies the 5x5 rows only: 4 gives the stencils as printed (the
+    scale of Z^T A Z), for use with the unscaled restriction R = Z^T.
     """
     nx, ny, H = coarse.nx, coarse.ny, coarse.h
     jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
@@ -362,7 +364,7 @@ def red_glk(coarse, variant=2):
     full_glk = stencil_with_ghosts(coarse, ~o2_rows, coef, 2)
     full_o2 = five_point_full(nx, ny, H, coarse.k2, coarse.bc, 1.0)
     keep = sp.diags(o2_rows.ravel().astype(np.float64))
-    full = (keep @ full_o2 + full_glk).tocsr()
+    full = (keep @ full_o2 + glk_scale * full_glk).tocsr()
     return _restrict_to_unknowns(full, coarse, coarse)
 
 

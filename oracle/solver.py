@@ -48,13 +48,22 @@ class Oracle:
     level-1 coarse system solved by flexible GMRES with A-DEF1 built from
     it, deflating to level 2 with ``e2``: 'red_glk2' (default), 'red_o2' or
     'galerkin' = R_1 E Z_1; the multilevel direction of Sec. 1 / Sec. 7).
+    ``deflation_scaling``: 'consistent' (default) restricts with
+    R_Z = Z^T / 4, under which R_Z A Z matches the re-discretised operators'
+    scale (those of A_2h); 'printed' restricts with the unscaled R_Z = Z^T
+    that the paper prints (the 1-D 1/2 [1 2 1] of Sec. 3.2.1 and the
+    higher-order restriction of eq. O4 matrix-free restriction, stencil sums
+    2 and 4), keeps the re-discretised operators and the ReD-O2 rows of
+    ReD-Glk at the A_2h scale, and takes the 5x5 ReD-Glk rows as printed
+    (the scale of Z^T A Z).  The Galerkin E and TLKM do not depend on the
+    choice; the re-discretised E do.
     """
 
     def __init__(self, nx, ny, h, k2, bc, z="ho", e="galerkin",
                  beta=(1.0, -0.5), omega=0.8, min_coarse_intervals=2,
                  coarsest="gmres", coarsest_tol=1e-8, coarse_tol=1e-6,
                  coarse_maxit=3000, precond="adef1", deflation_levels=1,
-                 e2="red_glk2"):
+                 e2="red_glk2", deflation_scaling="consistent"):
         self.levels = ops.build_levels(nx, ny, h, k2, bc,
                                        min_coarse_intervals)
         self.L = len(self.levels) - 1
@@ -78,19 +87,24 @@ class Oracle:
         self.precond = self.adef1 if precond == "adef1" else self.tlkm
         self.coarse_tol, self.coarse_maxit = coarse_tol, coarse_maxit
         self.inner_log = []
+        if deflation_scaling not in ("consistent", "printed"):
+            raise ValueError(deflation_scaling)
+        printed = deflation_scaling == "printed"
+        glk_scale = 4.0 if printed else 1.0
         if z is not None:
             if self.L < 1:
                 raise ValueError("deflation needs at least one coarsening")
             self.Z = ops.prolongation(self.levels[0], self.levels[1], z)
-            self.RZ = ops.restriction(self.Z)
+            self.RZ = self.Z.T.tocsr() if printed else ops.restriction(self.Z)
             if e == "galerkin":
-                self.E = ops.galerkin(self.A, self.Z)
+                self.E = ((self.RZ @ self.A @ self.Z).tocsr() if printed
+                          else ops.galerkin(self.A, self.Z))
             elif e == "red_o2":
                 self.E = ops.red_o2(self.levels[1])
             elif e == "red_glk1":
-                self.E = ops.red_glk(self.levels[1], 1)
+                self.E = ops.red_glk(self.levels[1], 1, glk_scale)
             elif e == "red_glk2":
-                self.E = ops.red_glk(self.levels[1], 2)
+                self.E = ops.red_glk(self.levels[1], 2, glk_scale)
             elif e == "red_o4":
                 self.E = ops.red_o4(self.levels[1])
             elif e == "red_cmpo4":
@@ -111,11 +125,11 @@ class Oracle:
                                  "two coarsenings")
             l1, l2 = self.levels[1], self.levels[2]
             self.Z1 = ops.prolongation(l1, l2, z)
-            self.R1 = ops.restriction(self.Z1)
+            self.R1 = self.Z1.T.tocsr() if printed else ops.restriction(self.Z1)
             if e2 == "galerkin":
                 self.E2 = (self.R1 @ self.E @ self.Z1).tocsr()
             elif e2 == "red_glk2":
-                self.E2 = ops.red_glk(l2, 2)
+                self.E2 = ops.red_glk(l2, 2, glk_scale)
             elif e2 == "red_o2":
                 self.E2 = ops.red_o2(l2)
             else:
