@@ -24,6 +24,10 @@ solver     -- multigrid V-cycle for the CSLP, inner coarse solve, A-DEF1
               preconditioner and the outer flexible GMRES (Sec. 3, 5, 6).
 gradient   -- adjoint misfit gradient with respect to squared slowness.
 
+Scripts: ``record_bench_counts`` writes the oracle's iteration counts for
+the benchmark workloads (scales the CPU baseline); ``paper_tables`` prints
+the oracle's outer counts beside those printed in Tables 2, 3 and 5.
+
 Parity status: every function is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` except the corner ghost value of the ReD-Glk2
 boundary rule, which the paper leaves open (parity unpinned for the four
