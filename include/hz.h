@@ -104,7 +104,9 @@ typedef struct {
   hz_precision prec;
   double beta1, beta2;        /* CSLP shift, default (1, -0.5) (Sec. 3.1),
                                  entering M = -Lap - (beta1 - i beta2) k^2 as
-                                 the coefficient printed in Sec. 5.1        */
+                                 the coefficient printed in Sec. 5.1;
+                                 beta2 = +0.5 gives the sign of the Sec. 3.1
+                                 definition, M = -Lap - (1 - 0.5i) k^2      */
   double jacobi_omega;        /* damped Jacobi weight, default 0.8 (Sec. 3.1)*/
   int min_coarse_intervals;   /* coarsening stop rule, default 2 (Sec. 4)    */
   double coarse_tol;          /* inner coarse-solve tolerance (Sec. 6.3)     */
