@@ -95,6 +95,18 @@ typedef enum { HZ_OUTER_FGMRES = 0, HZ_OUTER_GCR = 1 } hz_outer;
  * GMRES on that operator (R_Z Z after a V-cycle on M_2h after E). */
 typedef enum { HZ_PRECOND_ADEF1 = 0, HZ_PRECOND_TLKM = 1 } hz_precond;
 
+/* Scale of the deflation restriction R_Z.  CONSISTENT: R_Z = Z^T / 4, the
+ * scale on which R_Z A Z matches the re-discretised coarse operators (those
+ * of A_2h).  PRINTED: the unscaled Z^T that Sec. 3.2.1 prints (1/2 [1 2 1]
+ * in 1-D; the higher-order restriction of eq. O4 matrix-free restriction,
+ * stencil sum 4), with the re-discretised operators and the ReD-O2 rows of
+ * ReD-Glk kept at the A_2h scale and the 5x5 ReD-Glk rows as printed (the
+ * scale of Z^T A Z); this combination reproduces the outer iteration counts
+ * the paper prints for re-discretised coarse operators.  The Galerkin E and
+ * TLKM do not depend on the scale: with HZ_E_GALERKIN the library keeps
+ * Z^T / 4 under either choice. */
+typedef enum { HZ_DEFL_SCALE_CONSISTENT = 0, HZ_DEFL_SCALE_PRINTED = 1 } hz_defl_scale;
+
 typedef struct {
   int nx, ny;                 /* nodes; each >= 3                            */
   double h;                   /* grid spacing                                */
@@ -137,6 +149,8 @@ typedef struct {
                                  node; 1: the same kernels issued one by one
                                  with a host completion check every 4 inner
                                  iterations.  Results are the same.         */
+  int deflation_scaling;      /* hz_defl_scale; default CONSISTENT.  PRINTED
+                                 needs deflation_levels <= 1.             */
 } hz_desc;
 
 typedef struct {

@@ -87,8 +87,10 @@ class Oracle:
         self.precond = self.adef1 if precond == "adef1" else self.tlkm
         self.coarse_tol, self.coarse_maxit = coarse_tol, coarse_maxit
         self.inner_log = []
-        if deflation_scaling not in ("consistent", "printed"):
-            raise ValueError(deflation_scaling)
+        if deflation_scaling not in ("consistent", "printed") or (
+                deflation_scaling == "printed" and deflation_levels == 2):
+            raise ValueError("deflation_scaling must be 'consistent', or "
+                             "'printed' with two levels")
         printed = deflation_scaling == "printed"
         glk_scale = 4.0 if printed else 1.0
         if z is not None:

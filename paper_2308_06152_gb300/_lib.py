@@ -26,7 +26,8 @@ class HzDesc(ctypes.Structure):
                 ("outer_solver", c_int),
                 ("preconditioner", c_int),
                 ("deflation_levels", c_int),
-                ("no_cuda_graph", c_int)]
+                ("no_cuda_graph", c_int),
+                ("deflation_scaling", c_int)]
 
 
 class HzSolveInfo(ctypes.Structure):

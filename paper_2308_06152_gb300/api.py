@@ -19,6 +19,7 @@ EKIND = {"galerkin": 0, "red_o2": 1, "red_glk1": 2, "red_glk2": 3,
 PREC = {"fp64": 0, "mixed": 1, "mixed_bf16": 2}
 OUTER = {"fgmres": 0, "gcr": 1}
 PRECOND = {"adef1": 0, "tlkm": 1}
+DEFL_SCALE = {"consistent": 0, "printed": 1}
 OPS = {"helmholtz": 0, "cslp": 1, "vcycle": 2, "restrict_fw": 3,
        "prolong_bilinear": 4, "restrict_z": 5, "prolong_z": 6, "coarse_e": 7,
        "coarse_solve": 8, "precond": 9}
@@ -56,6 +57,7 @@ class Desc:
     precond: str = "adef1"
     deflation_levels: int = 1
     cuda_graph: bool = True
+    deflation_scaling: str = "consistent"
 
     def to_c(self):
         d = HzDesc()
@@ -76,6 +78,7 @@ class Desc:
         d.preconditioner = PRECOND[self.precond]
         d.deflation_levels = int(self.deflation_levels)
         d.no_cuda_graph = int(not self.cuda_graph)
+        d.deflation_scaling = DEFL_SCALE[self.deflation_scaling]
         return d
 
 

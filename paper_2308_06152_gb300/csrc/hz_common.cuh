@@ -215,11 +215,12 @@ void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
                      const int* done, cudaStream_t st);
-// coarse = R_Z fine  (zk = bilinear: full weighting; ho: 5x5 / 256)
+// coarse = scale * R_Z fine  (zk = bilinear: full weighting; ho: 5x5 / 256;
+// scale 4 gives the unscaled Z^T)
 template <class T>
 void launch_restrict_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
                        VRef<T> fine, C<T>* coarse, int nrhs, const int* done,
-                       cudaStream_t st);
+                       cudaStream_t st, double scale = 1.0);
 // fine = Z coarse (or fine += Z coarse when add != 0)
 template <class T>
 void launch_prolong_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
@@ -256,10 +257,12 @@ void launch_red_o6(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
 template <class T>
 void launch_red_9pt(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
                     const int* done, cudaStream_t st);
-// y = E_glk x on level 1 (variant 1 or 2)
+// y = E_glk x on level 1 (variant 1 or 2); the 5x5 rows are multiplied by
+// gscale (4: the stencil as printed, on the scale of Z^T A Z), the ReD-O2
+// boundary rows are not
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
-                int nrhs, const int* done, cudaStream_t st);
+                int nrhs, const int* done, cudaStream_t st, double gscale = 1.0);
 // zero the Dirichlet boundary nodes of nrhs vectors in place (no-op for
 // Sommerfeld grids)
 template <class T>

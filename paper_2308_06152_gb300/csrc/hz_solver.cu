@@ -112,6 +112,11 @@ bool valid_desc(const hz_desc* d, std::string* why) {
     *why = "deflation_levels must be 0/1, or 2 with deflation vectors and A-DEF1";
     return false;
   }
+  if (d->deflation_scaling != HZ_DEFL_SCALE_CONSISTENT &&
+      (d->deflation_scaling != HZ_DEFL_SCALE_PRINTED || d->deflation_levels == 2)) {
+    *why = "deflation_scaling must be CONSISTENT, or PRINTED with at most two levels";
+    return false;
+  }
   return true;
 }
 
@@ -386,6 +391,19 @@ hz_status init_shapes(hz_solver* s) {
 // / h^2, i.e. M = -Lap - (beta1 - i beta2) k^2 (with beta2 = -0.5 the shift
 // damps with the same sign as the Sommerfeld rows).
 inline Shift cslp(const hz_solver* s) { return Shift{s->d.beta1, -s->d.beta2}; }
+
+// Deflation restriction scale (hz_defl_scale): 4 turns R_Z = Z^T / 4 into
+// the printed Z^T, for re-discretised E only (the Galerkin E's deflation
+// does not depend on the scale); the printed 5x5 ReD-Glk rows are 4 times
+// those on the Z^T / 4 scale.
+inline double rz_scale(const hz_solver* s) {
+  return (s->d.deflation_scaling == HZ_DEFL_SCALE_PRINTED && s->d.ekind != HZ_E_GALERKIN)
+             ? 4.0
+             : 1.0;
+}
+inline double glk_scale(const hz_solver* s) {
+  return s->d.deflation_scaling == HZ_DEFL_SCALE_PRINTED ? 4.0 : 1.0;
+}
 inline Shift helm1() { return Shift{1.0, 0.0}; }
 
 // FP64 view of level l (k2d present at every level)
@@ -492,7 +510,7 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
                      done, st);
       break;
     case HZ_E_RED_GLK1:
-      launch_glk<T>(Cc.dev(), bc, 1, x, y, nrhs, done, st);
+      launch_glk<T>(Cc.dev(), bc, 1, x, y, nrhs, done, st, glk_scale(s));
       break;
     case HZ_E_RED_O4:
       launch_red_o4<T>(Cc.dev(), bc, x, y, nrhs, done, st);
@@ -507,7 +525,7 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
       launch_red_9pt<T>(Cc.dev(), bc, x, y, nrhs, done, st);
       break;
     default:
-      launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st);
+      launch_glk<T>(Cc.dev(), bc, 2, x, y, nrhs, done, st, glk_scale(s));
       break;
   }
 }
@@ -632,7 +650,7 @@ void inner_pre(hz_solver* s, int nrhs) {
     launch_prolong_z<T>(F, Cc, s->d.bc, s->d.zkind, (const C<T>*)s->eb, (C<T>*)s->q, 0,
                         nrhs, ks.done, s->st);
     launch_restrict_z<T>(F, Cc, s->d.bc, s->d.zkind, vref<T>((C<T>*)s->q), (C<T>*)s->eb,
-                         nrhs, ks.done, s->st);
+                         nrhs, ks.done, s->st, rz_scale(s));
     return;
   }
   const long long n1 = s->lv[1].n;
@@ -891,7 +909,7 @@ VRef<T> precond_begin(hz_solver* s, VRef<double> vin, int nrhs, const int* done)
   }
   if (s->d.zkind != HZ_Z_NONE)
     launch_restrict_z<T>(s->lv[0].dev(), s->lv[1].dev(), s->d.bc, s->d.zkind, v,
-                         (C<T>*)s->v1, nrhs, done, s->st);
+                         (C<T>*)s->v1, nrhs, done, s->st, rz_scale(s));
   return v;
 }
 // (last part, after v2 = E^-1 v1: q = Z v2, z = M^-1 (v - A q) + q)
@@ -933,7 +951,8 @@ hz_status precond_tlkm(hz_solver* s, VRef<double> vin, VRef<double> zout, int nr
   const LevelDev F = s->lv[0].dev(), Cc = s->lv[1].dev();
   C<T>* w = (C<T>*)s->yv;
   vcycle<T>(s, 0, v, w, nrhs, done);
-  launch_restrict_z<T>(F, Cc, bc, s->d.zkind, vref<T>(w), (C<T>*)s->v1, nrhs, done, st);
+  launch_restrict_z<T>(F, Cc, bc, s->d.zkind, vref<T>(w), (C<T>*)s->v1, nrhs, done, st,
+                       rz_scale(s));
   const hz_status e = coarse_solve<T>(s, (const C<T>*)s->v1, (C<T>*)s->v2, nrhs, done);
   if (e != HZ_OK) return e;
   launch_prolong_z<T>(F, Cc, bc, s->d.zkind, (const C<T>*)s->v2, (C<T>*)s->q, 0, nrhs,
@@ -1618,7 +1637,7 @@ hz_status apply_op(hz_solver* s, hz_op op, int level, const double2* x, double2*
     case HZ_OP_RESTRICT_Z:
       conv_in(s->lv[0].n);
       launch_restrict_z<T>(s->lv[0].dev(), s->lv[1].dev(), bc, s->d.zkind, vref<T>(tin),
-                           yout, nrhs, nullptr, st);
+                           yout, nrhs, nullptr, st, rz_scale(s));
       conv_out(s->lv[1].n);
       return cuda_check(s, "apply restrict_z");
     case HZ_OP_PROLONG_Z:

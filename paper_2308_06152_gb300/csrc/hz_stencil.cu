@@ -39,7 +39,7 @@ __global__ void k_helm(LevelDev L, int bc, T sre, T sim, VRef<T> xin,
 template <class T>
 __global__ void k_restrict_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
                              VRef<T> fin, C<T>* __restrict__ coarse,
-                             const int* __restrict__ done) {
+                             const int* __restrict__ done, T scale) {
   const int I = blockIdx.x * BX + threadIdx.x, J = blockIdx.y * BY + threadIdx.y;
   const int r = blockIdx.z;
   if (I >= Lc.nx || J >= Lc.ny || (done && done[r])) return;
@@ -66,7 +66,7 @@ __global__ void k_restrict_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
       acc = rfma(wx * wy * T(0.25), f[(long long)jf * Lf.nx + ifn], acc);
     }
   }
-  coarse[r * nc + idc] = acc;
+  coarse[r * nc + idc] = scale * acc;
 }
 
 // 1-D interpolation weights of a fine node: (coarse index, weight) pairs.
@@ -348,7 +348,7 @@ __device__ C<T> glk_node(const LevelDev& L, int bc, const C<T>* __restrict__ x,
 
 template <class T>
 __global__ void k_glk(LevelDev L, int bc, int variant, const C<T>* __restrict__ x,
-                      C<T>* __restrict__ y, const int* __restrict__ done) {
+                      C<T>* __restrict__ y, const int* __restrict__ done, T gscale) {
   const int i = blockIdx.x * BX + threadIdx.x, j = blockIdx.y * BY + threadIdx.y;
   const int r = blockIdx.z;
   if (i >= L.nx || j >= L.ny || (done && done[r])) return;
@@ -379,7 +379,7 @@ __global__ void k_glk(LevelDev L, int bc, int variant, const C<T>* __restrict__ 
       acc = rfma(c, glk_node<T>(L, bc, xr, in, jn), acc);
     }
   }
-  y[r * n + id] = acc;
+  y[r * n + id] = gscale * acc;
 }
 
 // ReD-O4 (Sec. 5.2.3): nodes whose 4th-order cross stays inside the grid use
@@ -850,10 +850,10 @@ void launch_helm(const LevelDev& L, int bc, Shift s, VRef<T> x, VRef<T> b,
 template <class T>
 void launch_restrict_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
                        VRef<T> fine, C<T>* coarse, int nrhs, const int* done,
-                       cudaStream_t st) {
+                       cudaStream_t st, double scale) {
   HZ_COUNT();
   k_restrict_z<T><<<grid2d(Lc.nx, Lc.ny, nrhs), dim3(BX, BY), 0, st>>>(
-      Lf, Lc, bc, zk, fine, coarse, done);
+      Lf, Lc, bc, zk, fine, coarse, done, T(scale));
 }
 template <class T>
 void launch_prolong_z(const LevelDev& Lf, const LevelDev& Lc, int bc, int zk,
@@ -900,10 +900,10 @@ void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C
 }
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,
-                int nrhs, const int* done, cudaStream_t st) {
+                int nrhs, const int* done, cudaStream_t st, double gscale) {
   HZ_COUNT();
   k_glk<T><<<grid2d(L.nx, L.ny, nrhs), dim3(BX, BY), 0, st>>>(L, bc, variant, x,
-                                                               y, done);
+                                                               y, done, T(gscale));
 }
 template <class T>
 void launch_red_o4(const LevelDev& L, int bc, const C<T>* x, C<T>* y, int nrhs,
@@ -1011,7 +1011,7 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                                cudaStream_t);                                   \
   template void launch_restrict_z<T>(const LevelDev&, const LevelDev&, int,     \
                                      int, VRef<T>, C<T>*, int, const int*,      \
-                                     cudaStream_t);                             \
+                                     cudaStream_t, double);                     \
   template void launch_prolong_z<T>(const LevelDev&, const LevelDev&, int, int, \
                                     const C<T>*, C<T>*, int, int, const int*,   \
                                     cudaStream_t);                              \
@@ -1019,7 +1019,7 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                                          int, const C<T>*, C<T>*, int,          \
                                          const int*, cudaStream_t);             \
   template void launch_glk<T>(const LevelDev&, int, int, const C<T>*, C<T>*,    \
-                              int, const int*, cudaStream_t);                   \
+                              int, const int*, cudaStream_t, double);           \
   template void launch_mask_dirichlet<T>(const LevelDev&, int, C<T>*, int,      \
                                          cudaStream_t);                        \
   template void launch_red_o4<T>(const LevelDev&, int, const C<T>*, C<T>*, int, \
