@@ -99,6 +99,12 @@ MUTATIONS = [
      SOL + "test_gradient_matches_central_differences"),
     ("gradient.py", "grad -= np.real(np.conj(lam) * ap * u)", "grad -= np.real(lam * ap * u)",
      SOL + "test_gradient_matches_central_differences"),
+    ("operators.py", "full = (keep @ full_o2 + glk_scale * full_glk).tocsr()",
+     "full = (keep @ full_o2 + full_glk).tocsr()",
+     SOL + "test_printed_scaling_reproduces_table5_row"),
+    ("solver.py", "self.RZ = self.Z.T.tocsr() if printed else ops.restriction(self.Z)",
+     "self.RZ = ops.restriction(self.Z)",
+     SOL + "test_printed_scaling_reproduces_tables_2_and_3"),
     ("krylov.py", "g[j + 1] = -np.conj(sn[j]) * g[j]", "g[j + 1] = np.conj(sn[j]) * g[j]", KRY),
     ("krylov.py", "H[i + 1, j] = -np.conj(sn[i]) * H[i, j] + cs[i] * H[i + 1, j]",
      "H[i + 1, j] = -sn[i] * H[i, j] + cs[i] * H[i + 1, j]", KRY),
