@@ -309,13 +309,15 @@ def test_printed_scaling_reproduces_tables_2_and_3(table, row):
     assert all(_near(o, int(p)) for o, p in zip(ours, g[2:])), (ours, g[2:])
 
 
-def test_printed_scaling_reproduces_table5_row():
-    """Table 5, MP-2b 65^2, k = 40, higher-order deflation vectors: with
+@pytest.mark.parametrize("block", ["outer", "outer_kh03125"])
+def test_printed_scaling_reproduces_table5_row(block):
+    """Table 5, MP-2b, higher-order deflation vectors, 65^2 / k = 40
+    (kh = 0.625) and 129^2 / k = 40 (kh = 0.3125, with ReD-O6): with
     R_Z = Z^T and the ReD-Glk 5x5 rows as printed, every coarse operator's
     outer count is the printed one to +-2, including ReD-Glk1 needing more
     iterations than ReD-Glk2 (its two ReD-O2 boundary rings are off the
     Z^T A Z scale, ReD-Glk2's one ring less so)."""
-    g = load_golden("table5_mp2b.txt")["outer"][0]
+    g = load_golden("table5_mp2b.txt")[block][0]
     n, k = int(g[0]), float(g[1])
     ours = {e: _outer_printed(n, k, ops.SOMMERFELD, "ho", e, "adef1")
             for e, p in zip(E_COLS, g[2:]) if p}
