@@ -250,10 +250,13 @@ def test_table5_comparisons_of_coarse_operators():
     fewer than ReD-O2 and ReD-O6 no fewer than ReD-O4; ReD-cmpO4 needs
     the fewest inner iterations per coarse solve among the re-discretised
     O-family; ReD-Glk1 and ReD-Glk2 keep their outer counts across the
-    rows (+-1).  The oracle's counts are lower than the printed ones for
-    every re-discretised E and its inner counts about half; the paper's
-    ReD-Glk1 > ReD-Glk2 does not hold for the oracle (7 / 8 on both rows),
-    so it is not asserted."""
+    rows (+-1).  This runs the oracle at a coarse tolerance of 1e-6 with
+    R_Z = Z^T / 4: its outer counts are lower than the printed ones for
+    every re-discretised E (the printed scaling restores them), its inner
+    counts about half (the printed ones are taken at 1e-12, pinned in
+    test_table5_inner_counts_at_the_stated_coarse_tolerance); the paper's
+    ReD-Glk1 > ReD-Glk2 does not hold here (7 / 8 on both rows), so it is
+    not asserted."""
     g = load_golden("table5_mp2b.txt")
     rows = []
     for r in range(2):
@@ -324,6 +327,48 @@ def test_printed_scaling_reproduces_table5_row(block):
     paper = {e: int(p) for e, p in zip(E_COLS, g[2:]) if p}
     assert all(_near(ours[e], paper[e]) for e in paper), (ours, paper)
     assert ours["red_glk1"] > ours["red_glk2"]
+
+
+TABLE5_TAU_C = 1e-12   # Sec. 6, introduction: the coarse-grid solver's
+                       # tolerance of the convergence study
+
+
+def _table5_counts_printed(n, k, e):
+    """Outer iterations and mean inner iterations per coarse solve of a
+    Table 5 run: MP-2b, higher-order Z, left-preconditioned GMRES to 1e-6
+    (Alg. 1), the coarse problem by CSLP-GMRES to the coarse tolerance the
+    convergence study states (1e-12), deflation restriction as printed."""
+    orc = Oracle(n, n, 1.0 / (n - 1), np.full((n, n), k * k), ops.SOMMERFELD,
+                 z="ho", e=e, coarse_tol=TABLE5_TAU_C,
+                 deflation_scaling="printed")
+    b = np.zeros((n, n), complex)
+    b[n // 2, n // 2] = 1.0
+    info = orc.solve_left(b, tol=1e-6)[1]
+    return info.outer_iters, float(np.mean(info.inner_iters))
+
+
+@pytest.mark.parametrize("row,cols", [
+    (0, ["galerkin", "red_o2", "red_o4", "red_cmpo4", "red_glk1", "red_glk2"]),
+    (1, ["galerkin", "red_glk2"])])
+def test_table5_inner_counts_at_the_stated_coarse_tolerance(row, cols):
+    """Table 5's parenthesised counts (iterations of one coarse solve) are
+    taken with the coarse-grid solver's tolerance at 1e-12, the value the
+    introduction of Sec. 6 sets for the convergence study.  With that
+    tolerance (and the printed deflation restriction, under which the
+    outer counts are the printed ones) the oracle's mean inner iterations
+    per coarse solve are the printed ones to within 20 % on the 65^2 row
+    for every coarse operator and on the 129^2 row for str-Glk and
+    ReD-Glk2 (measured ratios 0.93 ... 1.19; at a coarse tolerance of 1e-6
+    they are about half).  A mistake in the coarse V-cycle, the CSLP
+    shift, the coarse operators or the inner GMRES moves them off."""
+    g = load_golden("table5_mp2b.txt")
+    n, k = int(g["outer"][row, 0]), float(g["outer"][row, 1])
+    po = dict(zip(E_COLS, g["outer"][row, 2:]))
+    pi = dict(zip(E_COLS, g["inner"][row, 2:]))
+    for e in cols:
+        outer, inner = _table5_counts_printed(n, k, e)
+        assert _near(outer, int(po[e])), (e, outer, po[e])
+        assert 0.8 * pi[e] <= inner <= 1.2 * pi[e], (e, inner, pi[e])
 
 
 def test_coarse_tolerance_study_sec63():
