@@ -264,8 +264,16 @@ def ghost_values(level):
 
     Edge ghosts follow eq. (GhostPoint) (Sommerfeld) or eq.
     (DirchletGhostPoint) (Dirichlet) with k of the boundary node.  A corner
-    ghost can be reached through either direction; the wavenumber of a
-    ghost node is zero (Sec. 5.2.4), and the two orders are averaged.
+    ghost is reached by applying the rule once more along the ghost row (x
+    first) or the ghost column (y first); the two orders are averaged.  In
+    that second application the boundary node is itself a ghost; the
+    boundary condition holds along the boundary line continued past the
+    corner, so the rule takes the wavenumber of the corner node (the
+    nearest real node on that line).  The wavenumber zero of a ghost node
+    (Sec. 5.2.4) belongs to the mass stencil of eq. (ReD-Glk Kh), not to
+    this rule: with zero here the corner ghost would lose one 2 i k H u
+    term, an O(H) error that the 1/H^2 weight of the 5x5 Laplacian turns
+    into an O(1/H) inconsistency of the corner rows.
     """
     nx, ny, H, bc = level.nx, level.ny, level.h, level.bc
     k = np.sqrt(level.k2)
@@ -289,10 +297,10 @@ def ghost_values(level):
                                  real(i, ny - 2))
     for gi, bi, ii in ((-1, 0, 1), (nx, nx - 1, nx - 2)):
         for gj, bj, jj in ((-1, 0, 1), (ny, ny - 1, ny - 2)):
-            # x rule on the ghost row gj (ghost k = 0 at (bi, gj))
-            ox = _ghost_rule(bc, H, kb(bi, gj), g[(bi, gj)], g[(ii, gj)])
-            # y rule on the ghost column gi (ghost k = 0 at (gi, bj))
-            oy = _ghost_rule(bc, H, kb(gi, bj), g[(gi, bj)], g[(gi, jj)])
+            # x rule on the ghost row gj, y rule on the ghost column gi,
+            # both with k of the corner node (bi, bj)
+            ox = _ghost_rule(bc, H, kb(bi, bj), g[(bi, gj)], g[(ii, gj)])
+            oy = _ghost_rule(bc, H, kb(bi, bj), g[(gi, bj)], g[(gi, jj)])
             avg = {}
             for d in (ox, oy):
                 for key, c in d.items():

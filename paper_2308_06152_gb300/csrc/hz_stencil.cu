@@ -293,8 +293,12 @@ __constant__ float c_glk_mass[25] = {
 // Value of x at a node one layer outside the grid (ghost), Sec. 5.2.4:
 // Sommerfeld u_g = u_in + 2 i H k_b u_b (eq. GhostPoint), Dirichlet
 // u_g = 2 u_b - u_in with u_b = 0 (eq. DirchletGhostPoint).  Corner ghosts:
-// the average of reaching them through x first and through y first, with
-// the wavenumber of a ghost node taken as zero.
+// the average of reaching them through x first (the rule along the ghost
+// row) and through y first (along the ghost column).  That second
+// application's boundary node is a ghost; the boundary condition holds on
+// the boundary line continued past the corner, so it takes the wavenumber
+// of the corner node.  (The zero wavenumber of ghost nodes belongs to the
+// mass stencil only; here it would leave the corner rows inconsistent.)
 template <class T>
 __device__ C<T> glk_node(const LevelDev& L, int bc, const C<T>* __restrict__ x,
                          int i, int j) {
@@ -336,9 +340,11 @@ __device__ C<T> glk_node(const LevelDev& L, int bc, const C<T>* __restrict__ x,
   const int bi = (i < 0) ? 0 : nx - 1, ii = (i < 0) ? 1 : nx - 2;
   const int bj = (j < 0) ? 0 : ny - 1, jj = (j < 0) ? 1 : ny - 2;
   C<T> ox, oy;
-  if (bc == BC_SOMMERFELD) {  // ghost k = 0: the rule returns the inner value
-    ox = gyv(ii, j);
-    oy = gxv(i, jj);
+  if (bc == BC_SOMMERFELD) {
+    const T kc = sqrt(k2[(long long)bj * nx + bi]);
+    const C<T> bx = gyv(bi, j), by = gxv(i, bj), ix = gyv(ii, j), iy = gxv(i, jj);
+    ox = mkc(ix.x - H2 * kc * bx.y, ix.y + H2 * kc * bx.x);
+    oy = mkc(iy.x - H2 * kc * by.y, iy.y + H2 * kc * by.x);
   } else {
     ox = T(2) * gyv(bi, j) - gyv(ii, j);
     oy = T(2) * gxv(i, bj) - gxv(i, jj);

@@ -58,6 +58,9 @@ MUTATIONS = [
      "            for d in (g[(bi, gj)], g[(gi, bj)]):\n                for key, c in d.items():\n"
      "                    avg[key] = avg.get(key, 0) + c",
      OPS + "test_red_cmpo4_sommerfeld_ghost_rule"),
+    ("operators.py", "ox = _ghost_rule(bc, H, kb(bi, bj), g[(bi, gj)], g[(ii, gj)])",
+     "ox = _ghost_rule(bc, H, kb(bi, gj), g[(bi, gj)], g[(ii, gj)])",
+     OPS + "test_glk2_sommerfeld_second_ring_rows_are_consistent"),
     ("operators.py", "    [-98, 56, 980, 56, -98],", "    [-98, 56, 988, 56, -98],",
      OPS + "test_galerkin_ho_matches_printed_glk_stencils"),
     ("operators.py", "    [70, 1960, 4900, 1960, 70],", "    [70, 1960, 4800, 1960, 70],",

@@ -284,6 +284,46 @@ def test_glk2_dirichlet_laplacian_sine_modes():
                                    atol=1e-9 * abs(S).max())
 
 
+def test_glk2_sommerfeld_second_ring_rows_are_consistent():
+    """ReD-Glk2's 5x5 rows on the second ring reach one layer of ghost nodes,
+    filled by eq. (GhostPoint); the rows next to a corner also reach the
+    corner ghost.  For a smooth u that satisfies the first-order Sommerfeld
+    condition on every side (u = p(x) p(y) with -p'(0) = i k p(0) and
+    p'(1) = i k p(1)), the Laplacian part of those rows must approximate
+    -Lap u with an error that falls like H^2 under refinement, at an edge
+    row and at the corner row alike.  The mass part takes ghost k^2 = 0
+    (Sec. 5.2.4), so it is summed over the real nodes with the printed mass
+    stencil and added back.  A corner ghost built with the wavenumber of a
+    ghost node in its second application of eq. (GhostPoint) drops a
+    2 i k H u term: its corner-row error then grows like 1/H."""
+    g = load_golden("glk_stencils.txt")
+    mass = g["mass"] / g["mass_scale"][0, 0] / 4.0
+    k = 7.0
+    a = -1j * k
+    b = (2j * k + k * k) / (2 - 1j * k)
+
+    def p(x):
+        return 1 + a * x + b * x * x
+
+    assert abs(-a - 1j * k * p(0.0)) < 1e-12
+    assert abs((a + 2 * b) - 1j * k * p(1.0)) < 1e-10
+    errs = {"corner": [], "edge": []}
+    for n in (17, 33, 65):
+        H = 1.0 / (n - 1)
+        lv = ops.Level(n, n, H, np.full((n, n), k * k), ops.SOMMERFELD)
+        x = np.arange(n) * H
+        U = np.outer(p(x), p(x))
+        EU = lv.to_full(ops.red_glk(lv, 2) @ lv.to_unknowns(U))
+        for key, (i, j) in (("corner", (1, 1)), ("edge", (n // 2, 1))):
+            m = sum(mass[dj + 2, di + 2] * k * k * U[j + dj, i + di]
+                    for dj in range(-2, 3) for di in range(-2, 3)
+                    if 0 <= i + di < n and 0 <= j + dj < n)
+            exact = -2 * b * (p(x[j]) + p(x[i]))
+            errs[key].append(abs(EU[j, i] + m - exact) / abs(exact))
+    for key, e in errs.items():
+        assert e[1] < e[0] / 3 and e[2] < e[1] / 3, (key, e)
+
+
 @pytest.mark.parametrize("variant", [1, 2])
 @pytest.mark.parametrize("bc", [ops.DIRICHLET, ops.SOMMERFELD])
 def test_red_glk_mass_part_takes_each_nodes_own_wavenumber(variant, bc):

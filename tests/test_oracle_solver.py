@@ -30,7 +30,10 @@ def _vcycle_matrix(orc, level):
 def test_vcycle_error_propagation_identity(bc):
     """Textbook multigrid identity, level by level:
     I - B_l M_l = S_l (I - P_l B_{l+1} R_l M_l) S_l with S_l = I - w D^-1 M_l,
-    and B_L = M_L^{-1} at the coarsest level."""
+    and B_L = M_L^{-1} at the coarsest level.  The weight is Sec. 3.1's
+    relaxation parameter 0.8, written here rather than read from the oracle,
+    so the identity also pins the weight the oracle's V-cycle uses by
+    default."""
     nx, ny = 17, 9
     orc = Oracle(nx, ny, 0.05, _k2(ny, nx, 0), bc, z=None,
                  coarsest="direct")
@@ -42,7 +45,7 @@ def test_vcycle_error_propagation_identity(bc):
     for l in range(orc.L):
         M = orc.M[l].toarray()
         n = M.shape[0]
-        S = np.eye(n) - np.diag(orc.omega / np.diag(M)) @ M
+        S = np.eye(n) - np.diag(0.8 / np.diag(M)) @ M
         P, R = orc.P[l].toarray(), orc.R[l].toarray()
         lhs = np.eye(n) - Bs[l] @ M
         rhs = S @ (np.eye(n) - P @ Bs[l + 1] @ R @ M) @ S
