@@ -42,7 +42,10 @@ typedef enum {
                                  iterate, info.relres its true residual     */
   HZ_BREAKDOWN = 5,           /* Arnoldi breakdown without convergence      */
   HZ_NAN = 6,                 /* NaN / Inf met in a residual norm           */
-  HZ_TIMEOUT = 7,             /* reserved: no kernel of this library waits */
+  HZ_TIMEOUT = 7,             /* a bounded pipeline wait inside a kernel ran
+                                 out (the TMA-ring Gram-Schmidt kernels wait
+                                 on mbarriers for at most 2 s each); the
+                                 solve stopped, the solver stays usable    */
   HZ_CUDA_ERROR = 8
 } hz_status;
 
@@ -223,7 +226,10 @@ hz_status hz_last_inner_iters(hz_solver* s, int* iters_host, int nrhs);
 int hz_num_levels(const hz_solver* s);
 hz_status hz_level_shape(const hz_solver* s, int level, int* nx, int* ny);
 
-/* Adjoint gradient of J(m) = 1/2 sum_s ||S u_s - d_s||^2 with respect to the
+/* The paper solves forward problems only and has no counterpart of this
+ * entry point; it builds on the paper's solver (the adjoint solve reuses it
+ * unchanged, see below).
+ * Adjoint gradient of J(m) = 1/2 sum_s ||S u_s - d_s||^2 with respect to the
  * squared slowness m, k^2 = omega^2 m (k^2 is the array given to hz_setup).
  * S samples u at the nrec flat node indices rec_idx_dev (device int32).
  * src_dev: device complex128 [nshots][ny][nx]; d_obs_dev: device complex128
@@ -238,7 +244,8 @@ hz_status hz_gradient(hz_solver* s, double omega, const void* src_dev,
                       const void* d_obs_dev, double tol, double* J_host,
                       double* grad_dev, hz_solve_info* info_host);
 
-/* Releases the host handle (the workspace stays the caller's). */
+/* Releases the host handle (the workspace stays the caller's).  Resource
+ * handling only; the paper has no counterpart. */
 hz_status hz_destroy(hz_solver* s);
 
 /* Size of the fixed device scratch array used by
@@ -265,11 +272,15 @@ hz_status hz_destroy(hz_solver* s);
  *   cuda_stream cudaStream_t the work is issued on (NULL = default stream)
  * Returns HZ_WORKSPACE_TOO_SMALL when 2 * nrhs * nx * ny * 16 bytes exceed
  * HZ_NOALLOC_SCRATCH_BYTES (no work is issued), HZ_INVALID_ARG for bad
- * arguments, HZ_CUDA_ERROR if a launch fails.
+ * arguments, HZ_CUDA_ERROR if a launch fails, or, before any work is
+ * issued, if a CUDA error is already pending on the calling thread (that
+ * error is left pending for the caller).
  *
  * The first call on each device looks up the array's device address with
  * cudaGetSymbolAddress (with that device current); make that first call
- * before any stream capture begins.  All calls share the one array: calls
+ * before any stream capture begins.  The address is kept for the life of
+ * the process: it assumes the device's primary context is not reset
+ * (cudaDeviceReset) while the library is loaded.  All calls share the one array: calls
  * whose work overlaps on the GPU (other streams, other threads) race and
  * must be serialised by the caller.  No state carries over between calls:
  * every scratch entry read is written by the same call first. */

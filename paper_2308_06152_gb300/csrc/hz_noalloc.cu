@@ -66,6 +66,9 @@ extern "C" hz_status hz_coarse_galerkin_noalloc(int nx, int ny, double h,
       (bc != HZ_BC_DIRICHLET && bc != HZ_BC_SOMMERFELD) ||
       (zkind != HZ_Z_BILINEAR && zkind != HZ_Z_HO))
     return HZ_INVALID_ARG;
+  // an error left pending by the caller's earlier work would otherwise be
+  // reported (and cleared) by the check after this call's launches
+  if (cudaPeekAtLastError() != cudaSuccess) return HZ_CUDA_ERROR;
   // two fine-grid complex FP64 intermediates per right-hand side
   const unsigned long long need =
       2ull * (unsigned long long)nrhs * (unsigned long long)nx * ny * sizeof(double2);
