@@ -81,10 +81,11 @@ WORKLOADS = {
                                  coarse_tol=1e-1, coarse_maxit=160,
                                  outer_maxit=30, tol=1e-6),
 }
-DEFAULT_WORKLOAD = "mp2b_1281_k800_b16"
+DEFAULT_WORKLOAD = "layered_2305x769_b64"
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_bench_counts.json")
 ORACLE_COUNT_KEY = {"mp2b_1281_k800_b16": "mp2b_1281_k800",
-                    "mp2a_81_k50": "mp2a_81_k50"}
+                    "mp2a_81_k50": "mp2a_81_k50",
+                    "layered_2305x769_b64": "layered_2305x769_b64"}
 
 
 def rank_sources(nodes, rank):
@@ -213,84 +214,100 @@ def hbm_peak():
 
 
 # ------------------------------------------------------------------ oracle
-def _oracle_iteration(wl_name, steps=1, warmup=0):
-    """Seconds of one outer flexible-GMRES iteration of the oracle (one
-    A-DEF1 application with its inner coarse solve, one A product and the
-    Gram-Schmidt step) on one right-hand side, and the inner iterations it
-    took."""
-    from oracle.solver import Oracle
-    cfg, model, b = build_inputs(wl_name)
-    orc = Oracle(model.nx, model.ny, model.h, model.k2, cfg["bc"], z=cfg["z"],
-                 e=cfg["e"], coarse_tol=cfg["coarse_tol"],
-                 coarse_maxit=cfg["coarse_maxit"])
-    lv = orc.levels[0]
-    bu = lv.to_unknowns(b[0])
-    v = bu / np.linalg.norm(bu)
-    times, inner = [], []
-    for it in range(warmup + steps):
-        orc.inner_log = []
-        t0 = time.perf_counter()
-        z = orc.adef1(v)
-        w = orc.A @ z
-        w = w - np.vdot(v, w) * v
-        np.linalg.norm(w)
-        dt = time.perf_counter() - t0
-        if it >= warmup:
-            times.append(dt)
-            inner.append(sum(orc.inner_log) or 1)
-    return float(np.mean(times)), float(np.mean(inner)), len(times)
+def _oracle_recorded(wl_name):
+    key = ORACLE_COUNT_KEY.get(wl_name)
+    if not key or not os.path.exists(ORACLE_COUNTS):
+        return key, None
+    with open(ORACLE_COUNTS) as fh:
+        rec = json.load(fh).get(key)
+    if rec and "sample_seconds" in rec and "seconds" in rec:
+        return key, rec
+    return key, None
 
 
-def _oracle_worker(wl_name):
-    return _oracle_iteration(wl_name)
+def _oracle_sample_worker(key):
+    """Set up the oracle for the workload's first shot and time its
+    calibration sample once (one spawned process per host core)."""
+    from oracle.record_bench_counts import (SAMPLE_INNER, calibration_sample,
+                                            make_oracle)
+    orc, b, _ = make_oracle(key)
+    return calibration_sample(orc, b, SAMPLE_INNER[key])
 
 
 def oracle_sample(wl_name, steps, warmup, all_cores=False):
-    """Bounded CPU sample of the oracle, scaled to a whole solve by the
-    oracle's own iteration counts for this workload.  With all_cores, the
-    same sample also runs in one process per host core at once (spawned
-    processes, each its own shot), as the batched CPU baseline."""
+    """CPU baseline: the FP64 oracle (SciPy CSR, one core) on the
+    workload's first shot.  A whole oracle solve of that shot was timed by
+    oracle/record_bench_counts.py, together with a bounded calibration
+    sample (the first coarse solve, stopped after a fixed number of inner
+    iterations) in the same process.  Here the same sample is timed again
+    on this host (``warmup`` untimed and ``steps`` timed repetitions), and
+    the recorded whole-solve time is carried over to this host by the ratio
+    of the two sample times.  With all_cores the sample also runs in one
+    spawned process per host core at once (each its own copy of the shot),
+    and the batched figure uses the per-process sample time."""
     cfg, model, _ = build_inputs(wl_name)
-    key = ORACLE_COUNT_KEY.get(wl_name)
-    counts = {}
-    if os.path.exists(ORACLE_COUNTS):
-        with open(ORACLE_COUNTS) as fh:
-            counts = json.load(fh)
-    outer = counts.get(key, {}).get("outer_iters") if key else None
-    inner_total = counts.get(key, {}).get("inner_iters_total") if key else None
-    t_iter, inner_mean, nsamp = _oracle_iteration(wl_name, steps, warmup)
     n_unk = unknowns(cfg, model)
-    value = None
-    how = "no recorded oracle iteration counts for this workload"
-    if outer and inner_total:
-        # full solve ~ outer iterations, each costing the sample's time per
-        # inner iteration times the inner iterations it needs on average
-        t_full = t_iter / inner_mean * inner_total
-        value = n_unk / t_full
-        how = (f"scaled to the oracle's {outer} outer / {inner_total} inner "
-               f"iterations for a full solve ({t_full:.0f} s)")
-    out = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-           "arithmetic": ("FP64 throughout (SciPy CSR), the oracle's own "
-                          "iteration counts"),
-           "sample": (f"one outer FGMRES iteration (A-DEF1 with its "
-                      f"{int(inner_mean)}-iteration inner coarse solve) "
-                      f"of 1 RHS of {wl_name}, {t_iter:.2f} s mean over "
-                      f"{nsamp}; {how}")}
-    if all_cores and value is not None:
+    key, rec = _oracle_recorded(wl_name)
+    if rec is None:
+        return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": f"no recorded whole oracle solve for {wl_name}"}
+    from oracle.record_bench_counts import (SAMPLE_INNER, calibration_sample,
+                                            make_oracle)
+    t0 = time.perf_counter()
+    orc, b, _ = make_oracle(key)
+    t_setup = time.perf_counter() - t0
+    times = []
+    for it in range(warmup + steps):
+        dt = calibration_sample(orc, b, SAMPLE_INNER[key])
+        if it >= warmup:
+            times.append(dt)
+    del orc
+    t_s = float(np.mean(times))
+    scale = t_s / rec["sample_seconds"]
+    t_full = rec["seconds"] * scale
+    out = {"value": n_unk / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "arithmetic": "FP64 throughout (SciPy CSR), the oracle's own "
+                         "iteration counts",
+           "seconds_per_solve": t_full,
+           "sample": (f"one shot of {wl_name} (its first source). Timed whole "
+                      f"oracle solve: {rec['seconds']:.1f} s, "
+                      f"{rec['outer_iters']} outer / {rec['inner_iters_total']} "
+                      f"inner iterations, on {rec.get('host_cpu', 'the recording host')} "
+                      f"(oracle/record_bench_counts.py); carried to this host "
+                      f"({_host_cpu()}) by a calibration sample (the first "
+                      f"coarse solve stopped after {SAMPLE_INNER[key]} inner "
+                      f"iterations): {t_s:.2f} s here against "
+                      f"{rec['sample_seconds']:.2f} s there (mean of {len(times)} "
+                      f"after {warmup} untimed; set-up {t_setup:.1f} s not "
+                      f"counted), so {t_full:.0f} s per solve here")}
+    if all_cores:
         import multiprocessing as mp
         procs = os.cpu_count() or 1
         t0 = time.perf_counter()
         with mp.get_context("spawn").Pool(procs) as pool:
-            res = pool.map(_oracle_worker, [wl_name] * procs)
+            res = pool.map(_oracle_sample_worker, [key] * procs)
         wall = time.perf_counter() - t0
-        per = [t / i * inner_total for (t, i, _) in res]
+        t_par = float(np.mean(res))
+        t_full_par = rec["seconds"] * t_par / rec["sample_seconds"]
         out["all_cores"] = {
-            "value": n_unk * procs / float(np.mean(per)), "unit": UNIT,
-            "cores": procs,
-            "sample": (f"the same sample in {procs} spawned processes at once "
-                       f"(one shot each, {wall:.0f} s wall incl. set-up), "
-                       "scaled the same way")}
+            "value": n_unk * procs / t_full_par, "unit": UNIT, "cores": procs,
+            "sample": (f"the calibration sample in {procs} spawned processes at "
+                       f"once, one shot each: {t_par:.2f} s per process "
+                       f"({wall:.0f} s wall incl. set-up), so "
+                       f"{t_full_par:.0f} s per solve per core")}
     return out
+
+
+def _host_cpu():
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
 
 
 def workload_config(args, cfg, model, world, b_np):
@@ -310,6 +327,43 @@ def workload_config(args, cfg, model, world, b_np):
             "parallelism": f"replicas{world}",
             "l2": ("inputs larger than L2 (each batch vector "
                    f"{b_np.nbytes / 1e6:.0f} MB)")}
+
+
+# DRAM bytes / algorithmic bytes of a profiled kernel class, measured with
+# ncu on the same kernel and storage (the summary under profiles/ names the
+# command); traffic scales with the rows streamed, so a bench launch's
+# traffic is this ratio times its algorithmic bytes.
+TRAFFIC = {}
+
+
+def roofline_entry(args, tuning, kc, prof, prof_ms):
+    if not prof or prof[0] <= 0:
+        return None
+    n_l, ms_k, by = prof
+    peak, peak_src = hbm_peak()
+    achieved = by / (ms_k / 1e3) / 1e9
+    ratio = TRAFFIC.get((kc, args.workload, _variant(kc, tuning)))
+    return {"kernel": KERNEL_NAMES[kc], "bound": "hbm",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src,
+            "traffic": (ratio[0] * by / n_l if ratio else None),
+            "traffic_source": (ratio[1] if ratio else None),
+            "launches": int(n_l),
+            "alg_bytes_per_launch": by / n_l,
+            "avg_launch_us": 1e3 * ms_k / n_l,
+            "timed_over": (f"{args.profile_steps} further step(s) of the "
+                           "same workload with the kernels issued one by "
+                           "one (events around each launch)"),
+            "profiled_step_ms": prof_ms,
+            "share_of_step": ms_k / (prof_ms * args.profile_steps)}
+
+
+def _variant(kc, tuning):
+    if kc == "mdot":
+        return tuning.get("mdot_kernel")
+    if kc == "maxpy":
+        return tuning.get("maxpy_kernel")
+    return None
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -382,10 +436,10 @@ def run_ours(args):
     # per-kernel timing: CUDA events must bracket every launch of the
     # profiled kernel class, which a replayed graph does not allow, so these
     # steps issue the same kernels one by one
-    prof = None
-    prof_ms = None
-    if args.profile_kernel != "none":
-        solver.profile_begin(args.profile_kernel, max_launches=200000)
+    profs = []
+    classes = [c for c in args.profile_kernel.split(",") if c and c != "none"]
+    for kc in classes:
+        solver.profile_begin(kc, max_launches=200000)
         pe0 = torch.cuda.Event(enable_timing=True)
         pe1 = torch.cuda.Event(enable_timing=True)
         pe0.record(stream)
@@ -393,8 +447,8 @@ def run_ours(args):
             solver.solve(b, tol=tol)
         pe1.record(stream)
         torch.cuda.synchronize()
-        prof = solver.profile_end()
-        prof_ms = pe0.elapsed_time(pe1) / args.profile_steps
+        profs.append((kc, solver.profile_end(),
+                      pe0.elapsed_time(pe1) / args.profile_steps))
     clocks = sampler.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     if world > 1:
@@ -418,63 +472,41 @@ def run_ours(args):
                            "cuda")
     io_bytes = int(b_np.nbytes)
 
-    roof = None
-    # DRAM bytes / algorithmic bytes of the profiled kernel, measured with ncu
-    # on a smaller case of the same kernel and storage (the summary under
-    # profiles/ names the command); traffic scales with the rows streamed,
-    # so a bench launch's traffic is this ratio times its bytes.  The two
-    # TMA-ring widths (8 or 16 consumer warps) issue the same bulk copies,
-    # w loads and partial-sum stores; only the split of a stage among the
-    # consumer warps differs, so the ratio taken on the 16-warp one holds
-    # for both.
-    traffic_ratio = None
-    if (args.profile_kernel == "mdot" and tuning.get("mdot_kernel") in (1, 2)
-            and args.prec == "mixed_bf16" and args.basis16):
-        src = "profiles/k_mdot_tma_dram_mp2b_641_k400_b8_prof.md"
-        if tuning.get("mdot_kernel") == 1:
-            src += (" (captured on the 16-consumer-warp instantiation; this "
-                    "8-warp one issues the same copies and loads)")
-        traffic_ratio = (1.013, src)
-    if prof and prof[0] > 0:
-        n_l, ms_k, by = prof
-        peak, peak_src = hbm_peak()
-        achieved = by / (ms_k / 1e3) / 1e9
-        roof = {"kernel": KERNEL_NAMES[args.profile_kernel], "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "traffic": (traffic_ratio[0] * by / n_l if traffic_ratio else None),
-                "traffic_source": (traffic_ratio[1] if traffic_ratio else None),
-                "launches": int(n_l),
-                "alg_bytes_per_launch": by / n_l,
-                "avg_launch_us": 1e3 * ms_k / n_l,
-                "timed_over": (f"{args.profile_steps} further step(s) of the "
-                               "same workload with the kernels issued one by "
-                               "one (events around each launch)"),
-                "profiled_step_ms": prof_ms,
-                "share_of_step": ms_k / (prof_ms * args.profile_steps)}
+    roofs = [roofline_entry(args, tuning, kc, prof, prof_ms)
+             for kc, prof, prof_ms in profs]
+    roofs = [r for r in roofs if r]
+    roof = roofs[0] if roofs else None
 
     fp64 = None
     if args.compare_fp64 and args.prec != "fp64":
-        # the same workload with the preconditioner in FP64 (one timed solve)
+        # the same workload's first shots with the preconditioner in FP64
+        # (one untimed and one timed solve); a sub-batch bounds the run time
+        # of this roughly 16x slower form
         solver.close()
         del solver
         torch.cuda.synchronize()
         import dataclasses
-        s64 = Solver(dataclasses.replace(desc, prec="fp64",
-                                         inner_basis_fp16=False), model.k2)
-        s64.solve(b, tol=tol)
+        nsub = max(1, min(cfg["nrhs"], args.fp64_shots))
+        s64 = Solver(dataclasses.replace(desc, prec="fp64", inner_basis_fp16=False,
+                                         nrhs_max=nsub), model.k2)
+        b64 = b[:nsub].contiguous()
+        s64.solve(b64, tol=tol)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s64.stream)
-        _, info64 = s64.solve(b, tol=tol)
+        _, info64 = s64.solve(b64, tol=tol)
         e1.record(s64.stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
-        fp64 = {"value": units / (ms64 / 1e3), "unit": UNIT,
+        units64 = n_unk * nsub * world
+        fp64 = {"value": units64 / (ms64 / 1e3), "unit": UNIT,
                 "ms_per_step": ms64, "steps": 1, "warmup": 1,
+                "shots": nsub,
+                "sub_batch": (f"the first {nsub} of the workload's "
+                              f"{cfg['nrhs']} shots in one batch"),
                 "outer_iters": [i.outer_iters for i in info64],
                 "max_true_relres": max(i.relres for i in info64),
-                "mixed_over_fp64": value / (units / (ms64 / 1e3))}
+                "mixed_over_fp64": value / (units64 / (ms64 / 1e3))}
         s64.close()
 
     cpu = None
@@ -497,6 +529,7 @@ def run_ours(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
             "roofline": roof,
+            "roofline_more": roofs[1:],
             "cpu_baseline": cpu,
             "fp64": fp64,
             "solve": {"outer_iters": outer, "inner_iters_total": inner,
@@ -569,9 +602,13 @@ def main():
                     help="force hz_tuning.vcycle_fused")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
-    ap.add_argument("--profile-kernel", choices=["mdot", "maxpy", "none"],
-                    default="mdot",
-                    help="kernel class timed live for the roofline entry")
+    ap.add_argument("--profile-kernel", default="mdot,maxpy",
+                    help="comma-separated kernel classes (mdot, maxpy) timed "
+                         "live for the roofline entries (the first one is "
+                         "'roofline', the others 'roofline_more'); 'none' "
+                         "skips them")
+    ap.add_argument("--fp64-shots", type=int, default=16,
+                    help="shots of the FP64 comparison batch")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
