@@ -405,6 +405,10 @@ def run_ours(args):
         solver.set_tuning(galerkin_apply=args.galerkin_apply)
     if args.vcycle_fused is not None:
         solver.set_tuning(vcycle_fused=args.vcycle_fused)
+    if args.vcycle_rpb is not None:
+        solver.set_tuning(vcycle_rhs_per_block=args.vcycle_rpb)
+    if args.vcycle_tile is not None:
+        solver.set_tuning(vcycle_tile=args.vcycle_tile)
     tuning = solver.get_tuning()
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
@@ -540,6 +544,50 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_kernel_bench(args):
+    """V-cycle kernels alone at the size they run at inside the workload's
+    inner solve: a solver on the workload's deflation coarse grid (level 1:
+    ((nx+1)/2) x ((ny+1)/2) nodes, spacing 2h, the injected k^2), without
+    deflation and with one-vector Krylov bases, so one V-cycle from its
+    level 0 is the inner solve's V-cycle (FP32 input and output, the
+    workload's level storage) on about 2.5 GB of device memory.  Prints
+    the autotuner's time per V-cycle for every V-cycle candidate, then
+    applies --kb-reps V-cycles with the tuning given on the command line
+    (for ncu captures of single kernels)."""
+    import torch
+
+    from paper_2308_06152_gb300.api import Desc, Solver
+    torch.cuda.set_device(0)
+    cfg, model, _ = build_inputs(args.workload)
+    k2c = np.ascontiguousarray(model.k2[::2, ::2])
+    ny1, nx1 = k2c.shape
+    nrhs = cfg["nrhs"]
+    s = Solver(Desc(nx1, ny1, 2 * model.h, bc=cfg["bc"], z=None, e="galerkin",
+                    prec=args.prec, nrhs_max=nrhs, coarse_maxit=1, outer_maxit=1,
+                    inner_basis_fp16=bool(args.basis16)), k2c)
+    vc = None
+    if args.autotune:
+        ms = s.autotune(nrhs)["ms"]
+        vc = {k: v for k, v in ms.items() if k.startswith("vcycle")}
+    choice = {}
+    for key, val in (("vcycle_fused", args.vcycle_fused),
+                     ("vcycle_rhs_per_block", args.vcycle_rpb),
+                     ("vcycle_tile", args.vcycle_tile)):
+        if val is not None:
+            choice[key] = val
+    if choice:
+        s.set_tuning(**choice)
+    f = torch.zeros((nrhs, ny1, nx1), dtype=torch.complex128, device="cuda")
+    f[:, ny1 // 2, nx1 // 2] = 1.0
+    for _ in range(args.kb_reps):
+        s.apply("vcycle", f, 0)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel_bench": "vcycle", "workload": args.workload,
+                      "grid": [nx1, ny1], "nrhs": nrhs, "levels": s.num_levels,
+                      "vcycle_ms": vc, "tuning": s.get_tuning()}), flush=True)
+    s.close()
+
+
 def run_reference(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -598,8 +646,12 @@ def main():
                     help="force hz_tuning.maxpy_kernel")
     ap.add_argument("--galerkin-apply", type=int, choices=[0, 1], default=None,
                     help="force hz_tuning.galerkin_apply")
-    ap.add_argument("--vcycle-fused", type=int, choices=[0, 1], default=None,
+    ap.add_argument("--vcycle-fused", type=int, choices=[0, 1, 2], default=None,
                     help="force hz_tuning.vcycle_fused")
+    ap.add_argument("--vcycle-rpb", type=int, default=None,
+                    help="force hz_tuning.vcycle_rhs_per_block")
+    ap.add_argument("--vcycle-tile", type=int, choices=[0, 1], default=None,
+                    help="force hz_tuning.vcycle_tile")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
     ap.add_argument("--profile-kernel", default="mdot,maxpy",
@@ -609,8 +661,15 @@ def main():
                          "skips them")
     ap.add_argument("--fp64-shots", type=int, default=16,
                     help="shots of the FP64 comparison batch")
+    ap.add_argument("--kernel-bench", action="store_true",
+                    help="time the V-cycle kernels alone on the workload's "
+                         "level-1 grid (see run_kernel_bench)")
+    ap.add_argument("--kb-reps", type=int, default=3,
+                    help="V-cycles applied by --kernel-bench after timing")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.kernel_bench:
+        run_kernel_bench(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -300,9 +300,15 @@ hz_status hz_coarse_galerkin_noalloc(int nx, int ny, double h, hz_bc bc,
  * tiles, so small grids share the GPU instead of taking turns.  A member
  * that converged only skips its work.  Members must agree in precision class
  * (FP64 or mixed), inner-basis storage and deflation on/off (HZ_INVALID_ARG
- * otherwise, and for a repeated member); they run on members[0]'s stream,
- * eagerly (no CUDA graph).  info[g] (nrhs[g] entries) may be null.  Returns
- * the worst status over the members. */
+ * otherwise, and for a repeated member); they run on members[0]'s stream.
+ * Each outer iteration of the active members is one CUDA graph launch
+ * (unless a member was set up with no_cuda_graph): in the graph every
+ * member's own kernels run on a branch of their own, concurrently with the
+ * other members', joined before each grouped Gram-Schmidt step, and the
+ * inner coarse solves advance together in a device-side WHILE loop.  The
+ * graphs are captured on first use within the call (one per set of active
+ * members) and released before it returns.  info[g] (nrhs[g] entries) may
+ * be null.  Returns the worst status over the members. */
 #define HZ_MAX_GROUP 8
 hz_status hz_solve_group(hz_solver* const* members, int count, const void* const* b_dev,
                          void* const* x_dev, const int* nrhs, double tol,
@@ -341,6 +347,12 @@ hz_status hz_profile_end(hz_solver* s, long long* launches, double* ms_total,
  * (read from the current device's counter). */
 long long hz_kernel_launches(void);
 
+/* Launch operations the host issued since the library was loaded: each
+ * kernel launched directly and each CUDA graph launched counts one (a
+ * graph's kernels count once, with the graph).  The paper has no
+ * counterpart; it measures how much of the work runs from graphs. */
+long long hz_host_launches(void);
+
 /* Implementation choices that leave the method's arithmetic unchanged up to
  * rounding order.  hz_setup starts from hz_tuning_default; hz_autotune
  * times the candidates on the solver's own workspace and keeps the fastest;
@@ -367,13 +379,23 @@ typedef struct {
                        kernels; 1 pre-smoothing + residual + restriction and
                        prolongation + post-smoothing fused into one tiled
                        kernel each (the intermediate iterate stays in shared
-                       memory)                                             */
+                       memory), one block per tile and right-hand side;
+                       2 the same fused kernels with each block walking over
+                       vcycle_rhs_per_block right-hand sides, its tile's
+                       coefficients held in registers and the input tiles
+                       copied ahead into a ring of shared-memory stages   */
+  int vcycle_rhs_per_block; /* vcycle_fused = 2: right-hand sides per block
+                       (0 = all of them; else 1..1024)                     */
+  int vcycle_tile;  /* vcycle_fused = 2: fine nodes per prolongation block,
+                       0 = 32 x 8, 1 = 64 x 8                              */
 } hz_tuning;
 
 /* Candidates hz_autotune times, in the order of its ms[] output:
  * mdot_kernel 0, 1, 2; maxpy_kernel 0, 1, 2; galerkin_apply 0, 1;
- * e_rhs_per_block 0, 8, 4; vcycle_fused 0, 1. */
-#define HZ_TUNE_CANDIDATES 13
+ * e_rhs_per_block 0, 8, 4; vcycle_fused 0, 1; then vcycle_fused 2 with
+ * (vcycle_rhs_per_block, vcycle_tile) = (4, 0), (8, 0), (16, 0), (4, 1),
+ * (8, 1), (16, 1). */
+#define HZ_TUNE_CANDIDATES 19
 
 void hz_tuning_default(hz_tuning* t);
 
@@ -392,6 +414,19 @@ hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms);
 /* HZ_INVALID_ARG for a null pointer or an out-of-range field. */
 hz_status hz_get_tuning(const hz_solver* s, hz_tuning* t);
 hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t);
+
+/* Fault drill (a test control; the paper has no counterpart).  The TMA-ring
+ * Gram-Schmidt kernels (hz_tuning.mdot_kernel / maxpy_kernel 1 or 2) bound
+ * every pipeline wait; a wait that runs out stops the kernel's work, sets a
+ * flag the host reads after the launch, and the call returns HZ_TIMEOUT
+ * with the solver still usable (the flag is cleared as it is reported).
+ * This call sets the bound of those waits to wait_seconds (0 < w <= 2; 2 is
+ * the default) and, with starve_copies nonzero, makes the kernels' producer
+ * warp issue no copies, so that every consumer wait runs out with nothing in
+ * flight: the way to check the timeout path without a fault.
+ * hz_fault_drill(s, 0, 2.0) restores normal operation.  HZ_INVALID_ARG for a
+ * null solver or a bound outside (0, 2]. */
+hz_status hz_fault_drill(hz_solver* s, int starve_copies, double wait_seconds);
 
 const char* hz_status_str(hz_status st);
 const char* hz_last_error(const hz_solver* s);

@@ -44,10 +44,13 @@ class Oracle:
     exact coarsest solve is wanted for tight comparisons).
     ``precond``: 'adef1' (A-DEF1 / APD, eq. ADEF1) or 'tlkm' (the practical
     TLKM preconditioner of Sec. 3.2.2 with the coarse system of Sec. 5.2).
-    ``deflation_levels``: 1 (the paper's two-level method) or 2 (the
-    level-1 coarse system solved by flexible GMRES with A-DEF1 built from
-    it, deflating to level 2 with ``e2``: 'red_glk2' (default), 'red_o2' or
-    'galerkin' = R_1 E Z_1; the multilevel direction of Sec. 1 / Sec. 7).
+    ``deflation_levels``: D = 1 (the paper's two-level method) or D >= 2,
+    multilevel deflation (the direction of Sec. 1 / Sec. 7): the coarse
+    system of level l < D is solved by flexible GMRES preconditioned by
+    A-DEF1 built from it, deflating to level l + 1 with ``e2`` there
+    ('red_glk2' (default; Sec. 5.2.4 suggests ReD-Glk for multilevel use),
+    'red_o2' or 'galerkin' = R_l E_l Z_l); the deepest system (level D) by
+    V-cycle-preconditioned GMRES.  Every level uses the coarse tolerance.
     ``deflation_scaling``: 'consistent' (default) restricts with
     R_Z = Z^T / 4, under which R_Z A Z matches the re-discretised operators'
     scale (those of A_2h); 'printed' restricts with the unscaled R_Z = Z^T
@@ -88,7 +91,7 @@ class Oracle:
         self.coarse_tol, self.coarse_maxit = coarse_tol, coarse_maxit
         self.inner_log = []
         if deflation_scaling not in ("consistent", "printed") or (
-                deflation_scaling == "printed" and deflation_levels == 2):
+                deflation_scaling == "printed" and deflation_levels != 1):
             raise ValueError("deflation_scaling must be 'consistent', or "
                              "'printed' with two levels")
         printed = deflation_scaling == "printed"
@@ -117,25 +120,31 @@ class Oracle:
                 self.E = ops.red_9pt(self.levels[1])
             else:
                 raise ValueError(e)
-        # multilevel deflation: the level-1 coarse system deflated again
+        # multilevel deflation: coarse system l deflated again, down to D
         self.deflation_levels = deflation_levels
-        if deflation_levels not in (1, 2):
-            raise ValueError("deflation_levels must be 1 or 2")
-        if deflation_levels == 2:
-            if z is None or self.L < 2 or precond != "adef1":
-                raise ValueError("three-level deflation needs Z, A-DEF1 and "
-                                 "two coarsenings")
-            l1, l2 = self.levels[1], self.levels[2]
-            self.Z1 = ops.prolongation(l1, l2, z)
-            self.R1 = self.Z1.T.tocsr() if printed else ops.restriction(self.Z1)
-            if e2 == "galerkin":
-                self.E2 = (self.R1 @ self.E @ self.Z1).tocsr()
-            elif e2 == "red_glk2":
-                self.E2 = ops.red_glk(l2, 2, glk_scale)
-            elif e2 == "red_o2":
-                self.E2 = ops.red_o2(l2)
-            else:
-                raise ValueError(e2)
+        if not isinstance(deflation_levels, (int, np.integer)) or deflation_levels < 1:
+            raise ValueError("deflation_levels must be an integer >= 1")
+        self.Zd, self.Rd, self.Ed = {}, {}, {}
+        if deflation_levels >= 2:
+            if z is None or self.L < deflation_levels or precond != "adef1":
+                raise ValueError("multilevel deflation needs Z, A-DEF1 and "
+                                 "deflation_levels coarsenings")
+            self.Ed[1] = self.E
+            for l in range(1, deflation_levels):
+                lf, lc = self.levels[l], self.levels[l + 1]
+                self.Zd[l] = ops.prolongation(lf, lc, z)
+                self.Rd[l] = (self.Zd[l].T.tocsr() if printed
+                              else ops.restriction(self.Zd[l]))
+                if e2 == "galerkin":
+                    self.Ed[l + 1] = (self.Rd[l] @ self.Ed[l] @ self.Zd[l]).tocsr()
+                elif e2 == "red_glk2":
+                    self.Ed[l + 1] = ops.red_glk(lc, 2, glk_scale)
+                elif e2 == "red_o2":
+                    self.Ed[l + 1] = ops.red_o2(lc)
+                else:
+                    raise ValueError(e2)
+            # names of the three-level case
+            self.Z1, self.R1, self.E2 = self.Zd[1], self.Rd[1], self.Ed[2]
 
     # ---- CSLP multigrid V-cycle (Sec. 3.1) -------------------------------
     def coarsest_solve(self, f):
@@ -162,32 +171,47 @@ class Oracle:
     # ---- deflation (Sec. 3.2, 5.2) ----------------------------------------
     def coarse_solve(self, v1, tol=None, maxit=None):
         """E v2 = v1 by GMRES right-preconditioned with the V-cycle on the
-        coarse CSLP (levels 1..L), x0 = 0.  With three-level deflation the
-        preconditioner is A-DEF1 of the coarse system itself (adef1_level1),
+        coarse CSLP (levels 1..L), x0 = 0.  With multilevel deflation the
+        preconditioner is A-DEF1 of the coarse system itself (adef1_at),
         which contains an inexact solve, so the GMRES is flexible."""
         tol = self.coarse_tol if tol is None else tol
         maxit = self.coarse_maxit if maxit is None else maxit
-        if self.deflation_levels == 2:
+        if self.deflation_levels >= 2:
             res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
-                              prec=self.adef1_level1, flexible=True)
+                              prec=lambda v: self.adef1_at(1, v), flexible=True)
         else:
             res = gmres_right(lambda v: self.E @ v, v1, tol, maxit,
                               prec=lambda v: self.vcycle(v, 1))
         self.inner_log.append(res.iters)
         return res.x
 
+    def solve_level(self, l, v):
+        """E_l x = v (2 <= l <= D) to the coarse tolerance, x0 = 0: at the
+        deepest level D by GMRES right-preconditioned with the V-cycle from
+        level D, above it by flexible GMRES preconditioned by A-DEF1 of
+        level l."""
+        E = self.Ed[l]
+        if l == self.deflation_levels:
+            return gmres_right(lambda u: E @ u, v, self.coarse_tol,
+                               self.coarse_maxit,
+                               prec=lambda u: self.vcycle(u, l)).x
+        return gmres_right(lambda u: E @ u, v, self.coarse_tol,
+                           self.coarse_maxit, prec=lambda u: self.adef1_at(l, u),
+                           flexible=True).x
+
+    def adef1_at(self, l, v):
+        """A-DEF1 for the coarse system of level l < D (eq. ADEF1 applied
+        l levels down): M_l^-1 (v - E_l q) + q with q = Z_l E_{l+1}^-1 R_l v."""
+        q = self.Zd[l] @ self.solve_level(l + 1, self.Rd[l] @ v)
+        return self.vcycle(v - self.Ed[l] @ q, l) + q
+
     def coarse_solve_level2(self, v):
-        """E_2 v2 = v (level 2) by GMRES right-preconditioned with the
-        V-cycle on the CSLP from level 2, x0 = 0, to the coarse tolerance."""
-        res = gmres_right(lambda u: self.E2 @ u, v, self.coarse_tol,
-                          self.coarse_maxit, prec=lambda u: self.vcycle(u, 2))
-        return res.x
+        """E_2 v2 = v (three-level deflation's level 2)."""
+        return self.solve_level(2, v)
 
     def adef1_level1(self, v):
-        """A-DEF1 for the level-1 coarse system E (eq. ADEF1 one level
-        down): M_1^-1 (v - E q) + q with q = Z_1 E_2^-1 R_1 v."""
-        q = self.Z1 @ self.coarse_solve_level2(self.R1 @ v)
-        return self.vcycle(v - self.E @ q, 1) + q
+        """A-DEF1 for the level-1 coarse system E (three-level naming)."""
+        return self.adef1_at(1, v)
 
     def deflation_Q(self, v):
         """Q v = Z E^{-1} R v with the inexact coarse solve (Sec. 5.2)."""

@@ -39,7 +39,8 @@ class HzSolveInfo(ctypes.Structure):
 class HzTuning(ctypes.Structure):
     _fields_ = [("mdot_kernel", c_int), ("maxpy_kernel", c_int),
                 ("galerkin_apply", c_int), ("e_rhs_per_block", c_int),
-                ("vcycle_fused", c_int)]
+                ("vcycle_fused", c_int), ("vcycle_rhs_per_block", c_int),
+                ("vcycle_tile", c_int)]
 
 
 STATUS = {0: "HZ_OK", 1: "HZ_INVALID_ARG", 2: "HZ_INVALID_GRID",
@@ -69,6 +70,8 @@ SIGNATURES = {
                                            c_void_p, c_int, c_void_p]),
     "hz_destroy": (c_int, [c_void_p]),
     "hz_kernel_launches": (ctypes.c_longlong, []),
+    "hz_host_launches": (ctypes.c_longlong, []),
+    "hz_fault_drill": (c_int, [c_void_p, c_int, c_double]),
     "hz_profile_begin": (c_int, [c_void_p, c_int, c_int]),
     "hz_profile_end": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "hz_tuning_default": (None, [c_void_p]),

@@ -274,7 +274,10 @@ class Solver:
                        "galerkin_apply=0", "galerkin_apply=1",
                        "e_rhs_per_block=0", "e_rhs_per_block=8",
                        "e_rhs_per_block=4", "vcycle_fused=0",
-                       "vcycle_fused=1")
+                       "vcycle_fused=1",
+                       "vcycle_fused=2,rpb=4,tile=0", "vcycle_fused=2,rpb=8,tile=0",
+                       "vcycle_fused=2,rpb=16,tile=0", "vcycle_fused=2,rpb=4,tile=1",
+                       "vcycle_fused=2,rpb=8,tile=1", "vcycle_fused=2,rpb=16,tile=1")
 
     def tuning_key(self, nrhs):
         """Cache key of a tuning: the device and every descriptor field

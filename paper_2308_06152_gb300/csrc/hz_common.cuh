@@ -10,12 +10,20 @@
 
 namespace hz {
 
-// Number of kernels this library has launched (all launchers count).
+// Number of kernels this library has launched (all launchers count), and
+// of launch operations the host issued (a kernel launched directly or a
+// CUDA graph launched counts one each).
 inline std::atomic<long long>& launch_counter() {
   static std::atomic<long long> c{0};
   return c;
 }
-#define HZ_COUNT() (::hz::launch_counter().fetch_add(1, std::memory_order_relaxed))
+inline std::atomic<long long>& host_op_counter() {
+  static std::atomic<long long> c{0};
+  return c;
+}
+#define HZ_COUNT()                                                       \
+  (::hz::launch_counter().fetch_add(1, std::memory_order_relaxed),      \
+   ::hz::host_op_counter().fetch_add(1, std::memory_order_relaxed))
 
 enum { BC_DIRICHLET = 0, BC_SOMMERFELD = 1 };
 enum { ZK_NONE = 0, ZK_BILINEAR = 1, ZK_HO = 2 };
@@ -211,6 +219,19 @@ template <class T, class SC, class SX, class SF, class SO>
 void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift s,
                            const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
                            const int* done, cudaStream_t st);
+// the same two fused kernels, each block walking over a group of rpb
+// right-hand sides (0 = all) with its per-node constants in registers and
+// the input tiles staged ahead in shared memory (cp.async ring); omega is
+// the Jacobi weight D^-1 was built with (the kernels use D^-1 diag(M) =
+// omega); prolongation tile 0 = 32 x 8 fine nodes, 1 = 64 x 8
+template <class T, class SF, class SX, class SC>
+void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
+                            VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
+                            cudaStream_t st);
+template <class T, class SC, class SX, class SF, class SO>
+void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
+                              const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
+                              int rpb, int tile, const int* done, cudaStream_t st);
 // x = Minv f on the coarsest level (dense)
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
@@ -320,6 +341,9 @@ struct KState {
   int* fault;       // [1] set when a pipeline wait of a Krylov kernel timed out
   int dotk, updk;   // multi-dot / multi-update kernels: 0 register-pipelined,
                     // 1 / 2 TMA ring with 8 / 16 consumer warps
+  unsigned long long wait_ns;   // bound of every pipeline wait (2 s)
+  int starve;       // fault drill: the TMA producers issue no copies, so
+                    // the consumers' bounded waits run out
   int m;            // basis size (max iterations)
   int nblk_max;
 };
@@ -415,10 +439,18 @@ void launch_tune_state(const KState& ks, int nrhs, int j, cudaStream_t st);
 // node of the body) counts the iteration, adds *body_kernels to the device
 // total of graph-executed kernels and repeats while *alldone is clear and
 // fewer than maxit iterations ran.
-void launch_loop_begin(const int* alldone, int* it, cudaGraphConditionalHandle h,
-                       cudaStream_t st);
-void launch_loop_next(const int* alldone, int* it, int maxit, const int* body_kernels,
-                      cudaGraphConditionalHandle h, cudaStream_t st);
+void launch_loop_begin(const int* alldone, const int* fault, int* it,
+                       cudaGraphConditionalHandle h, cudaStream_t st);
+void launch_loop_next(const int* alldone, const int* fault, int* it, int maxit,
+                      const int* body_kernels, cudaGraphConditionalHandle h,
+                      cudaStream_t st);
+// *out = 1 if every flag of fs is set, else 0 (the all-converged flag of a
+// group of solvers)
+struct FlagSet {
+  const int* f[8];
+  int n;
+};
+void launch_all_of(const FlagSet& fs, int* out, cudaStream_t st);
 // Kernels run by WHILE-node bodies on the current device so far (0 if the
 // counter cannot be read).
 unsigned long long graph_body_kernels_run();

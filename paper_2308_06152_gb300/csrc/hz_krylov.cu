@@ -363,7 +363,7 @@ k_maxpy_group(const __grid_constant__ GroupDesc gd, int pass) {
 // stage from shared memory.  The bytes in flight per SM are set by the ring
 // (NSTAGE x 32 KB), not by registers, and the next tile's chunk of w is
 // prefetched into registers while the current tile streams.  Every wait is
-// bounded: after kWaitNs the kernel raises ks.fault, stops waiting and
+// bounded: after KState::wait_ns (kWaitNs) the kernel raises ks.fault, stops waiting and
 // still takes part in every block barrier, so the launch always ends; the
 // host reports the flag.
 constexpr int NSTAGE = 6;
@@ -410,14 +410,16 @@ __device__ __forceinline__ unsigned long long gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait for the phase of parity `parity` of barrier b; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity) {
+// Wait for the phase of parity `parity` of barrier b; false after limit ns
+// (KState::wait_ns: kWaitNs unless a fault drill shortened it).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* b, unsigned parity,
+                                          unsigned long long limit) {
   if (mbar_test(b, parity)) return true;
   const unsigned long long t0 = gtimer();
   for (;;) {
     for (int k = 0; k < 64; ++k)
       if (mbar_test(b, parity)) return true;
-    if (gtimer() - t0 > kWaitNs) return false;
+    if (gtimer() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
@@ -531,8 +533,9 @@ struct Slot {
 
 // Producer lane: wait until the consumers released the stage of slot q.
 __device__ __forceinline__ bool producer_acquire(unsigned long long* empty, Slot q,
-                                                 volatile int* s_abort, int* fault) {
-  if (*s_abort || !mbar_wait(&empty[q.s], q.ph ^ 1u)) {
+                                                 volatile int* s_abort, int* fault,
+                                                 unsigned long long limit) {
+  if (*s_abort || !mbar_wait(&empty[q.s], q.ph ^ 1u, limit)) {
     *s_abort = 1;
     atomicExch(fault, 1);
     return false;
@@ -542,7 +545,7 @@ __device__ __forceinline__ bool producer_acquire(unsigned long long* empty, Slot
 // No bulk copy may still be landing when the block exits: wait for the last
 // min(issued, NSTAGE) stages (slot `at` is the one after the last issued).
 __device__ __forceinline__ void producer_drain(unsigned long long* full, long long issued,
-                                               Slot at, int* fault) {
+                                               Slot at, int* fault, unsigned long long limit) {
   const int cnt = issued < NSTAGE ? (int)issued : NSTAGE;
   for (int u = 0; u < cnt; ++u) {
     // step back one slot
@@ -552,12 +555,13 @@ __device__ __forceinline__ void producer_drain(unsigned long long* full, long lo
     } else {
       --at.s;
     }
-    if (!mbar_wait(&full[at.s], at.ph)) atomicExch(fault, 1);
+    if (!mbar_wait(&full[at.s], at.ph, limit)) atomicExch(fault, 1);
   }
 }
 __device__ __forceinline__ bool consumer_acquire(unsigned long long* full, Slot q,
-                                                 volatile int* s_abort, int* fault) {
-  if (*s_abort || !mbar_wait(&full[q.s], q.ph)) {
+                                                 volatile int* s_abort, int* fault,
+                                                 unsigned long long limit) {
+  if (*s_abort || !mbar_wait(&full[q.s], q.ph, limit)) {
     *s_abort = 1;
     atomicExch(fault, 1);
     return false;
@@ -641,20 +645,20 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
     it0.blk = (int)(tile - (long long)it0.a * nblk);
   }
 
-  if (warp == NCW) {  // producer
-    if (lane == 0) {
+  if (warp == NCW) {  // producer (a fault drill's starve mode issues nothing)
+    if (lane == 0 && !ks.starve) {
       Slot sl;
       Item it = it0;
       int t = 0;
       for (; t < nitems; ++t) {
-        if (!producer_acquire(empty, sl, &s_abort, ks.fault)) break;
+        if (!producer_acquire(empty, sl, &s_abort, ks.fault, ks.wait_ns)) break;
         const int i0 = it.grp * G, nv = min(G, j + 1 - i0);
         produce<SB>(stages + sl.s * STAGE_BYTES, &full[sl.s], V, vstride, rs, act[it.a],
                     it.blk, i0, nv);
         sl.next();
         it.next(nblk, ngrp);
       }
-      producer_drain(full, t, sl, ks.fault);
+      producer_drain(full, t, sl, ks.fault, ks.wait_ns);
     }
   } else {  // consumers
     int cur_a = -1, cur_blk = -1;
@@ -696,7 +700,7 @@ k_mdot_tma(const SB* __restrict__ V, long long vstride, long long rs,
       T acc[NV];
 #pragma unroll
       for (int c = 0; c < NV; ++c) acc[c] = T(0);
-      if (consumer_acquire(full, sl, &s_abort, ks.fault)) {
+      if (consumer_acquire(full, sl, &s_abort, ks.fault, ks.wait_ns)) {
         const int nv = min(G, j + 1 - it.grp * G);
         const long long valid = n - off;   // values of this chunk inside the row
         const unsigned char* sb = stages + sl.s * STAGE_BYTES;
@@ -806,15 +810,15 @@ k_maxpy_tma(const SB* __restrict__ V, long long vstride, long long rs,
   const int ngrp = (j + 1 + G - 1) / G;
   const int tiles = s_nact * nblk;
 
-  if (warp == NCW) {  // producer
-    if (lane == 0) {
+  if (warp == NCW) {  // producer (a fault drill's starve mode issues nothing)
+    if (lane == 0 && !ks.starve) {
       Slot sl;
       long long t = 0;
       bool stop = false;
       for (int tile = blockIdx.x; tile < tiles && !stop; tile += gridDim.x) {
         const int a = tile / nblk, blk = tile - a * nblk;
         for (int grp = 0; grp < ngrp; ++grp, ++t) {
-          if (!producer_acquire(empty, sl, &s_abort, ks.fault)) {
+          if (!producer_acquire(empty, sl, &s_abort, ks.fault, ks.wait_ns)) {
             stop = true;
             break;
           }
@@ -823,7 +827,7 @@ k_maxpy_tma(const SB* __restrict__ V, long long vstride, long long rs,
           sl.next();
         }
       }
-      producer_drain(full, t, sl, ks.fault);
+      producer_drain(full, t, sl, ks.fault, ks.wait_ns);
     }
   } else {  // consumers
     Slot sl;
@@ -858,7 +862,7 @@ k_maxpy_tma(const SB* __restrict__ V, long long vstride, long long rs,
 #pragma unroll
         for (int qq = 0; qq < G; ++qq)
           h[qq] = (qq < nv) ? cvt_to<T>(hc[grp * G + qq]) : czero<T>();
-        if (consumer_acquire(full, sl, &s_abort, ks.fault)) {
+        if (consumer_acquire(full, sl, &s_abort, ks.fault, ks.wait_ns)) {
           const unsigned char* sb = stages + sl.s * STAGE_BYTES;
 #pragma unroll
           for (int qq = 0; qq < G; ++qq) {
@@ -1013,9 +1017,10 @@ __global__ void k_krylov_init(KState ks, int nrhs, const int* done_in,
 }
 
 template <class T, class SB>
-__global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
-                             const double* __restrict__ s, long long n,
-                             const int* __restrict__ done, C<T>* __restrict__ copy) {
+__global__ void __launch_bounds__(256)
+k_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* __restrict__ s,
+             long long n, const int* __restrict__ done, C<T>* __restrict__ copy) {
+  constexpr int U = 4;   // values per thread and trip: one 16-byte FP16 group
   const int r = blockIdx.y;
   if (done && done[r]) return;
   // one FP64 reciprocal per block (FP64 division is slow on this GPU)
@@ -1028,18 +1033,29 @@ __global__ void k_scale_into(VRef<T> w, VRefE<SB> out, long long rs,
   const T f = f_s;
   const C<T>* wr = w.get() + r * n;
   SB* orow = out.get() + r * rs;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
-       e += (long long)gridDim.x * blockDim.x)
-  {
+  C<T>* crow = copy ? copy + r * n : nullptr;
+  // rows of the basis are padded to rs >= n (a multiple of 4), so groups of
+  // U values start 16-byte aligned in the FP16 basis; the padding is written
+  // as zero (group loads read it)
+  for (long long e0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) * U; e0 < rs;
+       e0 += (long long)gridDim.x * blockDim.x * U) {
+    C<T> v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = (e0 + u < n) ? wr[e0 + u] : czero<T>();
+    SB sv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) st2(sv, u, f * v[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (e0 + u < rs) orow[e0 + u] = sv[u];
     // the stored (rounded) value, also kept in compute precision as the
     // V-cycle's input of the next step
-    SB sv;
-    st2(&sv, 0, f * wr[e]);
-    orow[e] = sv;
-    if (copy) copy[r * n + e] = ld2(&sv, 0);
+    if (crow) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (e0 + u < n) crow[e0 + u] = ld2(sv, u);
+    }
   }
-  // the padding of the row reads as zero in the group loads
-  if (blockIdx.x == 0 && threadIdx.x < rs - n) st2(orow, n + threadIdx.x, czero<T>());
 }
 
 // Apply the previous rotations to column j, build the rotation that
@@ -1216,18 +1232,19 @@ k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
 // the host; the iterations of a device-side loop only here).
 __device__ unsigned long long g_body_kernels_run;
 
-__global__ void k_loop_begin(const int* alldone, int* it,
+// (a raised fault flag ends the loop too: a bounded wait ran out)
+__global__ void k_loop_begin(const int* alldone, const int* fault, int* it,
                              cudaGraphConditionalHandle h) {
   *it = 0;
-  cudaGraphSetConditional(h, *alldone ? 0u : 1u);
+  cudaGraphSetConditional(h, (*alldone || (fault && *fault)) ? 0u : 1u);
 }
 
-__global__ void k_loop_next(const int* alldone, int* it, int maxit,
+__global__ void k_loop_next(const int* alldone, const int* fault, int* it, int maxit,
                             const int* body_kernels, cudaGraphConditionalHandle h) {
   const int k = *it + 1;
   *it = k;
   atomicAdd(&g_body_kernels_run, (unsigned long long)*body_kernels);
-  cudaGraphSetConditional(h, (!*alldone && k < maxit) ? 1u : 0u);
+  cudaGraphSetConditional(h, (!*alldone && !(fault && *fault) && k < maxit) ? 1u : 0u);
 }
 
 // GCR step (Sec. 6.3's outer iteration): x += g u_k and r -= g c_k with
@@ -1471,8 +1488,8 @@ void launch_scale_into(VRef<T> w, VRefE<SB> out, long long rs, const double* s,
                        long long n, int nrhs, const int* done, cudaStream_t st,
                        C<T>* copy) {
   HZ_COUNT();
-  long long nb = (n + 255) / 256;
-  if (nb > 2048) nb = 2048;
+  long long nb = (rs + 1023) / 1024;
+  if (nb > 1024) nb = 1024;
   k_scale_into<T, SB><<<dim3((unsigned)nb, nrhs), 256, 0, st>>>(w, out, rs, s, n, done,
                                                                 copy);
 }
@@ -1532,16 +1549,29 @@ void launch_tune_state(const KState& ks, int nrhs, int j, cudaStream_t st) {
   HZ_COUNT();
   k_tune_state<<<1, 1024, 0, st>>>(ks, nrhs, j);
 }
-void launch_loop_begin(const int* alldone, int* it, cudaGraphConditionalHandle h,
-                       cudaStream_t st) {
+void launch_loop_begin(const int* alldone, const int* fault, int* it,
+                       cudaGraphConditionalHandle h, cudaStream_t st) {
   HZ_COUNT();
-  k_loop_begin<<<1, 1, 0, st>>>(alldone, it, h);
+  k_loop_begin<<<1, 1, 0, st>>>(alldone, fault, it, h);
 }
-void launch_loop_next(const int* alldone, int* it, int maxit, const int* body_kernels,
-                      cudaGraphConditionalHandle h, cudaStream_t st) {
+void launch_loop_next(const int* alldone, const int* fault, int* it, int maxit,
+                      const int* body_kernels, cudaGraphConditionalHandle h,
+                      cudaStream_t st) {
   HZ_COUNT();
-  k_loop_next<<<1, 1, 0, st>>>(alldone, it, maxit, body_kernels, h);
+  k_loop_next<<<1, 1, 0, st>>>(alldone, fault, it, maxit, body_kernels, h);
 }
+namespace {
+__global__ void k_all_of(FlagSet fs, int* out) {
+  int a = 1;
+  for (int i = 0; i < fs.n; ++i) a &= (*fs.f[i] != 0) ? 1 : 0;
+  *out = a;
+}
+}  // namespace
+void launch_all_of(const FlagSet& fs, int* out, cudaStream_t st) {
+  HZ_COUNT();
+  k_all_of<<<1, 1, 0, st>>>(fs, out);
+}
+
 unsigned long long graph_body_kernels_run() {
   unsigned long long v = 0;
   if (cudaMemcpyFromSymbol(&v, g_body_kernels_run, sizeof v) != cudaSuccess) {

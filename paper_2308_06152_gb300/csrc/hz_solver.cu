@@ -37,6 +37,7 @@ constexpr int kMaxLevels = 24;
 constexpr int kMaxCoarsest = 1024;
 constexpr int kMaxRhs = 1024;
 constexpr int kMaxIters = 3000;   // Krylov basis size (Givens column in smem)
+constexpr unsigned long long kPipelineWaitNs = 2000000000ull;   // bounded waits
 
 struct LevelHost {
   int nx = 0, ny = 0;
@@ -106,14 +107,14 @@ bool valid_desc(const hz_desc* d, std::string* why) {
     *why = "TLKM needs deflation vectors";
     return false;
   }
-  if (d->deflation_levels < 0 || d->deflation_levels > 2 ||
-      (d->deflation_levels == 2 &&
+  if (d->deflation_levels < 0 || d->deflation_levels >= kMaxLevels ||
+      (d->deflation_levels >= 2 &&
        (d->zkind == HZ_Z_NONE || d->preconditioner != HZ_PRECOND_ADEF1))) {
-    *why = "deflation_levels must be 0/1, or 2 with deflation vectors and A-DEF1";
+    *why = "deflation_levels must be 0/1, or 2 .. 23 with deflation vectors and A-DEF1";
     return false;
   }
   if (d->deflation_scaling != HZ_DEFL_SCALE_CONSISTENT &&
-      (d->deflation_scaling != HZ_DEFL_SCALE_PRINTED || d->deflation_levels == 2)) {
+      (d->deflation_scaling != HZ_DEFL_SCALE_PRINTED || d->deflation_levels >= 2)) {
     *why = "deflation_scaling must be CONSISTENT, or PRINTED with at most two levels";
     return false;
   }
@@ -154,13 +155,20 @@ struct hz_solver {
   void *v1 = nullptr, *v2 = nullptr, *sb = nullptr, *eb = nullptr, *Qb = nullptr;
   void* qf = nullptr;      // current basis vector in compute precision (FP16 basis)
   void* Sglk = nullptr;    // stcl-op-Glk coefficient planes [P*P][n1] (Galerkin E)
-  // three-level deflation: level-1 flexible directions and work vectors,
-  // the level-2 Krylov state, basis and vectors (all compute precision)
+  // multilevel deflation (deflation_levels = D >= 2): the Krylov solve of
+  // the coarse system E_l v2 = v1 of every deflation level l = 1 .. D.
+  // Level 1's basis, state and vectors are Qb, kin, qf, sb, eb above; its
+  // flexible directions and A-DEF1 vectors are in dl[1].  Levels below 1
+  // keep their bases in compute precision.
+  struct DefLevel {
+    KState ks{};
+    void *Q = nullptr, *Zb = nullptr;
+    void *v1 = nullptr, *v2 = nullptr, *qf = nullptr, *sb = nullptr, *eb = nullptr;
+    void *zj = nullptr, *q = nullptr, *u = nullptr;
+  };
   bool ml = false;
-  void *Z1b = nullptr, *zj = nullptr, *q1 = nullptr, *u1 = nullptr;
-  void *v1_2 = nullptr, *v2_2 = nullptr, *sb2 = nullptr, *eb2 = nullptr, *qf2 = nullptr,
-       *Q2 = nullptr;
-  KState kin2{};
+  int D = 1;
+  DefLevel dl[kMaxLevels];
   bool basis16 = false;    // inner Krylov basis stored as FP16 pairs
   KState kin{}, kout{};
   int* in_total = nullptr;
@@ -194,14 +202,19 @@ struct hz_solver {
     long long kernels;   // kernels of one launch outside WHILE bodies
   };
   std::vector<OuterGraph> graphs;
+  // (the WHILE body of deflation level l is captured on cap_body for
+  // l = 1, on cap_nest[l] below it, and nested in its parent's body)
   cudaStream_t cap_main = nullptr, cap_body = nullptr;
+  cudaStream_t cap_nest[kMaxLevels] = {};
   bool capturing = false;
-  long long body_count = 0;      // kernels of one WHILE body
-  int* loop_it = nullptr;        // device: iterations of the running loop
-  int* body_kernels = nullptr;   // device: body_count
+  long long body_count = 0;      // kernels of all WHILE bodies, one pass each
+  long long body_count_l[kMaxLevels] = {};   // own kernels of level l's body
+  int* loop_it = nullptr;        // device [kMaxLevels]: iterations per loop
+  int* body_kernels = nullptr;   // device [kMaxLevels]: body_count_l
   int* fault = nullptr;          // device: a Krylov pipeline wait timed out
+  int* grp = nullptr;            // device [4]: flags of a group solve's graph
   hz_tuning tune{};
-  int body_kernels_host = 0;
+  int body_kernels_host[kMaxLevels] = {};
 
   ~hz_solver() {
     for (OuterGraph& g : graphs) {
@@ -210,6 +223,8 @@ struct hz_solver {
     }
     if (cap_main) cudaStreamDestroy(cap_main);
     if (cap_body) cudaStreamDestroy(cap_body);
+    for (cudaStream_t c : cap_nest)
+      if (c) cudaStreamDestroy(c);
   }
 };
 
@@ -262,6 +277,8 @@ KState plan_kstate(Arena& a, int B, int m, long long n) {
   k.fault = nullptr;   // set by plan(): one flag per solver
   k.dotk = 0;
   k.updk = 0;
+  k.wait_ns = kPipelineWaitNs;
+  k.starve = 0;
   return k;
 }
 
@@ -307,18 +324,26 @@ void plan(hz_solver* s, Arena& a) {
       s->Sglk = a.take(es * (size_t)P * P * n1);
     }
     if (s->ml) {
-      const long long n2 = s->lv[2].n;
-      s->Z1b = a.take(es * (size_t)B * n1 * d.coarse_maxit);
-      s->zj = a.take(es * B * n1);
-      s->q1 = a.take(es * B * n1);
-      s->u1 = a.take(es * B * n1);
-      s->v1_2 = a.take(es * B * n2);
-      s->v2_2 = a.take(es * B * n2);
-      s->sb2 = a.take(es * B * n2);
-      s->eb2 = a.take(es * B * n2);
-      s->qf2 = a.take(es * B * n2);
-      s->Q2 = a.take(es * (size_t)B * inner_row(n2) * (d.coarse_maxit + 1));
-      s->kin2 = plan_kstate(a, B, d.coarse_maxit, n2);
+      const int m = d.coarse_maxit;
+      for (int l = 1; l <= s->D; ++l) {
+        hz_solver::DefLevel& D = s->dl[l];
+        const long long nl = s->lv[l].n;
+        if (l >= 2) {
+          D.Q = a.take(es * (size_t)B * inner_row(nl) * (m + 1));
+          D.ks = plan_kstate(a, B, m, nl);
+          D.v1 = a.take(es * B * nl);
+          D.v2 = a.take(es * B * nl);
+          D.qf = a.take(es * B * nl);
+          D.sb = a.take(es * B * nl);
+          D.eb = a.take(es * B * nl);
+        }
+        if (l < s->D) {
+          D.Zb = a.take(es * (size_t)B * nl * m);
+          D.zj = a.take(es * B * nl);
+          D.q = a.take(es * B * nl);
+          D.u = a.take(es * B * nl);
+        }
+      }
     }
   }
   s->in_total = (int*)a.take(sizeof(int) * B);
@@ -338,14 +363,17 @@ void plan(hz_solver* s, Arena& a) {
   s->ro = d.outer_solver == HZ_OUTER_GCR
               ? (double2*)a.take(sizeof(double2) * (size_t)B * n0)
               : nullptr;
-  s->loop_it = (int*)a.take(sizeof(int));
-  s->body_kernels = (int*)a.take(sizeof(int));
+  s->loop_it = (int*)a.take(sizeof(int) * kMaxLevels);
+  s->body_kernels = (int*)a.take(sizeof(int) * kMaxLevels);
   s->fault = (int*)a.take(sizeof(int));
+  s->grp = (int*)a.take(sizeof(int) * 4);
   s->kin.fault = s->fault;
   s->kout.fault = s->fault;
-  s->kin2.fault = s->fault;
-  s->kin2.dotk = s->tune.mdot_kernel;
-  s->kin2.updk = s->tune.maxpy_kernel;
+  for (int l = 2; l <= s->D; ++l) {
+    s->dl[l].ks.fault = s->fault;
+    s->dl[l].ks.dotk = s->tune.mdot_kernel;
+    s->dl[l].ks.updk = s->tune.maxpy_kernel;
+  }
   s->kin.dotk = s->kout.dotk = s->tune.mdot_kernel;
   s->kin.updk = s->kout.updk = s->tune.maxpy_kernel;
 }
@@ -379,9 +407,10 @@ hz_status init_shapes(hz_solver* s) {
   s->esz = s->mixed ? sizeof(float2) : sizeof(double2);
   s->lsz = s->lvbf16 ? sizeof(__nv_bfloat162) : s->esz;
   s->basis16 = s->mixed && d.inner_basis_fp16;
-  s->ml = d.deflation_levels == 2;
-  if (s->ml && s->L < 2) {
-    set_err(s, "three-level deflation needs a grid that coarsens twice");
+  s->D = d.deflation_levels < 1 ? 1 : d.deflation_levels;
+  s->ml = s->D >= 2;
+  if (s->ml && s->L < s->D) {
+    set_err(s, "deflation to level %d needs a grid that coarsens %d times", s->D, s->D);
     return HZ_INVALID_GRID;
   }
   return HZ_OK;
@@ -425,9 +454,21 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
     return;
   }
   const bool fused = s->tune.vcycle_fused != 0;
+  const bool staged = s->tune.vcycle_fused == 2;
+  const int rpb = s->tune.vcycle_rhs_per_block, tile = s->tune.vcycle_tile;
+  const double om = s->d.jacobi_omega;
   for (int l = l0; l < s->L; ++l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
+    if (staged) {
+      if (l == l0)
+        launch_pre_restrict_mr<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, om, f, (SL*)A.xa,
+                                                (SL*)Bc.f, nrhs, rpb, done, st);
+      else
+        launch_pre_restrict_mr<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, om, vrefe<SL>(A.f),
+                                              (SL*)A.xa, (SL*)Bc.f, nrhs, rpb, done, st);
+      continue;
+    }
     if (fused) {
       if (l == l0)
         launch_pre_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f, (SL*)A.xa,
@@ -455,6 +496,18 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
   for (int l = s->L - 1; l >= l0; --l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
+    if (staged) {
+      if (l == l0)
+        launch_prolong_smooth_mr<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, om,
+                                                        (const SL*)Bc.x, (const SL*)A.xa, f,
+                                                        xout, nrhs, rpb, tile, done, st);
+      else
+        launch_prolong_smooth_mr<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, om,
+                                                    (const SL*)Bc.x, (const SL*)A.xa,
+                                                    vrefe<SL>(A.f), (SL*)A.x, nrhs, rpb, tile,
+                                                    done, st);
+      continue;
+    }
     if (fused) {
       if (l == l0)
         launch_prolong_smooth<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, sh,
@@ -560,6 +613,20 @@ hz_status read_flag(hz_solver* s, const int* dptr, int* out) {
       cudaSuccess)
     return cuda_check(s, "flag copy");
   if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "flag sync");
+  return HZ_OK;
+}
+
+// The outer loop's stopping flag, raised also when a Krylov kernel's bounded
+// wait ran out (the fault stays set for the report, which returns HZ_TIMEOUT).
+hz_status read_outer_flag(hz_solver* s, int* out) {
+  int v[2] = {0, 0};
+  if (cudaMemcpyAsync(&v[0], s->kout.alldone, sizeof(int), cudaMemcpyDeviceToHost,
+                      s->st) != cudaSuccess ||
+      cudaMemcpyAsync(&v[1], s->fault, sizeof(int), cudaMemcpyDeviceToHost, s->st) !=
+          cudaSuccess)
+    return cuda_check(s, "flag copy");
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) return cuda_check(s, "flag sync");
+  *out = v[0] || v[1];
   return HZ_OK;
 }
 
@@ -684,27 +751,31 @@ void inner_step(hz_solver* s, int nrhs) {
   inner_post<T, SB>(s, nrhs);
 }
 
-// While s->st is being captured: appends to the captured graph a WHILE node
-// whose body is one inner_step plus the loop control, preceded by the kernel
-// that sets the loop condition from the all-converged flag.  The loop ends
-// when every RHS is done or after coarse_maxit iterations (k_givens marks
-// every RHS done at the cap, so the count bound is a second guard).
-template <class T, class SB>
-hz_status capture_inner_loop(hz_solver* s, int nrhs) {
+// While s->st is being captured: appends to the graph being captured (the
+// outer iteration's, or the body of an enclosing loop) a WHILE node for the
+// Krylov loop of deflation level l, whose body is body() plus the loop
+// control, preceded by the kernel that sets the loop condition from the
+// all-converged flag of ks.  The loop ends when every RHS is done or after
+// coarse_maxit iterations (k_givens marks every RHS done at the cap, so the
+// count bound is a second guard).  body() may capture the loop of level
+// l + 1 inside this body; every body counts only its own kernels
+// (body_count_l[l]).
+template <class F>
+hz_status capture_loop(hz_solver* s, int l, KState& ks, F&& body) {
   cudaStream_t st = s->st;
-  KState& ks = s->kin;
+  cudaStream_t cap = l == 1 ? s->cap_body : s->cap_nest[l];
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaGraph_t G = nullptr;
   const cudaGraphNode_t* deps = nullptr;
   size_t nd = 0;
-  if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, nullptr, nullptr, nullptr) !=
-          cudaSuccess ||
+  if (!cap || cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, nullptr, nullptr, nullptr) !=
+                  cudaSuccess ||
       cs != cudaStreamCaptureStatusActive)
-    return cuda_check(s, "inner loop capture: stream not capturing");
+    return cuda_check(s, "loop capture: stream not capturing");
   cudaGraphConditionalHandle h;
   if (cudaGraphConditionalHandleCreate(&h, G, 0, 0) != cudaSuccess)
     return cuda_check(s, "conditional handle");
-  launch_loop_begin(ks.alldone, s->loop_it, h, st);
+  launch_loop_begin(ks.alldone, s->fault, s->loop_it + l, h, st);
   if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, &deps, nullptr, &nd) !=
       cudaSuccess)
     return cuda_check(s, "capture info");
@@ -716,25 +787,33 @@ hz_status capture_inner_loop(hz_solver* s, int nrhs) {
   cudaGraphNode_t node;
   if (cudaGraphAddNode(&node, G, deps, nullptr, nd, &p) != cudaSuccess)
     return cuda_check(s, "WHILE node");
-  cudaGraph_t body = p.conditional.phGraph_out[0];
-  if (cudaStreamBeginCaptureToGraph(s->cap_body, body, nullptr, nullptr, 0,
+  cudaGraph_t body_g = p.conditional.phGraph_out[0];
+  if (cudaStreamBeginCaptureToGraph(cap, body_g, nullptr, nullptr, 0,
                                     cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return cuda_check(s, "body capture");
   const long long c0 = launch_counter().load();
-  s->st = s->cap_body;
-  inner_step<T, SB>(s, nrhs);
-  launch_loop_next(ks.alldone, s->loop_it, s->d.coarse_maxit, s->body_kernels, h,
-                   s->st);
+  for (int k = l + 1; k < kMaxLevels; ++k) s->body_count_l[k] = 0;
+  s->st = cap;
+  body();
+  launch_loop_next(ks.alldone, s->fault, s->loop_it + l, s->d.coarse_maxit,
+                   s->body_kernels + l, h, s->st);
   s->st = st;
-  s->body_count = launch_counter().load() - c0;
+  long long nested = 0;
+  for (int k = l + 1; k < kMaxLevels; ++k) nested += s->body_count_l[k];
+  s->body_count_l[l] = launch_counter().load() - c0 - nested;
   cudaGraph_t body_out = nullptr;
-  if (cudaStreamEndCapture(s->cap_body, &body_out) != cudaSuccess)
+  if (cudaStreamEndCapture(cap, &body_out) != cudaSuccess)
     return cuda_check(s, "body capture end");
   if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
                                           cudaStreamSetCaptureDependencies) !=
       cudaSuccess)
     return cuda_check(s, "capture dependencies");
-  return cuda_check(s, "inner loop capture");
+  return cuda_check(s, "loop capture");
+}
+
+template <class T, class SB>
+hz_status capture_inner_loop(hz_solver* s, int nrhs) {
+  return capture_loop(s, 1, s->kin, [&] { inner_step<T, SB>(s, nrhs); });
 }
 
 // E v2 = v1 by right-preconditioned GMRES (V-cycle on the coarse CSLP from
@@ -769,100 +848,135 @@ void coarse_finish(hz_solver* s, C<T>* v2, int nrhs, const int* done_in) {
   launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
 }
 
-// ------------------------------------------------------------ three levels
-// Level-2 coarse system E_2 v2 = v1 (E_2 = ReD-Glk2 at level 2) by GMRES
-// right-preconditioned with the V-cycle from level 2, x0 = 0, to the coarse
-// tolerance; RHS done at level 1 (done_in) are skipped.  Buffers: v1_2 in,
-// v2_2 out.
+// ------------------------------------------------------------ multilevel
+// Multilevel deflation (deflation_levels = D >= 2; the multilevel direction
+// of Sec. 1 / Sec. 7, our reading): the coarse system of level l < D is
+// solved by flexible GMRES right-preconditioned by A-DEF1 built from it,
+// z = M_l^-1 (v - E_l q) + q, q = Z_l E_{l+1}^-1 R_l v, with the same solve
+// one level down inside; level D by GMRES right-preconditioned by the
+// V-cycle from level D.  Every level stops at the coarse tolerance.
+
+// E_l x: the chosen coarse operator at level 1, ReD-Glk2 below it (the
+// re-discretisation Sec. 5.2.4 suggests for a multilevel method)
 template <class T>
-hz_status coarse_solve_level2(hz_solver* s, int nrhs, const int* done_in) {
-  cudaStream_t st = s->st;
-  KState& ks = s->kin2;
-  const LevelDev L2 = s->lv[2].dev();
-  const long long n2 = s->lv[2].n;
-  const long long rs = inner_row(n2);
-  const long long vs = (long long)s->d.nrhs_max * rs;
-  C<T>* Q = (C<T>*)s->Q2;
-  const int m = s->d.coarse_maxit;
-  launch_norm2_part<T>(vref<T>((C<T>*)s->v1_2), n2, nrhs, ks, nullptr, st);
-  launch_reduce_norm(ks, n2, nrhs, ks.beta, 1, st);
-  launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, st);
-  launch_scale_into<T, C<T>>(vref<T>((C<T>*)s->v1_2), vrefe<C<T>>(Q), rs, ks.hnorm, n2,
-                             nrhs, ks.done, st, (C<T>*)s->qf2);
-  int all = 0;
-  for (int it = 0; it < m; ++it) {
-    vcycle<T>(s, 2, vref<T>((C<T>*)s->qf2), (C<T>*)s->sb2, nrhs, ks.done);
-    launch_glk<T>(L2, s->d.bc, 2, (const C<T>*)s->sb2, (C<T>*)s->eb2, nrhs, ks.done, st);
-    cgs2<T, C<T>>(s, ks, Q, vs, rs, (C<T>*)s->eb2, n2, nrhs);
-    launch_givens(ks, nrhs, s->d.coarse_tol, m, st);
-    launch_scale_into<T, C<T>>(vref<T>((C<T>*)s->eb2), vrefe_j<C<T>>(Q, ks.jctr, 0, vs), rs,
-                               ks.hnorm, n2, nrhs, ks.done, st, (C<T>*)s->qf2);
-    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
-      const hz_status e = read_flag(s, ks.alldone, &all);
-      if (e != HZ_OK) return e;
-      if (all) break;
-    }
-  }
-  launch_trisolve(ks, nrhs, st);
-  launch_update<C<T>, T>(Q, vs, rs, ks, (C<T>*)s->eb2, 0, n2, nrhs, st);
-  vcycle<T>(s, 2, vref<T>((C<T>*)s->eb2), (C<T>*)s->v2_2, nrhs, done_in);
-  return cuda_check(s, "level-2 coarse solve");
+void apply_El(hz_solver* s, int l, const C<T>* x, C<T>* y, int nrhs, const int* done) {
+  if (l == 1)
+    apply_E<T>(s, x, y, nrhs, done);
+  else
+    launch_glk<T>(s->lv[l].dev(), s->d.bc, 2, x, y, nrhs, done, s->st);
 }
 
-// The level-1 coarse system with three-level deflation: flexible GMRES on
-// E right-preconditioned by A-DEF1 one level down,
-// z_j = M_1^-1 (v_j - E q) + q, q = Z_1 E_2^-1 R_1 v_j; the directions z_j
-// are kept (Z1b) and v2 = Z1 y at the end.
+// Krylov state, basis and vectors of deflation level l
+struct MLView {
+  KState* ks;
+  void *Q, *qf, *sb, *eb;
+};
+MLView ml_view(hz_solver* s, int l) {
+  if (l == 1) return MLView{&s->kin, s->Qb, s->qf, s->sb, s->eb};
+  hz_solver::DefLevel& D = s->dl[l];
+  return MLView{&D.ks, D.Q, D.qf, D.sb, D.eb};
+}
+
 template <class T, class SB>
-hz_status coarse_solve_ml(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
-                          const int* done_in) {
-  cudaStream_t st = s->st;
-  KState& ks = s->kin;
+hz_status ml_solve(hz_solver* s, int l, const C<T>* v1, C<T>* v2, int nrhs,
+                   const int* done_in);
+
+// One Arnoldi step at level l (basis vector j in compute precision in qf):
+// z_j = P_l v_j above the deepest level (its directions kept in Zb), the
+// V-cycle from level l at the deepest one; w = E_l z_j, Gram-Schmidt,
+// Givens, v_{j+1}.  Every launch reads s->st when it is issued: a nested
+// loop captured inside switches it and restores it.
+template <class T, class SB>
+hz_status ml_step(hz_solver* s, int l, int nrhs) {
+  const MLView V = ml_view(s, l);
+  KState& ks = *V.ks;
   const int bc = s->d.bc, zk = s->d.zkind;
-  const LevelDev L1 = s->lv[1].dev(), L2 = s->lv[2].dev();
-  const long long n1 = s->lv[1].n;
-  const long long rs = inner_row(n1);
+  const long long nl = s->lv[l].n, rs = inner_row(nl);
   const long long vs = (long long)s->d.nrhs_max * rs;
-  const long long zs = (long long)s->d.nrhs_max * n1;
-  const int m = s->d.coarse_maxit;
-  C<T>* zj = (C<T>*)s->zj;
-  coarse_begin<T, SB>(s, v1, nrhs, done_in);
-  int all = 0;
-  for (int it = 0; it < m; ++it) {
-    // z_j = P_1 v_j (v_j in compute precision in s->qf)
-    launch_restrict_z<T>(L1, L2, bc, zk, vref<T>((C<T>*)s->qf), (C<T>*)s->v1_2, nrhs,
-                         ks.done, st);
-    hz_status e = coarse_solve_level2<T>(s, nrhs, ks.done);
+  C<T>* qf = (C<T>*)V.qf;
+  C<T>* sb = (C<T>*)V.sb;
+  C<T>* eb = (C<T>*)V.eb;
+  if (l < s->D) {
+    hz_solver::DefLevel& D = s->dl[l];
+    hz_solver::DefLevel& Dn = s->dl[l + 1];
+    const LevelDev Lf = s->lv[l].dev(), Lc = s->lv[l + 1].dev();
+    const long long zs = (long long)s->d.nrhs_max * nl;
+    launch_restrict_z<T>(Lf, Lc, bc, zk, vref<T>(qf), (C<T>*)Dn.v1, nrhs, ks.done, s->st);
+    const hz_status e =
+        ml_solve<T, C<T>>(s, l + 1, (const C<T>*)Dn.v1, (C<T>*)Dn.v2, nrhs, ks.done);
     if (e != HZ_OK) return e;
-    launch_prolong_z<T>(L1, L2, bc, zk, (const C<T>*)s->v2_2, (C<T>*)s->q1, 0, nrhs,
-                        ks.done, st);
-    apply_E<T>(s, (const C<T>*)s->q1, (C<T>*)s->u1, nrhs, ks.done);
-    launch_sub<T>((const C<T>*)s->qf, (const C<T>*)s->u1, (C<T>*)s->u1, n1, nrhs, ks.done,
-                  st);
-    vcycle<T>(s, 1, vref<T>((C<T>*)s->u1), (C<T>*)s->sb, nrhs, ks.done);
-    launch_add_conv<T, T>(vref<T>((C<T>*)s->sb), (const C<T>*)s->q1, vref<T>(zj), n1, nrhs,
-                          ks.done, st);
-    launch_add_conv<T, T>(vref<T>(zj), nullptr, vref_j<T>((C<T>*)s->Z1b, ks.jctr, 0, zs),
-                          n1, nrhs, ks.done, st);
-    apply_E<T>(s, zj, (C<T>*)s->eb, nrhs, ks.done);
-    cgs2<T, SB>(s, ks, (SB*)s->Qb, vs, rs, (C<T>*)s->eb, n1, nrhs);
-    inner_post<T, SB>(s, nrhs);
-    if ((it + 1) % s->check_every == 0 || it + 1 == m) {
-      e = read_flag(s, ks.alldone, &all);
+    launch_prolong_z<T>(Lf, Lc, bc, zk, (const C<T>*)Dn.v2, (C<T>*)D.q, 0, nrhs, ks.done,
+                        s->st);
+    apply_El<T>(s, l, (const C<T>*)D.q, (C<T>*)D.u, nrhs, ks.done);
+    launch_sub<T>(qf, (const C<T>*)D.u, (C<T>*)D.u, nl, nrhs, ks.done, s->st);
+    vcycle<T>(s, l, vref<T>((C<T>*)D.u), sb, nrhs, ks.done);
+    launch_add_conv<T, T>(vref<T>(sb), (const C<T>*)D.q, vref<T>((C<T>*)D.zj), nl, nrhs,
+                          ks.done, s->st);
+    launch_add_conv<T, T>(vref<T>((C<T>*)D.zj), nullptr,
+                          vref_j<T>((C<T>*)D.Zb, ks.jctr, 0, zs), nl, nrhs, ks.done, s->st);
+    apply_El<T>(s, l, (const C<T>*)D.zj, eb, nrhs, ks.done);
+  } else {
+    vcycle<T>(s, l, vref<T>(qf), sb, nrhs, ks.done);
+    apply_El<T>(s, l, sb, eb, nrhs, ks.done);
+  }
+  cgs2<T, SB>(s, ks, (const SB*)V.Q, vs, rs, eb, nl, nrhs);
+  launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, s->st);
+  debug_trace(s, ks, "multilevel");
+  launch_scale_into<T, SB>(vref<T>(eb), vrefe_j<SB>((SB*)V.Q, ks.jctr, 0, vs), rs, ks.hnorm,
+                           nl, nrhs, ks.done, s->st, qf);
+  return cuda_check(s, "multilevel step");
+}
+
+// E_l v2 = v1 at deflation level l, x0 = 0; RHS done in the caller
+// (done_in) are skipped.  Under capture the loop becomes a WHILE node
+// (nested in the enclosing level's body), else it runs on the host with a
+// completion check every check_every iterations.
+template <class T, class SB>
+hz_status ml_solve(hz_solver* s, int l, const C<T>* v1, C<T>* v2, int nrhs,
+                   const int* done_in) {
+  const MLView V = ml_view(s, l);
+  KState& ks = *V.ks;
+  const long long nl = s->lv[l].n, rs = inner_row(nl);
+  const long long vs = (long long)s->d.nrhs_max * rs;
+  const int m = s->d.coarse_maxit;
+  launch_norm2_part<T>(vref<T>(v1), nl, nrhs, ks, nullptr, s->st);
+  launch_reduce_norm(ks, nl, nrhs, ks.beta, 1, s->st);
+  launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, s->st);
+  launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>((SB*)V.Q), rs, ks.hnorm, nl, nrhs, ks.done,
+                           s->st, (C<T>*)V.qf);
+  if (s->capturing) {
+    hz_status e = HZ_OK;
+    const hz_status ce = capture_loop(s, l, ks, [&] { e = ml_step<T, SB>(s, l, nrhs); });
+    if (ce != HZ_OK) return ce;
+    if (e != HZ_OK) return e;
+  } else {
+    int all = 0;
+    for (int it = 0; it < m; ++it) {
+      hz_status e = ml_step<T, SB>(s, l, nrhs);
       if (e != HZ_OK) return e;
-      if (all) break;
+      if ((it + 1) % s->check_every == 0 || it + 1 == m) {
+        e = read_flag(s, ks.alldone, &all);
+        if (e != HZ_OK) return e;
+        if (all) break;
+      }
     }
   }
-  launch_trisolve(ks, nrhs, st);
-  launch_update<C<T>, T>((const C<T>*)s->Z1b, zs, n1, ks, v2, 0, n1, nrhs, st);
-  launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, st);
-  return cuda_check(s, "three-level coarse solve");
+  launch_trisolve(ks, nrhs, s->st);
+  if (l < s->D) {
+    launch_update<C<T>, T>((const C<T>*)s->dl[l].Zb, (long long)s->d.nrhs_max * nl, nl, ks,
+                           v2, 0, nl, nrhs, s->st);
+  } else {
+    launch_update<SB, T>((const SB*)V.Q, vs, rs, ks, (C<T>*)V.eb, 0, nl, nrhs, s->st);
+    vcycle<T>(s, l, vref<T>((C<T>*)V.eb), v2, nrhs, done_in);
+  }
+  if (l == 1) launch_accum_iters(ks.iters, s->in_total, s->in_max, nrhs, done_in, s->st);
+  return cuda_check(s, "multilevel coarse solve");
 }
 
 template <class T, class SB>
 hz_status coarse_solve_sb(hz_solver* s, const C<T>* v1, C<T>* v2, int nrhs,
                           const int* done_in) {
-  if (s->ml) return coarse_solve_ml<T, SB>(s, v1, v2, nrhs, done_in);
+  if (s->ml) return ml_solve<T, SB>(s, 1, v1, v2, nrhs, done_in);
   KState& ks = s->kin;
   const int m = s->d.coarse_maxit;
   coarse_begin<T, SB>(s, v1, nrhs, done_in);
@@ -1014,6 +1128,12 @@ constexpr size_t kMaxGraphs = 4;
 void end_failed_capture(hz_solver* s) {
   cudaGraph_t g = nullptr;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  for (int l = kMaxLevels - 1; l >= 2; --l)
+    if (s->cap_nest[l] && cudaStreamIsCapturing(s->cap_nest[l], &cs) == cudaSuccess &&
+        cs != cudaStreamCaptureStatusNone) {
+      cudaStreamEndCapture(s->cap_nest[l], &g);
+      g = nullptr;
+    }
   if (s->cap_body && cudaStreamIsCapturing(s->cap_body, &cs) == cudaSuccess &&
       cs != cudaStreamCaptureStatusNone) {
     cudaStreamEndCapture(s->cap_body, &g);
@@ -1038,27 +1158,34 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
     cudaGraphDestroy(s->graphs.front().g);
     s->graphs.erase(s->graphs.begin());
   }
-  if ((!s->cap_main &&
-       cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking) != cudaSuccess) ||
-      (!s->cap_body &&
-       cudaStreamCreateWithFlags(&s->cap_body, cudaStreamNonBlocking) != cudaSuccess)) {
+  bool ok = (s->cap_main ||
+             cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking) == cudaSuccess) &&
+            (s->cap_body ||
+             cudaStreamCreateWithFlags(&s->cap_body, cudaStreamNonBlocking) == cudaSuccess);
+  for (int l = 2; ok && l <= s->D; ++l)
+    ok = s->cap_nest[l] ||
+         cudaStreamCreateWithFlags(&s->cap_nest[l], cudaStreamNonBlocking) == cudaSuccess;
+  if (!ok) {
     cuda_check(s, "capture streams");
     return nullptr;
   }
   cudaStream_t st0 = s->st;
-  const long long c0 = launch_counter().load();
+  const long long c0 = launch_counter().load(), h0 = host_op_counter().load();
   if (cudaStreamBeginCapture(s->cap_main, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
     cuda_check(s, "begin capture");
     return nullptr;
   }
   s->st = s->cap_main;
   s->capturing = true;
-  s->body_count = 0;
+  for (long long& c : s->body_count_l) c = 0;
   hz_status e = outer_step(s, nrhs, tol);
+  s->body_count = 0;
+  for (long long c : s->body_count_l) s->body_count += c;
   s->capturing = false;
   s->st = st0;
   const long long captured = launch_counter().load() - c0;
   launch_counter().fetch_sub(captured);   // nothing ran yet
+  host_op_counter().fetch_sub(host_op_counter().load() - h0);
   if (e != HZ_OK) {
     const std::string why = s->err;
     end_failed_capture(s);
@@ -1076,8 +1203,8 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
     cudaGraphDestroy(og.g);
     return nullptr;
   }
-  s->body_kernels_host = (int)s->body_count;
-  if (cudaMemcpyAsync(s->body_kernels, &s->body_kernels_host, sizeof(int),
+  for (int l = 0; l < kMaxLevels; ++l) s->body_kernels_host[l] = (int)s->body_count_l[l];
+  if (cudaMemcpyAsync(s->body_kernels, s->body_kernels_host, sizeof(int) * kMaxLevels,
                       cudaMemcpyHostToDevice, st0) != cudaSuccess ||
       cudaStreamSynchronize(st0) != cudaSuccess) {
     cuda_check(s, "graph counter");
@@ -1228,9 +1355,11 @@ double time_cgs_any(hz_solver* s, int nrhs, bool upd, int variant) {
 
 // One V-cycle from level 1 (level 0 without deflation) on synthetic data.
 template <class T>
-double time_vcycle(hz_solver* s, int nrhs, int fused) {
+double time_vcycle(hz_solver* s, int nrhs, int fused, int rpb = 0, int tile = 0) {
   const hz_tuning saved = s->tune;
   s->tune.vcycle_fused = fused;
+  s->tune.vcycle_rhs_per_block = rpb;
+  s->tune.vcycle_tile = tile;
   const int l0 = (s->d.zkind != HZ_Z_NONE && s->L >= 1) ? 1 : 0;
   const long long n = s->lv[l0].n;
   C<T>* in = (C<T>*)(l0 == 1 ? s->sb : s->t);
@@ -1350,22 +1479,23 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   // graphs replay fixed launches: the per-launch events of the profiler
   // and the trace's host reads need the launches issued one by one
   hz_solver::OuterGraph* og = nullptr;
-  if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on() && !s->ml) {
+  if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on()) {
     og = outer_graph(s, nrhs, tol);
     if (!og) return HZ_CUDA_ERROR;
   }
-  e = read_flag(s, ko.alldone, &all);
+  e = read_outer_flag(s, &all);
   if (e != HZ_OK) return e;
   for (int it = 0; it < m && !all; ++it) {
     if (og) {
       if (cudaGraphLaunch(og->ex, st) != cudaSuccess) return cuda_check(s, "graph launch");
       launch_counter().fetch_add(og->kernels);
+      host_op_counter().fetch_add(1);
       g_graph_launched.store(true);
     } else {
       e = outer_step(s, nrhs, tol);
       if (e != HZ_OK) return e;
     }
-    e = read_flag(s, ko.alldone, &all);
+    e = read_outer_flag(s, &all);
     if (e != HZ_OK) return e;
   }
   return outer_end(s, b, x, nrhs, info);
@@ -1427,70 +1557,231 @@ hz_status read_flags(const std::vector<Member>& M, bool inner, std::vector<int>&
   return HZ_OK;
 }
 
-template <class T, class SB>
-hz_status coarse_solve_group(const std::vector<Member>& M, cudaStream_t st) {
-  int m = 0;
-  for (const Member& g : M) {
-    coarse_begin<T, SB>(g.s, (const C<T>*)g.s->v1, g.nrhs, g.s->kout.done);
-    m = g.s->d.coarse_maxit > m ? g.s->d.coarse_maxit : m;
+// A group solve issued as CUDA graphs: one graph per outer iteration of the
+// active members (captured on first use for each set of active members and
+// destroyed when the call returns).  In it every member's own work (its
+// stencil, transfer and E kernels) runs on a branch of its own, so the
+// members' grids share the GPU; the branches join before each grouped
+// Gram-Schmidt step.  The inner coarse solves advance together in a WHILE
+// node that repeats while some member's inner solve is not done.
+struct GroupCtx {
+  bool capturing = false;
+  cudaStream_t main = nullptr;           // stream being captured (outer level)
+  cudaStream_t body = nullptr;           // WHILE body capture stream
+  std::vector<cudaStream_t> br_out, br_in;   // member branches (outer, body)
+  std::vector<cudaEvent_t> ev;           // fork + one join per member
+  long long body_count = 0;              // own kernels of the WHILE body
+  int* flag = nullptr;                   // device: all members' inner solves done
+  int* loop_it = nullptr;                // device: WHILE iterations
+  int* body_kernels = nullptr;           // device: body_count
+  ~GroupCtx() {
+    for (cudaStream_t c : br_out) if (c) cudaStreamDestroy(c);
+    for (cudaStream_t c : br_in) if (c) cudaStreamDestroy(c);
+    for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
   }
-  const int every = M[0].s->check_every;
-  std::vector<int> all;
-  for (int it = 0; it < m; ++it) {
-    for (const Member& g : M) inner_pre<T, SB>(g.s, g.nrhs);
-    cgs2_group<T, SB>(M, true, st);
-    for (const Member& g : M) inner_post<T, SB>(g.s, g.nrhs);
-    if ((it + 1) % every == 0 || it + 1 == m) {
-      const hz_status e = read_flags(M, true, all, st);
-      if (e != HZ_OK) return e;
-      bool done = true;
-      for (int a : all) done = done && a;
-      if (done) break;
+};
+
+// f(g) for every member g: on its own branch of the captured graph
+// (forked from and joined back to st), or in order on st.
+template <class F>
+void each_member(const std::vector<Member>& M, GroupCtx* gc, bool body, cudaStream_t st,
+                 F&& f) {
+  if (!gc || !gc->capturing) {
+    for (size_t g = 0; g < M.size(); ++g) f(g);
+    return;
+  }
+  const std::vector<cudaStream_t>& br = body ? gc->br_in : gc->br_out;
+  cudaEventRecord(gc->ev[0], st);
+  for (size_t g = 0; g < M.size(); ++g) {
+    cudaStreamWaitEvent(br[g], gc->ev[0], 0);
+    M[g].s->st = br[g];
+    f(g);
+    M[g].s->st = st;
+    cudaEventRecord(gc->ev[1 + g], br[g]);
+  }
+  for (size_t g = 0; g < M.size(); ++g) cudaStreamWaitEvent(st, gc->ev[1 + g], 0);
+}
+
+FlagSet inner_flags(const std::vector<Member>& M) {
+  FlagSet fs{};
+  fs.n = (int)M.size();
+  for (size_t g = 0; g < M.size(); ++g) fs.f[g] = M[g].s->kin.alldone;
+  return fs;
+}
+
+template <class T, class SB>
+hz_status coarse_solve_group(const std::vector<Member>& M, cudaStream_t st, GroupCtx* gc) {
+  int m = 0;
+  for (const Member& g : M) m = g.s->d.coarse_maxit > m ? g.s->d.coarse_maxit : m;
+  each_member(M, gc, false, st, [&](size_t g) {
+    coarse_begin<T, SB>(M[g].s, (const C<T>*)M[g].s->v1, M[g].nrhs, M[g].s->kout.done);
+  });
+  if (gc && gc->capturing) {
+    // the loop as a WHILE node over all members
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaGraph_t G = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t nd = 0;
+    if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, nullptr, nullptr, nullptr) !=
+            cudaSuccess ||
+        cs != cudaStreamCaptureStatusActive)
+      return cuda_check(M[0].s, "group loop capture: stream not capturing");
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, G, 0, 0) != cudaSuccess)
+      return cuda_check(M[0].s, "conditional handle");
+    launch_all_of(inner_flags(M), gc->flag, st);
+    launch_loop_begin(gc->flag, nullptr, gc->loop_it, h, st);
+    if (cudaStreamGetCaptureInfo(st, &cs, nullptr, &G, &deps, nullptr, &nd) != cudaSuccess)
+      return cuda_check(M[0].s, "capture info");
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, G, deps, nullptr, nd, &p) != cudaSuccess)
+      return cuda_check(M[0].s, "WHILE node");
+    if (cudaStreamBeginCaptureToGraph(gc->body, p.conditional.phGraph_out[0], nullptr,
+                                      nullptr, 0, cudaStreamCaptureModeRelaxed) !=
+        cudaSuccess)
+      return cuda_check(M[0].s, "body capture");
+    const long long c0 = launch_counter().load();
+    each_member(M, gc, true, gc->body, [&](size_t g) { inner_pre<T, SB>(M[g].s, M[g].nrhs); });
+    cgs2_group<T, SB>(M, true, gc->body);
+    each_member(M, gc, true, gc->body,
+                [&](size_t g) { inner_post<T, SB>(M[g].s, M[g].nrhs); });
+    launch_all_of(inner_flags(M), gc->flag, gc->body);
+    launch_loop_next(gc->flag, nullptr, gc->loop_it, m, gc->body_kernels, h, gc->body);
+    gc->body_count = launch_counter().load() - c0;
+    cudaGraph_t bo = nullptr;
+    if (cudaStreamEndCapture(gc->body, &bo) != cudaSuccess)
+      return cuda_check(M[0].s, "body capture end");
+    if (cudaStreamUpdateCaptureDependencies(st, &node, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies) != cudaSuccess)
+      return cuda_check(M[0].s, "capture dependencies");
+  } else {
+    const int every = M[0].s->check_every;
+    std::vector<int> all;
+    for (int it = 0; it < m; ++it) {
+      for (const Member& g : M) inner_pre<T, SB>(g.s, g.nrhs);
+      cgs2_group<T, SB>(M, true, st);
+      for (const Member& g : M) inner_post<T, SB>(g.s, g.nrhs);
+      if ((it + 1) % every == 0 || it + 1 == m) {
+        const hz_status e = read_flags(M, true, all, st);
+        if (e != HZ_OK) return e;
+        bool done = true;
+        for (int a : all) done = done && a;
+        if (done) break;
+      }
     }
   }
-  for (const Member& g : M) coarse_finish<T, SB>(g.s, (C<T>*)g.s->v2, g.nrhs, g.s->kout.done);
+  each_member(M, gc, false, st, [&](size_t g) {
+    coarse_finish<T, SB>(M[g].s, (C<T>*)M[g].s->v2, M[g].nrhs, M[g].s->kout.done);
+  });
   return cuda_check(M[0].s, "group coarse solve");
 }
 
 template <class T>
-hz_status outer_step_group(const std::vector<Member>& M, double tol, cudaStream_t st) {
+hz_status outer_step_group(const std::vector<Member>& M, double tol, cudaStream_t st,
+                           GroupCtx* gc) {
   std::vector<VRef<T>> v(M.size());
-  for (size_t g = 0; g < M.size(); ++g) {
+  each_member(M, gc, false, st, [&](size_t g) {
     hz_solver* s = M[g].s;
     const long long vs = (long long)s->d.nrhs_max * s->lv[0].n;
     v[g] = precond_begin<T>(s, vref_j<double>(s->Vo, s->kout.jctr, 0, vs), M[g].nrhs,
                             s->kout.done);
-  }
+  });
   if (M[0].s->d.zkind != HZ_Z_NONE) {
     hz_status e;
     if constexpr (std::is_same<T, float>::value) {
-      e = M[0].s->basis16 ? coarse_solve_group<T, __half2>(M, st)
-                          : coarse_solve_group<T, C<T>>(M, st);
+      e = M[0].s->basis16 ? coarse_solve_group<T, __half2>(M, st, gc)
+                          : coarse_solve_group<T, C<T>>(M, st, gc);
     } else {
-      e = coarse_solve_group<T, C<T>>(M, st);
+      e = coarse_solve_group<T, C<T>>(M, st, gc);
     }
     if (e != HZ_OK) return e;
   }
-  for (size_t g = 0; g < M.size(); ++g) {
+  each_member(M, gc, false, st, [&](size_t g) {
     hz_solver* s = M[g].s;
     const long long vs = (long long)s->d.nrhs_max * s->lv[0].n;
     precond_finish<T>(s, v[g], vref_j<double>(s->Zo, s->kout.jctr, 0, vs), M[g].nrhs,
                       s->kout.done);
     launch_helm<double>(dev64(s, 0), s->d.bc, helm1(),
                         vref_j<double>(s->Zo, s->kout.jctr, 0, vs), vref<double>(nullptr),
-                        s->wo, M[g].nrhs, s->kout.done, st);
-  }
+                        s->wo, M[g].nrhs, s->kout.done, s->st);
+  });
   cgs2_group<double, double2>(M, false, st);
-  for (const Member& g : M) {
-    hz_solver* s = g.s;
+  each_member(M, gc, false, st, [&](size_t g) {
+    hz_solver* s = M[g].s;
     const long long n0 = s->lv[0].n;
     const long long vs = (long long)s->d.nrhs_max * n0;
-    launch_givens(s->kout, g.nrhs, tol, s->d.outer_maxit, st);
+    launch_givens(s->kout, M[g].nrhs, tol, s->d.outer_maxit, s->st);
     launch_scale_into<double, double2>(vref<double>(s->wo),
                                       vref_j<double>(s->Vo, s->kout.jctr, 0, vs), n0,
-                                      s->kout.hnorm, n0, g.nrhs, s->kout.done, st);
-  }
+                                      s->kout.hnorm, n0, M[g].nrhs, s->kout.done, s->st);
+  });
   return cuda_check(M[0].s, "group outer step");
+}
+
+struct GroupGraph {
+  unsigned mask;
+  cudaGraph_t g;
+  cudaGraphExec_t ex;
+  long long kernels;   // kernels of one launch outside the WHILE body
+};
+
+// Captures (or returns the captured) graph of one outer iteration of the
+// active members act (bit g of mask = member g active).
+GroupGraph* group_graph(const std::vector<Member>& act, unsigned mask, double tol,
+                        GroupCtx& gc, std::vector<GroupGraph>& graphs, cudaStream_t st) {
+  for (GroupGraph& g : graphs)
+    if (g.mask == mask) return &g;
+  hz_solver* s0 = act[0].s;
+  const long long c0 = launch_counter().load(), h0 = host_op_counter().load();
+  if (cudaStreamBeginCapture(gc.main, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    cuda_check(s0, "begin group capture");
+    return nullptr;
+  }
+  for (const Member& m : act) m.s->st = gc.main;
+  gc.capturing = true;
+  gc.body_count = 0;
+  const hz_status e = s0->mixed ? outer_step_group<float>(act, tol, gc.main, &gc)
+                                : outer_step_group<double>(act, tol, gc.main, &gc);
+  gc.capturing = false;
+  for (const Member& m : act) m.s->st = st;
+  const long long captured = launch_counter().load() - c0;
+  launch_counter().fetch_sub(captured);
+  host_op_counter().fetch_sub(host_op_counter().load() - h0);
+  GroupGraph gg{mask, nullptr, nullptr, captured - gc.body_count};
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(gc.body, &cs) == cudaSuccess &&
+      cs != cudaStreamCaptureStatusNone) {   // a failure inside the WHILE body
+    cudaGraph_t bg = nullptr;
+    cudaStreamEndCapture(gc.body, &bg);
+  }
+  const cudaError_t ce = cudaStreamEndCapture(gc.main, &gg.g);
+  if (e != HZ_OK || ce != cudaSuccess) {
+    if (ce == cudaSuccess && gg.g) cudaGraphDestroy(gg.g);
+    cudaGetLastError();
+    if (e == HZ_OK) set_err(s0, "group graph capture failed");
+    return nullptr;
+  }
+  if (cudaGraphInstantiate(&gg.ex, gg.g, 0) != cudaSuccess) {
+    cuda_check(s0, "group graph instantiate");
+    cudaGraphDestroy(gg.g);
+    return nullptr;
+  }
+  const int bc = (int)gc.body_count;
+  if (cudaMemcpyAsync(gc.body_kernels, &bc, sizeof(int), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cuda_check(s0, "group graph counter");
+    cudaGraphExecDestroy(gg.ex);
+    cudaGraphDestroy(gg.g);
+    return nullptr;
+  }
+  graphs.push_back(gg);
+  return &graphs.back();
 }
 
 // Member g solves b[g] -> x[g] (x0 = 0); all members already run on st.
@@ -1499,28 +1790,81 @@ hz_status solve_group_dev(const std::vector<Member>& M, const double2* const* b,
                           cudaStream_t st) {
   const int K = (int)M.size();
   int m = 0;
+  bool graphs_ok = true;
   for (int g = 0; g < K; ++g) {
     const hz_status e = outer_begin(M[g].s, b[g], x[g], M[g].nrhs, tol, 0);
     if (e != HZ_OK) return e;
     m = M[g].s->d.outer_maxit > m ? M[g].s->d.outer_maxit : m;
+    graphs_ok = graphs_ok && !M[g].s->d.no_cuda_graph && M[g].s->prof_kc == HZ_KC_NONE;
+  }
+  graphs_ok = graphs_ok && !debug_on();
+  // graph mode: branch streams, fork/join events and the group's device
+  // flags (in member 0's workspace)
+  GroupCtx gc;
+  std::vector<GroupGraph> graphs;
+  if (graphs_ok) {
+    hz_solver* s0 = M[0].s;
+    bool ok = s0->cap_main ||
+              cudaStreamCreateWithFlags(&s0->cap_main, cudaStreamNonBlocking) == cudaSuccess;
+    ok = ok && (s0->cap_body ||
+                cudaStreamCreateWithFlags(&s0->cap_body, cudaStreamNonBlocking) == cudaSuccess);
+    gc.main = s0->cap_main;
+    gc.body = s0->cap_body;
+    gc.br_out.assign(K, nullptr);
+    gc.br_in.assign(K, nullptr);
+    gc.ev.assign(K + 1, nullptr);
+    for (int g = 0; ok && g < K; ++g)
+      ok = cudaStreamCreateWithFlags(&gc.br_out[g], cudaStreamNonBlocking) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&gc.br_in[g], cudaStreamNonBlocking) == cudaSuccess;
+    for (int g = 0; ok && g <= K; ++g)
+      ok = cudaEventCreateWithFlags(&gc.ev[g], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return cuda_check(s0, "group graph streams");
+    gc.flag = s0->grp;
+    gc.loop_it = s0->grp + 1;
+    gc.body_kernels = s0->grp + 2;
   }
   std::vector<int> all;
   hz_status e = read_flags(M, false, all, st);
   if (e != HZ_OK) return e;
   for (int it = 0; it < m; ++it) {
     std::vector<Member> act;
+    unsigned mask = 0;
     for (int g = 0; g < K; ++g)
-      if (!all[g]) act.push_back(M[g]);
+      if (!all[g]) {
+        act.push_back(M[g]);
+        mask |= 1u << g;
+      }
     if (act.empty()) break;
-    e = M[0].s->mixed ? outer_step_group<float>(act, tol, st)
-                      : outer_step_group<double>(act, tol, st);
-    if (e != HZ_OK) return e;
+    if (graphs_ok) {
+      GroupGraph* gg = group_graph(act, mask, tol, gc, graphs, st);
+      if (!gg) {
+        e = HZ_CUDA_ERROR;
+        break;
+      }
+      if (cudaGraphLaunch(gg->ex, st) != cudaSuccess) {
+        e = cuda_check(M[0].s, "group graph launch");
+        break;
+      }
+      launch_counter().fetch_add(gg->kernels);
+      host_op_counter().fetch_add(1);
+      g_graph_launched.store(true);
+    } else {
+      e = M[0].s->mixed ? outer_step_group<float>(act, tol, st, nullptr)
+                        : outer_step_group<double>(act, tol, st, nullptr);
+      if (e != HZ_OK) break;
+    }
     std::vector<int> now;
     e = read_flags(act, false, now, st);
-    if (e != HZ_OK) return e;
+    if (e != HZ_OK) break;
     for (size_t a = 0, g = 0; g < (size_t)K; ++g)
       if (!all[g]) all[g] = now[a++];
   }
+  if (!graphs.empty()) cudaStreamSynchronize(st);
+  for (GroupGraph& g : graphs) {
+    cudaGraphExecDestroy(g.ex);
+    cudaGraphDestroy(g.g);
+  }
+  if (e != HZ_OK) return e;
   hz_status worst = HZ_OK;
   for (int g = 0; g < K; ++g) {
     e = outer_end(M[g].s, b[g], x[g], M[g].nrhs, info ? info[g] : nullptr);
@@ -2039,6 +2383,8 @@ void hz_tuning_default(hz_tuning* t) {
   t->galerkin_apply = 0;
   t->e_rhs_per_block = 0;
   t->vcycle_fused = 0;
+  t->vcycle_rhs_per_block = 0;
+  t->vcycle_tile = 0;
 }
 
 hz_status hz_get_tuning(const hz_solver* s, hz_tuning* t) {
@@ -2051,7 +2397,8 @@ hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
   if (!s || !t || t->mdot_kernel < 0 || t->mdot_kernel > 2 || t->maxpy_kernel < 0 ||
       t->maxpy_kernel > 2 || t->galerkin_apply < 0 || t->galerkin_apply > 1 ||
       t->e_rhs_per_block < 0 || t->e_rhs_per_block > kMaxRhs || t->vcycle_fused < 0 ||
-      t->vcycle_fused > 1)
+      t->vcycle_fused > 2 || t->vcycle_rhs_per_block < 0 ||
+      t->vcycle_rhs_per_block > kMaxRhs || t->vcycle_tile < 0 || t->vcycle_tile > 1)
     return HZ_INVALID_ARG;
   if (t->galerkin_apply == 1 && !s->Sglk) {
     set_err(s, "galerkin_apply = 1 needs the Galerkin coarse operator (HZ_E_GALERKIN)");
@@ -2067,10 +2414,19 @@ hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
     s->graphs.clear();
   }
   s->tune = *t;
-  s->kin.dotk = s->kout.dotk = s->kin2.dotk = t->mdot_kernel;
-  s->kin.updk = s->kout.updk = s->kin2.updk = t->maxpy_kernel;
+  s->kin.dotk = s->kout.dotk = t->mdot_kernel;
+  s->kin.updk = s->kout.updk = t->maxpy_kernel;
+  for (int l = 2; l <= s->D; ++l) {
+    s->dl[l].ks.dotk = t->mdot_kernel;
+    s->dl[l].ks.updk = t->maxpy_kernel;
+  }
   return HZ_OK;
 }
+
+// staged V-cycle candidates: RHS per block x prolongation tile
+constexpr int kVcycleRpb[3] = {4, 8, 16};
+constexpr int kVcycleStaged = 6;
+static_assert(11 + 2 + kVcycleStaged == HZ_TUNE_CANDIDATES, "candidate count");
 
 hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
   if (!s || nrhs < 1 || nrhs > s->d.nrhs_max) return HZ_INVALID_ARG;
@@ -2101,9 +2457,22 @@ hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
     t.galerkin_apply = tm[7] < tm[6] ? 1 : 0;
   }
   if (s->L >= 1) {
-    for (int f = 0; f <= 1; ++f)
-      tm[11 + f] = s->mixed ? time_vcycle<float>(s, nrhs, f) : time_vcycle<double>(s, nrhs, f);
-    t.vcycle_fused = tm[12] < tm[11] ? 1 : 0;
+    // separate, fused, then the staged multi-RHS kernels for each
+    // (RHS per block, prolongation tile) of kVcycleStaged
+    int pick = 0;
+    for (int c = 0; c < 2 + kVcycleStaged; ++c) {
+      const int f = c < 2 ? c : 2;
+      const int rpb = c < 2 ? 0 : kVcycleRpb[(c - 2) % 3];
+      const int tile = c < 2 ? 0 : (c - 2) / 3;
+      tm[11 + c] = s->mixed ? time_vcycle<float>(s, nrhs, f, rpb, tile)
+                            : time_vcycle<double>(s, nrhs, f, rpb, tile);
+      if (tm[11 + c] < tm[11 + pick]) pick = c;
+    }
+    t.vcycle_fused = pick < 2 ? pick : 2;
+    if (pick >= 2) {
+      t.vcycle_rhs_per_block = kVcycleRpb[(pick - 2) % 3];
+      t.vcycle_tile = (pick - 2) / 3;
+    }
   }
   s->prof_kc = saved_prof;
   hz_status e = take_fault(s);
@@ -2116,6 +2485,30 @@ hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
     for (int k = 0; k < HZ_TUNE_CANDIDATES; ++k) ms[k] = tm[k];
   return HZ_OK;
 }
+
+hz_status hz_fault_drill(hz_solver* s, int starve_copies, double wait_seconds) {
+  if (!s || !(wait_seconds > 0) || wait_seconds > 2.0) return HZ_INVALID_ARG;
+  const unsigned long long ns = (unsigned long long)(wait_seconds * 1e9);
+  auto set = [&](KState& k) {
+    k.starve = starve_copies ? 1 : 0;
+    k.wait_ns = ns;
+  };
+  set(s->kin);
+  set(s->kout);
+  for (int l = 2; l <= s->D; ++l) set(s->dl[l].ks);
+  // captured graphs hold the previous kernel arguments
+  if (!s->graphs.empty()) {
+    cudaStreamSynchronize(s->st);
+    for (hz_solver::OuterGraph& g : s->graphs) {
+      cudaGraphExecDestroy(g.ex);
+      cudaGraphDestroy(g.g);
+    }
+    s->graphs.clear();
+  }
+  return HZ_OK;
+}
+
+long long hz_host_launches(void) { return hz::host_op_counter().load(); }
 
 long long hz_kernel_launches(void) {
   long long n = hz::launch_counter().load();

@@ -4,6 +4,8 @@
 // ReD-Glk coarse stencils (Sec. 5.2.4), the dense coarsest-level solve and
 // the setup kernels.  Every kernel serves nrhs right-hand sides (blockIdx.z)
 // and skips those flagged done.
+#include <mutex>
+
 #include "hz_common.cuh"
 #include "hz_stencil_dev.cuh"
 
@@ -586,16 +588,32 @@ __global__ void k_probe_extract(LevelDev Lc, int P, int c0,
 
 // y = E x with the stored stencil; one thread per coarse node keeps its
 // coefficients in registers while the block walks over its right-hand sides
-// (blockIdx.z selects a group of rpb of them), each x tile with its halo
-// staged in shared memory; the next right-hand side's tile is loaded into
-// registers while the current one is applied.
+// (blockIdx.z selects a group of rpb of them).  Each right-hand side's x
+// tile with its halo is copied into a ring of NS shared-memory stages by
+// cp.async, NS-1 right-hand sides ahead of the one being applied, so the
+// DRAM bytes in flight per SM are set by the ring (the coefficients take
+// the registers).
+constexpr int kStencilNS = 6;
+
+template <class T, int R>
+struct StencilE {
+  static constexpr int P = 2 * R + 1, K = P * P, TX = BX + 2 * R, TY = BY + 2 * R;
+  static constexpr int NT = BX * BY, NPT = (TY * TX + NT - 1) / NT;
+  static constexpr int STAGE = ((TY * TX * (int)sizeof(C<T>)) + 15) & ~15;
+  static constexpr int smem(int rpb) { return kStencilNS * STAGE + 4 * rpb; }
+};
+
 template <class T, int R>
 __global__ void __launch_bounds__(BX * BY)
 k_stencil_e(LevelDev Lc, const C<T>* __restrict__ S, const C<T>* __restrict__ x,
             C<T>* __restrict__ y, int nrhs, int rpb, const int* __restrict__ done) {
-  constexpr int P = 2 * R + 1, K = P * P, TX = BX + 2 * R, TY = BY + 2 * R;
-  constexpr int NT = BX * BY, NPT = (TY * TX + NT - 1) / NT;
-  __shared__ C<T> xs[TY * TX];
+  using Q = StencilE<T, R>;
+  constexpr int P = Q::P, K = Q::K, TX = Q::TX, TY = Q::TY, NT = Q::NT, NPT = Q::NPT;
+  constexpr int NS = kStencilNS, SV = Q::STAGE / (int)sizeof(C<T>);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<T>* xs = reinterpret_cast<C<T>*>(smraw);
+  int* act = reinterpret_cast<int*>(smraw + NS * Q::STAGE);
+  __shared__ int nact_s;
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
   const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
   const int I = I0 + tx, J = J0 + ty;
@@ -604,46 +622,61 @@ k_stencil_e(LevelDev Lc, const C<T>* __restrict__ S, const C<T>* __restrict__ x,
   const bool in = I < ncx && J < ncy;
   const long long id = (long long)J * ncx + I;
   const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  // active right-hand sides of the group, listed by warp 0
+  if (tid < 32) {
+    int cnt = 0;
+    for (int base = r0; base < r1; base += 32) {
+      const int r = base + tid;
+      const bool a = r < r1 && !(done && done[r]);
+      const unsigned m = __ballot_sync(0xffffffffu, a);
+      if (a) act[cnt + __popc(m & ((1u << tid) - 1u))] = r;
+      cnt += __popc(m);
+    }
+    if (tid == 0) nact_s = cnt;
+  }
+  __syncthreads();
+  const int na = nact_s;
+  if (na == 0) return;
   C<T> cf[K];
 #pragma unroll
   for (int k = 0; k < K; ++k) cf[k] = in ? S[(long long)k * nc + id] : czero<T>();
-  // tile values of right-hand side r held by this thread
-  auto fetch = [&](int r, C<T>* v) {
-    const C<T>* xr = x + r * nc;
+  // tile entries: node index, or -1 outside the grid (zero in every stage)
+  int gid[NPT];
 #pragma unroll
-    for (int u = 0; u < NPT; ++u) {
-      const int q = tid + u * NT;
-      const int gi = I0 - R + q % TX, gj = J0 - R + q / TX;
-      v[u] = (q < TY * TX && gi >= 0 && gi < ncx && gj >= 0 && gj < ncy)
-                 ? xr[(long long)gj * ncx + gi]
-                 : czero<T>();
+  for (int u = 0; u < NPT; ++u) {
+    const int q = tid + u * NT;
+    const int gi = I0 - R + q % TX, gj = J0 - R + q / TX;
+    gid[u] = (q < TY * TX && gi >= 0 && gi < ncx && gj >= 0 && gj < ncy) ? gj * ncx + gi : -1;
+    if (q < TY * TX && gid[u] < 0)
+      for (int sidx = 0; sidx < NS; ++sidx) xs[sidx * SV + q] = czero<T>();
+  }
+  auto issue = [&](int k) {
+    if (k < na) {
+      const C<T>* xr = x + (long long)act[k] * nc;
+      C<T>* stg = xs + (k % NS) * SV;
+#pragma unroll
+      for (int u = 0; u < NPT; ++u)
+        if (gid[u] >= 0) cp_async_el<sizeof(C<T>)>(stg + tid + u * NT, xr + gid[u]);
     }
+    cp_async_commit();
   };
-  auto next_active = [&](int r) {
-    while (r < r1 && done && done[r]) ++r;
-    return r;
-  };
-  C<T> pv[NPT];
-  int r = next_active(r0);
-  if (r < r1) fetch(r, pv);
-  while (r < r1) {
 #pragma unroll
-    for (int u = 0; u < NPT; ++u)
-      if (tid + u * NT < TY * TX) xs[tid + u * NT] = pv[u];
+  for (int k = 0; k < NS - 1; ++k) issue(k);
+  for (int k = 0; k < na; ++k) {
+    cp_async_wait<NS - 2>();
     __syncthreads();
-    const int rn = next_active(r + 1);
-    if (rn < r1) fetch(rn, pv);
+    issue(k + NS - 1);
     if (in) {
+      const C<T>* stg = xs + (k % NS) * SV;
       C<T> acc = czero<T>();
 #pragma unroll
       for (int b = 0; b < P; ++b)
 #pragma unroll
-        for (int a = 0; a < P; ++a) acc = cfma(cf[b * P + a], xs[(ty + b) * TX + tx + a], acc);
-      y[r * nc + id] = acc;
+        for (int a = 0; a < P; ++a) acc = cfma(cf[b * P + a], stg[(ty + b) * TX + tx + a], acc);
+      y[(long long)act[k] * nc + id] = acc;
     }
-    __syncthreads();
-    r = rn;
   }
+  cp_async_wait<0>();
 }
 
 
@@ -899,10 +932,21 @@ void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C
   HZ_COUNT();
   if (rpb <= 0 || rpb > nrhs) rpb = nrhs;
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute((const void*)k_stencil_e<T, 2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         StencilE<T, 2>::smem(1024));
+    cudaFuncSetAttribute((const void*)k_stencil_e<T, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         StencilE<T, 1>::smem(1024));
+  });
   if (R == 2)
-    k_stencil_e<T, 2><<<grid, dim3(BX, BY), 0, st>>>(Lc, S, x, y, nrhs, rpb, done);
+    k_stencil_e<T, 2><<<grid, dim3(BX, BY), StencilE<T, 2>::smem(rpb), st>>>(Lc, S, x, y,
+                                                                           nrhs, rpb, done);
   else
-    k_stencil_e<T, 1><<<grid, dim3(BX, BY), 0, st>>>(Lc, S, x, y, nrhs, rpb, done);
+    k_stencil_e<T, 1><<<grid, dim3(BX, BY), StencilE<T, 1>::smem(rpb), st>>>(Lc, S, x, y,
+                                                                           nrhs, rpb, done);
 }
 template <class T>
 void launch_glk(const LevelDev& L, int bc, int variant, const C<T>* x, C<T>* y,

@@ -108,4 +108,32 @@ __device__ __forceinline__ C<T> interp_bilinear(const LevelDev& Lc,
                     (ld2(xc, b0 + Lc.nx) + ld2(xc, b0 + Lc.nx + 1)));
 }
 
+// Asynchronous global -> shared copies of one element (cp.async, completing
+// per thread in commit groups; the data is visible to other threads after
+// cp.async.wait_group and a block barrier).  The element size (4, 8 or 16
+// bytes) is also the alignment both addresses have.
+template <int BYTES>
+__device__ __forceinline__ void cp_async_el(void* smem, const void* gmem) {
+  static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+// zero of a storage type (for tile entries outside the grid)
+template <class S> __device__ __forceinline__ S szero() {
+  S v;
+  memset(&v, 0, sizeof(S));
+  return v;
+}
+
 }  // namespace hz

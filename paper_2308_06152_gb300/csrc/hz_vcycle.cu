@@ -4,6 +4,8 @@
 // bilinear operator) and the dense coarsest-level solve.  Vectors of the
 // level hierarchy may be stored in a narrower type than the arithmetic
 // (BF16 pairs for the smoother variant); the arithmetic is C<T>.
+#include <mutex>
+
 #include "hz_common.cuh"
 #include "hz_stencil_dev.cuh"
 
@@ -275,6 +277,424 @@ k_prolong_smooth(LevelDev Lf, LevelDev Lc, int bc, T sre, T sim,
   st2(xo, r * nf + id, cfma(down, res, xp[c]));
 }
 
+// ---------------------------------------------------------------------------
+// Multi-RHS staged variants of the two fused kernels.  One block keeps its
+// tile's per-node constants (D^-1, neighbour weights, smem offsets) in
+// registers and walks over a group of right-hand sides; each right-hand
+// side's input tile (with its halo) is copied into a ring of NS
+// shared-memory stages by cp.async, NS-1 right-hand sides ahead of the one
+// being computed.  The arithmetic uses D^-1 = w / diag(M) to drop the
+// diagonal of M: with x = D^-1 f, (M x)_c = w f_c + sum_nb m_nb x_nb, so
+//   residual   f - M x          = (1 - w) f_c - sum_nb m_nb x_nb,
+//   smoothing  x + D^-1 (f - M x) = (1 - w) x_c + D^-1_c (f_c - sum_nb m_nb x_nb),
+// the same quantities as the kernels above (to rounding) without k^2 or
+// the complex diagonal.  The off-diagonal m_nb is -1/h^2 times 1 inside the
+// grid, 2 toward the interior at a Sommerfeld side (ghost elimination), 0
+// outside the grid or toward a Dirichlet boundary node; tiles whose halo
+// stays off the boundary take a path without those tests.
+
+// RHS of [r0, r1) not yet done, listed in act[] by warp 0; returns the count
+// to every thread.
+__device__ __forceinline__ int list_active(const int* __restrict__ done, int r0, int r1,
+                                           int* act, int* cnt_s) {
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  if (tid < 32) {
+    int cnt = 0;
+    for (int base = r0; base < r1; base += 32) {
+      const int r = base + tid;
+      const bool a = r < r1 && !(done && done[r]);
+      const unsigned m = __ballot_sync(0xffffffffu, a);
+      if (a) act[cnt + __popc(m & ((1u << tid) - 1u))] = r;
+      cnt += __popc(m);
+    }
+    if (tid == 0) *cnt_s = cnt;
+  }
+  __syncthreads();
+  return *cnt_s;
+}
+
+__host__ __device__ constexpr int align16(int b) { return (b + 15) & ~15; }
+
+// Off-diagonal weights of row (i, j) of M (an unknown node) as multiples of
+// -1/h^2, two bits each: west, east, south, north (see helm_row).
+__device__ __forceinline__ unsigned nb_code(int bc, int i, int j, int nx, int ny) {
+  unsigned w = 1, e = 1, so = 1, no = 1;
+  if (bc == BC_SOMMERFELD) {
+    if (i == 0) { w = 0; e = 2; }
+    if (i == nx - 1) { e = 0; w = 2; }
+    if (j == 0) { so = 0; no = 2; }
+    if (j == ny - 1) { no = 0; so = 2; }
+  } else {
+    if (i == 1) w = 0;
+    if (i == nx - 2) e = 0;
+    if (j == 1) so = 0;
+    if (j == ny - 2) no = 0;
+  }
+  return w | (e << 2) | (so << 4) | (no << 6);
+}
+// -sum_nb m_nb x_nb / (1/h^2) = sum of the neighbours with their weights
+template <class T, bool INTERIOR>
+__device__ __forceinline__ C<T> nb_sum(const C<T>* xs, int c, int row, unsigned code) {
+  const C<T> xw = xs[c - 1], xe = xs[c + 1], xso = xs[c - row], xno = xs[c + row];
+  if (INTERIOR) return (xw + xe) + (xso + xno);
+  C<T> a = T(code & 3u) * xw;
+  a = rfma(T((code >> 2) & 3u), xe, a);
+  a = rfma(T((code >> 4) & 3u), xso, a);
+  return rfma(T((code >> 6) & 3u), xno, a);
+}
+
+template <class T, class SF>
+struct PreRestrictMR {
+  static constexpr int XW = 2 * BX + 3, XH = 2 * BY + 3, RW = 2 * BX + 1, RH = 2 * BY + 1;
+  static constexpr int NX = XW * XH, NR = RW * RH, NT = BX * BY;
+  static constexpr int N1 = (NX + NT - 1) / NT, N2 = (NR + NT - 1) / NT;
+  static constexpr int STAGE = align16(NX * (int)sizeof(SF));
+  static constexpr int XS = align16(NX * (int)sizeof(C<T>));
+  static constexpr int RS = align16(NR * (int)sizeof(C<T>));
+  static constexpr int smem(int ns, int rpb) { return ns * STAGE + XS + RS + 4 * rpb; }
+};
+
+// Fused pre-smoothing, residual and full-weighting restriction for one
+// BX x BY tile of coarse nodes and a group of rpb right-hand sides.
+template <class T, class SF, class SX, class SC, int NS, bool INTERIOR>
+__device__ __forceinline__ void pre_restrict_mr_body(
+    const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, VRefE<SF> fin, SX* x, SC* fc,
+    int na, const int* act, unsigned char* smraw) {
+  using P = PreRestrictMR<T, SF>;
+  constexpr int XW = P::XW, RW = P::RW, NX = P::NX, NR = P::NR, NT = P::NT;
+  constexpr int N1 = P::N1, N2 = P::N2, SV = P::STAGE / (int)sizeof(SF);
+  SF* fst = reinterpret_cast<SF*>(smraw);
+  C<T>* xs = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE);
+  C<T>* rsd = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE + P::XS);
+  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int nfx = Lf.nx, nfy = Lf.ny;
+  const long long nf = (long long)nfx * nfy, nc = (long long)Lc.nx * Lc.ny;
+  const SF* fbase = fin.get();
+  const T ih2 = ih2_of<T>(Lf);
+  // x-tile entries: node (-1 outside the grid), copied (not a Dirichlet
+  // boundary node), one of the tile's own fine nodes (x written out)
+  int gid[N1];
+  unsigned cpm = 0, own = 0;
+  C<T> dv[N1];
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
+    const int gi = 2 * I0 - 2 + q % XW, gj = 2 * J0 - 2 + q / XW;
+    gid[u] = -1;
+    dv[u] = czero<T>();
+    if (q < NX && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+      gid[u] = gj * nfx + gi;
+      if (INTERIOR || !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
+        cpm |= 1u << u;
+        dv[u] = dinv_of<T>(Lf)[gid[u]];
+      }
+      if (gi >= 2 * I0 && gi < 2 * I0 + 2 * BX && gj >= 2 * J0 && gj < 2 * J0 + 2 * BY)
+        own |= 1u << u;
+    }
+  }
+  // residual nodes: their x-tile offset and neighbour weights (unknowns)
+  int cix[N2];
+  unsigned code[N2];
+  unsigned rok = 0;
+#pragma unroll
+  for (int u = 0; u < N2; ++u) {
+    const int q = tid + u * NT;
+    const int ri = q % RW, rj = q / RW;
+    const int gi = 2 * I0 - 1 + ri, gj = 2 * J0 - 1 + rj;
+    cix[u] = (rj + 1) * XW + (ri + 1);
+    code[u] = 0;
+    if (q < NR && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
+        (INTERIOR || !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy)))) {
+      rok |= 1u << u;
+      if (!INTERIOR) code[u] = nb_code(bc, gi, gj, nfx, nfy);
+    }
+  }
+  // entries that are never copied hold zero in every stage
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
+    if (q < NX && !(cpm >> u & 1u))
+      for (int sidx = 0; sidx < NS; ++sidx) fst[sidx * SV + q] = szero<SF>();
+  }
+  auto issue = [&](int k) {
+    if (k < na) {
+      const SF* fr = fbase + (long long)act[k] * nf;
+      SF* stg = fst + (k % NS) * SV;
+#pragma unroll
+      for (int u = 0; u < N1; ++u)
+        if (cpm >> u & 1u) cp_async_el<sizeof(SF)>(stg + tid + u * NT, fr + gid[u]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) issue(k);
+  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
+  const bool cown = I < Lc.nx && J < Lc.ny;
+  const bool cdir = bc == BC_DIRICHLET && cown && on_bnd(I, J, Lc.nx, Lc.ny);
+  const int rc = (2 * threadIdx.y + 1) * RW + 2 * threadIdx.x + 1;
+  for (int k = 0; k < na; ++k) {
+    cp_async_wait<NS - 2>();
+    __syncthreads();
+    issue(k + NS - 1);
+    const SF* stg = fst + (k % NS) * SV;
+    const int r = act[k];
+    SX* xr = x + (long long)r * nf;
+#pragma unroll
+    for (int u = 0; u < N1; ++u) {
+      const int q = tid + u * NT;
+      if (q < NX) {
+        const C<T> v = cmul(dv[u], ld2(stg, q));
+        xs[q] = v;
+        if (own >> u & 1u) st2(xr, gid[u], v);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < N2; ++u) {
+      const int q = tid + u * NT;
+      if (q < NR) {
+        C<T> v = czero<T>();
+        if (rok >> u & 1u) {
+          const int c = cix[u];
+          v = rfma(ih2, nb_sum<T, INTERIOR>(xs, c, XW, code[u]), omc * ld2(stg, c));
+        }
+        rsd[q] = v;
+      }
+    }
+    __syncthreads();
+    if (cown) {
+      C<T> acc = czero<T>();
+      if (!cdir) {
+        const C<T> r0 = (rsd[rc - RW - 1] + rsd[rc - RW + 1]) + T(2) * rsd[rc - RW];
+        const C<T> r1 = (rsd[rc - 1] + rsd[rc + 1]) + T(2) * rsd[rc];
+        const C<T> r2 = (rsd[rc + RW - 1] + rsd[rc + RW + 1]) + T(2) * rsd[rc + RW];
+        acc = T(0.0625) * ((r0 + r2) + T(2) * r1);
+      }
+      st2(fc, r * nc + (long long)J * Lc.nx + I, acc);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <class T, class SF, class SX, class SC, int NS>
+__global__ void __launch_bounds__(BX * BY)
+k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin,
+                  SX* __restrict__ x, SC* __restrict__ fc, int nrhs, int rpb,
+                  const int* __restrict__ done) {
+  using P = PreRestrictMR<T, SF>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XS + P::RS);
+  __shared__ int nact_s;
+  const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  const int na = list_active(done, r0, r1, act, &nact_s);
+  if (na == 0) return;
+  // the x tile [2I0-2, 2I0+2BX] x [2J0-2, 2J0+2BY] inside the grid and off
+  // its boundary rows and columns
+  const int fx0 = 2 * blockIdx.x * BX - 2, fy0 = 2 * blockIdx.y * BY - 2;
+  const bool interior = fx0 >= 1 && fy0 >= 1 && fx0 + P::XW <= Lf.nx - 1 &&
+                        fy0 + P::XH <= Lf.ny - 1;
+  if (interior)
+    pre_restrict_mr_body<T, SF, SX, SC, NS, true>(Lf, Lc, bc, omc, fin, x, fc, na, act,
+                                                  smraw);
+  else
+    pre_restrict_mr_body<T, SF, SX, SC, NS, false>(Lf, Lc, bc, omc, fin, x, fc, na, act,
+                                                   smraw);
+}
+
+template <class T, class SC, class SX, class SF, int TXW>
+struct ProlongSmoothMR {
+  static constexpr int NPX = TXW / BX;
+  static constexpr int PW = TXW + 2, PH = BY + 2, NP = PW * PH;
+  static constexpr int CW = TXW / 2 + 2, CH = BY / 2 + 2, NC = CW * CH;
+  static constexpr int NF = TXW * BY, NT = BX * BY;
+  static constexpr int N1 = (NP + NT - 1) / NT, N3 = (NC + NT - 1) / NT;
+  static constexpr int OX = 0, OC = align16(NP * (int)sizeof(SX)),
+                       OF = OC + align16(NC * (int)sizeof(SC)),
+                       STAGE = OF + align16(NF * (int)sizeof(SF));
+  static constexpr int XP = align16(NP * (int)sizeof(C<T>));
+  static constexpr int smem(int ns, int rpb) { return ns * STAGE + XP + 4 * rpb; }
+};
+
+// Fused coarse-grid correction and post-smoothing, xo = x' + D^-1 (f - M x')
+// with x' = x + P xc, for one TXW x BY tile of fine nodes and a group of rpb
+// right-hand sides (each thread owns TXW / BX nodes of a tile row).
+template <class T, class SC, class SX, class SF, class SO, int NS, int TXW, bool INTERIOR>
+__device__ __forceinline__ void prolong_smooth_mr_body(
+    const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, const SC* xc, const SX* x,
+    VRefE<SF> fin, SO* xo, int na, const int* act, unsigned char* smraw) {
+  using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
+  constexpr int PW = P::PW, NP = P::NP, CW = P::CW, NC = P::NC, NT = P::NT;
+  constexpr int N1 = P::N1, N3 = P::N3, NPX = P::NPX;
+  C<T>* xp = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE);
+  const int i0 = blockIdx.x * TXW, j0 = blockIdx.y * BY;
+  const int ic0 = i0 / 2 - 1, jc0 = j0 / 2 - 1;
+  const int tid = threadIdx.y * BX + threadIdx.x;
+  const int nfx = Lf.nx, nfy = Lf.ny, ncx = Lc.nx, ncy = Lc.ny;
+  const long long nf = (long long)nfx * nfy, nc = (long long)ncx * ncy;
+  const SF* fbase = fin.get();
+  const T ih2 = ih2_of<T>(Lf);
+  auto sx_of = [&](int k) {
+    return reinterpret_cast<SX*>(smraw + (k % NS) * P::STAGE + P::OX);
+  };
+  auto sc_of = [&](int k) {
+    return reinterpret_cast<SC*>(smraw + (k % NS) * P::STAGE + P::OC);
+  };
+  auto sf_of = [&](int k) {
+    return reinterpret_cast<SF*>(smraw + (k % NS) * P::STAGE + P::OF);
+  };
+  // x tile with its 1-node halo: node, and the staged coarse values its
+  // bilinear interpolation reads (b0, one step right if x is odd, one row
+  // down if y is odd; the even directions read the same value twice)
+  int gx[N1], cb[N1], cdx[N1], cdy[N1];
+  unsigned ing = 0, corr = 0;
+#pragma unroll
+  for (int u = 0; u < N1; ++u) {
+    const int q = tid + u * NT;
+    const int gi = i0 - 1 + q % PW, gj = j0 - 1 + q / PW;
+    gx[u] = -1;
+    cb[u] = 0;
+    cdx[u] = 0;
+    cdy[u] = 0;
+    if (q < NP && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
+      gx[u] = gj * nfx + gi;
+      ing |= 1u << u;
+      if (INTERIOR || !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) corr |= 1u << u;
+      cb[u] = ((gj >> 1) - jc0) * CW + ((gi >> 1) - ic0);
+      cdx[u] = gi & 1;
+      cdy[u] = (gj & 1) * CW;
+    }
+  }
+  int gc[N3];
+#pragma unroll
+  for (int u = 0; u < N3; ++u) {
+    const int q = tid + u * NT;
+    const int I = ic0 + q % CW, J = jc0 + q / CW;
+    gc[u] = (q < NC && I >= 0 && I < ncx && J >= 0 && J < ncy) ? J * ncx + I : -1;
+  }
+  // own nodes: D^-1 and neighbour weights in registers, f staged
+  int go[NPX];
+  unsigned code[NPX];
+  unsigned dir = 0;
+  C<T> down[NPX];
+  const int j = j0 + threadIdx.y;
+#pragma unroll
+  for (int p = 0; p < NPX; ++p) {
+    const int i = i0 + threadIdx.x + p * BX;
+    go[p] = (i < nfx && j < nfy) ? j * nfx + i : -1;
+    down[p] = go[p] >= 0 ? dinv_of<T>(Lf)[go[p]] : czero<T>();
+    code[p] = 0;
+    if (go[p] >= 0 && !INTERIOR) {
+      if (bc == BC_DIRICHLET && on_bnd(i, j, nfx, nfy))
+        dir |= 1u << p;
+      else
+        code[p] = nb_code(bc, i, j, nfx, nfy);
+    }
+  }
+  for (int sidx = 0; sidx < NS; ++sidx) {
+#pragma unroll
+    for (int u = 0; u < N1; ++u)
+      if (tid + u * NT < NP && gx[u] < 0) sx_of(sidx)[tid + u * NT] = szero<SX>();
+#pragma unroll
+    for (int u = 0; u < N3; ++u)
+      if (tid + u * NT < NC && gc[u] < 0) sc_of(sidx)[tid + u * NT] = szero<SC>();
+#pragma unroll
+    for (int p = 0; p < NPX; ++p)
+      if (go[p] < 0) sf_of(sidx)[threadIdx.y * TXW + threadIdx.x + p * BX] = szero<SF>();
+  }
+  auto issue = [&](int k) {
+    if (k < na) {
+      const int r = act[k];
+      const SX* xr = x + (long long)r * nf;
+      const SC* xcr = xc + (long long)r * nc;
+      const SF* fr = fbase + (long long)r * nf;
+      SX* sx = sx_of(k);
+      SC* sc = sc_of(k);
+      SF* sf = sf_of(k);
+#pragma unroll
+      for (int u = 0; u < N1; ++u)
+        if (gx[u] >= 0) cp_async_el<sizeof(SX)>(sx + tid + u * NT, xr + gx[u]);
+#pragma unroll
+      for (int u = 0; u < N3; ++u)
+        if (gc[u] >= 0) cp_async_el<sizeof(SC)>(sc + tid + u * NT, xcr + gc[u]);
+#pragma unroll
+      for (int p = 0; p < NPX; ++p)
+        if (go[p] >= 0)
+          cp_async_el<sizeof(SF)>(sf + threadIdx.y * TXW + threadIdx.x + p * BX, fr + go[p]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) issue(k);
+  for (int k = 0; k < na; ++k) {
+    cp_async_wait<NS - 2>();
+    __syncthreads();
+    issue(k + NS - 1);
+    const SX* sx = sx_of(k);
+    const SC* sc = sc_of(k);
+    const SF* sf = sf_of(k);
+    const int r = act[k];
+#pragma unroll
+    for (int u = 0; u < N1; ++u) {
+      const int q = tid + u * NT;
+      if (q < NP) {
+        C<T> v = czero<T>();
+        if (ing >> u & 1u) {
+          v = ld2(sx, q);
+          if (corr >> u & 1u) {
+            const int b0 = cb[u], b1 = cb[u] + cdy[u];
+            const C<T> a = T(0.5) * (ld2(sc, b0) + ld2(sc, b0 + cdx[u]));
+            const C<T> c = T(0.5) * (ld2(sc, b1) + ld2(sc, b1 + cdx[u]));
+            v = v + T(0.5) * (a + c);
+          }
+        }
+        xp[q] = v;
+      }
+    }
+    __syncthreads();
+    SO* orow = xo + (long long)r * nf;
+#pragma unroll
+    for (int p = 0; p < NPX; ++p) {
+      if (go[p] < 0) continue;
+      if (!INTERIOR && (dir >> p & 1u)) {
+        st2(orow, go[p], czero<T>());
+        continue;
+      }
+      const int c = (threadIdx.y + 1) * PW + (threadIdx.x + p * BX + 1);
+      const C<T> g =
+          rfma(ih2, nb_sum<T, INTERIOR>(xp, c, PW, code[p]),
+               ld2(sf, threadIdx.y * TXW + threadIdx.x + p * BX));
+      st2(orow, go[p], cfma(down[p], g, omc * xp[c]));
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <class T, class SC, class SX, class SF, class SO, int NS, int TXW>
+__global__ void __launch_bounds__(BX * BY)
+k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restrict__ xc,
+                    const SX* __restrict__ x, VRefE<SF> fin, SO* __restrict__ xo, int nrhs,
+                    int rpb, const int* __restrict__ done) {
+  using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XP);
+  __shared__ int nact_s;
+  const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  const int na = list_active(done, r0, r1, act, &nact_s);
+  if (na == 0) return;
+  // the x' tile [i0-1, i0+TXW] x [j0-1, j0+BY] inside the grid and off its
+  // boundary rows and columns
+  const int fx0 = blockIdx.x * TXW - 1, fy0 = blockIdx.y * BY - 1;
+  const bool interior = fx0 >= 1 && fy0 >= 1 && fx0 + P::PW <= Lf.nx - 1 &&
+                        fy0 + P::PH <= Lf.ny - 1;
+  if (interior)
+    prolong_smooth_mr_body<T, SC, SX, SF, SO, NS, TXW, true>(Lf, Lc, bc, omc, xc, x, fin,
+                                                             xo, na, act, smraw);
+  else
+    prolong_smooth_mr_body<T, SC, SX, SF, SO, NS, TXW, false>(Lf, Lc, bc, omc, xc, x, fin,
+                                                              xo, na, act, smraw);
+}
+
 // x = Minv f on the coarsest level (dense inverse built at setup)
 template <class T, class SF, class SO>
 __global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRefE<SF> fin,
@@ -341,6 +761,62 @@ void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift
   k_prolong_smooth<T, SC, SX, SF, SO><<<grid2d(Lf.nx, Lf.ny, nrhs), dim3(BX, BY), 0, st>>>(
       Lf, Lc, bc, (T)s.re, (T)s.im, xc, x, f, xo, done);
 }
+// Multi-RHS staged kernels: grid (tiles, ceil(nrhs / rpb)); the dynamic
+// shared memory (the stage ring, the tile, the active-RHS list) is allowed
+// up to its largest size once per instantiation.
+constexpr int kPreNS = 3, kProNS = 4;
+
+inline int clamp_rpb(int rpb, int nrhs) { return (rpb <= 0 || rpb > nrhs) ? nrhs : rpb; }
+
+template <class T, class SF, class SX, class SC>
+void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
+                            VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
+                            cudaStream_t st) {
+  HZ_COUNT();
+  using P = PreRestrictMR<T, SF>;
+  auto kern = k_pre_restrict_mr<T, SF, SX, SC, kPreNS>;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P::smem(kPreNS, 1024));
+  });
+  rpb = clamp_rpb(rpb, nrhs);
+  const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  kern<<<grid, dim3(BX, BY), P::smem(kPreNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), f,
+                                                         x, fc, nrhs, rpb, done);
+}
+
+template <class T, class SC, class SX, class SF, class SO, int TXW>
+void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
+                                const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
+                                int rpb, const int* done, cudaStream_t st) {
+  using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
+  auto kern = k_prolong_smooth_mr<T, SC, SX, SF, SO, kProNS, TXW>;
+  static std::once_flag once;
+  std::call_once(once, [&] {
+    cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         P::smem(kProNS, 1024));
+  });
+  rpb = clamp_rpb(rpb, nrhs);
+  const dim3 grid((Lf.nx + TXW - 1) / TXW, (Lf.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  kern<<<grid, dim3(BX, BY), P::smem(kProNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), xc,
+                                                         x, f, xo, nrhs, rpb, done);
+}
+
+// tile 0: 32 x 8 fine nodes per block, 1: 64 x 8
+template <class T, class SC, class SX, class SF, class SO>
+void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
+                              const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
+                              int rpb, int tile, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  if (tile == 1)
+    launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, 2 * BX>(Lf, Lc, bc, omega, xc, x, f, xo,
+                                                          nrhs, rpb, done, st);
+  else
+    launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, BX>(Lf, Lc, bc, omega, xc, x, f, xo, nrhs,
+                                                      rpb, done, st);
+}
+
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
                      const int* done, cudaStream_t st) {
@@ -403,6 +879,12 @@ template void launch_dense_mv<float, bf2, bf2>(int, const float2*, VRefE<bf2>, b
   template void launch_pre_restrict<T, SF, SX, SC>(                             \
       const LevelDev&, const LevelDev&, int, Shift, VRefE<SF>, SX*, SC*, int,   \
       const int*, cudaStream_t);                                                \
+  template void launch_pre_restrict_mr<T, SF, SX, SC>(                          \
+      const LevelDev&, const LevelDev&, int, double, VRefE<SF>, SX*, SC*, int,  \
+      int, const int*, cudaStream_t);                                           \
+  template void launch_prolong_smooth_mr<T, SC, SX, SF, SO>(                    \
+      const LevelDev&, const LevelDev&, int, double, const SC*, const SX*,      \
+      VRefE<SF>, SO*, int, int, int, const int*, cudaStream_t);                 \
   template void launch_prolong_smooth<T, SC, SX, SF, SO>(                       \
       const LevelDev&, const LevelDev&, int, Shift, const SC*, const SX*,       \
       VRefE<SF>, SO*, int, const int*, cudaStream_t);

@@ -124,7 +124,11 @@ def test_workspace_bytes_checks_method_choices(lib):
     assert _ws(lib, deflation_levels=2)[1] > base
     assert _ws(lib, deflation_levels=2, zkind=0)[0] == 1
     assert _ws(lib, deflation_levels=2, preconditioner=1)[0] == 1
-    assert _ws(lib, deflation_levels=3)[0] == 1
+    # multilevel deflation down to level D needs D coarsenings (33: 4)
+    assert _ws(lib, deflation_levels=3)[0] == 0
+    assert _ws(lib, deflation_levels=4)[1] > _ws(lib, deflation_levels=3)[1]
+    assert _ws(lib, deflation_levels=5)[0] == 2
+    assert _ws(lib, deflation_levels=24)[0] == 1
     assert _ws(lib, nx=5, ny=5, deflation_levels=2)[0] == 2   # one coarsening
     # the printed deflation scaling: two levels only, no extra workspace
     assert _ws(lib, deflation_scaling=1, ekind=3) == (0, _ws(lib, ekind=3)[1])

@@ -151,25 +151,59 @@ def test_vcycle(bc, prec, tol):
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 5e-5),
                                       ("mixed_bf16", 2e-2)])
 def test_fused_vcycle_matches_oracle(bc, prec, tol):
-    """The fused smoothing/transfer kernels (vcycle_fused = 1) give the same
-    V-cycle as the oracle from levels 0, 1 and L, and as the unfused
-    kernels to rounding."""
+    """The fused smoothing/transfer kernels (vcycle_fused = 1) and their
+    staged multi-RHS form (vcycle_fused = 2, with groups of right-hand sides
+    that leave a ragged last group, both prolongation tiles) give the same
+    V-cycle as the oracle from levels 0, 1 and L; the fused and staged
+    kernels match the unfused ones to rounding (the staged ones form the
+    residual as (1 - w) f + off-diagonal terms, with D^-1 diag(M) = w)."""
     k2 = rk2(NY, NX, 6)
-    s = solver(NX, NY, H, k2, bc, z="ho", prec=prec, nrhs=2)
+    s = solver(NX, NY, H, k2, bc, z="ho", prec=prec, nrhs=3)
     orc = Oracle(NX, NY, H, k2, bc, z="ho", coarsest="direct")
     for l in (0, 1, orc.L):
         lv = orc.levels[l]
-        f = wl.random_complex((2, lv.ny, lv.nx), 30 + l)
+        f = wl.random_complex((3, lv.ny, lv.nx), 30 + l)
         s.set_tuning(vcycle_fused=0)
         y0 = to_np(s.apply("vcycle", f, l))
         s.set_tuning(vcycle_fused=1)
         y1 = to_np(s.apply("vcycle", f, l))
-        for r in range(2):
+        for r in range(3):
             ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[r]), l))
             assert rel(y1[r], ref) < tol, (l, r, rel(y1[r], ref))
             # unfused BF16 storage rounds x + P xc once more
             bound = {"fp64": 1e-13, "mixed": 1e-6, "mixed_bf16": 2e-2}[prec]
             assert rel(y1[r], y0[r]) < bound
+        for rpb, tile in ((2, 0), (1, 1), (0, 1), (16, 0)):
+            s.set_tuning(vcycle_fused=2, vcycle_rhs_per_block=rpb, vcycle_tile=tile)
+            y2 = to_np(s.apply("vcycle", f, l))
+            for r in range(3):
+                ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[r]), l))
+                assert rel(y2[r], ref) < tol, (l, rpb, tile, r, rel(y2[r], ref))
+                assert rel(y2[r], y0[r]) < bound, (l, rpb, tile, r)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed_bf16"])
+def test_staged_vcycle_solve_matches_fused(prec):
+    """A batched solve whose right-hand sides converge at different
+    iterations (so the staged kernels skip done RHS inside their groups)
+    gives the same iterations (+-1) and solutions with the staged multi-RHS
+    V-cycle as with the fused one."""
+    n, k = 65, 40.0
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    b = wl.point_sources(n, n, [(32, 32), (5, 60), (60, 5)])
+    out = []
+    for tune in (dict(vcycle_fused=1),
+                 dict(vcycle_fused=2, vcycle_rhs_per_block=2, vcycle_tile=1)):
+        s = solver(n, n, h, k2, "sommerfeld", prec=prec, nrhs=3, coarse_tol=1e-6,
+                   coarse_maxit=300)
+        s.set_tuning(**tune)
+        x, info = s.solve(torch.from_numpy(b).cuda(), tol=1e-8)
+        out.append((to_np(x), [(i.outer_iters, i.inner_iters_total) for i in info]))
+        s.close()
+    for r in range(3):
+        assert abs(out[0][1][r][0] - out[1][1][r][0]) <= 1, (r, out[0][1], out[1][1])
+        assert rel(out[1][0][r], out[0][0][r]) < 1e-6, r
 
 
 @pytest.mark.parametrize("bc", BCS)
@@ -413,6 +447,49 @@ def test_three_level_deflation_matches_oracle(bc, z):
     assert im[0].status == "HZ_OK" and res <= 1e-6
 
 
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_multilevel_deflation_matches_oracle(depth):
+    """Recursive A-DEF1 down to level D = depth (flexible GMRES with A-DEF1
+    on every coarse system above D, ReD-Glk2 below level 1, V-cycle GMRES at
+    D; every level to the coarse tolerance): one level-1 coarse solve and a
+    tight whole solve against the oracle (1e-8; outer +-1), the whole solve
+    issued as CUDA graphs (one WHILE node per level, nested) and kernel by
+    kernel giving the same iterations and solution, and the mixed-precision
+    form reaching the FP64 residual target."""
+    n, k = 33, 12.0
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    kw = dict(coarse_tol=1e-1, coarse_maxit=6, deflation_levels=depth)
+    s = solver(n, n, h, k2, "sommerfeld", z="ho", nrhs=2, outer_maxit=200, **kw)
+    orc = Oracle(n, n, h, k2, "sommerfeld", z="ho", **kw)
+    lc = orc.levels[1]
+    v1 = wl.random_complex((1, lc.ny, lc.nx), 17 + depth)
+    v2 = to_np(s.apply("coarse_solve", v1))[0]
+    ref = lc.to_full(orc.coarse_solve(lc.to_unknowns(v1[0])))
+    assert rel(v2, ref) < 1e-8
+    b = wl.point_sources(n, n, [wl.centre_node(n, n), (3, 29)])
+    x, info = s.solve(b, tol=1e-11)
+    sg = solver(n, n, h, k2, "sommerfeld", z="ho", nrhs=2, outer_maxit=200,
+                cuda_graph=False, **kw)
+    xg, ig = sg.solve(b, tol=1e-11)
+    for r in range(2):
+        xo, io = orc.solve(b[r], tol=1e-11)
+        assert info[r].status == "HZ_OK"
+        assert abs(info[r].outer_iters - io.outer_iters) <= 1, (r, info[r], io.outer_iters)
+        assert rel(to_np(x)[r], xo) < 1e-8
+        assert (ig[r].outer_iters, ig[r].inner_iters_total) == \
+            (info[r].outer_iters, info[r].inner_iters_total)
+        assert rel(to_np(xg)[r], to_np(x)[r]) < 1e-13
+    sm = solver(n, n, h, k2, "sommerfeld", z="ho", prec="mixed", nrhs=2,
+                outer_maxit=200, **kw)
+    xm, im = sm.solve(b, tol=1e-6)
+    lv = orc.levels[0]
+    for r in range(2):
+        bu = lv.to_unknowns(b[r])
+        res = np.linalg.norm(bu - orc.A @ lv.to_unknowns(to_np(xm)[r])) / np.linalg.norm(bu)
+        assert im[r].status == "HZ_OK" and res <= 1e-6
+
+
 def test_mixed_precision_reaches_fp64_residual():
     n, k = 129, 80
     orc, b, x, info = _solve_pair(n, k, "sommerfeld", "ho", "galerkin", 1e-6,
@@ -536,8 +613,12 @@ def test_autotune_picks_valid_choices_and_caches(tmp_path):
     assert ms["galerkin_apply=1"] == ms[f"e_rhs_per_block={rpb}"]
     ga = 1 if ms["galerkin_apply=1"] < ms["galerkin_apply=0"] else 0
     assert t["galerkin_apply"] == ga
-    vf = 1 if ms["vcycle_fused=1"] < ms["vcycle_fused=0"] else 0
-    assert t["vcycle_fused"] == vf
+    vc = [c for c in s.TUNE_CANDIDATES if c.startswith("vcycle_fused")]
+    best = dict(kv.split("=") for kv in min(vc, key=lambda c: ms[c]).split(","))
+    assert t["vcycle_fused"] == int(best["vcycle_fused"])
+    if "rpb" in best:
+        assert t["vcycle_rhs_per_block"] == int(best["rpb"])
+        assert t["vcycle_tile"] == int(best["tile"])
     x1, i1 = s.solve(b, tol=1e-8)
     for r in range(2):
         assert i1[r].status == "HZ_OK"
@@ -582,6 +663,79 @@ def test_group_of_uneven_grids_equals_separate_solves():
     c = solver(33, 33, 1 / 32, rk2(33, 33, 1), "sommerfeld", prec="mixed")
     with pytest.raises(HzError):
         solve_group([a, c], [wl.random_complex((1, 33, 33), 1)] * 2)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_group_graph_equals_eager_group(prec):
+    """hz_solve_group issued as one CUDA graph per outer iteration (members'
+    kernels on concurrent branches, the inner solves in a WHILE node) gives
+    every member the iterations and solution of the same group issued
+    kernel by kernel (1e-13), with far fewer host launch operations; the
+    counts of both forms are printed."""
+    from paper_2308_06152_gb300._lib import load_library
+    from paper_2308_06152_gb300.api import solve_group
+    lib = load_library()
+    specs = [(97, 73, 1.0 / 96, "sommerfeld", "ho", "galerkin", 2, 11),
+             (65, 129, 1.0 / 64, "dirichlet", "bilinear", "galerkin", 1, 12),
+             (129, 65, 1.0 / 128, "sommerfeld", "ho", "red_glk2", 3, 13)]
+    res, ops = {}, {}
+    for graph in (False, True):
+        solvers, bs = [], []
+        for nx, ny, h, bc, z, e, nr, seed in specs:
+            k2 = rk2(ny, nx, seed, lo=8.0, hi=30.0)
+            solvers.append(solver(nx, ny, h, k2, bc, z=z, e=e, prec=prec, nrhs=nr,
+                                  coarse_tol=1e-3, coarse_maxit=200,
+                                  inner_basis_fp16=(prec == "mixed"), cuda_graph=graph))
+            bs.append(wl.random_complex((nr, ny, nx), seed + 100))
+        torch.cuda.synchronize()
+        h0, k0 = lib.hz_host_launches(), lib.hz_kernel_launches()
+        res[graph] = solve_group(solvers, bs, tol=1e-8)
+        torch.cuda.synchronize()
+        ops[graph] = (lib.hz_host_launches() - h0, lib.hz_kernel_launches() - k0)
+    for (xe, ie), (xg, ig) in zip(res[False], res[True]):
+        for r in range(len(ie)):
+            assert ig[r].status == "HZ_OK"
+            assert (ig[r].outer_iters, ig[r].inner_iters_total) == \
+                (ie[r].outer_iters, ie[r].inner_iters_total)
+            assert rel(to_np(xg)[r], to_np(xe)[r]) < 1e-13, (prec, r)
+    print(f"group {prec}: host launches eager {ops[False][0]}, graphs {ops[True][0]}; "
+          f"kernels {ops[False][1]} / {ops[True][1]}")
+    assert ops[True][0] * 5 < ops[False][0]
+    assert abs(ops[True][1] - ops[False][1]) <= 0.02 * ops[False][1]
+
+
+def test_timeout_path_with_fault_drill():
+    """The TMA-ring dot kernel bounds every pipeline wait.  With the fault
+    drill its producer warp issues no copies and the bound is 1 ms, so every
+    consumer wait runs out with nothing in flight: the solve returns
+    HZ_TIMEOUT instead of hanging.  After the drill is lifted the next solve
+    on the same solver succeeds and gives the result of a solver that never
+    saw the drill (the flag was cleared as it was reported)."""
+    from paper_2308_06152_gb300._lib import load_library
+    from paper_2308_06152_gb300.api import HzError
+    lib = load_library()
+    n, k = 65, 40.0
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    b = wl.point_sources(n, n, [(32, 32), (10, 50)])
+    kw = dict(nrhs=2, coarse_tol=1e-6, coarse_maxit=300)
+    ref = solver(n, n, h, k2, "sommerfeld", **kw)
+    ref.set_tuning(mdot_kernel=1)
+    x_ref, i_ref = ref.solve(b, tol=1e-8)
+    s = solver(n, n, h, k2, "sommerfeld", **kw)
+    s.set_tuning(mdot_kernel=1)
+    assert lib.hz_fault_drill(None, 1, 1e-3) == 1
+    assert lib.hz_fault_drill(s.handle, 1, 3.0) == 1
+    assert lib.hz_fault_drill(s.handle, 1, 1e-3) == 0
+    with pytest.raises(HzError) as err:
+        s.solve(b, tol=1e-8)
+    assert err.value.status == 7          # HZ_TIMEOUT
+    assert lib.hz_fault_drill(s.handle, 0, 2.0) == 0
+    x, info = s.solve(b, tol=1e-8)
+    for r in range(2):
+        assert info[r].status == "HZ_OK"
+        assert info[r].outer_iters == i_ref[r].outer_iters
+        assert rel(to_np(x)[r], to_np(x_ref)[r]) < 1e-13
 
 
 def test_gradient_group_equals_separate_gradients():

@@ -94,8 +94,11 @@ MUTATIONS = [
     ("solver.py", "return w - self.vcycle(self.A @ q, 0) + gamma * q",
      "return w - self.vcycle(self.A @ q, 0)",
      SOL + "test_tlkm_converges_to_the_direct_solution"),
-    ("solver.py", "return self.vcycle(v - self.E @ q, 1) + q", "return self.vcycle(v, 1) + q",
+    ("solver.py", "return self.vcycle(v - self.Ed[l] @ q, l) + q", "return self.vcycle(v, l) + q",
      SOL + "test_three_level_deflation_invariant_and_direct_solution"),
+    ("solver.py", "q = self.Zd[l] @ self.solve_level(l + 1, self.Rd[l] @ v)",
+     "q = self.Zd[l] @ self.solve_level(l + 1, 2.0 * (self.Rd[l] @ v))",
+     SOL + "test_multilevel_deflation_invariant_and_direct_solution"),
     ("gradient.py", "return -omega ** 2 - c * 1j * omega", "return -omega ** 2 + c * 1j * omega",
      SOL + "test_gradient_matches_central_differences"),
     ("gradient.py", "x = solve(A, np.conj(g / D))", "x = solve(A, np.conj(g))",

@@ -446,6 +446,38 @@ def test_three_level_deflation_invariant_and_direct_solution():
         assert info.converged and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
 
 
+@pytest.mark.parametrize("depth", [2, 3, 4])
+def test_multilevel_deflation_invariant_and_direct_solution(depth):
+    """Recursive A-DEF1 down to level D = depth.  (1) With Galerkin
+    operators below level 1 (E_{l+1} = R_l E_l Z_l) and a tight solve of
+    level l + 1 (the deepest one, D = l + 1), A-DEF1 of level l's coarse
+    system deflates its coarse space exactly, P_l E_l Z_l = Z_l for
+    l = D - 1 (the eq. ADEF1 identity l levels down).  (2) With ReD-Glk2 on
+    every level below 1 and loose, capped inner solves at every level, a
+    tight flexible-GMRES whole solve reaches the direct solution."""
+    n = 33
+    l = depth - 1
+    k2 = _k2(n, n, 5, lo=6, hi=12)
+    orc = Oracle(n, n, 1 / 32, k2, ops.SOMMERFELD, z="ho", coarsest="direct",
+                 coarse_tol=1e-13, coarse_maxit=300, deflation_levels=depth,
+                 e2="galerkin")
+    assert sorted(orc.Ed) == list(range(1, depth + 1))
+    Zl = orc.Zd[l].tocsc()
+    for j in (0, Zl.shape[1] // 2, Zl.shape[1] - 1):
+        zj = Zl[:, j].toarray().ravel().astype(complex)
+        out = orc.adef1_at(l, orc.Ed[l] @ zj)
+        assert np.linalg.norm(out - zj) <= 1e-9 * np.linalg.norm(zj), (l, j)
+    k2 = _k2(n, n, 7, lo=8, hi=16)
+    orc = Oracle(n, n, 1 / 32, k2, ops.SOMMERFELD, z="ho", coarse_tol=1e-1,
+                 coarse_maxit=6, deflation_levels=depth)
+    rng = np.random.default_rng(depth)
+    b = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    x, info = orc.solve(b, tol=1e-11, maxit=200)
+    lv = orc.levels[0]
+    xd = lv.to_full(spla.spsolve(orc.A.tocsc(), lv.to_unknowns(b)))
+    assert info.converged and np.linalg.norm(x - xd) / np.linalg.norm(xd) < 1e-9
+
+
 def test_gmres_lucky_breakdown_identity():
     b = np.arange(1, 6) + 0j
     res = gmres_right(lambda v: 3.0 * v, b, 1e-14, 10)
