@@ -200,7 +200,9 @@ PREC_TEXT = {"mixed": "complex-FP32 preconditioner in FP64 FGMRES",
              "fp64": "complex-FP64 throughout"}
 
 KERNEL_NAMES = {"mdot": "k_mdot (CGS2 multi-vector dot product)",
-                "maxpy": "k_maxpy (CGS2 multi-vector update)"}
+                "maxpy": "k_maxpy (CGS2 multi-vector update)",
+                "vcycle": ("k_pre_restrict_mr + k_prolong_smooth_mr (top level of "
+                           "every V-cycle, staged form)")}
 
 
 def hbm_peak():
@@ -654,8 +656,8 @@ def main():
                     help="force hz_tuning.vcycle_tile")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
-    ap.add_argument("--profile-kernel", default="mdot,maxpy",
-                    help="comma-separated kernel classes (mdot, maxpy) timed "
+    ap.add_argument("--profile-kernel", default="mdot,maxpy,vcycle",
+                    help="comma-separated kernel classes (mdot, maxpy, vcycle) timed "
                          "live for the roofline entries (the first one is "
                          "'roofline', the others 'roofline_more'); 'none' "
                          "skips them")

@@ -87,8 +87,9 @@ typedef enum {
 /* Outer Krylov iteration, both right-preconditioned by A-DEF1 and flexible
  * (variable inner tolerance, Sec. 6.3): FGMRES (Arnoldi + Givens, the
  * iterate formed at the end) or the preconditioned GCR of Sec. 3.3 / 6.3
- * (the iterate and residual updated every step; issued without CUDA
- * graphs).  Both store two sets of outer_maxit FP64 vectors. */
+ * (the iterate and residual updated every step; each step one CUDA graph
+ * launch, one graph per step index for the first 128 steps).  Both store
+ * two sets of outer_maxit FP64 vectors. */
 typedef enum { HZ_OUTER_FGMRES = 0, HZ_OUTER_GCR = 1 } hz_outer;
 
 /* Two-level preconditioner: A-DEF1 (APD with the higher-order Z), eq. ADEF1,
@@ -137,15 +138,19 @@ typedef struct {
   int preconditioner;         /* HZ_PRECOND_ADEF1 (default) or HZ_PRECOND_TLKM
                                  (needs zkind != HZ_Z_NONE)                 */
   int deflation_levels;       /* 0 or 1 (default): the paper's two-level
-                                 method.  2: three-level deflation (the
-                                 multilevel direction of Sec. 1 / 7, our
-                                 reading): the level-1 coarse system is
-                                 solved by flexible GMRES preconditioned by
-                                 A-DEF1 built from it, with ReD-Glk2 at level
-                                 2 solved by V-cycle-preconditioned GMRES to
-                                 coarse_tol; needs deflation vectors, A-DEF1
-                                 and two coarsenings; issued without CUDA
-                                 graphs; not in groups.                     */
+                                 method.  D = 2 .. 23: multilevel deflation
+                                 (the multilevel direction of Sec. 1 / 7,
+                                 our reading): the coarse system of every
+                                 level l < D is solved by flexible GMRES
+                                 preconditioned by A-DEF1 built from it,
+                                 deflating to level l + 1 (ReD-Glk2 below
+                                 level 1); level D by V-cycle-preconditioned
+                                 GMRES; every level to coarse_tol with
+                                 coarse_maxit iterations at most.  Needs
+                                 deflation vectors, A-DEF1 and D coarsenings
+                                 (HZ_INVALID_GRID otherwise); each level's
+                                 loop is a WHILE node nested in its parent's
+                                 in the CUDA graph; not in groups.          */
   int no_cuda_graph;          /* 0 (default): each outer iteration of hz_solve
                                  runs as one CUDA graph launch whose inner
                                  coarse-solve loop is a device-side WHILE
@@ -154,6 +159,12 @@ typedef struct {
                                  iterations.  Results are the same.         */
   int deflation_scaling;      /* hz_defl_scale; default CONSISTENT.  PRINTED
                                  needs deflation_levels <= 1.             */
+  int restart;                /* FGMRES only: 0 (default) no restart; m in
+                                 1 .. outer_maxit: after every m iterations
+                                 the iterate is formed and the Arnoldi process
+                                 starts again from the true residual b - A x
+                                 (GMRES(m)); the stopping test keeps ||b||;
+                                 outer_maxit still caps the total           */
 } hz_desc;
 
 typedef struct {
@@ -206,6 +217,20 @@ hz_status hz_setup(const hz_desc* d, const double* k2_dev,
  * failing status. */
 hz_status hz_solve(hz_solver* s, const void* b_dev, void* x_dev, int nrhs,
                    double tol, int use_x0, hz_solve_info* info_host);
+
+/* hz_solve without a host synchronisation (the paper has no counterpart):
+ * the whole solve (start, the outer FGMRES loop as a device-side WHILE loop
+ * holding the inner one, the update of x, the true residual and the report)
+ * is one CUDA graph, captured on the first call for these buffers, nrhs,
+ * tol and use_x0 (up to 4 are kept) and launched on the solver's stream;
+ * the call returns as soon as it is enqueued.  info_dev: device memory for
+ * nrhs hz_solve_info records, written by the graph's last kernel (status
+ * HZ_TIMEOUT for every RHS if a bounded wait ran out).  x_dev and info_dev
+ * are valid once the stream reaches the end of the solve.  Needs FGMRES
+ * without restart and with CUDA graphs (HZ_INVALID_ARG otherwise); the
+ * first call on new buffers must not be made during a stream capture. */
+hz_status hz_solve_async(hz_solver* s, const void* b_dev, void* x_dev, int nrhs,
+                         double tol, int use_x0, hz_solve_info* info_dev);
 
 /* hz_solve with host buffers: copies b_host to the device, solves, copies
  * the solution back to x_host, all on the solver's stream. */
@@ -327,8 +352,12 @@ hz_status hz_gradient_group(hz_solver* const* members, int count, const double* 
 
 /* Kernel classes that hz_profile_* can time: the multi-vector dot product
  * and the multi-vector update of the Gram-Schmidt step (Alg. 1 inner loop),
- * which carry the basis traffic of both Krylov solvers. */
-typedef enum { HZ_KC_NONE = 0, HZ_KC_MDOT = 1, HZ_KC_MAXPY = 2 } hz_kernel_class;
+ * which carry the basis traffic of both Krylov solvers, and the two fused
+ * smoothing/transfer kernels at the top level of every V-cycle (Sec. 3.1;
+ * their staged form, hz_tuning.vcycle_fused = 2, only). */
+typedef enum {
+  HZ_KC_NONE = 0, HZ_KC_MDOT = 1, HZ_KC_MAXPY = 2, HZ_KC_VCYCLE = 3
+} hz_kernel_class;
 
 /* Starts timing every launch of kernel class kc on the solver's stream:
  * CUDA events bracket each launch (at most max_launches are kept) and the

@@ -81,28 +81,41 @@ def _arnoldi_lsq(apply_op, v0, beta, tol_abs, maxit, keep_dirs=None):
     return V, Zs, y, k, res
 
 
-def gmres_right(matvec, b, tol, maxit, x0=None, prec=None, flexible=False):
-    """Right-preconditioned (flexible) GMRES for matvec(x) = b."""
+def gmres_right(matvec, b, tol, maxit, x0=None, prec=None, flexible=False,
+                restart=None):
+    """Right-preconditioned (flexible) GMRES for matvec(x) = b.  With
+    ``restart`` = m > 0 the Arnoldi process starts again from the true
+    residual b - A x after every m iterations (GMRES(m)); the stopping test
+    keeps the reference ||b||, and the count is the total over the cycles."""
     b = np.asarray(b, dtype=np.complex128)
-    x0 = np.zeros_like(b) if x0 is None else np.asarray(x0, np.complex128)
+    x = np.zeros_like(b) if x0 is None else np.asarray(x0, np.complex128).copy()
     bnorm = np.linalg.norm(b)
-    r0 = b - matvec(x0) if np.any(x0) else b.copy()
-    beta = np.linalg.norm(r0)
-    if bnorm == 0.0 or beta <= tol * bnorm:
-        return Result(x0.copy(), 0, beta, True)
     prec = prec if prec is not None else (lambda v: v)
 
     def op(v):
         z = prec(v)
         return matvec(z), z
 
-    V, Zs, y, k, res = _arnoldi_lsq(op, r0 / beta, beta, tol * bnorm, maxit,
-                                    keep_dirs=flexible)
-    if flexible:
-        upd = sum(y[i] * Zs[i] for i in range(k))
-    else:
-        upd = prec(sum(y[i] * V[i] for i in range(k)))
-    return Result(x0 + upd, k, res, res <= tol * bnorm)
+    total, res = 0, np.inf
+    while True:
+        r0 = b - matvec(x) if np.any(x) else b.copy()
+        beta = np.linalg.norm(r0)
+        if bnorm == 0.0 or beta <= tol * bnorm:
+            return Result(x, total, beta, True)
+        cycle = maxit - total
+        if restart:
+            cycle = min(cycle, restart)
+        if cycle <= 0:
+            return Result(x, total, res, False)
+        V, Zs, y, k, res = _arnoldi_lsq(op, r0 / beta, beta, tol * bnorm, cycle,
+                                        keep_dirs=flexible)
+        if flexible:
+            x = x + sum(y[i] * Zs[i] for i in range(k))
+        else:
+            x = x + prec(sum(y[i] * V[i] for i in range(k)))
+        total += k
+        if res <= tol * bnorm or not restart or k < cycle:
+            return Result(x, total, res, res <= tol * bnorm)
 
 
 def gmres_left(matvec, prec, b, tol, maxit, x0=None):

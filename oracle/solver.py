@@ -248,16 +248,16 @@ class Oracle:
         return w - self.vcycle(self.A @ q, 0) + gamma * q
 
     # ---- outer solve (Sec. 6.3) -------------------------------------------
-    def solve(self, b_full, tol=1e-6, maxit=500, x0_full=None):
-        """Flexible GMRES on A x = b right-preconditioned by A-DEF1.  Returns
-        the full-grid solution and a SolveInfo with the true relative
-        residual."""
+    def solve(self, b_full, tol=1e-6, maxit=500, x0_full=None, restart=None):
+        """Flexible GMRES on A x = b right-preconditioned by A-DEF1 (restarted
+        every ``restart`` iterations if given).  Returns the full-grid
+        solution and a SolveInfo with the true relative residual."""
         lv = self.levels[0]
         b = lv.to_unknowns(b_full)
         x0 = None if x0_full is None else lv.to_unknowns(x0_full)
         self.inner_log = []
         res = gmres_right(lambda v: self.A @ v, b, tol, maxit, x0=x0,
-                          prec=self.precond, flexible=True)
+                          prec=self.precond, flexible=True, restart=restart)
         info = SolveInfo()
         info.outer_iters = res.iters
         info.inner_iters = list(self.inner_log)

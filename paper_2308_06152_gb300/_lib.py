@@ -27,7 +27,7 @@ class HzDesc(ctypes.Structure):
                 ("preconditioner", c_int),
                 ("deflation_levels", c_int),
                 ("no_cuda_graph", c_int),
-                ("deflation_scaling", c_int)]
+                ("deflation_scaling", c_int), ("restart", c_int)]
 
 
 class HzSolveInfo(ctypes.Structure):
@@ -56,6 +56,8 @@ SIGNATURES = {
                          c_void_p]),
     "hz_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int,
                          c_void_p]),
+    "hz_solve_async": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int,
+                               c_void_p]),
     "hz_solve_host": (c_int, [c_void_p, c_void_p, c_void_p, c_int, c_double,
                               c_void_p]),
     "hz_apply": (c_int, [c_void_p, c_int, c_int, c_void_p, c_void_p, c_int]),

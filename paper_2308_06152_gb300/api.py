@@ -58,6 +58,7 @@ class Desc:
     deflation_levels: int = 1
     cuda_graph: bool = True
     deflation_scaling: str = "consistent"
+    restart: int = 0
 
     def to_c(self):
         d = HzDesc()
@@ -79,6 +80,7 @@ class Desc:
         d.deflation_levels = int(self.deflation_levels)
         d.no_cuda_graph = int(not self.cuda_graph)
         d.deflation_scaling = DEFL_SCALE[self.deflation_scaling]
+        d.restart = int(self.restart)
         return d
 
 
@@ -181,6 +183,34 @@ class Solver:
             self._check(st, "hz_solve")
         return x, _infos(infos, nrhs)
 
+    def solve_async(self, b, tol=1e-6, x0=None):
+        """x, info_dev = solve_async(b): enqueues the whole solve as one CUDA
+        graph (hz_solve_async) and returns at once; info_dev is a device
+        buffer of nrhs hz_solve_info records (read it with infos_from_device
+        after the stream reached the end of the solve)."""
+        b = self._rhs(b)
+        nrhs = b.shape[0]
+        if x0 is None:
+            x = torch.empty_like(b)
+            use_x0 = 0
+        else:
+            x = self._rhs(x0).clone()
+            use_x0 = 1
+        info = torch.zeros(nrhs * ctypes.sizeof(HzSolveInfo), dtype=torch.uint8,
+                           device=self.device)
+        self._check(self.lib.hz_solve_async(self.handle, b.data_ptr(), x.data_ptr(), nrhs,
+                                            float(tol), use_x0, info.data_ptr()),
+                    "hz_solve_async")
+        return x, info
+
+    @staticmethod
+    def infos_from_device(info):
+        """The hz_solve_info records of a device buffer (copies to the host)."""
+        raw = info.cpu().numpy().tobytes()
+        nrhs = len(raw) // ctypes.sizeof(HzSolveInfo)
+        recs = (HzSolveInfo * nrhs).from_buffer_copy(raw)
+        return _infos(recs, nrhs)
+
     def solve_host(self, b_host, x_host=None, tol=1e-6):
         """End-to-end solve from and to host (ideally pinned) memory."""
         nrhs = b_host.shape[0]
@@ -230,7 +260,7 @@ class Solver:
             self._check(st, "hz_gradient")
         return J.value, grad, _infos(infos, 2 * nshots)
 
-    KERNEL_CLASSES = {"mdot": 1, "maxpy": 2}
+    KERNEL_CLASSES = {"mdot": 1, "maxpy": 2, "vcycle": 3}
 
     def profile_begin(self, kernel, max_launches=100000):
         """Time every launch of one kernel class (see hz_profile_begin)."""

@@ -224,14 +224,16 @@ void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift
 // the input tiles staged ahead in shared memory (cp.async ring); omega is
 // the Jacobi weight D^-1 was built with (the kernels use D^-1 diag(M) =
 // omega); prolongation tile 0 = 32 x 8 fine nodes, 1 = 64 x 8
+// (abytes, if not null, accumulates the algorithmic bytes of the launch)
 template <class T, class SF, class SX, class SC>
 void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
-                            cudaStream_t st);
+                            cudaStream_t st, unsigned long long* abytes = nullptr);
 template <class T, class SC, class SX, class SF, class SO>
 void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                               const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
-                              int rpb, int tile, const int* done, cudaStream_t st);
+                              int rpb, int tile, const int* done, cudaStream_t st,
+                              unsigned long long* abytes = nullptr);
 // x = Minv f on the coarsest level (dense)
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,

@@ -113,6 +113,11 @@ bool valid_desc(const hz_desc* d, std::string* why) {
     *why = "deflation_levels must be 0/1, or 2 .. 23 with deflation vectors and A-DEF1";
     return false;
   }
+  if (d->restart < 0 || d->restart > d->outer_maxit ||
+      (d->restart > 0 && d->outer_solver != HZ_OUTER_FGMRES)) {
+    *why = "restart must be in 0 .. outer_maxit (FGMRES only)";
+    return false;
+  }
   if (d->deflation_scaling != HZ_DEFL_SCALE_CONSISTENT &&
       (d->deflation_scaling != HZ_DEFL_SCALE_PRINTED || d->deflation_levels >= 2)) {
     *why = "deflation_scaling must be CONSISTENT, or PRINTED with at most two levels";
@@ -173,9 +178,12 @@ struct hz_solver {
   KState kin{}, kout{};
   int* in_total = nullptr;
   int* in_max = nullptr;
+  int* out_total = nullptr;   // outer iterations of finished restart cycles
+  int* out_max = nullptr;     // (scratch of the accumulation)
   // outer FGMRES (FP64)
   double2 *Vo = nullptr, *Zo = nullptr, *wo = nullptr;
   double2* ro = nullptr;   // GCR residual
+  double2* xg = nullptr;   // GCR iterate (the solver's own, so graphs can hold it)
   int* izero = nullptr;    // a device 0 (column index of a one-vector dot)
   double* bnorm_o = nullptr;
   double* relres = nullptr;
@@ -197,11 +205,23 @@ struct hz_solver {
   struct OuterGraph {
     int nrhs;
     double tol;
+    int step;            // -1: an FGMRES iteration; k: GCR step k
     cudaGraph_t g;
     cudaGraphExec_t ex;
     long long kernels;   // kernels of one launch outside WHILE bodies
   };
   std::vector<OuterGraph> graphs;
+  // whole solves captured for hz_solve_async, one per (nrhs, tol, use_x0,
+  // buffers); the outer loop is a WHILE node (level 0) holding the inner one
+  struct SolveGraph {
+    int nrhs, use_x0;
+    double tol;
+    const void *b, *x, *info;
+    cudaGraph_t g;
+    cudaGraphExec_t ex;
+    long long kernels;
+  };
+  std::vector<SolveGraph> solve_graphs;
   // (the WHILE body of deflation level l is captured on cap_body for
   // l = 1, on cap_nest[l] below it, and nested in its parent's body)
   cudaStream_t cap_main = nullptr, cap_body = nullptr;
@@ -218,6 +238,10 @@ struct hz_solver {
 
   ~hz_solver() {
     for (OuterGraph& g : graphs) {
+      cudaGraphExecDestroy(g.ex);
+      cudaGraphDestroy(g.g);
+    }
+    for (SolveGraph& g : solve_graphs) {
       cudaGraphExecDestroy(g.ex);
       cudaGraphDestroy(g.g);
     }
@@ -348,6 +372,8 @@ void plan(hz_solver* s, Arena& a) {
   }
   s->in_total = (int*)a.take(sizeof(int) * B);
   s->in_max = (int*)a.take(sizeof(int) * B);
+  s->out_total = (int*)a.take(sizeof(int) * B);
+  s->out_max = (int*)a.take(sizeof(int) * B);
   s->Vo = (double2*)a.take(sizeof(double2) * (size_t)B * n0 * (d.outer_maxit + 1));
   s->Zo = (double2*)a.take(sizeof(double2) * (size_t)B * n0 * d.outer_maxit);
   s->wo = (double2*)a.take(sizeof(double2) * (size_t)B * n0);
@@ -361,6 +387,9 @@ void plan(hz_solver* s, Arena& a) {
   s->prof_bytes = (unsigned long long*)a.take(sizeof(unsigned long long));
   s->izero = (int*)a.take(sizeof(int));
   s->ro = d.outer_solver == HZ_OUTER_GCR
+              ? (double2*)a.take(sizeof(double2) * (size_t)B * n0)
+              : nullptr;
+  s->xg = d.outer_solver == HZ_OUTER_GCR
               ? (double2*)a.take(sizeof(double2) * (size_t)B * n0)
               : nullptr;
   s->loop_it = (int*)a.take(sizeof(int) * kMaxLevels);
@@ -438,6 +467,15 @@ inline Shift helm1() { return Shift{1.0, 0.0}; }
 // FP64 view of level l (k2d present at every level)
 inline LevelDev dev64(const hz_solver* s, int l) { return s->lv[l].dev(); }
 
+// launch-bracketing events of the live per-kernel profiler (hz_profile_*)
+inline void prof_mark(hz_solver* s, int kc) {
+  if (s->prof_kc != kc) return;
+  if (s->prof_used < s->prof_ev.size())
+    cudaEventRecord(s->prof_ev[s->prof_used++], s->st);
+  else
+    ++s->prof_dropped;
+}
+
 // ------------------------------------------------------------ V-cycle
 // One V-cycle from level l0 for M_l0 x = f.  The hierarchy's own vectors are
 // stored as SL (C<T>, or BF16 pairs for the BF16-storage smoother); the
@@ -457,14 +495,17 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
   const bool staged = s->tune.vcycle_fused == 2;
   const int rpb = s->tune.vcycle_rhs_per_block, tile = s->tune.vcycle_tile;
   const double om = s->d.jacobi_omega;
+  unsigned long long* vbytes = s->prof_kc == HZ_KC_VCYCLE ? s->prof_bytes : nullptr;
   for (int l = l0; l < s->L; ++l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
     if (staged) {
-      if (l == l0)
+      if (l == l0) {
+        prof_mark(s, HZ_KC_VCYCLE);
         launch_pre_restrict_mr<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, om, f, (SL*)A.xa,
-                                                (SL*)Bc.f, nrhs, rpb, done, st);
-      else
+                                                (SL*)Bc.f, nrhs, rpb, done, st, vbytes);
+        prof_mark(s, HZ_KC_VCYCLE);
+      } else
         launch_pre_restrict_mr<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, om, vrefe<SL>(A.f),
                                               (SL*)A.xa, (SL*)Bc.f, nrhs, rpb, done, st);
       continue;
@@ -497,11 +538,13 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
     if (staged) {
-      if (l == l0)
+      if (l == l0) {
+        prof_mark(s, HZ_KC_VCYCLE);
         launch_prolong_smooth_mr<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, om,
                                                         (const SL*)Bc.x, (const SL*)A.xa, f,
-                                                        xout, nrhs, rpb, tile, done, st);
-      else
+                                                        xout, nrhs, rpb, tile, done, st, vbytes);
+        prof_mark(s, HZ_KC_VCYCLE);
+      } else
         launch_prolong_smooth_mr<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, om,
                                                     (const SL*)Bc.x, (const SL*)A.xa,
                                                     vrefe<SL>(A.f), (SL*)A.x, nrhs, rpb, tile,
@@ -660,13 +703,6 @@ void debug_trace(hz_solver* s, const KState& ks, const char* label) {
 }
 
 // Event pair around one launch of the profiled kernel class.
-inline void prof_mark(hz_solver* s, int kc) {
-  if (s->prof_kc != kc) return;
-  if (s->prof_used < s->prof_ev.size())
-    cudaEventRecord(s->prof_ev[s->prof_used++], s->st);
-  else
-    ++s->prof_dropped;
-}
 
 // Classical Gram-Schmidt of w against basis columns 0..j with a second pass
 // only where the first one cancelled more than a factor 2 (Kahan-Parlett
@@ -761,9 +797,10 @@ void inner_step(hz_solver* s, int nrhs) {
 // l + 1 inside this body; every body counts only its own kernels
 // (body_count_l[l]).
 template <class F>
-hz_status capture_loop(hz_solver* s, int l, KState& ks, F&& body) {
+hz_status capture_loop(hz_solver* s, int l, KState& ks, F&& body, int maxit = -1) {
   cudaStream_t st = s->st;
   cudaStream_t cap = l == 1 ? s->cap_body : s->cap_nest[l];
+  if (maxit < 0) maxit = s->d.coarse_maxit;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaGraph_t G = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -795,8 +832,8 @@ hz_status capture_loop(hz_solver* s, int l, KState& ks, F&& body) {
   for (int k = l + 1; k < kMaxLevels; ++k) s->body_count_l[k] = 0;
   s->st = cap;
   body();
-  launch_loop_next(ks.alldone, s->fault, s->loop_it + l, s->d.coarse_maxit,
-                   s->body_kernels + l, h, s->st);
+  launch_loop_next(ks.alldone, s->fault, s->loop_it + l, maxit, s->body_kernels + l, h,
+                   s->st);
   s->st = st;
   long long nested = 0;
   for (int k = l + 1; k < kMaxLevels; ++k) nested += s->body_count_l[k];
@@ -1124,11 +1161,12 @@ hz_status outer_step(hz_solver* s, int nrhs, double tol) {
 
 std::atomic<bool> g_graph_launched{false};
 constexpr size_t kMaxGraphs = 4;
+constexpr size_t kMaxGcrGraphs = 128;   // one per GCR step
 
 void end_failed_capture(hz_solver* s) {
   cudaGraph_t g = nullptr;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  for (int l = kMaxLevels - 1; l >= 2; --l)
+  for (int l = kMaxLevels - 1; l >= 0; --l)
     if (s->cap_nest[l] && cudaStreamIsCapturing(s->cap_nest[l], &cs) == cudaSuccess &&
         cs != cudaStreamCaptureStatusNone) {
       cudaStreamEndCapture(s->cap_nest[l], &g);
@@ -1147,12 +1185,17 @@ void end_failed_capture(hz_solver* s) {
   cudaGetLastError();
 }
 
-// The instantiated graph of outer_step for (nrhs, tol), captured on first
-// use.  Returns nullptr (with s->err set) if capture or instantiation fails.
-hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
+// The instantiated graph of one outer iteration for (nrhs, tol, step),
+// captured on first use from issue() (outer_step for FGMRES, step -1; GCR
+// step k).  Returns nullptr (with s->err set) if capture or instantiation
+// fails.
+template <class F>
+hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol, int step,
+                                   F&& issue) {
   for (hz_solver::OuterGraph& g : s->graphs)
-    if (g.nrhs == nrhs && g.tol == tol) return &g;
-  if (s->graphs.size() >= kMaxGraphs) {
+    if (g.nrhs == nrhs && g.tol == tol && g.step == step) return &g;
+  const size_t cap = s->d.outer_solver == HZ_OUTER_GCR ? kMaxGcrGraphs : kMaxGraphs;
+  if (s->graphs.size() >= cap) {
     cudaStreamSynchronize(s->st);
     cudaGraphExecDestroy(s->graphs.front().ex);
     cudaGraphDestroy(s->graphs.front().g);
@@ -1178,7 +1221,7 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
   s->st = s->cap_main;
   s->capturing = true;
   for (long long& c : s->body_count_l) c = 0;
-  hz_status e = outer_step(s, nrhs, tol);
+  hz_status e = issue();
   s->body_count = 0;
   for (long long c : s->body_count_l) s->body_count += c;
   s->capturing = false;
@@ -1192,7 +1235,7 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
     s->err = why;
     return nullptr;
   }
-  hz_solver::OuterGraph og{nrhs, tol, nullptr, nullptr, captured - s->body_count};
+  hz_solver::OuterGraph og{nrhs, tol, step, nullptr, nullptr, captured - s->body_count};
   if (cudaStreamEndCapture(s->cap_main, &og.g) != cudaSuccess) {
     cuda_check(s, "end capture");
     end_failed_capture(s);
@@ -1203,9 +1246,11 @@ hz_solver::OuterGraph* outer_graph(hz_solver* s, int nrhs, double tol) {
     cudaGraphDestroy(og.g);
     return nullptr;
   }
-  for (int l = 0; l < kMaxLevels; ++l) s->body_kernels_host[l] = (int)s->body_count_l[l];
-  if (cudaMemcpyAsync(s->body_kernels, s->body_kernels_host, sizeof(int) * kMaxLevels,
-                      cudaMemcpyHostToDevice, st0) != cudaSuccess ||
+  // (level 0, the outer loop of hz_solve_async's graphs, is not captured here)
+  for (int l = 1; l < kMaxLevels; ++l) s->body_kernels_host[l] = (int)s->body_count_l[l];
+  if (cudaMemcpyAsync(s->body_kernels + 1, s->body_kernels_host + 1,
+                      sizeof(int) * (kMaxLevels - 1), cudaMemcpyHostToDevice,
+                      st0) != cudaSuccess ||
       cudaStreamSynchronize(st0) != cudaSuccess) {
     cuda_check(s, "graph counter");
     cudaGraphExecDestroy(og.ex);
@@ -1226,6 +1271,7 @@ hz_status outer_begin(hz_solver* s, const double2* b, double2* x, int nrhs, doub
   const LevelDev F = dev64(s, 0);
   cudaMemsetAsync(s->in_total, 0, sizeof(int) * nrhs, st);
   cudaMemsetAsync(s->in_max, 0, sizeof(int) * nrhs, st);
+  cudaMemsetAsync(s->out_total, 0, sizeof(int) * nrhs, st);
   // ||b|| over the unknowns (Dirichlet boundary entries of b are ignored)
   launch_add_conv<double, double>(vref<double>(b), nullptr, vref<double>(s->wo), n0,
                                   nrhs, nullptr, st);
@@ -1267,7 +1313,9 @@ hz_status outer_report(hz_solver* s, const double2* b, double2* x, int nrhs,
   std::vector<double> rr(nrhs), bn(nrhs);
   int fault = 0;
   cudaMemcpyAsync(&fault, s->fault, sizeof(int), cudaMemcpyDeviceToHost, st);
+  std::vector<int> otot(nrhs);
   cudaMemcpyAsync(it.data(), ko.iters, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
+  cudaMemcpyAsync(otot.data(), s->out_total, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(stt.data(), ko.stat, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(itot.data(), s->in_total, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
   cudaMemcpyAsync(imax.data(), s->in_max, sizeof(int) * nrhs, cudaMemcpyDeviceToHost, st);
@@ -1281,6 +1329,7 @@ hz_status outer_report(hz_solver* s, const double2* b, double2* x, int nrhs,
   }
   hz_status worst = HZ_OK;
   for (int r = 0; r < nrhs; ++r) {
+    it[r] += otot[r];
     hz_status sr = (hz_status)stt[r];
     const double rel = bn[r] > 0 ? rr[r] / bn[r] : 0.0;
     if (sr == HZ_OK && !std::isfinite(rel)) sr = HZ_NAN;
@@ -1411,60 +1460,235 @@ hz_status outer_end(hz_solver* s, const double2* b, double2* x, int nrhs,
 // to c_0 .. c_{k-1} (V slots) by the same two-pass classical Gram-Schmidt as
 // FGMRES, with the coefficients also applied to u_k; both normalised by
 // ||c||; then x += (c_k, r) u_k, r -= (c_k, r) c_k.  Issued eagerly.
-hz_status solve_gcr(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
-                    int use_x0, hz_solve_info* info) {
+// One GCR step k on the solver's own iterate xg and residual ro; every
+// argument is fixed for (nrhs, tol, k), so the step can be captured.
+hz_status gcr_step(hz_solver* s, int nrhs, double tol, int k) {
   cudaStream_t st = s->st;
   KState& ko = s->kout;
   const long long n0 = s->lv[0].n;
   const long long vs = (long long)s->d.nrhs_max * n0;
   const int m = s->d.outer_maxit;
-  hz_status e = outer_begin(s, b, x, nrhs, tol, use_x0);
-  if (e != HZ_OK) return e;
-  // r = b - A x0, as left in wo by outer_begin
-  launch_add_conv<double, double>(vref<double>(s->wo), nullptr, vref<double>(s->ro), n0,
-                                  nrhs, nullptr, st);
   KState kg = ko;      // the dot (c_k, r): one basis vector
   kg.jctr = s->izero;
   kg.abytes = nullptr;
+  double2* u = s->Zo + k * vs;
+  double2* c = s->Vo + k * vs;
+  hz_status e = precond_any(s, vref<double>(s->ro), vref<double>(u), nrhs, ko.done);
+  if (e != HZ_OK) return e;
+  st = s->st;
+  launch_helm<double>(dev64(s, 0), s->d.bc, helm1(), vref<double>(u), vref<double>(nullptr),
+                      s->wo, nrhs, ko.done, st);
+  if (k > 0) {
+    launch_fill_int(ko.jctr, k - 1, 1, st);
+    for (int pass = 0; pass < 2; ++pass) {
+      launch_mdot<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
+      launch_reduce_cols(ko, n0, nrhs, pass, st);
+      // the directions first: the update of c leaves its norm in npart
+      launch_maxpy<double, double2>(s->Zo, vs, n0, u, n0, nrhs, ko, pass, st);
+      launch_maxpy<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
+      if (pass == 0) launch_reorth_decide(ko, n0, nrhs, kReorthEta, st);
+    }
+  } else {
+    launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  }
+  launch_reduce_norm(ko, n0, nrhs, ko.hnorm, 1, st);
+  launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(c), n0, ko.hnorm, n0,
+                                    nrhs, ko.done, st);
+  launch_scale_into<double, double2>(vref<double>(u), vref<double>(u), n0, ko.hnorm, n0,
+                                    nrhs, ko.done, st);
+  launch_mdot<double, double2>(c, vs, n0, s->ro, n0, nrhs, kg, 0, st);
+  launch_reduce_cols(kg, n0, nrhs, 0, st);
+  launch_gcr_update(s->xg, s->ro, u, c, n0, nrhs, ko, st);
+  launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
+  launch_gcr_check(ko, ko.beta, nrhs, tol, k, m, st);
+  return cuda_check(s, "gcr step");
+}
+
+// Flexible GCR as the outer iteration (Sec. 6.3), right-preconditioned by
+// A-DEF1.  Step k: u_k = P r (stored in Z slot k), c = A u_k made orthogonal
+// to c_0 .. c_{k-1} (V slots) by the same two-pass classical Gram-Schmidt as
+// FGMRES, with the coefficients also applied to u_k; both normalised by
+// ||c||; then x += (c_k, r) u_k, r -= (c_k, r) c_k.  Each step runs as a
+// CUDA graph of its own (captured on first use, one per step index), the
+// iterate accumulating in the solver's buffer and copied out at the end.
+hz_status solve_gcr(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
+                    int use_x0, hz_solve_info* info) {
+  cudaStream_t st = s->st;
+  const long long n0 = s->lv[0].n;
+  const int m = s->d.outer_maxit;
+  hz_status e = outer_begin(s, b, x, nrhs, tol, use_x0);
+  if (e != HZ_OK) return e;
+  // r = b - A x0, as left in wo by outer_begin; x0 (or 0) into xg
+  launch_add_conv<double, double>(vref<double>(s->wo), nullptr, vref<double>(s->ro), n0,
+                                  nrhs, nullptr, st);
+  launch_add_conv<double, double>(vref<double>(x), nullptr, vref<double>(s->xg), n0, nrhs,
+                                  nullptr, st);
+  const bool graphs = !s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on();
   int all = 0;
-  e = read_flag(s, ko.alldone, &all);
+  e = read_outer_flag(s, &all);
   if (e != HZ_OK) return e;
   for (int k = 0; k < m && !all; ++k) {
-    double2* u = s->Zo + k * vs;
-    double2* c = s->Vo + k * vs;
-    e = precond_any(s, vref<double>(s->ro), vref<double>(u), nrhs, ko.done);
-    if (e != HZ_OK) return e;
-    launch_helm<double>(dev64(s, 0), s->d.bc, helm1(), vref<double>(u),
-                        vref<double>(nullptr), s->wo, nrhs, ko.done, st);
-    if (k > 0) {
-      launch_fill_int(ko.jctr, k - 1, 1, st);
-      for (int pass = 0; pass < 2; ++pass) {
-        launch_mdot<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
-        launch_reduce_cols(ko, n0, nrhs, pass, st);
-        // the directions first: the update of c leaves its norm in npart
-        launch_maxpy<double, double2>(s->Zo, vs, n0, u, n0, nrhs, ko, pass, st);
-        launch_maxpy<double, double2>(s->Vo, vs, n0, s->wo, n0, nrhs, ko, pass, st);
-        if (pass == 0) launch_reorth_decide(ko, n0, nrhs, kReorthEta, st);
-      }
+    hz_solver::OuterGraph* og = nullptr;
+    if (graphs && k < (int)kMaxGcrGraphs) {
+      og = outer_graph(s, nrhs, tol, k, [&] { return gcr_step(s, nrhs, tol, k); });
+      if (!og) return HZ_CUDA_ERROR;
+      if (cudaGraphLaunch(og->ex, st) != cudaSuccess) return cuda_check(s, "graph launch");
+      launch_counter().fetch_add(og->kernels);
+      host_op_counter().fetch_add(1);
+      g_graph_launched.store(true);
     } else {
-      launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+      e = gcr_step(s, nrhs, tol, k);
+      if (e != HZ_OK) return e;
     }
-    launch_reduce_norm(ko, n0, nrhs, ko.hnorm, 1, st);
-    launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(c), n0, ko.hnorm,
-                                      n0, nrhs, ko.done, st);
-    launch_scale_into<double, double2>(vref<double>(u), vref<double>(u), n0, ko.hnorm, n0,
-                                      nrhs, ko.done, st);
-    launch_mdot<double, double2>(c, vs, n0, s->ro, n0, nrhs, kg, 0, st);
-    launch_reduce_cols(kg, n0, nrhs, 0, st);
-    launch_gcr_update(x, s->ro, u, c, n0, nrhs, ko, st);
-    launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
-    launch_gcr_check(ko, ko.beta, nrhs, tol, k, m, st);
-    e = cuda_check(s, "gcr step");
-    if (e != HZ_OK) return e;
-    e = read_flag(s, ko.alldone, &all);
+    e = read_outer_flag(s, &all);
     if (e != HZ_OK) return e;
   }
+  launch_add_conv<double, double>(vref<double>(s->xg), nullptr, vref<double>(x), n0, nrhs,
+                                  nullptr, st);
   return outer_report(s, b, x, nrhs, info);
+}
+
+// The per-RHS report of an outer solve written to device memory (the
+// device-side counterpart of outer_report; a raised fault flag reports
+// HZ_TIMEOUT for every RHS and is cleared).
+__global__ void k_solve_info(hz_solve_info* info, KState ko, const int* in_total,
+                             const int* in_max, const int* out_total, const double* relres,
+                             const double* bnorm, int* fault, int nrhs) {
+  const int r = threadIdx.x;
+  const int f = *fault;
+  __syncthreads();
+  if (r < nrhs) {
+    hz_status sr = (hz_status)ko.stat[r];
+    const double rel = bnorm[r] > 0 ? relres[r] / bnorm[r] : 0.0;
+    if (sr == HZ_OK && !isfinite(rel)) sr = HZ_NAN;
+    if (f) sr = HZ_TIMEOUT;
+    info[r].outer_iters = ko.iters[r] + out_total[r];
+    info[r].inner_iters_total = in_total[r];
+    info[r].inner_iters_max = in_max[r];
+    info[r].relres = rel;
+    info[r].status = sr;
+  }
+  __syncthreads();
+  if (r == 0) *fault = 0;
+}
+
+// The whole FGMRES solve as one graph (hz_solve_async): start, the outer
+// loop as a WHILE node with the inner loop nested in its body, the update
+// of x, the true residual and the report kernel.
+hz_status capture_solve(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
+                        int use_x0, hz_solve_info* info_dev) {
+  const long long n0 = s->lv[0].n;
+  KState& ko = s->kout;
+  hz_status e = outer_begin(s, b, x, nrhs, tol, use_x0);
+  if (e != HZ_OK) return e;
+  hz_status es = HZ_OK;
+  e = capture_loop(s, 0, ko, [&] { es = outer_step(s, nrhs, tol); }, s->d.outer_maxit);
+  if (e != HZ_OK) return e;
+  if (es != HZ_OK) return es;
+  cudaStream_t st = s->st;
+  launch_trisolve(ko, nrhs, st);
+  launch_update<double2, double>(s->Zo, (long long)s->d.nrhs_max * n0, n0, ko, x, 1, n0,
+                                 nrhs, st);
+  launch_helm<double>(dev64(s, 0), s->d.bc, helm1(), vref<double>(x), vref<double>(b),
+                      s->wo, nrhs, nullptr, st);
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, s->relres, 1, st);
+  HZ_COUNT();
+  k_solve_info<<<1, 1024, 0, st>>>(info_dev, ko, s->in_total, s->in_max, s->out_total,
+                                   s->relres, s->bnorm_o, s->fault, nrhs);
+  return cuda_check(s, "solve capture");
+}
+
+hz_status solve_async(hz_solver* s, const double2* b, double2* x, int nrhs, double tol,
+                      int use_x0, hz_solve_info* info_dev) {
+  hz_solver::SolveGraph* sg = nullptr;
+  for (hz_solver::SolveGraph& g : s->solve_graphs)
+    if (g.nrhs == nrhs && g.tol == tol && g.use_x0 == use_x0 && g.b == b && g.x == x &&
+        g.info == info_dev)
+      sg = &g;
+  if (!sg) {
+    if (s->solve_graphs.size() >= kMaxGraphs) {
+      cudaStreamSynchronize(s->st);
+      cudaGraphExecDestroy(s->solve_graphs.front().ex);
+      cudaGraphDestroy(s->solve_graphs.front().g);
+      s->solve_graphs.erase(s->solve_graphs.begin());
+    }
+    bool ok = (s->cap_main ||
+               cudaStreamCreateWithFlags(&s->cap_main, cudaStreamNonBlocking) == cudaSuccess) &&
+              (s->cap_body ||
+               cudaStreamCreateWithFlags(&s->cap_body, cudaStreamNonBlocking) == cudaSuccess);
+    for (int l = 0; ok && l <= s->D; ++l)
+      if (l != 1)
+        ok = s->cap_nest[l] ||
+             cudaStreamCreateWithFlags(&s->cap_nest[l], cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) return cuda_check(s, "capture streams");
+    cudaStream_t st0 = s->st;
+    const long long c0 = launch_counter().load(), h0 = host_op_counter().load();
+    if (cudaStreamBeginCapture(s->cap_main, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+      return cuda_check(s, "begin capture");
+    s->st = s->cap_main;
+    s->capturing = true;
+    for (long long& c : s->body_count_l) c = 0;
+    const hz_status e = capture_solve(s, b, x, nrhs, tol, use_x0, info_dev);
+    s->capturing = false;
+    s->st = st0;
+    long long body = 0;
+    for (long long c : s->body_count_l) body += c;
+    const long long captured = launch_counter().load() - c0;
+    launch_counter().fetch_sub(captured);
+    host_op_counter().fetch_sub(host_op_counter().load() - h0);
+    if (e != HZ_OK) {
+      const std::string why = s->err;
+      end_failed_capture(s);
+      s->err = why;
+      return e;
+    }
+    hz_solver::SolveGraph g{nrhs, use_x0, tol, b, x, info_dev, nullptr, nullptr,
+                            captured - body};
+    if (cudaStreamEndCapture(s->cap_main, &g.g) != cudaSuccess) {
+      const hz_status ce = cuda_check(s, "end capture");
+      end_failed_capture(s);
+      return ce;
+    }
+    if (cudaGraphInstantiate(&g.ex, g.g, 0) != cudaSuccess) {
+      const hz_status ce = cuda_check(s, "graph instantiate");
+      cudaGraphDestroy(g.g);
+      return ce;
+    }
+    for (int l = 0; l < kMaxLevels; ++l) s->body_kernels_host[l] = (int)s->body_count_l[l];
+    if (cudaMemcpyAsync(s->body_kernels, s->body_kernels_host, sizeof(int) * kMaxLevels,
+                        cudaMemcpyHostToDevice, s->st) != cudaSuccess)
+      return cuda_check(s, "graph counter");
+    s->solve_graphs.push_back(g);
+    sg = &s->solve_graphs.back();
+  }
+  if (cudaGraphLaunch(sg->ex, s->st) != cudaSuccess) return cuda_check(s, "graph launch");
+  launch_counter().fetch_add(sg->kernels);
+  host_op_counter().fetch_add(1);
+  g_graph_launched.store(true);
+  return HZ_OK;
+}
+
+// FGMRES restart (hz_desc.restart): x += Z_k y of the finished cycle, its
+// iterations added to out_total, then a new Arnoldi start from the true
+// residual b - A x with the stopping reference ||b|| kept; RHS that stopped
+// stay stopped.
+hz_status outer_restart(hz_solver* s, const double2* b, double2* x, int nrhs, double tol) {
+  cudaStream_t st = s->st;
+  KState& ko = s->kout;
+  const long long n0 = s->lv[0].n;
+  launch_trisolve(ko, nrhs, st);
+  launch_update<double2, double>(s->Zo, (long long)s->d.nrhs_max * n0, n0, ko, x, 1, n0,
+                                 nrhs, st);
+  launch_accum_iters(ko.iters, s->out_total, s->out_max, nrhs, nullptr, st);
+  launch_helm<double>(dev64(s, 0), s->d.bc, helm1(), vref<double>(x), vref<double>(b),
+                      s->wo, nrhs, nullptr, st);
+  launch_norm2_part<double>(vref<double>(s->wo), n0, nrhs, ko, nullptr, st);
+  launch_reduce_norm(ko, n0, nrhs, ko.beta, 1, st);
+  launch_krylov_init(ko, nrhs, ko.done, s->bnorm_o, tol, st);
+  launch_scale_into<double, double2>(vref<double>(s->wo), vref<double>(s->Vo), n0,
+                                    ko.hnorm, n0, nrhs, ko.done, st);
+  return cuda_check(s, "outer restart");
 }
 
 hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
@@ -1480,11 +1704,13 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
   // and the trace's host reads need the launches issued one by one
   hz_solver::OuterGraph* og = nullptr;
   if (!s->d.no_cuda_graph && s->prof_kc == HZ_KC_NONE && !debug_on()) {
-    og = outer_graph(s, nrhs, tol);
+    og = outer_graph(s, nrhs, tol, -1, [&] { return outer_step(s, nrhs, tol); });
     if (!og) return HZ_CUDA_ERROR;
   }
   e = read_outer_flag(s, &all);
   if (e != HZ_OK) return e;
+  const int restart = s->d.restart;
+  int cycle = 0;
   for (int it = 0; it < m && !all; ++it) {
     if (og) {
       if (cudaGraphLaunch(og->ex, st) != cudaSuccess) return cuda_check(s, "graph launch");
@@ -1497,6 +1723,13 @@ hz_status solve_dev(hz_solver* s, const double2* b, double2* x, int nrhs,
     }
     e = read_outer_flag(s, &all);
     if (e != HZ_OK) return e;
+    if (restart > 0 && ++cycle == restart && !all && it + 1 < m) {
+      e = outer_restart(s, b, x, nrhs, tol);
+      if (e != HZ_OK) return e;
+      cycle = 0;
+      e = read_outer_flag(s, &all);
+      if (e != HZ_OK) return e;
+    }
   }
   return outer_end(s, b, x, nrhs, info);
 }
@@ -2126,6 +2359,21 @@ hz_status hz_solve(hz_solver* s, const void* b_dev, void* x_dev, int nrhs, doubl
   return solve_dev(s, (const double2*)b_dev, (double2*)x_dev, nrhs, tol, use_x0, info);
 }
 
+hz_status hz_solve_async(hz_solver* s, const void* b_dev, void* x_dev, int nrhs, double tol,
+                         int use_x0, hz_solve_info* info_dev) {
+  if (!s || !b_dev || !x_dev || !info_dev || nrhs < 1 || nrhs > s->d.nrhs_max ||
+      !(tol > 0))
+    return HZ_INVALID_ARG;
+  if (s->d.outer_solver != HZ_OUTER_FGMRES || s->d.restart > 0 || s->d.no_cuda_graph ||
+      s->prof_kc != HZ_KC_NONE) {
+    set_err(s, "hz_solve_async needs FGMRES without restart and with CUDA graphs, and no "
+               "kernel profiling");
+    return HZ_INVALID_ARG;
+  }
+  return solve_async(s, (const double2*)b_dev, (double2*)x_dev, nrhs, tol, use_x0,
+                     (hz_solve_info*)info_dev);
+}
+
 hz_status hz_solve_host(hz_solver* s, const void* b_host, void* x_host, int nrhs,
                         double tol, hz_solve_info* info) {
   if (!s || !b_host || !x_host || nrhs < 1 || nrhs > s->d.nrhs_max || !(tol > 0))
@@ -2311,7 +2559,7 @@ hz_status hz_gradient_group(hz_solver* const* members, int count, const double* 
 }
 
 hz_status hz_profile_begin(hz_solver* s, hz_kernel_class kc, int max_launches) {
-  if (!s || kc < HZ_KC_NONE || kc > HZ_KC_MAXPY || max_launches < 0)
+  if (!s || kc < HZ_KC_NONE || kc > HZ_KC_VCYCLE || max_launches < 0)
     return HZ_INVALID_ARG;
   for (cudaEvent_t e : s->prof_ev) cudaEventDestroy(e);
   s->prof_ev.clear();

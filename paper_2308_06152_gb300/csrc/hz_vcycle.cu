@@ -481,7 +481,7 @@ template <class T, class SF, class SX, class SC, int NS>
 __global__ void __launch_bounds__(BX * BY)
 k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin,
                   SX* __restrict__ x, SC* __restrict__ fc, int nrhs, int rpb,
-                  const int* __restrict__ done) {
+                  const int* __restrict__ done, unsigned long long* abytes) {
   using P = PreRestrictMR<T, SF>;
   extern __shared__ __align__(16) unsigned char smraw[];
   int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XS + P::RS);
@@ -489,6 +489,19 @@ k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin,
   const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
   const int na = list_active(done, r0, r1, act, &nact_s);
   if (na == 0) return;
+  if (abytes && threadIdx.x == 0 && threadIdx.y == 0) {
+    // algorithmic bytes of the tile: f read and x written per own fine node,
+    // the coarse right-hand side written per own coarse node, for each
+    // active RHS; D^-1 once per launch
+    const long long fw = min(2 * BX, Lf.nx - 2 * (int)blockIdx.x * BX);
+    const long long fh = min(2 * BY, Lf.ny - 2 * (int)blockIdx.y * BY);
+    const long long cw = min(BX, Lc.nx - (int)blockIdx.x * BX);
+    const long long ch = min(BY, Lc.ny - (int)blockIdx.y * BY);
+    unsigned long long b = (unsigned long long)na *
+        (fw * fh * (sizeof(SF) + sizeof(SX)) + cw * ch * sizeof(SC));
+    if (blockIdx.z == 0) b += (unsigned long long)(fw * fh * sizeof(C<T>));
+    atomicAdd(abytes, b);
+  }
   // the x tile [2I0-2, 2I0+2BX] x [2J0-2, 2J0+2BY] inside the grid and off
   // its boundary rows and columns
   const int fx0 = 2 * blockIdx.x * BX - 2, fy0 = 2 * blockIdx.y * BY - 2;
@@ -674,7 +687,7 @@ template <class T, class SC, class SX, class SF, class SO, int NS, int TXW>
 __global__ void __launch_bounds__(BX * BY)
 k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restrict__ xc,
                     const SX* __restrict__ x, VRefE<SF> fin, SO* __restrict__ xo, int nrhs,
-                    int rpb, const int* __restrict__ done) {
+                    int rpb, const int* __restrict__ done, unsigned long long* abytes) {
   using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
   extern __shared__ __align__(16) unsigned char smraw[];
   int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XP);
@@ -682,6 +695,19 @@ k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restric
   const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
   const int na = list_active(done, r0, r1, act, &nact_s);
   if (na == 0) return;
+  if (abytes && threadIdx.x == 0 && threadIdx.y == 0) {
+    // algorithmic bytes of the tile: x and f read and the result written per
+    // own fine node, the correction read per coarse node under the tile
+    // (the tile's fine nodes with both indices even), for each active RHS;
+    // D^-1 once per launch
+    const long long fw = min(TXW, Lf.nx - (int)blockIdx.x * TXW);
+    const long long fh = min(BY, Lf.ny - (int)blockIdx.y * BY);
+    unsigned long long b = (unsigned long long)na *
+        (fw * fh * (sizeof(SX) + sizeof(SF) + sizeof(SO)) +
+         ((fw + 1) / 2) * ((fh + 1) / 2) * sizeof(SC));
+    if (blockIdx.z == 0) b += (unsigned long long)(fw * fh * sizeof(C<T>));
+    atomicAdd(abytes, b);
+  }
   // the x' tile [i0-1, i0+TXW] x [j0-1, j0+BY] inside the grid and off its
   // boundary rows and columns
   const int fx0 = blockIdx.x * TXW - 1, fy0 = blockIdx.y * BY - 1;
@@ -771,7 +797,7 @@ inline int clamp_rpb(int rpb, int nrhs) { return (rpb <= 0 || rpb > nrhs) ? nrhs
 template <class T, class SF, class SX, class SC>
 void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
-                            cudaStream_t st) {
+                            cudaStream_t st, unsigned long long* abytes) {
   HZ_COUNT();
   using P = PreRestrictMR<T, SF>;
   auto kern = k_pre_restrict_mr<T, SF, SX, SC, kPreNS>;
@@ -783,13 +809,14 @@ void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, doub
   rpb = clamp_rpb(rpb, nrhs);
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
   kern<<<grid, dim3(BX, BY), P::smem(kPreNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), f,
-                                                         x, fc, nrhs, rpb, done);
+                                                         x, fc, nrhs, rpb, done, abytes);
 }
 
 template <class T, class SC, class SX, class SF, class SO, int TXW>
 void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                                 const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
-                                int rpb, const int* done, cudaStream_t st) {
+                                int rpb, const int* done, cudaStream_t st,
+                                unsigned long long* abytes) {
   using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
   auto kern = k_prolong_smooth_mr<T, SC, SX, SF, SO, kProNS, TXW>;
   static std::once_flag once;
@@ -800,21 +827,22 @@ void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, 
   rpb = clamp_rpb(rpb, nrhs);
   const dim3 grid((Lf.nx + TXW - 1) / TXW, (Lf.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
   kern<<<grid, dim3(BX, BY), P::smem(kProNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), xc,
-                                                         x, f, xo, nrhs, rpb, done);
+                                                         x, f, xo, nrhs, rpb, done, abytes);
 }
 
 // tile 0: 32 x 8 fine nodes per block, 1: 64 x 8
 template <class T, class SC, class SX, class SF, class SO>
 void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                               const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
-                              int rpb, int tile, const int* done, cudaStream_t st) {
+                              int rpb, int tile, const int* done, cudaStream_t st,
+                              unsigned long long* abytes) {
   HZ_COUNT();
   if (tile == 1)
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, 2 * BX>(Lf, Lc, bc, omega, xc, x, f, xo,
-                                                          nrhs, rpb, done, st);
+                                                          nrhs, rpb, done, st, abytes);
   else
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, BX>(Lf, Lc, bc, omega, xc, x, f, xo, nrhs,
-                                                      rpb, done, st);
+                                                      rpb, done, st, abytes);
 }
 
 template <class T, class SF, class SO>
@@ -881,10 +909,11 @@ template void launch_dense_mv<float, bf2, bf2>(int, const float2*, VRefE<bf2>, b
       const int*, cudaStream_t);                                                \
   template void launch_pre_restrict_mr<T, SF, SX, SC>(                          \
       const LevelDev&, const LevelDev&, int, double, VRefE<SF>, SX*, SC*, int,  \
-      int, const int*, cudaStream_t);                                           \
+      int, const int*, cudaStream_t, unsigned long long*);                      \
   template void launch_prolong_smooth_mr<T, SC, SX, SF, SO>(                    \
       const LevelDev&, const LevelDev&, int, double, const SC*, const SX*,      \
-      VRefE<SF>, SO*, int, int, int, const int*, cudaStream_t);                 \
+      VRefE<SF>, SO*, int, int, int, const int*, cudaStream_t,                  \
+      unsigned long long*);                                                     \
   template void launch_prolong_smooth<T, SC, SX, SF, SO>(                       \
       const LevelDev&, const LevelDev&, int, Shift, const SC*, const SX*,       \
       VRefE<SF>, SO*, int, const int*, cudaStream_t);

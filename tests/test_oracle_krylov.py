@@ -67,6 +67,29 @@ def test_gmres_right_iterate_minimises_the_true_residual(k):
     assert abs(res.res_est - np.linalg.norm(b - A @ res.x)) < 1e-10 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("m,cycles", [(2, 2), (3, 3)])
+def test_restarted_gmres_is_a_sequence_of_least_squares_cycles(m, cycles):
+    """GMRES(m) (restart = m): after c cycles the iterate is x_c =
+    x_{c-1} + P V y, V spanning K_m(A P, r_{c-1}) from the true residual
+    r_{c-1} = b - A x_{c-1}, y minimising ||b - A x||; the count is c m."""
+    A, b, x0, P = _system(5)
+    res = gmres_right(lambda v: A @ v, b, 0.0, m * cycles, x0=x0,
+                      prec=lambda v: P @ v, restart=m)
+    assert res.iters == m * cycles
+    x = x0.copy()
+    for _ in range(cycles):
+        r = b - A @ x
+        V = _krylov(lambda v: A @ (P @ v), r, m)
+        y, *_ = np.linalg.lstsq(A @ P @ V, r, rcond=None)
+        x = x + P @ V @ y
+    assert _rel(res.x, x) < 1e-10
+    # more cycles than needed: the same as unrestarted GMRES once m >= N
+    full = gmres_right(lambda v: A @ v, b, 1e-12, N, x0=x0, prec=lambda v: P @ v)
+    big = gmres_right(lambda v: A @ v, b, 1e-12, N, x0=x0, prec=lambda v: P @ v,
+                      restart=N)
+    assert big.iters == full.iters and _rel(big.x, full.x) < 1e-12
+
+
 class _Variable:
     """A preconditioner that changes with every application (two fixed
     matrices, alternating) and records its outputs."""

@@ -120,8 +120,10 @@ MUTATIONS = [
     ("krylov.py", "r0 = prec(b - matvec(x0))", "r0 = b - matvec(x0)", KRY),
     ("krylov.py", "            u = u - beta * ui", "            pass", KRY),
     ("krylov.py", "        gamma = np.vdot(c, r)", "        gamma = np.vdot(r, c)", KRY),
-    ("krylov.py", "        upd = prec(sum(y[i] * V[i] for i in range(k)))",
-     "        upd = sum(y[i] * V[i] for i in range(k))", KRY),
+    ("krylov.py", "            x = x + prec(sum(y[i] * V[i] for i in range(k)))",
+     "            x = x + sum(y[i] * V[i] for i in range(k))", KRY),
+    ("krylov.py", "        r0 = b - matvec(x) if np.any(x) else b.copy()",
+     "        r0 = b.copy()", KRY),
 ]
 
 
