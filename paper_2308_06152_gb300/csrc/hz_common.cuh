@@ -224,16 +224,18 @@ void launch_prolong_smooth(const LevelDev& Lf, const LevelDev& Lc, int bc, Shift
 // the input tiles staged ahead in shared memory (cp.async ring); omega is
 // the Jacobi weight D^-1 was built with (the kernels use D^-1 diag(M) =
 // omega); prolongation tile 0 = 32 x 8 fine nodes, 1 = 64 x 8
-// (abytes, if not null, accumulates the algorithmic bytes of the launch)
+// (abytes, if not null, accumulates the algorithmic bytes of the launch;
+// frs is the distance between the right-hand sides of f, 0 = nx * ny)
 template <class T, class SF, class SX, class SC>
 void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
-                            cudaStream_t st, unsigned long long* abytes = nullptr);
+                            cudaStream_t st, unsigned long long* abytes = nullptr,
+                            long long frs = 0);
 template <class T, class SC, class SX, class SF, class SO>
 void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                               const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
                               int rpb, int tile, const int* done, cudaStream_t st,
-                              unsigned long long* abytes = nullptr);
+                              unsigned long long* abytes = nullptr, long long frs = 0);
 // x = Minv f on the coarsest level (dense)
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,

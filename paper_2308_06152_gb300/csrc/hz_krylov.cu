@@ -309,108 +309,17 @@ __device__ __forceinline__ void maxpy_tile(const SB* __restrict__ V, long long v
   if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = t;
 }
 
-// w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart.
-// Each block takes a contiguous range of (RHS, chunk) tiles, so the
-// coefficients hcol of an RHS are staged once per block rather than per
-// tile, and the chunk of w of its next tile is loaded into registers while
-// the current tile streams its basis rows (one tile's w latency per block
-// instead of one per tile).
+// w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
 template <class T, class SB>
 __global__ void __launch_bounds__(NT)
 k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
         C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
-  constexpr int TILE = MAXPY_TILE;
-  constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
   __shared__ C<T> hs[MAXPY_TILE];
   __shared__ double red[NT / 32];
   const int j = *ks.jctr;
-  const long long tiles = (long long)nrhs * nblk;
-  const long long lo = tiles * blockIdx.x / gridDim.x;
-  const long long hi = tiles * (blockIdx.x + 1) / gridDim.x;
-  auto active = [&](long long t) {
-    const int r = (int)(t / nblk);
-    return !ks.done[r] && (!pass || ks.reorth[r]);
-  };
-  // chunk blk of RHS r of w into v (zero beyond n)
-  auto load_w = [&](long long t, C<T>* v) {
-    const int r = (int)(t / nblk), blk = (int)(t % nblk);
-    const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
-    const C<T>* wr = w + r * n;
-#pragma unroll
-    for (int k = 0; k < VPT; ++k)
-#pragma unroll
-      for (int u = 0; u < W; ++u) {
-        const long long e = (g0 + (long long)k * NT) * W + u;
-        v[k * W + u] = (e < n) ? wr[e] : czero<T>();
-      }
-  };
-  long long t = lo;
-  while (t < hi && !active(t)) ++t;
-  C<T> nxt[EPT];
-  if (t < hi) load_w(t, nxt);
-  int hs_r = -1, hs_t0 = -1;
-  while (t < hi) {
-    const int r = (int)(t / nblk), blk = (int)(t % nblk);
-    if (ks.abytes && blk == 0 && threadIdx.x == 0)
-      atomicAdd(ks.abytes, (unsigned long long)n * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB)));
-    C<T> acc[EPT];
-#pragma unroll
-    for (int e = 0; e < EPT; ++e) acc[e] = nxt[e];
-    long long tn = t + 1;
-    while (tn < hi && !active(tn)) ++tn;
-    if (tn < hi) load_w(tn, nxt);
-    const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
-    for (int t0 = 0; t0 <= j; t0 += TILE) {
-      const int cnt = min(TILE, j + 1 - t0);
-      if (hs_r != r || hs_t0 != t0) {
-        __syncthreads();
-        for (int q = threadIdx.x; q < cnt; q += NT)
-          hs[q] = cvt_to<T>(ks.hcol[(long long)r * (ks.m + 1) + t0 + q]);
-        __syncthreads();
-        hs_r = r;
-        hs_t0 = t0;
-      }
-      for (int q0 = 0; q0 < cnt; q0 += G) {
-        uint4 raw[G][VPT];
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const SB* vr = V + (long long)(t0 + q0 + q) * vstride + r * rs;
-#pragma unroll
-          for (int k = 0; k < VPT; ++k) {
-            const long long g = g0 + (long long)k * NT;
-            raw[q][k] = (q0 + q < cnt && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < G; ++q) {
-          const C<T> h = (q0 + q < cnt) ? hs[q0 + q] : czero<T>();
-#pragma unroll
-          for (int k = 0; k < VPT; ++k) {
-            static_for<W>([&](auto U) {
-              const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
-              acc[k * W + U.value].x -= v.x * h.x - v.y * h.y;
-              acc[k * W + U.value].y -= v.x * h.y + v.y * h.x;
-            });
-          }
-        }
-      }
-    }
-    C<T>* wr = w + r * n;
-    T wn = T(0);
-#pragma unroll
-    for (int k = 0; k < VPT; ++k)
-#pragma unroll
-      for (int u = 0; u < W; ++u) {
-        const long long e = (g0 + (long long)k * NT) * W + u;
-        if (e < n) {
-          wr[e] = acc[k * W + u];
-          wn += acc[k * W + u].x * acc[k * W + u].x + acc[k * W + u].y * acc[k * W + u].y;
-        }
-      }
-    const double tot = block_sum((double)wn, red);
-    if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = tot;
-    t = tn;
-  }
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
+    maxpy_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
+                      (int)(tile % nblk), hs, red);
 }
 
 // The same two kernels over the tiles of several grids (GroupDesc).

@@ -480,16 +480,22 @@ inline void prof_mark(hz_solver* s, int kc) {
 // One V-cycle from level l0 for M_l0 x = f.  The hierarchy's own vectors are
 // stored as SL (C<T>, or BF16 pairs for the BF16-storage smoother); the
 // input f and the result xout are C<T>.
-template <class T, class SL>
-void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
-               const int* done) {
+template <class T, class SL, class SI = C<T>>
+void vcycle_sl(hz_solver* s, int l0, VRefE<SI> f, C<T>* xout, int nrhs,
+               const int* done, long long frs = 0) {
+  // SI: storage of the input f (C<T>, or FP16 pairs read straight from the
+  // inner Krylov basis, staged kernels only); frs: distance between its
+  // right-hand sides (0 = the level's node count; the basis rows are padded)
+  constexpr bool native_in = std::is_same<SI, C<T>>::value;
   cudaStream_t st = s->st;
   const int bc = s->d.bc;
   const Shift sh = cslp(s);
   const C<T>* minv = (const C<T>*)s->minv;
-  if (l0 == s->L) {
-    launch_dense_mv<T, C<T>, C<T>>(s->nL, minv, f, xout, nrhs, done, st);
-    return;
+  if constexpr (native_in) {
+    if (l0 == s->L) {
+      launch_dense_mv<T, C<T>, C<T>>(s->nL, minv, f, xout, nrhs, done, st);
+      return;
+    }
   }
   const bool fused = s->tune.vcycle_fused != 0;
   const bool staged = s->tune.vcycle_fused == 2;
@@ -502,34 +508,36 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
     if (staged) {
       if (l == l0) {
         prof_mark(s, HZ_KC_VCYCLE);
-        launch_pre_restrict_mr<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, om, f, (SL*)A.xa,
-                                                (SL*)Bc.f, nrhs, rpb, done, st, vbytes);
+        launch_pre_restrict_mr<T, SI, SL, SL>(A.dev(), Bc.dev(), bc, om, f, (SL*)A.xa,
+                                              (SL*)Bc.f, nrhs, rpb, done, st, vbytes, frs);
         prof_mark(s, HZ_KC_VCYCLE);
       } else
         launch_pre_restrict_mr<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, om, vrefe<SL>(A.f),
                                               (SL*)A.xa, (SL*)Bc.f, nrhs, rpb, done, st);
       continue;
     }
-    if (fused) {
-      if (l == l0)
-        launch_pre_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f, (SL*)A.xa,
-                                             (SL*)Bc.f, nrhs, done, st);
-      else
-        launch_pre_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, vrefe<SL>(A.f),
-                                           (SL*)A.xa, (SL*)Bc.f, nrhs, done, st);
-      continue;
-    }
-    if (l == l0) {
-      launch_jacobi0<T, C<T>, SL>(A.dev(), bc, f, (SL*)A.xa, nrhs, done, st);
-      launch_resid_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f,
-                                             (const SL*)A.xa, (SL*)Bc.f, nrhs,
-                                             done, st);
-    } else {
-      const VRefE<SL> fl = vrefe<SL>(A.f);
-      launch_jacobi0<T, SL, SL>(A.dev(), bc, fl, (SL*)A.xa, nrhs, done, st);
-      launch_resid_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, fl,
-                                           (const SL*)A.xa, (SL*)Bc.f, nrhs, done,
-                                           st);
+    if constexpr (native_in) {
+      if (fused) {
+        if (l == l0)
+          launch_pre_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f, (SL*)A.xa,
+                                               (SL*)Bc.f, nrhs, done, st);
+        else
+          launch_pre_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, vrefe<SL>(A.f),
+                                             (SL*)A.xa, (SL*)Bc.f, nrhs, done, st);
+        continue;
+      }
+      if (l == l0) {
+        launch_jacobi0<T, C<T>, SL>(A.dev(), bc, f, (SL*)A.xa, nrhs, done, st);
+        launch_resid_restrict<T, C<T>, SL, SL>(A.dev(), Bc.dev(), bc, sh, f,
+                                               (const SL*)A.xa, (SL*)Bc.f, nrhs,
+                                               done, st);
+      } else {
+        const VRefE<SL> fl = vrefe<SL>(A.f);
+        launch_jacobi0<T, SL, SL>(A.dev(), bc, fl, (SL*)A.xa, nrhs, done, st);
+        launch_resid_restrict<T, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh, fl,
+                                             (const SL*)A.xa, (SL*)Bc.f, nrhs, done,
+                                             st);
+      }
     }
   }
   launch_dense_mv<T, SL, SL>(s->nL, minv, vrefe<SL>(s->lv[s->L].f),
@@ -540,9 +548,10 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
     if (staged) {
       if (l == l0) {
         prof_mark(s, HZ_KC_VCYCLE);
-        launch_prolong_smooth_mr<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, om,
-                                                        (const SL*)Bc.x, (const SL*)A.xa, f,
-                                                        xout, nrhs, rpb, tile, done, st, vbytes);
+        launch_prolong_smooth_mr<T, SL, SL, SI, C<T>>(A.dev(), Bc.dev(), bc, om,
+                                                      (const SL*)Bc.x, (const SL*)A.xa, f,
+                                                      xout, nrhs, rpb, tile, done, st, vbytes,
+                                                      frs);
         prof_mark(s, HZ_KC_VCYCLE);
       } else
         launch_prolong_smooth_mr<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, om,
@@ -551,26 +560,49 @@ void vcycle_sl(hz_solver* s, int l0, VRef<T> f, C<T>* xout, int nrhs,
                                                     done, st);
       continue;
     }
-    if (fused) {
+    if constexpr (native_in) {
+      if (fused) {
+        if (l == l0)
+          launch_prolong_smooth<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, sh,
+                                                       (const SL*)Bc.x, (const SL*)A.xa, f,
+                                                       xout, nrhs, done, st);
+        else
+          launch_prolong_smooth<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh,
+                                                   (const SL*)Bc.x, (const SL*)A.xa,
+                                                   vrefe<SL>(A.f), (SL*)A.x, nrhs, done, st);
+        continue;
+      }
+      launch_prolong_add<T, SL, SL>(A.dev(), Bc.dev(), bc, (const SL*)Bc.x, (SL*)A.xa,
+                                    nrhs, done, st);
       if (l == l0)
-        launch_prolong_smooth<T, SL, SL, C<T>, C<T>>(A.dev(), Bc.dev(), bc, sh,
-                                                     (const SL*)Bc.x, (const SL*)A.xa, f,
-                                                     xout, nrhs, done, st);
+        launch_smooth<T, C<T>, SL, C<T>>(A.dev(), bc, sh, f, (const SL*)A.xa, xout,
+                                         nrhs, done, st);
       else
-        launch_prolong_smooth<T, SL, SL, SL, SL>(A.dev(), Bc.dev(), bc, sh,
-                                                 (const SL*)Bc.x, (const SL*)A.xa,
-                                                 vrefe<SL>(A.f), (SL*)A.x, nrhs, done, st);
-      continue;
+        launch_smooth<T, SL, SL, SL>(A.dev(), bc, sh, vrefe<SL>(A.f), (const SL*)A.xa,
+                                     (SL*)A.x, nrhs, done, st);
     }
-    launch_prolong_add<T, SL, SL>(A.dev(), Bc.dev(), bc, (const SL*)Bc.x, (SL*)A.xa,
-                                  nrhs, done, st);
-    if (l == l0)
-      launch_smooth<T, C<T>, SL, C<T>>(A.dev(), bc, sh, f, (const SL*)A.xa, xout,
-                                       nrhs, done, st);
-    else
-      launch_smooth<T, SL, SL, SL>(A.dev(), bc, sh, vrefe<SL>(A.f), (const SL*)A.xa,
-                                   (SL*)A.x, nrhs, done, st);
   }
+}
+
+// The inner solve's V-cycle reads the current basis vector straight from the
+// FP16 basis (no FP32 copy is written): the two-level A-DEF1 inner solve
+// with an FP16 basis and the staged V-cycle kernels, on a hierarchy below
+// level 1.  (The input is then exactly the stored basis vector.)
+inline bool inner_in16(const hz_solver* s) {
+  return s->basis16 && s->tune.vcycle_fused == 2 && s->d.preconditioner == HZ_PRECOND_ADEF1 &&
+         !s->ml && s->L > 1;
+}
+
+// One V-cycle from level l0 whose input f is stored as FP16 pairs (the
+// current vector of the FP16 inner Krylov basis, read in place); the staged
+// kernels only (hz_tuning.vcycle_fused = 2), with a level below l0.
+void vcycle_in16(hz_solver* s, int l0, VRefE<__half2> f, float2* xout, int nrhs,
+                 const int* done) {
+  const long long frs = inner_row(s->lv[l0].n);
+  if (s->lvbf16)
+    vcycle_sl<float, __nv_bfloat162, __half2>(s, l0, f, xout, nrhs, done, frs);
+  else
+    vcycle_sl<float, float2, __half2>(s, l0, f, xout, nrhs, done, frs);
 }
 
 template <class T>
@@ -760,8 +792,16 @@ void inner_pre(hz_solver* s, int nrhs) {
   const long long rs = inner_row(n1);
   const long long vs = (long long)s->d.nrhs_max * rs;
   C<T>* sb = (C<T>*)s->sb;
-  // the V-cycle reads the current basis vector in compute precision, which
-  // the scaling step left in s->qf next to its stored copy
+  // the V-cycle reads the current basis vector: straight from the FP16 basis
+  // (inner_in16), or in compute precision from s->qf, where the scaling step
+  // left it next to its stored copy
+  if constexpr (std::is_same<SB, __half2>::value) {
+    if (inner_in16(s)) {
+      vcycle_in16(s, 1, vrefe_j<__half2>(s->Qb, ks.jctr, 0, vs), sb, nrhs, ks.done);
+      apply_E<T>(s, sb, (C<T>*)s->eb, nrhs, ks.done);
+      return;
+    }
+  }
   vcycle<T>(s, 1, vref<T>(s->qf), sb, nrhs, ks.done);
   apply_E<T>(s, sb, (C<T>*)s->eb, nrhs, ks.done);
 }
@@ -775,7 +815,8 @@ void inner_post(hz_solver* s, int nrhs) {
   launch_givens(ks, nrhs, s->d.coarse_tol, s->d.coarse_maxit, s->st);
   debug_trace(s, ks, "inner");
   launch_scale_into<T, SB>(vref<T>((C<T>*)s->eb), vrefe_j<SB>((SB*)s->Qb, ks.jctr, 0, vs),
-                           rs, ks.hnorm, n1, nrhs, ks.done, s->st, (C<T>*)s->qf);
+                           rs, ks.hnorm, n1, nrhs, ks.done, s->st,
+                           inner_in16(s) ? nullptr : (C<T>*)s->qf);
 }
 template <class T, class SB>
 void inner_step(hz_solver* s, int nrhs) {
@@ -864,7 +905,7 @@ void coarse_begin(hz_solver* s, const C<T>* v1, int nrhs, const int* done_in) {
   launch_reduce_norm(ks, n1, nrhs, ks.beta, 1, st);
   launch_krylov_init(ks, nrhs, done_in, nullptr, s->d.coarse_tol, st);
   launch_scale_into<T, SB>(vref<T>(v1), vrefe<SB>((SB*)s->Qb), inner_row(n1), ks.hnorm,
-                           n1, nrhs, ks.done, st, (C<T>*)s->qf);
+                           n1, nrhs, ks.done, st, inner_in16(s) ? nullptr : (C<T>*)s->qf);
 }
 // x = Q_k y (k the iterations taken), then v2 = M_2h^-1 x (right
 // preconditioning)

@@ -358,8 +358,8 @@ struct PreRestrictMR {
 // BX x BY tile of coarse nodes and a group of rpb right-hand sides.
 template <class T, class SF, class SX, class SC, int NS, bool INTERIOR>
 __device__ __forceinline__ void pre_restrict_mr_body(
-    const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, VRefE<SF> fin, SX* x, SC* fc,
-    int na, const int* act, unsigned char* smraw) {
+    const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, VRefE<SF> fin, long long frs,
+    SX* x, SC* fc, int na, const int* act, unsigned char* smraw) {
   using P = PreRestrictMR<T, SF>;
   constexpr int XW = P::XW, RW = P::RW, NX = P::NX, NR = P::NR, NT = P::NT;
   constexpr int N1 = P::N1, N2 = P::N2, SV = P::STAGE / (int)sizeof(SF);
@@ -419,7 +419,7 @@ __device__ __forceinline__ void pre_restrict_mr_body(
   }
   auto issue = [&](int k) {
     if (k < na) {
-      const SF* fr = fbase + (long long)act[k] * nf;
+      const SF* fr = fbase + (long long)act[k] * frs;
       SF* stg = fst + (k % NS) * SV;
 #pragma unroll
       for (int u = 0; u < N1; ++u)
@@ -479,7 +479,7 @@ __device__ __forceinline__ void pre_restrict_mr_body(
 
 template <class T, class SF, class SX, class SC, int NS>
 __global__ void __launch_bounds__(BX * BY)
-k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin,
+k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin, long long frs,
                   SX* __restrict__ x, SC* __restrict__ fc, int nrhs, int rpb,
                   const int* __restrict__ done, unsigned long long* abytes) {
   using P = PreRestrictMR<T, SF>;
@@ -508,11 +508,11 @@ k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin,
   const bool interior = fx0 >= 1 && fy0 >= 1 && fx0 + P::XW <= Lf.nx - 1 &&
                         fy0 + P::XH <= Lf.ny - 1;
   if (interior)
-    pre_restrict_mr_body<T, SF, SX, SC, NS, true>(Lf, Lc, bc, omc, fin, x, fc, na, act,
+    pre_restrict_mr_body<T, SF, SX, SC, NS, true>(Lf, Lc, bc, omc, fin, frs, x, fc, na, act,
                                                   smraw);
   else
-    pre_restrict_mr_body<T, SF, SX, SC, NS, false>(Lf, Lc, bc, omc, fin, x, fc, na, act,
-                                                   smraw);
+    pre_restrict_mr_body<T, SF, SX, SC, NS, false>(Lf, Lc, bc, omc, fin, frs, x, fc, na,
+                                                   act, smraw);
 }
 
 template <class T, class SC, class SX, class SF, int TXW>
@@ -535,7 +535,7 @@ struct ProlongSmoothMR {
 template <class T, class SC, class SX, class SF, class SO, int NS, int TXW, bool INTERIOR>
 __device__ __forceinline__ void prolong_smooth_mr_body(
     const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, const SC* xc, const SX* x,
-    VRefE<SF> fin, SO* xo, int na, const int* act, unsigned char* smraw) {
+    VRefE<SF> fin, long long frs, SO* xo, int na, const int* act, unsigned char* smraw) {
   using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
   constexpr int PW = P::PW, NP = P::NP, CW = P::CW, NC = P::NC, NT = P::NT;
   constexpr int N1 = P::N1, N3 = P::N3, NPX = P::NPX;
@@ -620,7 +620,7 @@ __device__ __forceinline__ void prolong_smooth_mr_body(
       const int r = act[k];
       const SX* xr = x + (long long)r * nf;
       const SC* xcr = xc + (long long)r * nc;
-      const SF* fr = fbase + (long long)r * nf;
+      const SF* fr = fbase + (long long)r * frs;
       SX* sx = sx_of(k);
       SC* sc = sc_of(k);
       SF* sf = sf_of(k);
@@ -686,8 +686,9 @@ __device__ __forceinline__ void prolong_smooth_mr_body(
 template <class T, class SC, class SX, class SF, class SO, int NS, int TXW>
 __global__ void __launch_bounds__(BX * BY)
 k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restrict__ xc,
-                    const SX* __restrict__ x, VRefE<SF> fin, SO* __restrict__ xo, int nrhs,
-                    int rpb, const int* __restrict__ done, unsigned long long* abytes) {
+                    const SX* __restrict__ x, VRefE<SF> fin, long long frs,
+                    SO* __restrict__ xo, int nrhs, int rpb, const int* __restrict__ done,
+                    unsigned long long* abytes) {
   using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
   extern __shared__ __align__(16) unsigned char smraw[];
   int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XP);
@@ -715,10 +716,10 @@ k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restric
                         fy0 + P::PH <= Lf.ny - 1;
   if (interior)
     prolong_smooth_mr_body<T, SC, SX, SF, SO, NS, TXW, true>(Lf, Lc, bc, omc, xc, x, fin,
-                                                             xo, na, act, smraw);
+                                                             frs, xo, na, act, smraw);
   else
     prolong_smooth_mr_body<T, SC, SX, SF, SO, NS, TXW, false>(Lf, Lc, bc, omc, xc, x, fin,
-                                                              xo, na, act, smraw);
+                                                              frs, xo, na, act, smraw);
 }
 
 // x = Minv f on the coarsest level (dense inverse built at setup)
@@ -797,7 +798,7 @@ inline int clamp_rpb(int rpb, int nrhs) { return (rpb <= 0 || rpb > nrhs) ? nrhs
 template <class T, class SF, class SX, class SC>
 void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
-                            cudaStream_t st, unsigned long long* abytes) {
+                            cudaStream_t st, unsigned long long* abytes, long long frs) {
   HZ_COUNT();
   using P = PreRestrictMR<T, SF>;
   auto kern = k_pre_restrict_mr<T, SF, SX, SC, kPreNS>;
@@ -808,15 +809,16 @@ void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, doub
   });
   rpb = clamp_rpb(rpb, nrhs);
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
   kern<<<grid, dim3(BX, BY), P::smem(kPreNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), f,
-                                                         x, fc, nrhs, rpb, done, abytes);
+                                                         frs, x, fc, nrhs, rpb, done, abytes);
 }
 
 template <class T, class SC, class SX, class SF, class SO, int TXW>
 void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                                 const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
                                 int rpb, const int* done, cudaStream_t st,
-                                unsigned long long* abytes) {
+                                unsigned long long* abytes, long long frs) {
   using P = ProlongSmoothMR<T, SC, SX, SF, TXW>;
   auto kern = k_prolong_smooth_mr<T, SC, SX, SF, SO, kProNS, TXW>;
   static std::once_flag once;
@@ -826,8 +828,10 @@ void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, 
   });
   rpb = clamp_rpb(rpb, nrhs);
   const dim3 grid((Lf.nx + TXW - 1) / TXW, (Lf.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
+  if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
   kern<<<grid, dim3(BX, BY), P::smem(kProNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), xc,
-                                                         x, f, xo, nrhs, rpb, done, abytes);
+                                                         x, f, frs, xo, nrhs, rpb, done,
+                                                         abytes);
 }
 
 // tile 0: 32 x 8 fine nodes per block, 1: 64 x 8
@@ -835,14 +839,14 @@ template <class T, class SC, class SX, class SF, class SO>
 void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                               const SC* xc, const SX* x, VRefE<SF> f, SO* xo, int nrhs,
                               int rpb, int tile, const int* done, cudaStream_t st,
-                              unsigned long long* abytes) {
+                              unsigned long long* abytes, long long frs) {
   HZ_COUNT();
   if (tile == 1)
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, 2 * BX>(Lf, Lc, bc, omega, xc, x, f, xo,
-                                                          nrhs, rpb, done, st, abytes);
+                                                          nrhs, rpb, done, st, abytes, frs);
   else
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, BX>(Lf, Lc, bc, omega, xc, x, f, xo, nrhs,
-                                                      rpb, done, st, abytes);
+                                                      rpb, done, st, abytes, frs);
 }
 
 template <class T, class SF, class SO>
@@ -909,11 +913,11 @@ template void launch_dense_mv<float, bf2, bf2>(int, const float2*, VRefE<bf2>, b
       const int*, cudaStream_t);                                                \
   template void launch_pre_restrict_mr<T, SF, SX, SC>(                          \
       const LevelDev&, const LevelDev&, int, double, VRefE<SF>, SX*, SC*, int,  \
-      int, const int*, cudaStream_t, unsigned long long*);                      \
+      int, const int*, cudaStream_t, unsigned long long*, long long);           \
   template void launch_prolong_smooth_mr<T, SC, SX, SF, SO>(                    \
       const LevelDev&, const LevelDev&, int, double, const SC*, const SX*,      \
       VRefE<SF>, SO*, int, int, int, const int*, cudaStream_t,                  \
-      unsigned long long*);                                                     \
+      unsigned long long*, long long);                                          \
   template void launch_prolong_smooth<T, SC, SX, SF, SO>(                       \
       const LevelDev&, const LevelDev&, int, Shift, const SC*, const SX*,       \
       VRefE<SF>, SO*, int, const int*, cudaStream_t);
@@ -921,5 +925,17 @@ HZ_VC_FUSED(double, double2, double2, double2, double2)
 HZ_VC_FUSED(float, float2, float2, float2, float2)
 HZ_VC_FUSED(float, float2, bf2, bf2, float2)
 HZ_VC_FUSED(float, bf2, bf2, bf2, bf2)
+
+// staged kernels whose top-level input is the FP16 inner basis
+#define HZ_VC_STAGED_IN16(SL)                                                   \
+  template void launch_pre_restrict_mr<float, __half2, SL, SL>(                 \
+      const LevelDev&, const LevelDev&, int, double, VRefE<__half2>, SL*, SL*,  \
+      int, int, const int*, cudaStream_t, unsigned long long*, long long);      \
+  template void launch_prolong_smooth_mr<float, SL, SL, __half2, float2>(       \
+      const LevelDev&, const LevelDev&, int, double, const SL*, const SL*,      \
+      VRefE<__half2>, float2*, int, int, int, const int*, cudaStream_t,         \
+      unsigned long long*, long long);
+HZ_VC_STAGED_IN16(float2)
+HZ_VC_STAGED_IN16(bf2)
 
 }  // namespace hz

@@ -182,12 +182,15 @@ def test_fused_vcycle_matches_oracle(bc, prec, tol):
                 assert rel(y2[r], y0[r]) < bound, (l, rpb, tile, r)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed_bf16"])
-def test_staged_vcycle_solve_matches_fused(prec):
+@pytest.mark.parametrize("prec,basis16", [("fp64", False), ("mixed_bf16", False),
+                                          ("mixed_bf16", True), ("mixed", True)])
+def test_staged_vcycle_solve_matches_fused(prec, basis16):
     """A batched solve whose right-hand sides converge at different
     iterations (so the staged kernels skip done RHS inside their groups)
     gives the same iterations (+-1) and solutions with the staged multi-RHS
-    V-cycle as with the fused one."""
+    V-cycle as with the fused one.  With the FP16 inner basis the staged
+    V-cycle reads its right-hand side straight from the basis (padded rows)
+    instead of from an FP32 copy."""
     n, k = 65, 40.0
     h = 1.0 / (n - 1)
     k2 = np.full((n, n), k * k)
@@ -196,7 +199,7 @@ def test_staged_vcycle_solve_matches_fused(prec):
     for tune in (dict(vcycle_fused=1),
                  dict(vcycle_fused=2, vcycle_rhs_per_block=2, vcycle_tile=1)):
         s = solver(n, n, h, k2, "sommerfeld", prec=prec, nrhs=3, coarse_tol=1e-6,
-                   coarse_maxit=300)
+                   coarse_maxit=300, inner_basis_fp16=basis16)
         s.set_tuning(**tune)
         x, info = s.solve(torch.from_numpy(b).cuda(), tol=1e-8)
         out.append((to_np(x), [(i.outer_iters, i.inner_iters_total) for i in info]))
