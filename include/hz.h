@@ -412,11 +412,15 @@ typedef struct {
                        2 the same fused kernels with each block walking over
                        vcycle_rhs_per_block right-hand sides, its tile's
                        coefficients held in registers and the input tiles
-                       copied ahead into a ring of shared-memory stages   */
+                       copied ahead into a ring of shared-memory stages;
+                       the restriction kernel gives each thread one coarse
+                       node and its 2 x 2 fine nodes                       */
   int vcycle_rhs_per_block; /* vcycle_fused = 2: right-hand sides per block
                        (0 = all of them; else 1..1024)                     */
-  int vcycle_tile;  /* vcycle_fused = 2: fine nodes per prolongation block,
-                       0 = 32 x 8, 1 = 64 x 8                              */
+  int vcycle_tile;  /* vcycle_fused = 2, prolongation + post-smoothing:
+                       0 = blocks of 32 x 8 fine nodes, one thread per fine
+                       node; 1 = blocks of 64 x 16 fine nodes, one thread
+                       per coarse cell and its 2 x 2 fine nodes            */
 } hz_tuning;
 
 /* Candidates hz_autotune times, in the order of its ms[] output:

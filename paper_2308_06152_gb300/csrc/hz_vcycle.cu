@@ -343,148 +343,252 @@ __device__ __forceinline__ C<T> nb_sum(const C<T>* xs, int c, int row, unsigned 
   return rfma(T((code >> 6) & 3u), xno, a);
 }
 
-template <class T, class SF>
-struct PreRestrictMR {
-  static constexpr int XW = 2 * BX + 3, XH = 2 * BY + 3, RW = 2 * BX + 1, RH = 2 * BY + 1;
-  static constexpr int NX = XW * XH, NR = RW * RH, NT = BX * BY;
-  static constexpr int N1 = (NX + NT - 1) / NT, N2 = (NR + NT - 1) / NT;
-  static constexpr int STAGE = align16(NX * (int)sizeof(SF));
-  static constexpr int XS = align16(NX * (int)sizeof(C<T>));
-  static constexpr int RS = align16(NR * (int)sizeof(C<T>));
-  static constexpr int smem(int ns, int rpb) { return ns * STAGE + XS + RS + 4 * rpb; }
-};
+// Two adjacent values p[0], p[1] of a staged or shared array as one vector
+// load (p aligned to twice the element size) or store.
+template <class S>
+__device__ __forceinline__ void ld_pair(const S* p, decltype(ld2(p, 0))& a,
+                                        decltype(ld2(p, 0))& b) {
+  if constexpr (sizeof(S) == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    S v[2];
+    memcpy(v, &u, sizeof(u));
+    a = ld2(v, 0);
+    b = ld2(v, 1);
+  } else if constexpr (sizeof(S) == 8) {
+    const float4 u = *reinterpret_cast<const float4*>(p);
+    S v[2];
+    memcpy(v, &u, sizeof(u));
+    a = ld2(v, 0);
+    b = ld2(v, 1);
+  } else {
+    a = ld2(p, 0);
+    b = ld2(p, 1);
+  }
+}
+template <class T>
+__device__ __forceinline__ void st_pair(C<T>* p, C<T> a, C<T> b) {
+  if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  } else {
+    p[0] = a;
+    p[1] = b;
+  }
+}
 
 // Fused pre-smoothing, residual and full-weighting restriction for one
-// BX x BY tile of coarse nodes and a group of rpb right-hand sides.
+// BX x BY tile of coarse nodes and a group of right-hand sides, one thread
+// per coarse node (I, J) owning the 2 x 2 fine nodes (2I + a, 2J + b), a, b
+// in {0, 1}: their f, x = D^-1 f and residual stay in registers, the
+// neighbours come from shared memory as aligned pairs, and the restriction
+// exchanges column sums with the thread below (shared memory) and the one to
+// the left (warp shuffle).  The fine tile with its halo is [2I0-2, 2I0+2BX]
+// x [2J0-2, 2J0+2BY], stored with rows of CW = XW + 1 (even) entries so that
+// the pairs of every thread are aligned.  Tiles off the boundary
+// (INTERIOR) need no tests; the others zero what lies outside the grid,
+// keep Dirichlet boundary nodes at zero and weight the neighbours of
+// Sommerfeld boundary rows (nb_code).
+template <class T, class SF>
+struct PreRestrictCell {
+  static constexpr int XW = 2 * BX + 3, XH = 2 * BY + 3, CW = XW + 1;
+  static constexpr int NQ = XW * XH, NT = BX * BY, NU = (NQ + NT - 1) / NT;
+  static constexpr int NHX = 3 * XW + 3 * 2 * BY;  // halo x entries
+  static constexpr int NHR = 2 * BX + 2 * BY + 1;  // halo residual entries
+  static constexpr int STAGE = align16(CW * XH * (int)sizeof(SF));
+  static constexpr int XS = align16(CW * XH * (int)sizeof(C<T>));
+  static constexpr int TR = align16((BY + 1) * 2 * BX * (int)sizeof(C<T>));
+  static constexpr int HC = align16((2 * BY + 1) * (int)sizeof(C<T>));
+  static constexpr int smem(int ns, int rpb) { return ns * STAGE + XS + TR + HC + 4 * rpb; }
+  static_assert(NHX <= NT && NHR <= NT, "halo entries per thread");
+};
+
+// residual row of a fine node with neighbour weights code (see nb_code)
+template <class T, bool INTERIOR>
+__device__ __forceinline__ C<T> resid_row(T ih2, T omc, C<T> f, C<T> xw, C<T> xe, C<T> xs,
+                                          C<T> xn, unsigned code) {
+  if (INTERIOR) return rfma(ih2, (xw + xe) + (xs + xn), omc * f);
+  C<T> a = T(code & 3u) * xw;
+  a = rfma(T((code >> 2) & 3u), xe, a);
+  a = rfma(T((code >> 4) & 3u), xs, a);
+  a = rfma(T((code >> 6) & 3u), xn, a);
+  return rfma(ih2, a, omc * f);
+}
+
 template <class T, class SF, class SX, class SC, int NS, bool INTERIOR>
-__device__ __forceinline__ void pre_restrict_mr_body(
+__device__ __forceinline__ void pre_restrict_cell_body(
     const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, VRefE<SF> fin, long long frs,
     SX* x, SC* fc, int na, const int* act, unsigned char* smraw) {
-  using P = PreRestrictMR<T, SF>;
-  constexpr int XW = P::XW, RW = P::RW, NX = P::NX, NR = P::NR, NT = P::NT;
-  constexpr int N1 = P::N1, N2 = P::N2, SV = P::STAGE / (int)sizeof(SF);
+  using P = PreRestrictCell<T, SF>;
+  constexpr int XW = P::XW, XH = P::XH, CW = P::CW, NQ = P::NQ, NT = P::NT, NU = P::NU;
+  constexpr int SV = P::STAGE / (int)sizeof(SF);
   SF* fst = reinterpret_cast<SF*>(smraw);
   C<T>* xs = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE);
-  C<T>* rsd = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE + P::XS);
-  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
-  const int tid = threadIdx.y * BX + threadIdx.x;
+  C<T>* tr = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE + P::XS);
+  C<T>* hc = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE + P::XS + P::TR);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int I = blockIdx.x * BX + tx, J = blockIdx.y * BY + ty;
+  const int fx0 = 2 * blockIdx.x * BX - 2, fy0 = 2 * blockIdx.y * BY - 2;
   const int nfx = Lf.nx, nfy = Lf.ny;
   const long long nf = (long long)nfx * nfy, nc = (long long)Lc.nx * Lc.ny;
   const SF* fbase = fin.get();
   const T ih2 = ih2_of<T>(Lf);
-  // x-tile entries: node (-1 outside the grid), copied (not a Dirichlet
-  // boundary node), one of the tile's own fine nodes (x written out)
-  int gid[N1];
-  unsigned cpm = 0, own = 0;
-  C<T> dv[N1];
+  const C<T>* dinv = dinv_of<T>(Lf);
+  // fine node (gi, gj): inside the grid / an unknown (not a Dirichlet
+  // boundary node)
+  auto in_grid = [&](int gi, int gj) { return gi >= 0 && gi < nfx && gj >= 0 && gj < nfy; };
+  auto unknown = [&](int gi, int gj) {
+    return INTERIOR || (in_grid(gi, gj) && !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy)));
+  };
+  // copies of the tile: global offset of entry q (shared index q + q / XW),
+  // -1 outside the grid (zero in every stage)
+  int gq[NU];
 #pragma unroll
-  for (int u = 0; u < N1; ++u) {
+  for (int u = 0; u < NU; ++u) {
     const int q = tid + u * NT;
-    const int gi = 2 * I0 - 2 + q % XW, gj = 2 * J0 - 2 + q / XW;
-    gid[u] = -1;
-    dv[u] = czero<T>();
-    if (q < NX && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy) {
-      gid[u] = gj * nfx + gi;
-      if (INTERIOR || !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy))) {
-        cpm |= 1u << u;
-        dv[u] = dinv_of<T>(Lf)[gid[u]];
-      }
-      if (gi >= 2 * I0 && gi < 2 * I0 + 2 * BX && gj >= 2 * J0 && gj < 2 * J0 + 2 * BY)
-        own |= 1u << u;
+    const int gi = fx0 + q % XW, gj = fy0 + q / XW;
+    gq[u] = q < NQ && (INTERIOR || in_grid(gi, gj)) ? gj * nfx + gi : -1;
+    if (!INTERIOR && q < NQ && gq[u] < 0)
+      for (int sidx = 0; sidx < NS; ++sidx) fst[sidx * SV + q + q / XW] = szero<SF>();
+  }
+  // own fine nodes: shared index of (2I, 2J), global index, D^-1 (zero for
+  // nodes that are not unknowns, so that their x is zero), and outside the
+  // interior: which are inside the grid (x stored), which are unknowns
+  // (residual kept) and the neighbour weights of each
+  const int o0 = (2 * ty + 2) * CW + 2 * tx + 2;
+  const int g00 = (2 * J) * nfx + 2 * I;
+  C<T> d[4];
+  unsigned ing = 0xfu, unk = 0xfu, code = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gi = 2 * I + (c & 1), gj = 2 * J + (c >> 1);
+    if (!INTERIOR) {
+      if (!in_grid(gi, gj)) ing &= ~(1u << c);
+      if (!unknown(gi, gj)) unk &= ~(1u << c);
+      if (unk >> c & 1u) code |= nb_code(bc, gi, gj, nfx, nfy) << (8 * c);
+    }
+    d[c] = (unk >> c & 1u) ? dinv[(long long)gj * nfx + gi] : czero<T>();
+  }
+  // halo x entry of this thread (rows 0, 1, XH-1 of the tile, then columns
+  // 0, 1, XW-1 of its inner rows)
+  int hxi = -1;
+  C<T> hxd = czero<T>();
+  if (tid < P::NHX) {
+    int lx, ly;
+    if (tid < 3 * XW) {
+      const int rr = tid / XW;
+      lx = tid % XW;
+      ly = rr == 2 ? XH - 1 : rr;
+    } else {
+      const int e = tid - 3 * XW, cc = e / (2 * BY);
+      ly = 2 + e % (2 * BY);
+      lx = cc == 2 ? XW - 1 : cc;
+    }
+    hxi = ly * CW + lx;
+    if (unknown(fx0 + lx, fy0 + ly)) hxd = dinv[(long long)(fy0 + ly) * nfx + fx0 + lx];
+  }
+  // halo residual entry: row 2J0-1 (tr row 0) or column 2I0-1 (hc)
+  int hri = -1;
+  unsigned hcode = 0;
+  bool hunk = true;
+  if (tid < P::NHR) {
+    const int lx = tid < 2 * BX ? tid + 2 : 1, ly = tid < 2 * BX ? 1 : 1 + tid - 2 * BX;
+    hri = ly * CW + lx;
+    if (!INTERIOR) {
+      hunk = unknown(fx0 + lx, fy0 + ly);
+      if (hunk) hcode = nb_code(bc, fx0 + lx, fy0 + ly, nfx, nfy);
     }
   }
-  // residual nodes: their x-tile offset and neighbour weights (unknowns)
-  int cix[N2];
-  unsigned code[N2];
-  unsigned rok = 0;
-#pragma unroll
-  for (int u = 0; u < N2; ++u) {
-    const int q = tid + u * NT;
-    const int ri = q % RW, rj = q / RW;
-    const int gi = 2 * I0 - 1 + ri, gj = 2 * J0 - 1 + rj;
-    cix[u] = (rj + 1) * XW + (ri + 1);
-    code[u] = 0;
-    if (q < NR && gi >= 0 && gi < nfx && gj >= 0 && gj < nfy &&
-        (INTERIOR || !(bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy)))) {
-      rok |= 1u << u;
-      if (!INTERIOR) code[u] = nb_code(bc, gi, gj, nfx, nfy);
-    }
-  }
-  // entries that are never copied hold zero in every stage
-#pragma unroll
-  for (int u = 0; u < N1; ++u) {
-    const int q = tid + u * NT;
-    if (q < NX && !(cpm >> u & 1u))
-      for (int sidx = 0; sidx < NS; ++sidx) fst[sidx * SV + q] = szero<SF>();
-  }
+  // the coarse node: stored (inside the coarse grid), zero (Dirichlet
+  // boundary)
+  const bool cst = INTERIOR || (I < Lc.nx && J < Lc.ny);
+  const bool cdir = !INTERIOR && bc == BC_DIRICHLET && cst && on_bnd(I, J, Lc.nx, Lc.ny);
   auto issue = [&](int k) {
     if (k < na) {
       const SF* fr = fbase + (long long)act[k] * frs;
       SF* stg = fst + (k % NS) * SV;
 #pragma unroll
-      for (int u = 0; u < N1; ++u)
-        if (cpm >> u & 1u) cp_async_el<sizeof(SF)>(stg + tid + u * NT, fr + gid[u]);
+      for (int u = 0; u < NU; ++u) {
+        const int q = tid + u * NT;
+        if (gq[u] >= 0) cp_async_el<sizeof(SF)>(stg + q + q / XW, fr + gq[u]);
+      }
     }
     cp_async_commit();
   };
 #pragma unroll
   for (int k = 0; k < NS - 1; ++k) issue(k);
-  const int I = I0 + threadIdx.x, J = J0 + threadIdx.y;
-  const bool cown = I < Lc.nx && J < Lc.ny;
-  const bool cdir = bc == BC_DIRICHLET && cown && on_bnd(I, J, Lc.nx, Lc.ny);
-  const int rc = (2 * threadIdx.y + 1) * RW + 2 * threadIdx.x + 1;
   for (int k = 0; k < na; ++k) {
     cp_async_wait<NS - 2>();
     __syncthreads();
     issue(k + NS - 1);
     const SF* stg = fst + (k % NS) * SV;
     const int r = act[k];
-    SX* xr = x + (long long)r * nf;
-#pragma unroll
-    for (int u = 0; u < N1; ++u) {
-      const int q = tid + u * NT;
-      if (q < NX) {
-        const C<T> v = cmul(dv[u], ld2(stg, q));
-        xs[q] = v;
-        if (own >> u & 1u) st2(xr, gid[u], v);
-      }
+    // x = D^-1 f: own nodes in registers and shared memory, halo in shared
+    C<T> f00, f10, f01, f11;
+    ld_pair(stg + o0, f00, f10);
+    ld_pair(stg + o0 + CW, f01, f11);
+    const C<T> x00 = cmul(d[0], f00), x10 = cmul(d[1], f10);
+    const C<T> x01 = cmul(d[2], f01), x11 = cmul(d[3], f11);
+    st_pair<T>(xs + o0, x00, x10);
+    st_pair<T>(xs + o0 + CW, x01, x11);
+    SX* xr = x + (long long)r * nf + g00;
+    if (ing & 1u) st2(xr, 0, x00);
+    if (ing & 2u) st2(xr, 1, x10);
+    if (ing & 4u) st2(xr, nfx, x01);
+    if (ing & 8u) st2(xr, nfx + 1, x11);
+    if (hxi >= 0) xs[hxi] = cmul(hxd, ld2(stg, hxi));
+    __syncthreads();
+    // residuals (1 - w) f + (1/h^2) sum of the (weighted) neighbours' x
+    C<T> t0, t1, xs0, xs1, xn0, xn1, xw0, xw1, xe0, xe1;
+    ld_pair(xs + o0 - CW, xs0, xs1);
+    ld_pair(xs + o0 + 2 * CW, xn0, xn1);
+    ld_pair(xs + o0 - 2, t0, xw0);
+    ld_pair(xs + o0 - 2 + CW, t1, xw1);
+    ld_pair(xs + o0 + 2, xe0, t0);
+    ld_pair(xs + o0 + 2 + CW, xe1, t1);
+    C<T> r00 = resid_row<T, INTERIOR>(ih2, omc, f00, xw0, x10, xs0, x01, code);
+    C<T> r10 = resid_row<T, INTERIOR>(ih2, omc, f10, x00, xe0, xs1, x11, code >> 8);
+    C<T> r01 = resid_row<T, INTERIOR>(ih2, omc, f01, xw1, x11, x00, xn0, code >> 16);
+    C<T> r11 = resid_row<T, INTERIOR>(ih2, omc, f11, x01, xe1, x10, xn1, code >> 24);
+    if (!INTERIOR) {
+      if (!(unk & 1u)) r00 = czero<T>();
+      if (!(unk & 2u)) r10 = czero<T>();
+      if (!(unk & 4u)) r01 = czero<T>();
+      if (!(unk & 8u)) r11 = czero<T>();
+    }
+    st_pair<T>(tr + (ty + 1) * 2 * BX + 2 * tx, r01, r11);
+    if (hri >= 0) {
+      C<T> v = resid_row<T, INTERIOR>(ih2, omc, ld2(stg, hri), xs[hri - 1], xs[hri + 1],
+                                      xs[hri - CW], xs[hri + CW], hcode);
+      if (!hunk) v = czero<T>();
+      if (tid < 2 * BX)
+        tr[tid] = v;
+      else
+        hc[tid - 2 * BX] = v;
     }
     __syncthreads();
-#pragma unroll
-    for (int u = 0; u < N2; ++u) {
-      const int q = tid + u * NT;
-      if (q < NR) {
-        C<T> v = czero<T>();
-        if (rok >> u & 1u) {
-          const int c = cix[u];
-          v = rfma(ih2, nb_sum<T, INTERIOR>(xs, c, XW, code[u]), omc * ld2(stg, c));
-        }
-        rsd[q] = v;
-      }
-    }
-    __syncthreads();
-    if (cown) {
-      C<T> acc = czero<T>();
-      if (!cdir) {
-        const C<T> r0 = (rsd[rc - RW - 1] + rsd[rc - RW + 1]) + T(2) * rsd[rc - RW];
-        const C<T> r1 = (rsd[rc - 1] + rsd[rc + 1]) + T(2) * rsd[rc];
-        const C<T> r2 = (rsd[rc + RW - 1] + rsd[rc + RW + 1]) + T(2) * rsd[rc + RW];
-        acc = T(0.0625) * ((r0 + r2) + T(2) * r1);
-      }
-      st2(fc, r * nc + (long long)J * Lc.nx + I, acc);
-    }
+    // full weighting: column sums over rows 2J-1..2J+1, then columns
+    C<T> s0, s1;
+    ld_pair(tr + ty * 2 * BX + 2 * tx, s0, s1);
+    s0 = s0 + (T(2) * r00 + r01);
+    s1 = s1 + (T(2) * r10 + r11);
+    C<T> sw;
+    sw.x = __shfl_up_sync(0xffffffffu, s1.x, 1);
+    sw.y = __shfl_up_sync(0xffffffffu, s1.y, 1);
+    if (tx == 0) sw = (hc[2 * ty] + hc[2 * ty + 2]) + T(2) * hc[2 * ty + 1];
+    if (cst)
+      st2(fc, r * nc + (long long)J * Lc.nx + I,
+          cdir ? czero<T>() : T(0.0625) * ((sw + s1) + T(2) * s0));
   }
   cp_async_wait<0>();
 }
 
 template <class T, class SF, class SX, class SC, int NS>
-__global__ void __launch_bounds__(BX * BY)
+__global__ void __launch_bounds__(BX * BY, 3)
 k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin, long long frs,
                   SX* __restrict__ x, SC* __restrict__ fc, int nrhs, int rpb,
                   const int* __restrict__ done, unsigned long long* abytes) {
-  using P = PreRestrictMR<T, SF>;
+  using P = PreRestrictCell<T, SF>;
   extern __shared__ __align__(16) unsigned char smraw[];
-  int* act = reinterpret_cast<int*>(smraw + NS * P::STAGE + P::XS + P::RS);
+  int* act = reinterpret_cast<int*>(smraw + P::smem(NS, 0));
   __shared__ int nact_s;
   const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
   const int na = list_active(done, r0, r1, act, &nact_s);
@@ -508,11 +612,11 @@ k_pre_restrict_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, VRefE<SF> fin, long l
   const bool interior = fx0 >= 1 && fy0 >= 1 && fx0 + P::XW <= Lf.nx - 1 &&
                         fy0 + P::XH <= Lf.ny - 1;
   if (interior)
-    pre_restrict_mr_body<T, SF, SX, SC, NS, true>(Lf, Lc, bc, omc, fin, frs, x, fc, na, act,
-                                                  smraw);
+    pre_restrict_cell_body<T, SF, SX, SC, NS, true>(Lf, Lc, bc, omc, fin, frs, x, fc, na,
+                                                    act, smraw);
   else
-    pre_restrict_mr_body<T, SF, SX, SC, NS, false>(Lf, Lc, bc, omc, fin, frs, x, fc, na,
-                                                   act, smraw);
+    pre_restrict_cell_body<T, SF, SX, SC, NS, false>(Lf, Lc, bc, omc, fin, frs, x, fc, na,
+                                                     act, smraw);
 }
 
 template <class T, class SC, class SX, class SF, int TXW>
@@ -722,6 +826,280 @@ k_prolong_smooth_mr(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restric
                                                               frs, xo, na, act, smraw);
 }
 
+// Fused coarse-grid correction and post-smoothing with one thread per
+// coarse cell (I, J) owning the fine nodes (2I + a, 2J + b), a, b in {0, 1}:
+// x' = x + P xc for them from the four coarse values of the cell, kept in
+// registers, then xo = (1 - w) x' + D^-1 (f + (1/h^2) sum of the weighted
+// neighbours' x'), the neighbours from shared memory as aligned pairs.  A
+// block covers 2BX x 2BY fine nodes; x' is staged with a one-node halo in
+// rows of CW = 2BX + 4 entries whose column 0 (node i0 - 2) is unused, so
+// that the pairs of every thread are aligned.  INTERIOR as for the
+// restriction.
+template <class T, class SC, class SX, class SF>
+struct ProlongSmoothCell {
+  static constexpr int FW = 2 * BX, FH = 2 * BY;        // own fine nodes
+  static constexpr int CW = FW + 4, XH = FH + 2;        // x / x' tile rows
+  static constexpr int QW = FW + 2, NQ = QW * XH;       // x entries copied
+  static constexpr int KW = BX + 2, KH = BY + 2, NK = KW * KH;  // coarse entries
+  static constexpr int NT = BX * BY, NU = (NQ + NT - 1) / NT, NV = (NK + NT - 1) / NT;
+  static constexpr int NHX = 2 * QW + 2 * FH;           // halo x' entries
+  static constexpr int OC = align16(CW * XH * (int)sizeof(SX));
+  static constexpr int OF = OC + align16(NK * (int)sizeof(SC));
+  static constexpr int STAGE = OF + align16(FW * FH * (int)sizeof(SF));
+  static constexpr int XP = align16(CW * XH * (int)sizeof(C<T>));
+  static constexpr int smem(int ns, int rpb) { return ns * STAGE + XP + 4 * rpb; }
+  static_assert(NHX <= NT, "halo entries per thread");
+};
+
+template <class T, class SC, class SX, class SF, class SO, int NS, bool INTERIOR>
+__device__ __forceinline__ void prolong_smooth_cell_body(
+    const LevelDev& Lf, const LevelDev& Lc, int bc, T omc, const SC* xc, const SX* x,
+    VRefE<SF> fin, long long frs, SO* xo, int na, const int* act, unsigned char* smraw) {
+  using P = ProlongSmoothCell<T, SC, SX, SF>;
+  constexpr int FW = P::FW, CW = P::CW, QW = P::QW, NQ = P::NQ, KW = P::KW, NK = P::NK;
+  constexpr int NT = P::NT, NU = P::NU, NV = P::NV;
+  C<T>* xp = reinterpret_cast<C<T>*>(smraw + NS * P::STAGE);
+  auto sx_of = [&](int k) { return reinterpret_cast<SX*>(smraw + (k % NS) * P::STAGE); };
+  auto sc_of = [&](int k) {
+    return reinterpret_cast<SC*>(smraw + (k % NS) * P::STAGE + P::OC);
+  };
+  auto sf_of = [&](int k) {
+    return reinterpret_cast<SF*>(smraw + (k % NS) * P::STAGE + P::OF);
+  };
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+  const int i0 = 2 * I0, j0 = 2 * J0;     // first own fine node
+  const int I = I0 + tx, J = J0 + ty;
+  const int nfx = Lf.nx, nfy = Lf.ny, ncx = Lc.nx, ncy = Lc.ny;
+  const long long nf = (long long)nfx * nfy, nc = (long long)ncx * ncy;
+  const SF* fbase = fin.get();
+  const T ih2 = ih2_of<T>(Lf);
+  const C<T>* dinv = dinv_of<T>(Lf);
+  auto in_grid = [&](int gi, int gj) { return gi >= 0 && gi < nfx && gj >= 0 && gj < nfy; };
+  auto dir_bnd = [&](int gi, int gj) {
+    return !INTERIOR && bc == BC_DIRICHLET && on_bnd(gi, gj, nfx, nfy);
+  };
+  // copies: x over [i0-1, i0+FW] x [j0-1, j0+FH] (tile column 1 on), the
+  // coarse correction over [I0-1, I0+BX] x [J0-1, J0+BY], f over the own
+  // nodes; -1 outside the grid (zero in every stage)
+  int gx[NU], gc[NV];
+#pragma unroll
+  for (int u = 0; u < NU; ++u) {
+    const int q = tid + u * NT;
+    const int gi = i0 - 1 + q % QW, gj = j0 - 1 + q / QW;
+    gx[u] = q < NQ && (INTERIOR || in_grid(gi, gj)) ? gj * nfx + gi : -1;
+  }
+#pragma unroll
+  for (int u = 0; u < NV; ++u) {
+    const int q = tid + u * NT;
+    const int ci = I0 - 1 + q % KW, cj = J0 - 1 + q / KW;
+    gc[u] = q < NK && (INTERIOR || (ci >= 0 && ci < ncx && cj >= 0 && cj < ncy))
+                ? cj * ncx + ci
+                : -1;
+  }
+  // own nodes: shared index of (2I, 2J) in the x tile, global index, D^-1,
+  // and outside the interior: inside the grid (stored), Dirichlet boundary
+  // (stored as zero, no correction), neighbour weights
+  const int o0 = (2 * ty + 1) * CW + 2 * tx + 2;
+  const int of0 = (2 * ty) * FW + 2 * tx;
+  const int k0 = (ty + 1) * KW + tx + 1;
+  const int g00 = (2 * J) * nfx + 2 * I;
+  C<T> d[4];
+  unsigned ing = 0xfu, dir = 0, code = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int gi = 2 * I + (c & 1), gj = 2 * J + (c >> 1);
+    if (!INTERIOR) {
+      if (!in_grid(gi, gj)) ing &= ~(1u << c);
+      else if (dir_bnd(gi, gj)) dir |= 1u << c;
+      else code |= nb_code(bc, gi, gj, nfx, nfy) << (8 * c);
+    }
+    d[c] = (ing >> c & 1u) ? dinv[(long long)gj * nfx + gi] : czero<T>();
+  }
+  // halo x' entry of this thread (tile rows 0 and XH-1 over columns 1..QW,
+  // then columns 1 and QW of the inner rows): shared index, coarse base
+  // index and steps of the bilinear interpolation, inside the grid,
+  // corrected
+  int hxi = -1, hcb = 0, hdx = 0, hdy = 0;
+  bool hin = true, hcor = true;
+  if (tid < P::NHX) {
+    int lx, ly;
+    if (tid < 2 * QW) {
+      lx = 1 + tid % QW;
+      ly = tid < QW ? 0 : P::XH - 1;
+    } else {
+      const int e = tid - 2 * QW;
+      ly = 1 + e % P::FH;
+      lx = e < P::FH ? 1 : QW;
+    }
+    const int gi = i0 - 2 + lx, gj = j0 - 1 + ly;
+    hxi = ly * CW + lx;
+    if (!INTERIOR) {
+      hin = in_grid(gi, gj);
+      hcor = hin && !dir_bnd(gi, gj);
+    }
+    hcb = ((gj >> 1) - (J0 - 1)) * KW + ((gi >> 1) - (I0 - 1));
+    hdx = gi & 1;
+    hdy = (gj & 1) * KW;
+  }
+  if (!INTERIOR) {
+    for (int sidx = 0; sidx < NS; ++sidx) {
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int q = tid + u * NT;
+        if (q < NQ && gx[u] < 0) sx_of(sidx)[(q / QW) * CW + 1 + q % QW] = szero<SX>();
+      }
+#pragma unroll
+      for (int u = 0; u < NV; ++u) {
+        const int q = tid + u * NT;
+        if (q < NK && gc[u] < 0) sc_of(sidx)[q] = szero<SC>();
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (!(ing >> c & 1u)) sf_of(sidx)[of0 + (c >> 1) * FW + (c & 1)] = szero<SF>();
+    }
+  }
+  auto issue = [&](int k) {
+    if (k < na) {
+      const int r = act[k];
+      const SX* xr = x + (long long)r * nf;
+      const SC* xcr = xc + (long long)r * nc;
+      const SF* fr = fbase + (long long)r * frs + g00;
+      SX* sx = sx_of(k);
+      SC* sc = sc_of(k);
+      SF* sf = sf_of(k);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        const int q = tid + u * NT;
+        if (gx[u] >= 0) cp_async_el<sizeof(SX)>(sx + (q / QW) * CW + 1 + q % QW, xr + gx[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < NV; ++u)
+        if (gc[u] >= 0) cp_async_el<sizeof(SC)>(sc + tid + u * NT, xcr + gc[u]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (ing >> c & 1u)
+          cp_async_el<sizeof(SF)>(sf + of0 + (c >> 1) * FW + (c & 1),
+                                  fr + (c >> 1) * nfx + (c & 1));
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) issue(k);
+  for (int k = 0; k < na; ++k) {
+    cp_async_wait<NS - 2>();
+    __syncthreads();
+    issue(k + NS - 1);
+    const SX* sx = sx_of(k);
+    const SC* sc = sc_of(k);
+    const SF* sf = sf_of(k);
+    const int r = act[k];
+    // x' = x + P xc: own nodes (registers and shared memory), halo
+    C<T> x00, x10, x01, x11;
+    ld_pair(sx + o0, x00, x10);
+    ld_pair(sx + o0 + CW, x01, x11);
+    {
+      const C<T> c00 = ld2(sc, k0), c10 = ld2(sc, k0 + 1);
+      const C<T> c01 = ld2(sc, k0 + KW), c11 = ld2(sc, k0 + KW + 1);
+      const C<T> h0 = T(0.5) * (c00 + c10), h1 = T(0.5) * (c01 + c11);
+      const C<T> v0 = T(0.5) * (c00 + c01);
+      if (INTERIOR || !(dir & 1u)) x00 = x00 + c00;
+      if (INTERIOR || !(dir & 2u)) x10 = x10 + h0;
+      if (INTERIOR || !(dir & 4u)) x01 = x01 + v0;
+      if (INTERIOR || !(dir & 8u)) x11 = x11 + T(0.5) * (h0 + h1);
+      if (!INTERIOR) {
+        if (!(ing & 1u)) x00 = czero<T>();
+        if (!(ing & 2u)) x10 = czero<T>();
+        if (!(ing & 4u)) x01 = czero<T>();
+        if (!(ing & 8u)) x11 = czero<T>();
+      }
+    }
+    st_pair<T>(xp + o0, x00, x10);
+    st_pair<T>(xp + o0 + CW, x01, x11);
+    if (hxi >= 0) {
+      C<T> v = ld2(sx, hxi);
+      if (hcor) {
+        const int b1 = hcb + hdy;
+        const C<T> a = T(0.5) * (ld2(sc, hcb) + ld2(sc, hcb + hdx));
+        const C<T> c = T(0.5) * (ld2(sc, b1) + ld2(sc, b1 + hdx));
+        v = v + T(0.5) * (a + c);
+      }
+      xp[hxi] = hin ? v : czero<T>();
+    }
+    __syncthreads();
+    // xo = (1 - w) x' + D^-1 (f + (1/h^2) sum of the neighbours' x')
+    C<T> t0, t1, xs0, xs1, xn0, xn1, xw0, xw1, xe0, xe1, f00, f10, f01, f11;
+    ld_pair(xp + o0 - CW, xs0, xs1);
+    ld_pair(xp + o0 + 2 * CW, xn0, xn1);
+    ld_pair(xp + o0 - 2, t0, xw0);
+    ld_pair(xp + o0 - 2 + CW, t1, xw1);
+    ld_pair(xp + o0 + 2, xe0, t0);
+    ld_pair(xp + o0 + 2 + CW, xe1, t1);
+    ld_pair(sf + of0, f00, f10);
+    ld_pair(sf + of0 + FW, f01, f11);
+    const C<T> y00 = cfma(d[0], resid_row<T, INTERIOR>(ih2, T(1), f00, xw0, x10, xs0, x01, code),
+                          omc * x00);
+    const C<T> y10 =
+        cfma(d[1], resid_row<T, INTERIOR>(ih2, T(1), f10, x00, xe0, xs1, x11, code >> 8),
+             omc * x10);
+    const C<T> y01 =
+        cfma(d[2], resid_row<T, INTERIOR>(ih2, T(1), f01, xw1, x11, x00, xn0, code >> 16),
+             omc * x01);
+    const C<T> y11 =
+        cfma(d[3], resid_row<T, INTERIOR>(ih2, T(1), f11, x01, xe1, x10, xn1, code >> 24),
+             omc * x11);
+    SO* orow = xo + (long long)r * nf + g00;
+    if (INTERIOR) {
+      st2(orow, 0, y00);
+      st2(orow, 1, y10);
+      st2(orow, nfx, y01);
+      st2(orow, nfx + 1, y11);
+    } else {
+      if (ing & 1u) st2(orow, 0, (dir & 1u) ? czero<T>() : y00);
+      if (ing & 2u) st2(orow, 1, (dir & 2u) ? czero<T>() : y10);
+      if (ing & 4u) st2(orow, nfx, (dir & 4u) ? czero<T>() : y01);
+      if (ing & 8u) st2(orow, nfx + 1, (dir & 8u) ? czero<T>() : y11);
+    }
+  }
+  cp_async_wait<0>();
+}
+
+template <class T, class SC, class SX, class SF, class SO, int NS>
+__global__ void __launch_bounds__(BX * BY, 3)
+k_prolong_smooth_cell(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restrict__ xc,
+                      const SX* __restrict__ x, VRefE<SF> fin, long long frs,
+                      SO* __restrict__ xo, int nrhs, int rpb, const int* __restrict__ done,
+                      unsigned long long* abytes) {
+  using P = ProlongSmoothCell<T, SC, SX, SF>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int* act = reinterpret_cast<int*>(smraw + P::smem(NS, 0));
+  __shared__ int nact_s;
+  const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  const int na = list_active(done, r0, r1, act, &nact_s);
+  if (na == 0) return;
+  if (abytes && threadIdx.x == 0 && threadIdx.y == 0) {
+    // algorithmic bytes as for k_prolong_smooth_mr, over this block's tile
+    const long long fw = min(P::FW, Lf.nx - (int)blockIdx.x * P::FW);
+    const long long fh = min(P::FH, Lf.ny - (int)blockIdx.y * P::FH);
+    unsigned long long b = (unsigned long long)na *
+        (fw * fh * (sizeof(SX) + sizeof(SF) + sizeof(SO)) +
+         ((fw + 1) / 2) * ((fh + 1) / 2) * sizeof(SC));
+    if (blockIdx.z == 0) b += (unsigned long long)(fw * fh * sizeof(C<T>));
+    atomicAdd(abytes, b);
+  }
+  // the x' tile [i0-1, i0+FW] x [j0-1, j0+FH] inside the grid and off its
+  // boundary rows and columns
+  const int fx0 = blockIdx.x * P::FW - 1, fy0 = blockIdx.y * P::FH - 1;
+  const bool interior = fx0 >= 1 && fy0 >= 1 && fx0 + P::FW + 2 <= Lf.nx - 1 &&
+                        fy0 + P::FH + 2 <= Lf.ny - 1;
+  if (interior)
+    prolong_smooth_cell_body<T, SC, SX, SF, SO, NS, true>(Lf, Lc, bc, omc, xc, x, fin, frs,
+                                                          xo, na, act, smraw);
+  else
+    prolong_smooth_cell_body<T, SC, SX, SF, SO, NS, false>(Lf, Lc, bc, omc, xc, x, fin, frs,
+                                                           xo, na, act, smraw);
+}
+
 // x = Minv f on the coarsest level (dense inverse built at setup)
 template <class T, class SF, class SO>
 __global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRefE<SF> fin,
@@ -800,18 +1178,17 @@ void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, doub
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
                             cudaStream_t st, unsigned long long* abytes, long long frs) {
   HZ_COUNT();
-  using P = PreRestrictMR<T, SF>;
   auto kern = k_pre_restrict_mr<T, SF, SX, SC, kPreNS>;
   static std::once_flag once;
   std::call_once(once, [&] {
     cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         P::smem(kPreNS, 1024));
+                         PreRestrictCell<T, SF>::smem(kPreNS, 1024));
   });
   rpb = clamp_rpb(rpb, nrhs);
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
   if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
-  kern<<<grid, dim3(BX, BY), P::smem(kPreNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), f,
-                                                         frs, x, fc, nrhs, rpb, done, abytes);
+  kern<<<grid, dim3(BX, BY), PreRestrictCell<T, SF>::smem(kPreNS, rpb), st>>>(
+      Lf, Lc, bc, (T)(1.0 - omega), f, frs, x, fc, nrhs, rpb, done, abytes);
 }
 
 template <class T, class SC, class SX, class SF, class SO, int TXW>
@@ -841,10 +1218,22 @@ void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, do
                               int rpb, int tile, const int* done, cudaStream_t st,
                               unsigned long long* abytes, long long frs) {
   HZ_COUNT();
-  if (tile == 1)
-    launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, 2 * BX>(Lf, Lc, bc, omega, xc, x, f, xo,
-                                                          nrhs, rpb, done, st, abytes, frs);
-  else
+  if (tile == 1) {
+    using P = ProlongSmoothCell<T, SC, SX, SF>;
+    auto kern = k_prolong_smooth_cell<T, SC, SX, SF, SO, kProNS>;
+    static std::once_flag once;
+    std::call_once(once, [&] {
+      cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           P::smem(kProNS, 1024));
+    });
+    rpb = clamp_rpb(rpb, nrhs);
+    const dim3 grid((Lf.nx + P::FW - 1) / P::FW, (Lf.ny + P::FH - 1) / P::FH,
+                    (nrhs + rpb - 1) / rpb);
+    if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
+    kern<<<grid, dim3(BX, BY), P::smem(kProNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), xc,
+                                                           x, f, frs, xo, nrhs, rpb, done,
+                                                           abytes);
+  } else
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, BX>(Lf, Lc, bc, omega, xc, x, f, xo, nrhs,
                                                       rpb, done, st, abytes, frs);
 }

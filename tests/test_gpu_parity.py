@@ -182,6 +182,36 @@ def test_fused_vcycle_matches_oracle(bc, prec, tol):
                 assert rel(y2[r], y0[r]) < bound, (l, rpb, tile, r)
 
 
+@pytest.mark.parametrize("bc", BCS)
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("mixed", 5e-5),
+                                      ("mixed_bf16", 2e-2)])
+def test_staged_vcycle_interior_tiles_match_oracle(bc, prec, tol):
+    """On a grid large enough for tiles away from the boundary (257 x 97:
+    the staged restriction and the 64 x 16 prolongation blocks then take
+    their test-free interior path, the ragged edge tiles the general one),
+    the staged V-cycle matches the oracle's from levels 0 and 1 and the
+    unfused kernels to rounding."""
+    nx, ny = 257, 97
+    h = 1.0 / (nx - 1)
+    k2 = rk2(ny, nx, 7)
+    s = solver(nx, ny, h, k2, bc, z="ho", prec=prec, nrhs=3)
+    orc = Oracle(nx, ny, h, k2, bc, z="ho", coarsest="direct")
+    bound = {"fp64": 1e-13, "mixed": 1e-6, "mixed_bf16": 2e-2}[prec]
+    for l in (0, 1):
+        lv = orc.levels[l]
+        f = wl.random_complex((3, lv.ny, lv.nx), 40 + l)
+        s.set_tuning(vcycle_fused=0)
+        y0 = to_np(s.apply("vcycle", f, l))
+        for rpb, tile in ((2, 1), (0, 0)):
+            s.set_tuning(vcycle_fused=2, vcycle_rhs_per_block=rpb, vcycle_tile=tile)
+            y2 = to_np(s.apply("vcycle", f, l))
+            for r in range(3):
+                ref = lv.to_full(orc.vcycle(lv.to_unknowns(f[r]), l))
+                assert rel(y2[r], ref) < tol, (l, rpb, tile, r, rel(y2[r], ref))
+                assert rel(y2[r], y0[r]) < bound, (l, rpb, tile, r, rel(y2[r], y0[r]))
+    s.close()
+
+
 @pytest.mark.parametrize("prec,basis16", [("fp64", False), ("mixed_bf16", False),
                                           ("mixed_bf16", True), ("mixed", True)])
 def test_staged_vcycle_solve_matches_fused(prec, basis16):
