@@ -421,14 +421,17 @@ typedef struct {
                        0 = blocks of 32 x 8 fine nodes, one thread per fine
                        node; 1 = blocks of 64 x 16 fine nodes, one thread
                        per coarse cell and its 2 x 2 fine nodes            */
+  int e_column_pairs; /* stored-stencil E: 0 one coarse node per thread;
+                       1 two nodes of a column per thread, which share the
+                       rows of x they read                                 */
 } hz_tuning;
 
 /* Candidates hz_autotune times, in the order of its ms[] output:
  * mdot_kernel 0, 1, 2; maxpy_kernel 0, 1, 2; galerkin_apply 0, 1;
  * e_rhs_per_block 0, 8, 4; vcycle_fused 0, 1; then vcycle_fused 2 with
  * (vcycle_rhs_per_block, vcycle_tile) = (4, 0), (8, 0), (16, 0), (4, 1),
- * (8, 1), (16, 1). */
-#define HZ_TUNE_CANDIDATES 19
+ * (8, 1), (16, 1); e_column_pairs 1 (with the e_rhs_per_block picked). */
+#define HZ_TUNE_CANDIDATES 20
 
 void hz_tuning_default(hz_tuning* t);
 

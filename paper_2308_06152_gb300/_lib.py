@@ -40,7 +40,7 @@ class HzTuning(ctypes.Structure):
     _fields_ = [("mdot_kernel", c_int), ("maxpy_kernel", c_int),
                 ("galerkin_apply", c_int), ("e_rhs_per_block", c_int),
                 ("vcycle_fused", c_int), ("vcycle_rhs_per_block", c_int),
-                ("vcycle_tile", c_int)]
+                ("vcycle_tile", c_int), ("e_column_pairs", c_int)]
 
 
 STATUS = {0: "HZ_OK", 1: "HZ_INVALID_ARG", 2: "HZ_INVALID_GRID",

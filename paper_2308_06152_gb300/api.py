@@ -307,7 +307,8 @@ class Solver:
                        "vcycle_fused=1",
                        "vcycle_fused=2,rpb=4,tile=0", "vcycle_fused=2,rpb=8,tile=0",
                        "vcycle_fused=2,rpb=16,tile=0", "vcycle_fused=2,rpb=4,tile=1",
-                       "vcycle_fused=2,rpb=8,tile=1", "vcycle_fused=2,rpb=16,tile=1")
+                       "vcycle_fused=2,rpb=8,tile=1", "vcycle_fused=2,rpb=16,tile=1",
+                       "e_column_pairs=1")
 
     def tuning_key(self, nrhs):
         """Cache key of a tuning: the device and every descriptor field

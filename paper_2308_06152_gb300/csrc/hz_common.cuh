@@ -263,10 +263,11 @@ void launch_probe_fill(const LevelDev& Lc, int P, int c0, int nprobe, double2* o
 template <class T>
 void launch_probe_extract(const LevelDev& Lc, int P, int c0, int nprobe,
                           const double2* ep, C<T>* S, cudaStream_t st);
-// (rpb: right-hand sides per block, 0 = all)
+// (pairs: two nodes of a column per thread; rpb: right-hand sides per
+// block, 0 = all)
 template <class T>
-void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C<T>* y,
-                      int nrhs, int rpb, const int* done, cudaStream_t st);
+void launch_stencil_e(const LevelDev& Lc, int R, int pairs, const C<T>* S, const C<T>* x,
+                      C<T>* y, int nrhs, int rpb, const int* done, cudaStream_t st);
 // y = E x with ReD-O4 (4th-order cross, O2 near the boundary) or ReD-cmpO4
 // (compact 4th-order 3x3 with 4th-order Sommerfeld ghosts)
 template <class T>

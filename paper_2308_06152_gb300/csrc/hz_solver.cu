@@ -626,7 +626,7 @@ void apply_E(hz_solver* s, const C<T>* x, C<T>* y, int nrhs, const int* done) {
   switch (s->d.ekind) {
     case HZ_E_GALERKIN:
       if (s->tune.galerkin_apply == 1)
-        launch_stencil_e<T>(Cc.dev(), s->d.zkind == HZ_Z_HO ? 2 : 1,
+        launch_stencil_e<T>(Cc.dev(), s->d.zkind == HZ_Z_HO ? 2 : 1, s->tune.e_column_pairs,
                             (const C<T>*)s->Sglk, x, y, nrhs, s->tune.e_rhs_per_block,
                             done, st);
       else
@@ -1462,10 +1462,11 @@ double time_vcycle(hz_solver* s, int nrhs, int fused, int rpb = 0, int tile = 0)
 }
 
 template <class T>
-double time_e(hz_solver* s, int nrhs, int apply, int rpb) {
+double time_e(hz_solver* s, int nrhs, int apply, int rpb, int pairs) {
   const hz_tuning saved = s->tune;
   s->tune.galerkin_apply = apply;
   s->tune.e_rhs_per_block = rpb;
+  s->tune.e_column_pairs = pairs;
   const long long n1 = s->lv[1].n;
   launch_tune_fill<C<T>>((C<T>*)s->sb, n1 * nrhs, 0x27d4eb2fu, s->st);
   const double ms = time_ms(s, 8, [&]() {
@@ -2674,6 +2675,7 @@ void hz_tuning_default(hz_tuning* t) {
   t->vcycle_fused = 0;
   t->vcycle_rhs_per_block = 0;
   t->vcycle_tile = 0;
+  t->e_column_pairs = 0;
 }
 
 hz_status hz_get_tuning(const hz_solver* s, hz_tuning* t) {
@@ -2687,7 +2689,8 @@ hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
       t->maxpy_kernel > 2 || t->galerkin_apply < 0 || t->galerkin_apply > 1 ||
       t->e_rhs_per_block < 0 || t->e_rhs_per_block > kMaxRhs || t->vcycle_fused < 0 ||
       t->vcycle_fused > 2 || t->vcycle_rhs_per_block < 0 ||
-      t->vcycle_rhs_per_block > kMaxRhs || t->vcycle_tile < 0 || t->vcycle_tile > 1)
+      t->vcycle_rhs_per_block > kMaxRhs || t->vcycle_tile < 0 || t->vcycle_tile > 1 ||
+      t->e_column_pairs < 0 || t->e_column_pairs > 1)
     return HZ_INVALID_ARG;
   if (t->galerkin_apply == 1 && !s->Sglk) {
     set_err(s, "galerkin_apply = 1 needs the Galerkin coarse operator (HZ_E_GALERKIN)");
@@ -2715,7 +2718,7 @@ hz_status hz_set_tuning(hz_solver* s, const hz_tuning* t) {
 // staged V-cycle candidates: RHS per block x prolongation tile
 constexpr int kVcycleRpb[3] = {4, 8, 16};
 constexpr int kVcycleStaged = 6;
-static_assert(11 + 2 + kVcycleStaged == HZ_TUNE_CANDIDATES, "candidate count");
+static_assert(11 + 2 + kVcycleStaged + 1 == HZ_TUNE_CANDIDATES, "candidate count");
 
 hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
   if (!s || nrhs < 1 || nrhs > s->d.nrhs_max) return HZ_INVALID_ARG;
@@ -2736,13 +2739,16 @@ hz_status hz_autotune(hz_solver* s, int nrhs, hz_tuning* best, double* ms) {
     const int rpb[3] = {0, 8, 4};
     int pick = 0;
     for (int k = 0; k < 3; ++k) {
-      tm[8 + k] = s->mixed ? time_e<float>(s, nrhs, 1, rpb[k])
-                           : time_e<double>(s, nrhs, 1, rpb[k]);
+      tm[8 + k] = s->mixed ? time_e<float>(s, nrhs, 1, rpb[k], 0)
+                           : time_e<double>(s, nrhs, 1, rpb[k], 0);
       if (tm[8 + k] < tm[8 + pick]) pick = k;
     }
     t.e_rhs_per_block = rpb[pick];
-    tm[6] = s->mixed ? time_e<float>(s, nrhs, 0, 0) : time_e<double>(s, nrhs, 0, 0);
-    tm[7] = tm[8 + pick];
+    tm[19] = s->mixed ? time_e<float>(s, nrhs, 1, rpb[pick], 1)
+                      : time_e<double>(s, nrhs, 1, rpb[pick], 1);
+    t.e_column_pairs = tm[19] < tm[8 + pick] ? 1 : 0;
+    tm[6] = s->mixed ? time_e<float>(s, nrhs, 0, 0, 0) : time_e<double>(s, nrhs, 0, 0, 0);
+    tm[7] = t.e_column_pairs ? tm[19] : tm[8 + pick];
     t.galerkin_apply = tm[7] < tm[6] ? 1 : 0;
   }
   if (s->L >= 1) {

@@ -680,6 +680,93 @@ k_stencil_e(LevelDev Lc, const C<T>* __restrict__ S, const C<T>* __restrict__ x,
 }
 
 
+// The same product with each thread applying the stencil at two nodes of a
+// column, (I, J) and (I, J + 1): the 2R + 2 rows of x it reads serve both
+// (about 0.6 of the shared-memory loads per node of the one-node form), the
+// block is BX x BY / 2 threads over the same BX x BY tile of nodes.
+template <class T, int R>
+__global__ void __launch_bounds__(BX * BY / 2, 4)
+k_stencil_e2(LevelDev Lc, const C<T>* __restrict__ S, const C<T>* __restrict__ x,
+             C<T>* __restrict__ y, int nrhs, int rpb, const int* __restrict__ done) {
+  using Q = StencilE<T, R>;
+  constexpr int P = Q::P, K = Q::K, TX = Q::TX, TY = Q::TY;
+  constexpr int NT = BX * BY / 2, NPT = (TY * TX + NT - 1) / NT;
+  constexpr int NS = kStencilNS, SV = Q::STAGE / (int)sizeof(C<T>);
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C<T>* xs = reinterpret_cast<C<T>*>(smraw);
+  int* act = reinterpret_cast<int*>(smraw + NS * Q::STAGE);
+  __shared__ int nact_s;
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * BX + tx;
+  const int I0 = blockIdx.x * BX, J0 = blockIdx.y * BY;
+  const int I = I0 + tx, J = J0 + 2 * ty;
+  const int ncx = Lc.nx, ncy = Lc.ny;
+  const long long nc = (long long)ncx * ncy;
+  const bool in0 = I < ncx && J < ncy, in1 = I < ncx && J + 1 < ncy;
+  const long long id = (long long)J * ncx + I;
+  const int r0 = blockIdx.z * rpb, r1 = min(nrhs, r0 + rpb);
+  if (tid < 32) {
+    int cnt = 0;
+    for (int base = r0; base < r1; base += 32) {
+      const int r = base + tid;
+      const bool a = r < r1 && !(done && done[r]);
+      const unsigned m = __ballot_sync(0xffffffffu, a);
+      if (a) act[cnt + __popc(m & ((1u << tid) - 1u))] = r;
+      cnt += __popc(m);
+    }
+    if (tid == 0) nact_s = cnt;
+  }
+  __syncthreads();
+  const int na = nact_s;
+  if (na == 0) return;
+  C<T> c0[K], c1[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    c0[k] = in0 ? S[(long long)k * nc + id] : czero<T>();
+    c1[k] = in1 ? S[(long long)k * nc + id + ncx] : czero<T>();
+  }
+  int gid[NPT];
+#pragma unroll
+  for (int u = 0; u < NPT; ++u) {
+    const int q = tid + u * NT;
+    const int gi = I0 - R + q % TX, gj = J0 - R + q / TX;
+    gid[u] = (q < TY * TX && gi >= 0 && gi < ncx && gj >= 0 && gj < ncy) ? gj * ncx + gi : -1;
+    if (q < TY * TX && gid[u] < 0)
+      for (int sidx = 0; sidx < NS; ++sidx) xs[sidx * SV + q] = czero<T>();
+  }
+  auto issue = [&](int k) {
+    if (k < na) {
+      const C<T>* xr = x + (long long)act[k] * nc;
+      C<T>* stg = xs + (k % NS) * SV;
+#pragma unroll
+      for (int u = 0; u < NPT; ++u)
+        if (gid[u] >= 0) cp_async_el<sizeof(C<T>)>(stg + tid + u * NT, xr + gid[u]);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int k = 0; k < NS - 1; ++k) issue(k);
+  for (int k = 0; k < na; ++k) {
+    cp_async_wait<NS - 2>();
+    __syncthreads();
+    issue(k + NS - 1);
+    const C<T>* stg = xs + (k % NS) * SV + (2 * ty) * TX + tx;
+    C<T> a0 = czero<T>(), a1 = czero<T>();
+#pragma unroll
+    for (int b = 0; b <= P; ++b)
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        const C<T> v = stg[b * TX + a];
+        if (b < P) a0 = cfma(c0[b * P + a], v, a0);
+        if (b > 0) a1 = cfma(c1[(b - 1) * P + a], v, a1);
+      }
+    C<T>* yr = y + (long long)act[k] * nc + id;
+    if (in0) yr[0] = a0;
+    if (in1) yr[ncx] = a1;
+  }
+  cp_async_wait<0>();
+}
+
+
 template <class Ti, class To>
 __global__ void k_add_conv(VRef<Ti> a, const C<Ti>* __restrict__ b, VRef<To> out,
                            long long n, const int* __restrict__ done) {
@@ -927,8 +1014,8 @@ void launch_probe_extract(const LevelDev& Lc, int P, int c0, int nprobe,
                                                                           S);
 }
 template <class T>
-void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C<T>* y,
-                      int nrhs, int rpb, const int* done, cudaStream_t st) {
+void launch_stencil_e(const LevelDev& Lc, int R, int pairs, const C<T>* S, const C<T>* x,
+                      C<T>* y, int nrhs, int rpb, const int* done, cudaStream_t st) {
   HZ_COUNT();
   if (rpb <= 0 || rpb > nrhs) rpb = nrhs;
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
@@ -940,7 +1027,23 @@ void launch_stencil_e(const LevelDev& Lc, int R, const C<T>* S, const C<T>* x, C
     cudaFuncSetAttribute((const void*)k_stencil_e<T, 1>,
                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                          StencilE<T, 1>::smem(1024));
+    cudaFuncSetAttribute((const void*)k_stencil_e2<T, 2>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         StencilE<T, 2>::smem(1024));
+    cudaFuncSetAttribute((const void*)k_stencil_e2<T, 1>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         StencilE<T, 1>::smem(1024));
   });
+  if (pairs) {
+    const dim3 blk(BX, BY / 2);
+    if (R == 2)
+      k_stencil_e2<T, 2><<<grid, blk, StencilE<T, 2>::smem(rpb), st>>>(Lc, S, x, y, nrhs,
+                                                                      rpb, done);
+    else
+      k_stencil_e2<T, 1><<<grid, blk, StencilE<T, 1>::smem(rpb), st>>>(Lc, S, x, y, nrhs,
+                                                                      rpb, done);
+    return;
+  }
   if (R == 2)
     k_stencil_e<T, 2><<<grid, dim3(BX, BY), StencilE<T, 2>::smem(rpb), st>>>(Lc, S, x, y,
                                                                            nrhs, rpb, done);
@@ -1082,7 +1185,7 @@ void launch_extract_inverse(const LevelDev& L, int bc, const double2* aug,
                                  const int*, cudaStream_t);                     \
   template void launch_probe_extract<T>(const LevelDev&, int, int, int,         \
                                         const double2*, C<T>*, cudaStream_t);   \
-  template void launch_stencil_e<T>(const LevelDev&, int, const C<T>*,          \
+  template void launch_stencil_e<T>(const LevelDev&, int, int, const C<T>*,     \
                                     const C<T>*, C<T>*, int, int, const int*,   \
                                     cudaStream_t);                              \
   /* end */

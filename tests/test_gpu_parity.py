@@ -110,17 +110,19 @@ def test_stored_galerkin_stencil(bc, z, prec, tol):
     """stcl-op-Glk: the Galerkin product's per-node stencil, extracted at
     setup by FP64 probing, applied to several right-hand sides against the
     oracle's explicit R_Z A Z (FP64 to 1e-12; FP32-stored coefficients and
-    FP32 arithmetic to 2e-6, below the on-the-fly FP32 product's error)."""
+    FP32 arithmetic to 2e-6, below the on-the-fly FP32 product's error), by
+    the one-node and the two-nodes-per-thread kernels (the coarse grid's
+    odd row count leaves a half-filled pair in the last tile row)."""
     k2 = rk2(NY, NX, 2)
     s = solver(NX, NY, H, k2, bc, z=z, e="galerkin", prec=prec, nrhs=3)
     orc = Oracle(NX, NY, H, k2, bc, z=z, e="galerkin", coarsest="direct")
     lc = orc.levels[1]
     xc = wl.random_complex((3, lc.ny, lc.nx), 15)
-    for rpb in (0, 2, 1):
-        s.set_tuning(galerkin_apply=1, e_rhs_per_block=rpb)
+    for rpb, pairs in ((0, 0), (2, 0), (1, 0), (0, 1), (2, 1), (1, 1)):
+        s.set_tuning(galerkin_apply=1, e_rhs_per_block=rpb, e_column_pairs=pairs)
         y = to_np(s.apply("coarse_e", xc))
         for r in range(3):
-            assert rel(y[r], oapply(orc, orc.E, 1, 1, xc[r])) < tol, (rpb, r)
+            assert rel(y[r], oapply(orc, orc.E, 1, 1, xc[r])) < tol, (rpb, pairs, r)
     s.set_tuning(galerkin_apply=0)
     y0 = to_np(s.apply("coarse_e", xc))
     assert rel(y0[0], oapply(orc, orc.E, 1, 1, xc[0])) < max(tol, 2e-5)
@@ -643,7 +645,10 @@ def test_autotune_picks_valid_choices_and_caches(tmp_path):
         assert t[cls] == min(range(3), key=lambda v: ms[f"{cls}={v}"])
     rpb = min((0, 8, 4), key=lambda v: ms[f"e_rhs_per_block={v}"])
     assert t["e_rhs_per_block"] == rpb
-    assert ms["galerkin_apply=1"] == ms[f"e_rhs_per_block={rpb}"]
+    pairs = 1 if ms["e_column_pairs=1"] < ms[f"e_rhs_per_block={rpb}"] else 0
+    assert t["e_column_pairs"] == pairs
+    assert ms["galerkin_apply=1"] == min(ms[f"e_rhs_per_block={rpb}"],
+                                         ms["e_column_pairs=1"])
     ga = 1 if ms["galerkin_apply=1"] < ms["galerkin_apply=0"] else 0
     assert t["galerkin_apply"] == ga
     vc = [c for c in s.TUNE_CANDIDATES if c.startswith("vcycle_fused")]
