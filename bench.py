@@ -201,8 +201,8 @@ PREC_TEXT = {"mixed": "complex-FP32 preconditioner in FP64 FGMRES",
 
 KERNEL_NAMES = {"mdot": "k_mdot (CGS2 multi-vector dot product)",
                 "maxpy": "k_maxpy (CGS2 multi-vector update)",
-                "vcycle": ("k_pre_restrict_mr + k_prolong_smooth_mr (top level of "
-                           "every V-cycle, staged form)")}
+                "vcycle": ("k_pre_restrict_mr + k_prolong_smooth_mr / _cell (top "
+                           "level of every V-cycle, staged form)")}
 
 
 def hbm_peak():
@@ -335,7 +335,12 @@ def workload_config(args, cfg, model, world, b_np):
 # ncu on the same kernel and storage (the summary under profiles/ names the
 # command); traffic scales with the rows streamed, so a bench launch's
 # traffic is this ratio times its algorithmic bytes.
-TRAFFIC = {}
+TRAFFIC = {
+    ("mdot", "layered_2305x769_b64", 1): (1.006, "profiles/dram_layered_2305x769_b64.md"),
+    ("maxpy", "layered_2305x769_b64", 0): (0.999, "profiles/dram_layered_2305x769_b64.md"),
+    ("vcycle", "layered_2305x769_b64", (2, 8, 0)): (
+        0.885, "profiles/dram_layered_2305x769_b64.md"),
+}
 
 
 def roofline_entry(args, tuning, kc, prof, prof_ms):
@@ -365,6 +370,9 @@ def _variant(kc, tuning):
         return tuning.get("mdot_kernel")
     if kc == "maxpy":
         return tuning.get("maxpy_kernel")
+    if kc == "vcycle":
+        return (tuning.get("vcycle_fused"), tuning.get("vcycle_rhs_per_block"),
+                tuning.get("vcycle_tile"))
     return None
 
 
@@ -411,6 +419,8 @@ def run_ours(args):
         solver.set_tuning(vcycle_rhs_per_block=args.vcycle_rpb)
     if args.vcycle_tile is not None:
         solver.set_tuning(vcycle_tile=args.vcycle_tile)
+    if args.e_pairs is not None:
+        solver.set_tuning(e_column_pairs=args.e_pairs)
     tuning = solver.get_tuning()
     stream = solver.stream
     b = torch.from_numpy(b_np).cuda()
@@ -654,6 +664,8 @@ def main():
                     help="force hz_tuning.vcycle_rhs_per_block")
     ap.add_argument("--vcycle-tile", type=int, choices=[0, 1], default=None,
                     help="force hz_tuning.vcycle_tile")
+    ap.add_argument("--e-pairs", type=int, choices=[0, 1], default=None,
+                    help="force hz_tuning.e_column_pairs")
     ap.add_argument("--profile-steps", type=int, default=1,
                     help="steps timed per kernel for the roofline entry")
     ap.add_argument("--profile-kernel", default="mdot,maxpy,vcycle",
