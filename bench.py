@@ -80,6 +80,12 @@ WORKLOADS = {
                                  nrhs=64, sources="surface_line",
                                  coarse_tol=1e-1, coarse_maxit=160,
                                  outer_maxit=30, tol=1e-6),
+    # the same model with 4 shots, for ncu captures (about 6 GB of workspace)
+    "layered_2305x769_b4_prof": dict(model=("layered", 2301, 751, 31.25),
+                                     bc="sommerfeld", z="ho", e="galerkin",
+                                     nrhs=4, sources="surface_line",
+                                     coarse_tol=1e-1, coarse_maxit=160,
+                                     outer_maxit=4, tol=1e-6),
 }
 DEFAULT_WORKLOAD = "layered_2305x769_b64"
 ORACLE_COUNTS = os.path.join(ROOT, "tests", "golden", "oracle_bench_counts.json")

@@ -242,19 +242,25 @@ constexpr int MAXPY_TILE = 512;
 
 // One (RHS r, chunk blk) tile of k_maxpy: w's chunk is updated in registers
 // across all j+1 basis rows, written once, and its squared norm reduced.
+// The coefficients come straight from the (L1-resident) column hcol rather
+// than through shared memory, so the only block barrier of a tile is the
+// one of the norm reduction, whose per-warp sums alternate between the two
+// halves of red[2][NT/32] (par): a warp can write the next tile's sum while
+// thread 0 still reads this one's, and cannot get two tiles ahead of it.
+// Returns false (no barrier taken) for a tile whose RHS takes no part.
 template <class T, class SB>
-__device__ __forceinline__ void maxpy_tile(const SB* __restrict__ V, long long vstride,
+__device__ __forceinline__ bool maxpy_tile(const SB* __restrict__ V, long long vstride,
                                            long long rs, C<T>* __restrict__ w, long long n,
                                            const KState& ks, int pass, int j, int r,
-                                           int blk, C<T>* hs, double* red) {
-  constexpr int TILE = MAXPY_TILE;
+                                           int blk, double* red, int par) {
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
-  if (ks.done[r] || (pass && !ks.reorth[r])) return;
+  if (ks.done[r] || (pass && !ks.reorth[r])) return false;
   // algorithmic bytes of this RHS: read w and basis 0..j, write w
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (2 * sizeof(C<T>) + (j + 1) * sizeof(SB)));
   const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
   C<T>* wr = w + r * n;
+  const double2* hc = ks.hcol + (long long)r * (ks.m + 1);
   C<T> acc[EPT];
 #pragma unroll
   for (int k = 0; k < VPT; ++k)
@@ -263,34 +269,27 @@ __device__ __forceinline__ void maxpy_tile(const SB* __restrict__ V, long long v
       const long long e = (g0 + (long long)k * NT) * W + u;
       acc[k * W + u] = (e < n) ? wr[e] : czero<T>();
     }
-  for (int t0 = 0; t0 <= j; t0 += TILE) {
-    const int cnt = min(TILE, j + 1 - t0);
-    __syncthreads();
-    for (int q = threadIdx.x; q < cnt; q += NT)
-      hs[q] = cvt_to<T>(ks.hcol[(long long)r * (ks.m + 1) + t0 + q]);
-    __syncthreads();
-    for (int q0 = 0; q0 < cnt; q0 += G) {
-      uint4 raw[G][VPT];
+  for (int q0 = 0; q0 <= j; q0 += G) {
+    uint4 raw[G][VPT];
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const SB* vr = V + (long long)(t0 + q0 + q) * vstride + r * rs;
+    for (int q = 0; q < G; ++q) {
+      const SB* vr = V + (long long)(q0 + q) * vstride + r * rs;
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-          const long long g = g0 + (long long)k * NT;
-          raw[q][k] = (q0 + q < cnt && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
-        }
+      for (int k = 0; k < VPT; ++k) {
+        const long long g = g0 + (long long)k * NT;
+        raw[q][k] = (q0 + q <= j && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
       }
+    }
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        const C<T> h = (q0 + q < cnt) ? hs[q0 + q] : czero<T>();
+    for (int q = 0; q < G; ++q) {
+      const C<T> h = (q0 + q <= j) ? cvt_to<T>(hc[q0 + q]) : czero<T>();
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-          static_for<W>([&](auto U) {
-            const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
-            acc[k * W + U.value].x -= v.x * h.x - v.y * h.y;
-            acc[k * W + U.value].y -= v.x * h.y + v.y * h.x;
-          });
-        }
+      for (int k = 0; k < VPT; ++k) {
+        static_for<W>([&](auto U) {
+          const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
+          acc[k * W + U.value].x -= v.x * h.x - v.y * h.y;
+          acc[k * W + U.value].y -= v.x * h.y + v.y * h.x;
+        });
       }
     }
   }
@@ -305,21 +304,31 @@ __device__ __forceinline__ void maxpy_tile(const SB* __restrict__ V, long long v
         wn += acc[k * W + u].x * acc[k * W + u].x + acc[k * W + u].y * acc[k * W + u].y;
       }
     }
-  const double t = block_sum((double)wn, red);
-  if (threadIdx.x == 0) ks.npart[(long long)r * ks.nblk_max + blk] = t;
+  double v = (double)wn;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  double* rp = red + par * (NT / 32);
+  if ((threadIdx.x & 31) == 0) rp[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < NT / 32; ++q) t += rp[q];
+    ks.npart[(long long)r * ks.nblk_max + blk] = t;
+  }
+  return true;
 }
 
 // w -= sum_{i<=j} V_i hcol_i, and the partial ||w||^2 of the result in npart
 template <class T, class SB>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
         C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
-  __shared__ C<T> hs[MAXPY_TILE];
-  __shared__ double red[NT / 32];
+  __shared__ double red[2 * (NT / 32)];
   const int j = *ks.jctr;
+  int par = 0;
   for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
-    maxpy_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
-                      (int)(tile % nblk), hs, red);
+    if (maxpy_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
+                          (int)(tile % nblk), red, par))
+      par ^= 1;
 }
 
 // The same two kernels over the tiles of several grids (GroupDesc).
@@ -342,16 +351,17 @@ k_mdot_group(const __grid_constant__ GroupDesc gd, int pass) {
 template <class T, class SB>
 __global__ void __launch_bounds__(NT)
 k_maxpy_group(const __grid_constant__ GroupDesc gd, int pass) {
-  __shared__ C<T> hs[MAXPY_TILE];
-  __shared__ double red[NT / 32];
+  __shared__ double red[2 * (NT / 32)];
   const long long total = gd.start[gd.count];
+  int par = 0;
   for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
     int g = 0;
     while (tile >= gd.start[g + 1]) ++g;
     const GroupMember& M = gd.m[g];
     const long long lt = tile - gd.start[g];
-    maxpy_tile<T, SB>((const SB*)M.V, M.vstride, M.rs, (C<T>*)M.w, M.n, M.ks, pass,
-                      *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), hs, red);
+    if (maxpy_tile<T, SB>((const SB*)M.V, M.vstride, M.rs, (C<T>*)M.w, M.n, M.ks, pass,
+                          *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), red, par))
+      par ^= 1;
   }
 }
 
