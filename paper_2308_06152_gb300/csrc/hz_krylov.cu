@@ -104,25 +104,73 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
+// Warp sum of NV values at once (NV a power of two <= 8): log2(NV) halving
+// exchanges leave each lane one value, then plain xor steps finish the sum.
+// Returns the sum of value *idx; every lane of a group of 32/NV lanes holds
+// the same value.
+template <int CNT, class T>
+__device__ __forceinline__ void halve(T* v, int lane, int o) {
+  const bool up = (lane & o) != 0;
+#pragma unroll
+  for (int k = 0; k < CNT / 2; ++k) {
+    const T send = up ? v[k] : v[k + CNT / 2];
+    const T keep = up ? v[k + CNT / 2] : v[k];
+    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+  }
+}
+template <int NV, class T>
+__device__ __forceinline__ T multi_reduce(T* v, int lane, int* idx) {
+  int o = 16, id = 0;
+  if constexpr (NV >= 2) {
+    halve<NV>(v, lane, 16);
+    id += ((lane >> 4) & 1) * (NV / 2);
+    o = 8;
+  }
+  if constexpr (NV >= 4) {
+    halve<NV / 2>(v, lane, 8);
+    id += ((lane >> 3) & 1) * (NV / 4);
+    o = 4;
+  }
+  if constexpr (NV >= 8) {
+    halve<NV / 4>(v, lane, 4);
+    id += ((lane >> 2) & 1) * (NV / 8);
+    o = 2;
+  }
+  T s = v[0];
+  for (; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  *idx = id;
+  return s;
+}
+
 constexpr int MDOT_TILE = 32;
 
 // One (RHS r, chunk blk) tile of k_mdot: w's chunk stays in registers while
-// the j+1 basis rows stream through (G rows' loads issued before use).
+// the j+1 basis rows stream through (G rows' loads issued before use).  The
+// partial dots of up to four rows at a time are summed over the warp
+// together (9 shuffles for 8 values), the warps' sums of MDOT_TILE rows are combined
+// after one block barrier, and the staging wred[2][NW][MDOT_TILE] (and red,
+// for pass 0's ||w||^2) alternates between its halves (par, flipped after
+// every barrier), so that no second barrier is needed before the next rows'
+// sums are written.  Returns false (no barrier taken) when the RHS takes no
+// part.
 template <class T, class SB>
-__device__ __forceinline__ void mdot_tile(const SB* __restrict__ V, long long vstride,
+__device__ __forceinline__ bool mdot_tile(const SB* __restrict__ V, long long vstride,
                                           long long rs, const C<T>* __restrict__ w,
                                           long long n, const KState& ks, int pass, int j,
-                                          int r, int blk, double2 (*wred)[MDOT_TILE],
-                                          double* red) {
+                                          int r, int blk, double2* wred, double* red,
+                                          int& par) {
   constexpr int TILE = MDOT_TILE, NW = NT / 32;
   constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
-  if (ks.done[r] || (pass && !ks.reorth[r])) return;
+  constexpr int RB = G < 4 ? G : 4, NV2 = 2 * RB;  // rows per warp reduction
+  static_assert(G % RB == 0, "row groups");
+  if (ks.done[r] || (pass && !ks.reorth[r])) return false;
   // algorithmic bytes of this RHS: w and basis vectors 0..j, read once
   if (ks.abytes && blk == 0 && threadIdx.x == 0)
     atomicAdd(ks.abytes, (unsigned long long)n * (sizeof(C<T>) + (j + 1) * sizeof(SB)));
   // thread element e(k, u) = blk*CHUNK + (k*NT + tid)*W + u
   const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
   const C<T>* wr = w + r * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   C<T> wv[EPT];
   T wn = T(0);
 #pragma unroll
@@ -134,12 +182,14 @@ __device__ __forceinline__ void mdot_tile(const SB* __restrict__ V, long long vs
       wn += wv[k * W + u].x * wv[k * W + u].x + wv[k * W + u].y * wv[k * W + u].y;
     }
   if (pass == 0) {
-    const double t = block_sum((double)wn, red);
-    if (threadIdx.x == 0) ks.wpart[(long long)r * ks.nblk_max + blk] = t;
+    double v = (double)wn;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[par * NW + warp] = v;
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool first = true;
   for (int t0 = 0; t0 <= j; t0 += TILE) {
     const int tend = min(t0 + TILE, j + 1);
+    double2* wh = wred + par * NW * TILE + warp * TILE;
     for (int i0 = t0; i0 < tend; i0 += G) {
       // issue every load of the G basis vectors first (16 per thread)
       uint4 raw[G][VPT];
@@ -153,38 +203,52 @@ __device__ __forceinline__ void mdot_tile(const SB* __restrict__ V, long long vs
         }
       }
 #pragma unroll
-      for (int q = 0; q < G; ++q) {
-        C<T> d = czero<T>();
+      for (int q4 = 0; q4 < G; q4 += RB) {
+        T d[NV2];
 #pragma unroll
-        for (int k = 0; k < VPT; ++k) {
-          static_for<W>([&](auto U) {
-            const C<T> v = unpk<U.value>(raw[q][k], (const SB*)nullptr);
-            const C<T> wk = wv[k * W + U.value];
-            d.x += v.x * wk.x + v.y * wk.y;
-            d.y += v.x * wk.y - v.y * wk.x;
-          });
-        }
+        for (int c = 0; c < RB; ++c) {
+          C<T> a = czero<T>();
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const C<T> t = shfl_down2(d, o);
-          d.x += t.x;
-          d.y += t.y;
+          for (int k = 0; k < VPT; ++k) {
+            static_for<W>([&](auto U) {
+              const C<T> v = unpk<U.value>(raw[q4 + c][k], (const SB*)nullptr);
+              const C<T> wk = wv[k * W + U.value];
+              a.x += v.x * wk.x + v.y * wk.y;
+              a.y += v.x * wk.y - v.y * wk.x;
+            });
+          }
+          d[2 * c] = a.x;
+          d[2 * c + 1] = a.y;
         }
-        if (lane == 0 && i0 + q < tend) wred[warp][i0 + q - t0] = wide(d);
+        int idx;
+        const T sum = multi_reduce<NV2, T>(d, lane, &idx);
+        const int row = i0 + q4 + (idx >> 1);
+        if ((lane & (32 / NV2 - 1)) == 0 && row < tend) {
+          double* dst = reinterpret_cast<double*>(wh + (row - t0)) + (idx & 1);
+          *dst = (double)sum;
+        }
       }
     }
     __syncthreads();
     if (threadIdx.x < tend - t0) {
+      const double2* wp = wred + par * NW * TILE;
       double2 sum = make_double2(0.0, 0.0);
 #pragma unroll
       for (int q = 0; q < NW; ++q) {
-        sum.x += wred[q][threadIdx.x].x;
-        sum.y += wred[q][threadIdx.x].y;
+        sum.x += wp[q * TILE + threadIdx.x].x;
+        sum.y += wp[q * TILE + threadIdx.x].y;
       }
       ks.part[((long long)r * (ks.m + 1) + t0 + threadIdx.x) * ks.nblk_max + blk] = sum;
     }
-    __syncthreads();
+    if (first && pass == 0 && threadIdx.x == NT - 1) {
+      double t = 0.0;
+      for (int q = 0; q < NW; ++q) t += red[par * NW + q];
+      ks.wpart[(long long)r * ks.nblk_max + blk] = t;
+    }
+    first = false;
+    par ^= 1;
   }
+  return true;
 }
 
 // Pass `pass` (0 or 1) of classical Gram-Schmidt: partial dot products
@@ -192,17 +256,18 @@ __device__ __forceinline__ void mdot_tile(const SB* __restrict__ V, long long vs
 // stores the partial ||w||^2 in wpart; pass 1 runs only for the RHS whose
 // reorth flag the first pass raised.
 template <class T, class SB>
-__global__ void __launch_bounds__(NT)
+__global__ void __launch_bounds__(NT, 4)
 k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
        const C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs,
        int nblk) {
-  __shared__ double2 wred[NT / 32][MDOT_TILE];
-  __shared__ double red[NT / 32];
+  __shared__ double2 wred[2 * (NT / 32) * MDOT_TILE];
+  __shared__ double red[2 * (NT / 32)];
   const int j = *ks.jctr;
+  int par = 0;
   // persistent loop over (RHS, chunk) tiles
   for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
     mdot_tile<T, SB>(V, vstride, rs, w, n, ks, pass, j, (int)(tile / nblk),
-                     (int)(tile % nblk), wred, red);
+                     (int)(tile % nblk), wred, red, par);
 }
 
 // hcol[r][i] = sum_blk part[r][i][blk]; H[r][i][j] = (pass 0) or += (pass 1)
@@ -335,16 +400,17 @@ k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
 template <class T, class SB>
 __global__ void __launch_bounds__(NT)
 k_mdot_group(const __grid_constant__ GroupDesc gd, int pass) {
-  __shared__ double2 wred[NT / 32][MDOT_TILE];
-  __shared__ double red[NT / 32];
+  __shared__ double2 wred[2 * (NT / 32) * MDOT_TILE];
+  __shared__ double red[2 * (NT / 32)];
   const long long total = gd.start[gd.count];
+  int par = 0;
   for (long long tile = blockIdx.x; tile < total; tile += gridDim.x) {
     int g = 0;
     while (tile >= gd.start[g + 1]) ++g;
     const GroupMember& M = gd.m[g];
     const long long lt = tile - gd.start[g];
     mdot_tile<T, SB>((const SB*)M.V, M.vstride, M.rs, (const C<T>*)M.w, M.n, M.ks, pass,
-                     *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), wred, red);
+                     *M.ks.jctr, (int)(lt / M.nblk), (int)(lt % M.nblk), wred, red, par);
   }
 }
 
@@ -446,43 +512,6 @@ __device__ __forceinline__ void consumers_sync() {
   asm volatile("bar.sync 1, %0;" ::"n"(NTC) : "memory");
 }
 
-// Warp sum of NV values at once (NV a power of two <= 8): log2(NV) halving
-// exchanges leave each lane one value, then plain xor steps finish the sum.
-// Returns the sum of value *idx; every lane of a group of 32/NV lanes holds
-// the same value.
-template <int CNT, class T>
-__device__ __forceinline__ void halve(T* v, int lane, int o) {
-  const bool up = (lane & o) != 0;
-#pragma unroll
-  for (int k = 0; k < CNT / 2; ++k) {
-    const T send = up ? v[k] : v[k + CNT / 2];
-    const T keep = up ? v[k + CNT / 2] : v[k];
-    v[k] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-  }
-}
-template <int NV, class T>
-__device__ __forceinline__ T multi_reduce(T* v, int lane, int* idx) {
-  int o = 16, id = 0;
-  if constexpr (NV >= 2) {
-    halve<NV>(v, lane, 16);
-    id += ((lane >> 4) & 1) * (NV / 2);
-    o = 8;
-  }
-  if constexpr (NV >= 4) {
-    halve<NV / 2>(v, lane, 8);
-    id += ((lane >> 3) & 1) * (NV / 4);
-    o = 4;
-  }
-  if constexpr (NV >= 8) {
-    halve<NV / 4>(v, lane, 4);
-    id += ((lane >> 2) & 1) * (NV / 8);
-    o = 2;
-  }
-  T s = v[0];
-  for (; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  *idx = id;
-  return s;
-}
 
 // RHS that take part in this pass, compacted into act[] by warp 0.
 __device__ __forceinline__ void active_rhs(const KState& ks, int pass, int nrhs,
