@@ -416,7 +416,8 @@ typedef struct {
                        the restriction kernel gives each thread one coarse
                        node and its 2 x 2 fine nodes                       */
   int vcycle_rhs_per_block; /* vcycle_fused = 2: right-hand sides per block
-                       (0 = all of them; else 1..1024)                     */
+                       (0 = all of them; else 1..1024); levels with too few
+                       tiles for two blocks per SM halve it (down to 1)    */
   int vcycle_tile;  /* vcycle_fused = 2, prolongation + post-smoothing:
                        0 = blocks of 32 x 8 fine nodes, one thread per fine
                        node; 1 = blocks of 64 x 16 fine nodes, one thread

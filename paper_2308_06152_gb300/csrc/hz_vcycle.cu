@@ -1173,6 +1173,29 @@ constexpr int kPreNS = 3, kProNS = 4;
 
 inline int clamp_rpb(int rpb, int nrhs) { return (rpb <= 0 || rpb > nrhs) ? nrhs : rpb; }
 
+// SMs of the current device (looked up once per device)
+inline int sm_count_current() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int n = 0;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = n > 0 ? n : 1;
+  }
+  return cache[dev];
+}
+// Right-hand sides per block of a staged launch: the tuned rpb (clamped),
+// halved while the level has too few tiles for two blocks per SM, so that
+// the small levels run their right-hand sides side by side instead of one
+// after another in a few blocks.
+inline int level_rpb(int rpb, long long tiles, int nrhs) {
+  rpb = clamp_rpb(rpb, nrhs);
+  const long long want = 2LL * sm_count_current();
+  while (rpb > 1 && tiles * ((nrhs + rpb - 1) / rpb) < want) rpb = (rpb + 1) / 2;
+  return rpb;
+}
+
 template <class T, class SF, class SX, class SC>
 void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, double omega,
                             VRefE<SF> f, SX* x, SC* fc, int nrhs, int rpb, const int* done,
@@ -1184,7 +1207,7 @@ void launch_pre_restrict_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, doub
     cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          PreRestrictCell<T, SF>::smem(kPreNS, 1024));
   });
-  rpb = clamp_rpb(rpb, nrhs);
+  rpb = level_rpb(rpb, (long long)((Lc.nx + BX - 1) / BX) * ((Lc.ny + BY - 1) / BY), nrhs);
   const dim3 grid((Lc.nx + BX - 1) / BX, (Lc.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
   if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
   kern<<<grid, dim3(BX, BY), PreRestrictCell<T, SF>::smem(kPreNS, rpb), st>>>(
@@ -1203,7 +1226,7 @@ void launch_prolong_smooth_mr_w(const LevelDev& Lf, const LevelDev& Lc, int bc, 
     cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          P::smem(kProNS, 1024));
   });
-  rpb = clamp_rpb(rpb, nrhs);
+  rpb = level_rpb(rpb, (long long)((Lf.nx + TXW - 1) / TXW) * ((Lf.ny + BY - 1) / BY), nrhs);
   const dim3 grid((Lf.nx + TXW - 1) / TXW, (Lf.ny + BY - 1) / BY, (nrhs + rpb - 1) / rpb);
   if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
   kern<<<grid, dim3(BX, BY), P::smem(kProNS, rpb), st>>>(Lf, Lc, bc, (T)(1.0 - omega), xc,
@@ -1226,7 +1249,8 @@ void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, do
       cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            P::smem(kProNS, 1024));
     });
-    rpb = clamp_rpb(rpb, nrhs);
+    rpb = level_rpb(rpb, (long long)((Lf.nx + P::FW - 1) / P::FW) * ((Lf.ny + P::FH - 1) / P::FH),
+                    nrhs);
     const dim3 grid((Lf.nx + P::FW - 1) / P::FW, (Lf.ny + P::FH - 1) / P::FH,
                     (nrhs + rpb - 1) / rpb);
     if (frs <= 0) frs = (long long)Lf.nx * Lf.ny;
