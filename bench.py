@@ -342,6 +342,8 @@ def workload_config(args, cfg, model, world, b_np):
 # command); traffic scales with the rows streamed, so a bench launch's
 # traffic is this ratio times its algorithmic bytes.
 TRAFFIC = {
+    ("mdot", "layered_2305x769_b64", 0): (1.004, "profiles/dram_layered_2305x769_b64.md"),
+    ("maxpy", "layered_2305x769_b64", 0): (1.006, "profiles/dram_layered_2305x769_b64.md"),
     ("vcycle", "layered_2305x769_b64", (2, 8, 0)): (
         0.885, "profiles/dram_layered_2305x769_b64.md"),
 }
