@@ -144,6 +144,19 @@ __device__ __forceinline__ T multi_reduce(T* v, int lane, int* idx) {
 
 constexpr int MDOT_TILE = 32;
 
+// Pass 1 (re-orthogonalisation) with no RHS flagged: true in every thread,
+// so that the whole block leaves before walking its tiles.
+__device__ __forceinline__ bool no_reorth(const KState& ks, int nrhs, int* flag_s) {
+  if (threadIdx.x < 32) {
+    int any = 0;
+    for (int r = threadIdx.x; r < nrhs; r += 32) any |= ks.reorth[r] && !ks.done[r];
+    any = __any_sync(0xffffffffu, any);
+    if (threadIdx.x == 0) *flag_s = any;
+  }
+  __syncthreads();
+  return *flag_s == 0;
+}
+
 // One (RHS r, chunk blk) tile of k_mdot: w's chunk stays in registers while
 // the j+1 basis rows stream through (G rows' loads issued before use).  The
 // partial dots of up to four rows at a time are summed over the warp
@@ -262,6 +275,8 @@ k_mdot(const SB* __restrict__ V, long long vstride, long long rs,
        int nblk) {
   __shared__ double2 wred[2 * (NT / 32) * MDOT_TILE];
   __shared__ double red[2 * (NT / 32)];
+  __shared__ int anyr;
+  if (pass && no_reorth(ks, nrhs, &anyr)) return;
   const int j = *ks.jctr;
   int par = 0;
   // persistent loop over (RHS, chunk) tiles
@@ -388,6 +403,8 @@ __global__ void __launch_bounds__(NT, 4)
 k_maxpy(const SB* __restrict__ V, long long vstride, long long rs,
         C<T>* __restrict__ w, long long n, KState ks, int pass, int nrhs, int nblk) {
   __shared__ double red[2 * (NT / 32)];
+  __shared__ int anyr;
+  if (pass && no_reorth(ks, nrhs, &anyr)) return;
   const int j = *ks.jctr;
   int par = 0;
   for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x)
