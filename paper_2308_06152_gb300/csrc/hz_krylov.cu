@@ -1237,10 +1237,70 @@ __global__ void k_trisolve(KState ks) {
   }
 }
 
-// x (+)= sum_{i < iters} y_i V_i
+// x (+)= sum_{i < iters} y_i V_i.  Same tiling as k_maxpy: each block
+// takes (RHS, chunk) tiles round-robin, keeps the chunk of x in registers,
+// streams the basis rows in 16-byte groups with G rows' loads issued before
+// use, and reads y straight from its L1-resident column (no barrier).
+template <class SB, class Tx>
+__global__ void __launch_bounds__(NT, 4)
+k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
+         C<Tx>* __restrict__ x, int accumulate, long long n, int nrhs, int nblk) {
+  constexpr int W = VW<SB>::w, VPT = EPT / W, G = 16 / VPT;
+  for (long long tile = blockIdx.x; tile < (long long)nrhs * nblk; tile += gridDim.x) {
+    const int r = (int)(tile / nblk), blk = (int)(tile % nblk);
+    const int k = ks.iters[r];
+    if (accumulate && k == 0) continue;
+    const long long g0 = (long long)blk * (CHUNK / W) + threadIdx.x;
+    C<Tx>* xr = x + r * n;
+    const double2* yr = ks.y + (long long)r * ks.m;
+    C<Tx> acc[EPT];
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk)
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const long long e = (g0 + (long long)kk * NT) * W + u;
+        acc[kk * W + u] = (accumulate && e < n) ? xr[e] : czero<Tx>();
+      }
+    for (int q0 = 0; q0 < k; q0 += G) {
+      uint4 raw[G][VPT];
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const SB* vr = V + (long long)(q0 + q) * vstride + r * rs;
+#pragma unroll
+        for (int kk = 0; kk < VPT; ++kk) {
+          const long long g = g0 + (long long)kk * NT;
+          raw[q][kk] = (q0 + q < k && g * W < n) ? ldraw(vr, g) : make_uint4(0, 0, 0, 0);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const C<Tx> yi = (q0 + q < k) ? cvt_to<Tx>(yr[q0 + q]) : czero<Tx>();
+#pragma unroll
+        for (int kk = 0; kk < VPT; ++kk) {
+          static_for<W>([&](auto U) {
+            const auto v = unpk<U.value>(raw[q][kk], (const SB*)nullptr);
+            const Tx vx = (Tx)v.x, vy = (Tx)v.y;
+            acc[kk * W + U.value].x += vx * yi.x - vy * yi.y;
+            acc[kk * W + U.value].y += vx * yi.y + vy * yi.x;
+          });
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < VPT; ++kk)
+#pragma unroll
+      for (int u = 0; u < W; ++u) {
+        const long long e = (g0 + (long long)kk * NT) * W + u;
+        if (e < n) xr[e] = acc[kk * W + u];
+      }
+  }
+}
+
+// The same update one element at a time, for bases whose rows are not
+// 16-byte aligned (row length not a multiple of 16 bytes).
 template <class SB, class Tx>
 __global__ void __launch_bounds__(NT)
-k_update(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
+k_update_el(const SB* __restrict__ V, long long vstride, long long rs, KState ks,
          C<Tx>* __restrict__ x, int accumulate, long long n, int nrhs, int nblk) {
   constexpr int TILE = 512;
   __shared__ C<Tx> ys[TILE];
@@ -1574,6 +1634,16 @@ void launch_update(const SB* V, long long vstride, long long rs, const KState& k
                    cudaStream_t st) {
   HZ_COUNT();
   const int nblk = krylov_nblk(n);
+  // the 16-byte group loads need every row 16-byte aligned
+  const bool aligned = reinterpret_cast<uintptr_t>(V) % 16 == 0 &&
+                       (rs * (long long)sizeof(SB)) % 16 == 0 &&
+                       (vstride * (long long)sizeof(SB)) % 16 == 0;
+  if (!aligned) {
+    const unsigned grid =
+        persistent_grid((const void*)k_update_el<SB, Tx>, (long long)nblk * nrhs);
+    k_update_el<SB, Tx><<<grid, NT, 0, st>>>(V, vstride, rs, ks, x, accumulate, n, nrhs, nblk);
+    return;
+  }
   const unsigned grid = persistent_grid((const void*)k_update<SB, Tx>, (long long)nblk * nrhs);
   k_update<SB, Tx><<<grid, NT, 0, st>>>(V, vstride, rs, ks, x, accumulate, n, nrhs, nblk);
 }
