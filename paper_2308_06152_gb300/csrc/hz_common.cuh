@@ -237,6 +237,23 @@ void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, do
                               int rpb, int tile, const int* done, cudaStream_t st,
                               unsigned long long* abytes = nullptr, long long frs = 0);
 // x = Minv f on the coarsest level (dense)
+// The small levels of a V-cycle in one kernel (complex-FP32 preconditioner):
+// levels lv[0..nlev-1] of the hierarchy's tail, the last the coarsest (nL
+// nodes, dense inverse); off[k] is level k's first value in shared memory
+// (its f, x and a scratch vector follow each other).
+constexpr int kMaxSmallLevels = 12;
+constexpr int kSmallLevelBytes = 96 * 1024;
+struct SmallLevels {
+  int nlev, bc, nL;
+  float omc;
+  LevelDev lv[kMaxSmallLevels];
+  int off[kMaxSmallLevels];
+  int bytes;
+};
+template <class SL>
+void launch_vcycle_small(const SmallLevels& d, const SL* f, SL* x, const float2* minv,
+                         int nrhs, const int* done, cudaStream_t st);
+
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
                      const int* done, cudaStream_t st);

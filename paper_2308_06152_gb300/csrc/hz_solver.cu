@@ -477,6 +477,42 @@ inline void prof_mark(hz_solver* s, int kc) {
 }
 
 // ------------------------------------------------------------ V-cycle
+// The first level ls > l0 from which the rest of the hierarchy (levels ls ..
+// L, three vectors per level and two for the coarsest, in FP32) fits in the
+// shared memory of one block: k_vcycle_small takes those levels in one
+// launch.  Staged complex-FP32 V-cycles only, and only with at least one
+// level besides the coarsest; otherwise L + 1 (none).
+template <class T>
+int small_from(const hz_solver* s, int l0) {
+  if (!std::is_same<T, float>::value || s->tune.vcycle_fused != 2) return s->L + 1;
+  if (s->L - l0 < 2 || s->L - l0 > kMaxSmallLevels) return s->L + 1;
+  long long elems = 2LL * s->nL;
+  int ls = s->L;
+  while (ls - 1 > l0 && ls - 1 >= s->L - (kMaxSmallLevels - 1)) {
+    const long long n = s->lv[ls - 1].n;
+    if ((elems + 3 * n) * (long long)sizeof(float2) > kSmallLevelBytes) break;
+    elems += 3 * n;
+    --ls;
+  }
+  return ls < s->L ? ls : s->L + 1;
+}
+SmallLevels small_levels(const hz_solver* s, int ls) {
+  SmallLevels d;
+  std::memset(&d, 0, sizeof(d));
+  d.nlev = s->L - ls + 1;
+  d.bc = s->d.bc;
+  d.nL = (int)s->nL;
+  d.omc = (float)(1.0 - s->d.jacobi_omega);
+  int off = 0;
+  for (int k = 0; k < d.nlev; ++k) {
+    d.lv[k] = s->lv[ls + k].dev();
+    d.off[k] = off;
+    off += (k + 1 < d.nlev ? 3 : 2) * (int)s->lv[ls + k].n;
+  }
+  d.bytes = off * (int)sizeof(float2);
+  return d;
+}
+
 // One V-cycle from level l0 for M_l0 x = f.  The hierarchy's own vectors are
 // stored as SL (C<T>, or BF16 pairs for the BF16-storage smoother); the
 // input f and the result xout are C<T>.
@@ -502,7 +538,10 @@ void vcycle_sl(hz_solver* s, int l0, VRefE<SI> f, C<T>* xout, int nrhs,
   const int rpb = s->tune.vcycle_rhs_per_block, tile = s->tune.vcycle_tile;
   const double om = s->d.jacobi_omega;
   unsigned long long* vbytes = s->prof_kc == HZ_KC_VCYCLE ? s->prof_bytes : nullptr;
-  for (int l = l0; l < s->L; ++l) {
+  // levels from ls down in one launch (k_vcycle_small), if any
+  const int ls = small_from<T>(s, l0);
+  const int lend = ls <= s->L ? ls : s->L;
+  for (int l = l0; l < lend; ++l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
     if (staged) {
@@ -540,9 +579,15 @@ void vcycle_sl(hz_solver* s, int l0, VRefE<SI> f, C<T>* xout, int nrhs,
       }
     }
   }
-  launch_dense_mv<T, SL, SL>(s->nL, minv, vrefe<SL>(s->lv[s->L].f),
-                             (SL*)s->lv[s->L].x, nrhs, done, st);
-  for (int l = s->L - 1; l >= l0; --l) {
+  if (ls <= s->L) {
+    if constexpr (std::is_same<T, float>::value)
+      launch_vcycle_small<SL>(small_levels(s, ls), (const SL*)s->lv[ls].f, (SL*)s->lv[ls].x,
+                              (const float2*)minv, nrhs, done, st);
+  } else {
+    launch_dense_mv<T, SL, SL>(s->nL, minv, vrefe<SL>(s->lv[s->L].f),
+                               (SL*)s->lv[s->L].x, nrhs, done, st);
+  }
+  for (int l = lend - 1; l >= l0; --l) {
     const LevelHost& A = s->lv[l];
     const LevelHost& Bc = s->lv[l + 1];
     if (staged) {

@@ -1100,6 +1100,136 @@ k_prolong_smooth_cell(LevelDev Lf, LevelDev Lc, int bc, T omc, const SC* __restr
                                                            xo, na, act, smraw);
 }
 
+// The levels from one with few nodes down to the coarsest, for one right-hand
+// side per block, every level's f, x and a scratch vector in shared memory:
+// the same steps as the staged kernels (x = D^-1 f, residual (1 - w) f +
+// (1/h^2) sum of the weighted neighbours, full weighting; the dense solve;
+// x' = x + P xc, then (1 - w) x' + D^-1 (f + (1/h^2) sum of the neighbours'
+// x')), one block barrier between steps instead of a launch per step, and
+// the intermediate levels kept in FP32.  f is read from and x written to
+// the first of these levels' vectors (stored as SL).
+template <class SL>
+__global__ void __launch_bounds__(512)
+k_vcycle_small(const __grid_constant__ SmallLevels d, const SL* __restrict__ fin,
+               SL* __restrict__ xout, const float2* __restrict__ minv,
+               const int* __restrict__ done) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int r = blockIdx.x;
+  if (done && done[r]) return;
+  const int tid = threadIdx.x, nth = blockDim.x, bc = d.bc;
+  const float omc = d.omc;
+  auto dir_bnd = [&](int i, int j, int nx, int ny) {
+    return bc == BC_DIRICHLET && on_bnd(i, j, nx, ny);
+  };
+  {
+    const long long n0 = (long long)d.lv[0].nx * d.lv[0].ny;
+    float2* F = sm + d.off[0];
+    for (int i = tid; i < n0; i += nth) F[i] = ld2(fin + r * n0, i);
+  }
+  __syncthreads();
+  for (int k = 0; k + 1 < d.nlev; ++k) {
+    const LevelDev& L = d.lv[k];
+    const int nx = L.nx, ny = L.ny, n = nx * ny;
+    float2* F = sm + d.off[k];
+    float2* X = F + n;
+    float2* T = X + n;
+    const float2* dinv = dinv_of<float>(L);
+    const float ih2 = ih2_of<float>(L);
+    for (int i = tid; i < n; i += nth) {
+      const int gi = i % nx, gj = i / nx;
+      X[i] = dir_bnd(gi, gj, nx, ny) ? czero<float>() : cmul(dinv[i], F[i]);
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) {
+      const int gi = i % nx, gj = i / nx;
+      float2 v = czero<float>();
+      if (!dir_bnd(gi, gj, nx, ny)) {
+        const float2 xw = gi > 0 ? X[i - 1] : czero<float>();
+        const float2 xe = gi < nx - 1 ? X[i + 1] : czero<float>();
+        const float2 xs = gj > 0 ? X[i - nx] : czero<float>();
+        const float2 xn = gj < ny - 1 ? X[i + nx] : czero<float>();
+        v = resid_row<float, false>(ih2, omc, F[i], xw, xe, xs, xn,
+                                    nb_code(bc, gi, gj, nx, ny));
+      }
+      T[i] = v;
+    }
+    __syncthreads();
+    const LevelDev& Lc = d.lv[k + 1];
+    const int ncx = Lc.nx, ncy = Lc.ny, nc = ncx * ncy;
+    float2* Fc = sm + d.off[k + 1];
+    for (int I = tid; I < nc; I += nth) {
+      const int ci = I % ncx, cj = I / ncx;
+      float2 acc = czero<float>();
+      if (!dir_bnd(ci, cj, ncx, ncy)) {
+        for (int b = -1; b <= 1; ++b) {
+          const int jf = 2 * cj + b;
+          if (jf < 0 || jf >= ny) continue;
+          const float wb = b == 0 ? 2.f : 1.f;
+          for (int a = -1; a <= 1; ++a) {
+            const int ifn = 2 * ci + a;
+            if (ifn < 0 || ifn >= nx) continue;
+            acc = rfma((a == 0 ? 2.f : 1.f) * wb, T[jf * nx + ifn], acc);
+          }
+        }
+        acc = 0.0625f * acc;
+      }
+      Fc[I] = acc;
+    }
+    __syncthreads();
+  }
+  {
+    const int n = d.nL;
+    const float2* F = sm + d.off[d.nlev - 1];
+    float2* X = sm + d.off[d.nlev - 1] + n;
+    for (int i = tid; i < n; i += nth) {
+      float2 acc = czero<float>();
+      const float2* mr = minv + (long long)i * n;
+      for (int c = 0; c < n; ++c) acc = cfma(mr[c], F[c], acc);
+      X[i] = acc;
+    }
+  }
+  __syncthreads();
+  for (int k = d.nlev - 2; k >= 0; --k) {
+    const LevelDev& L = d.lv[k];
+    const LevelDev& Lc = d.lv[k + 1];
+    const int nx = L.nx, ny = L.ny, n = nx * ny;
+    float2* F = sm + d.off[k];
+    float2* X = F + n;
+    float2* T = X + n;
+    const float2* Xc = sm + d.off[k + 1] + Lc.nx * Lc.ny;
+    const float2* dinv = dinv_of<float>(L);
+    const float ih2 = ih2_of<float>(L);
+    for (int i = tid; i < n; i += nth) {
+      const int gi = i % nx, gj = i / nx;
+      float2 v = X[i];
+      if (!dir_bnd(gi, gj, nx, ny)) v = v + interp_bilinear<float>(Lc, Xc, gi, gj);
+      T[i] = v;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += nth) {
+      const int gi = i % nx, gj = i / nx;
+      float2 v = czero<float>();
+      if (!dir_bnd(gi, gj, nx, ny)) {
+        const float2 xw = gi > 0 ? T[i - 1] : czero<float>();
+        const float2 xe = gi < nx - 1 ? T[i + 1] : czero<float>();
+        const float2 xs = gj > 0 ? T[i - nx] : czero<float>();
+        const float2 xn = gj < ny - 1 ? T[i + nx] : czero<float>();
+        v = cfma(dinv[i],
+                 resid_row<float, false>(ih2, 1.f, F[i], xw, xe, xs, xn,
+                                         nb_code(bc, gi, gj, nx, ny)),
+                 omc * T[i]);
+      }
+      X[i] = v;
+    }
+    __syncthreads();
+  }
+  {
+    const long long n0 = (long long)d.lv[0].nx * d.lv[0].ny;
+    const float2* X = sm + d.off[0] + n0;
+    for (int i = tid; i < n0; i += nth) st2(xout + r * n0, i, X[i]);
+  }
+}
+
 // x = Minv f on the coarsest level (dense inverse built at setup)
 template <class T, class SF, class SO>
 __global__ void k_dense_mv(int n, const C<T>* __restrict__ minv, VRefE<SF> fin,
@@ -1261,6 +1391,23 @@ void launch_prolong_smooth_mr(const LevelDev& Lf, const LevelDev& Lc, int bc, do
     launch_prolong_smooth_mr_w<T, SC, SX, SF, SO, BX>(Lf, Lc, bc, omega, xc, x, f, xo, nrhs,
                                                       rpb, done, st, abytes, frs);
 }
+
+template <class SL>
+void launch_vcycle_small(const SmallLevels& d, const SL* f, SL* x, const float2* minv,
+                         int nrhs, const int* done, cudaStream_t st) {
+  HZ_COUNT();
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute((const void*)k_vcycle_small<SL>,
+                         cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallLevelBytes);
+  });
+  k_vcycle_small<SL><<<nrhs, 512, d.bytes, st>>>(d, f, x, minv, done);
+}
+template void launch_vcycle_small<float2>(const SmallLevels&, const float2*, float2*,
+                                          const float2*, int, const int*, cudaStream_t);
+template void launch_vcycle_small<__nv_bfloat162>(const SmallLevels&, const __nv_bfloat162*,
+                                                  __nv_bfloat162*, const float2*, int,
+                                                  const int*, cudaStream_t);
 
 template <class T, class SF, class SO>
 void launch_dense_mv(int n, const C<T>* minv, VRefE<SF> f, SO* x, int nrhs,
