@@ -318,7 +318,6 @@ __global__ void k_reduce_cols(KState ks, int nblk, int pass) {
   }
 }
 
-constexpr int MAXPY_TILE = 512;
 
 // One (RHS r, chunk blk) tile of k_maxpy: w's chunk is updated in registers
 // across all j+1 basis rows, written once, and its squared norm reduced.
