@@ -318,7 +318,6 @@ __global__ void k_reduce_cols(KState ks, int nblk, int pass) {
   }
 }
 
-
 // One (RHS r, chunk blk) tile of k_maxpy: w's chunk is updated in registers
 // across all j+1 basis rows, written once, and its squared norm reduced.
 // The coefficients come straight from the (L1-resident) column hcol rather
