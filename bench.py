@@ -346,6 +346,8 @@ TRAFFIC = {
     ("maxpy", "layered_2305x769_b64", 0): (1.006, "profiles/dram_layered_2305x769_b64.md"),
     ("vcycle", "layered_2305x769_b64", (2, 8, 0)): (
         0.885, "profiles/dram_layered_2305x769_b64.md"),
+    ("vcycle", "layered_2305x769_b64", (2, 16, 0)): (
+        0.889, "profiles/dram_layered_2305x769_b64.md"),
 }
 
 
