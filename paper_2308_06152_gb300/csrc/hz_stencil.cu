@@ -71,25 +71,12 @@ __global__ void k_restrict_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
   coarse[r * nc + idc] = scale * acc;
 }
 
-// 1-D interpolation weights of a fine node: (coarse index, weight) pairs.
+// Z x at fine node (i, j): the three taps of each dimension at coarse base
+// k, k+1, k+2 (ztaps below: weights 0 for the taps a rule does not use;
+// higher-order taps outside the coarse grid are dropped), unrolled so that
+// the taps stay in registers.
 template <class T>
-__device__ __forceinline__ int z1d(int zk, int i, int nc, int* idx, T* w) {
-  int k = 0;
-  if (i & 1) {
-    idx[0] = i >> 1; w[0] = T(0.5);
-    idx[1] = (i >> 1) + 1; w[1] = T(0.5);
-    return 2;
-  }
-  const int I = i >> 1;
-  if (zk != ZK_HO) {
-    idx[0] = I; w[0] = T(1);
-    return 1;
-  }
-  if (I - 1 >= 0) { idx[k] = I - 1; w[k] = T(0.125); ++k; }
-  idx[k] = I; w[k] = T(0.75); ++k;
-  if (I + 1 < nc) { idx[k] = I + 1; w[k] = T(0.125); ++k; }
-  return k;
-}
+__device__ __forceinline__ int ztaps(int zk, int g, T& w0, T& w1, T& w2);
 
 template <class T>
 __global__ void k_prolong_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
@@ -105,16 +92,21 @@ __global__ void k_prolong_z(LevelDev Lf, LevelDev Lc, int bc, int zk,
     if (!add) fine[r * nf + id] = czero<T>();
     return;
   }
-  int ix[3], iy[3];
   T wx[3], wy[3];
-  const int nxk = z1d<T>(zk, i, Lc.nx, ix, wx);
-  const int nyk = z1d<T>(zk, j, Lc.ny, iy, wy);
+  const int kx = ztaps<T>(zk, i, wx[0], wx[1], wx[2]);
+  const int ky = ztaps<T>(zk, j, wy[0], wy[1], wy[2]);
   const C<T>* c = coarse + r * nc;
   C<T> acc = czero<T>();
-  for (int b = 0; b < nyk; ++b) {
-    for (int a = 0; a < nxk; ++a) {
-      if (bc == BC_DIRICHLET && on_bnd(ix[a], iy[b], Lc.nx, Lc.ny)) continue;
-      acc = rfma(wx[a] * wy[b], c[(long long)iy[b] * Lc.nx + ix[a]], acc);
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const int cj = ky + b;
+    if (wy[b] == T(0) || cj < 0 || cj >= Lc.ny) continue;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const int ci = kx + a;
+      if (wx[a] == T(0) || ci < 0 || ci >= Lc.nx) continue;
+      if (bc == BC_DIRICHLET && on_bnd(ci, cj, Lc.nx, Lc.ny)) continue;
+      acc = rfma(wx[a] * wy[b], c[(long long)cj * Lc.nx + ci], acc);
     }
   }
   fine[r * nf + id] = add ? fine[r * nf + id] + acc : acc;
